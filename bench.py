@@ -1,0 +1,317 @@
+#!/usr/bin/env python3
+"""Benchmark of the multiphase curved-boundary LBM step on GB300.
+
+A "step" is one lattice Boltzmann time step of the whole hot path over the workload's
+lattice: density, solid-layer densities (Eq. 15), chemical potential (Eq. 12), force +
+collision + streaming, and every cut link by Eqs. 16-18.  The metric is MLUPS (million
+lattice-node updates per second, all nodes counted).
+
+Default workload: drop impact on a cylinder, 2048 x 4096 D2Q9, MRT, Carnahan-Starling EOS at
+0.6 Tc, gravity, FP32 populations (0.68 GB working set, larger than the 129 MB L2, so no L2
+flush is needed between steps).  `--workload c2` runs the 1024 x 1024, 16-cylinder lattice
+instead, flushing L2 before every timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun each rank advances its own replica of the workload (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.  `--impl reference` times the FP64
+reference oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % HBM roofline, FP32 vs FP64 oracle; batched and adjoint cost ratio"
+UNIT = "MLUPS"
+# algorithmic bytes of the fused force + collide + stream kernel per fluid node: read 9 and
+# write 9 FP32 populations (72 B) plus the density and chemical-potential planes (8 B)
+COLLIDE_BYTES_PER_FLUID_NODE = 80
+STEP_BYTES_PER_NODE = 72
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload(name):
+    import scenarios as S
+    if name == "c2":
+        return S.c2_fp32_single(), "c2 16 droplets on cylinders 1024x1024 D2Q9 MRT CS T=0.6Tc FP32"
+    return S.c3_impact(), "c3 drop impact on a cylinder 2048x4096 D2Q9 MRT CS T=0.6Tc gravity FP32"
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def collide_source_hash():
+    h = hashlib.sha256()
+    for f in ("lbm_step.cu", "lbm_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2203_04508_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload_name):
+    """DRAM bytes per launch of the collide kernel from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", f"k_collide_{workload_name}_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    for line in open(p):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.strip().split("=", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_hash") != collide_source_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch_full_size"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_rate(sc, max_seconds, max_steps, threads=None):
+    """MLUPS of the FP64 reference oracle on the host cores over a bounded number of steps."""
+    import oracle as O
+    O.build()
+    if threads:
+        O.set_threads(threads)
+    o = O.Oracle(O.OracleConfig(**sc.physics()))
+    d = sc.droplets()
+    o.init_droplets(d["x0"], d["y0"], d["r0"], d["width"], d["ux0"], d["uy0"])
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter()
+    per = t1 - t0
+    n = max(1, min(max_steps, int(max_seconds / max(per, 1e-6))))
+    t0 = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t0
+    return sc.nodes * n / dt / 1e6, n, O.get_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc, wname = workload(args.workload)
+    rate, n, cores = oracle_rate(sc, max_seconds=90.0, max_steps=max(1, args.steps))
+    ms = sc.nodes / rate / 1e3
+    sample = f"{n} of the {args.steps} requested steps of the full {sc.nx}x{sc.ny} lattice, FP64, {cores} threads"
+    line = {"metric": METRIC, "value": round(rate, 3), "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": n, "warmup": 1, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wname, "nodes": sc.nodes},
+            "cpu_baseline": {"value": round(rate, 3), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(rate, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", default="full", choices=["full", "kernels"],
+                    help="kernels: only warm-up and timed steps (for profiler captures)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    args.warmup = max(args.warmup, 3)
+
+    import torch
+    import torch.distributed as dist
+    import paper_2203_04508_gb300 as G
+    from paper_2203_04508_gb300 import build as cuda_build
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        cuda_build.build()
+    if world > 1:
+        dist.barrier()
+    G.load()
+
+    sc, wname = workload(args.workload)
+    lat = G.Lattice(sc.physics(), precision=G.LBM_FP32)
+    lat.init_droplets(sc.droplets())
+    counts = lat.counts()
+    if args.mode == "kernels":
+        for _ in range(args.warmup + args.steps):
+            lat.step(1)
+        lat.synchronize()
+        M, M0, _ = lat.mass()
+        print(json.dumps({"mode": "kernels", "workload": wname, "steps": args.steps, "warmup": args.warmup,
+                          "launches_per_step": lat.launches_per_step(), "mass_drift": M / M0 - 1}))
+        return
+    lps = lat.launches_per_step()
+    flush = None
+    if args.workload == "c2":
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    lat.step(args.warmup)
+    lat.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    s = lat.stream
+    if flush is None:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        lat.step(args.steps)
+        e1.record(s)
+        e1.synchronize()
+        ms_total = e0.elapsed_time(e1)
+    else:
+        ms_total = 0.0
+        for _ in range(args.steps):
+            with torch.cuda.stream(s):
+                flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            lat.step(1)
+            e1.record(s)
+            e1.synchronize()
+            ms_total += e0.elapsed_time(e1)
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        dist.barrier()
+    ms_step = ms_total / args.steps
+    value = world * sc.nodes * args.steps / (ms_total / 1e3) / 1e6
+
+    # dominant kernel: per-phase CUDA-event times on the library's stream
+    n_prof = max(10, min(200, args.steps // 10))
+    phase_ms = lat.profile_steps(n_prof) / n_prof
+    collide_ms = float(phase_ms[3])
+    peak, peak_src = measured_peak()
+    coll_bytes = COLLIDE_BYTES_PER_FLUID_NODE * counts["fluid"]
+    achieved = coll_bytes / (collide_ms / 1e3) / 1e9
+    traffic = recorded_traffic(args.workload)
+    step_eff = STEP_BYTES_PER_NODE * sc.nodes / (ms_step / 1e3) / 1e9
+    M, M0, _ = lat.mass()
+    del lat
+    torch.cuda.empty_cache()
+
+    # end to end through the public API with host buffers: set-up from host inputs, every step
+    # one C-ABI call plus an 8-byte read-back of its compensation sum, fields back to the host
+    e2e = None
+    if not args.no_e2e:
+        n_e2e = min(args.steps, 400)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat2 = G.Lattice(sc.physics(), precision=G.LBM_FP32)
+        lat2.init_droplets(sc.droplets())
+        for _ in range(n_e2e):
+            lat2.step(1)
+            lat2.last_dM()
+        r, vx, vy = lat2.fields()
+        dt = time.perf_counter() - t0
+        h2d = 8 * (4 * len(sc.r) + 5 * len(sc.r0)) + 4
+        d2h_fields = 3 * sc.nodes * 4
+        e2e = {"value": round(world * sc.nodes * n_e2e / dt / 1e6, 2), "unit": UNIT,
+               "h2d_bytes_per_step": round(h2d / n_e2e, 2),
+               "d2h_bytes_per_step": round(16 + d2h_fields / n_e2e, 2), "steps": n_e2e}
+        del lat2
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, n, cores = oracle_rate(sc, max_seconds=20.0, max_steps=50)
+        cpu = {"value": round(rate, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n} FP64 oracle steps of the full {sc.nx}x{sc.ny} lattice after one untimed step"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wname, "nodes": sc.nodes, "fluid_nodes": counts["fluid"],
+                       "cut_links": counts["links"], "parallelism": f"replicas x{world}",
+                       "l2": "flushed before every timed step" if flush is not None else
+                             "working set (0.68 GB) larger than L2, no flush"},
+            "roofline": {"bound": "hbm", "kernel": "k_collide (force+collide+stream)",
+                         "achieved": round(achieved, 1), "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "algorithmic_bytes_per_launch": coll_bytes, "launch_ms": round(collide_ms, 5),
+                         "step_effective_GBs": round(step_eff, 1),
+                         "step_effective_frac": round(step_eff / peak, 4),
+                         "phase_ms": {k: round(float(v), 5) for k, v in
+                                      zip(("rho", "solid", "mu", "collide", "bc"), phase_ms)}},
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": lps * args.steps,
+            "mass_drift": M / M0 - 1,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) implementation of one time step of the D2Q9
+ * chemical-potential multiphase lattice Boltzmann method with the multiphase curved boundary
+ * condition of Yao, Liu, Zhong & Wen, "Multiphase curved boundary condition in lattice
+ * Boltzmann method" (arXiv 2203.04508).
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns an lbm_status and never aborts the process.  After a failure,
+ *    lbm_last_error(ctx) holds a one-line explanation.  A context whose device work failed
+ *    (LBM_ECUDA) stays failed: every later call returns the same status.
+ *  - Device memory is never allocated by the library.  The caller allocates one device
+ *    workspace of at least lbm_workspace_size() bytes (for instance a PyTorch uint8 tensor),
+ *    passes it to lbm_create(), and keeps it alive until lbm_destroy().  The context itself
+ *    (a small host structure) is owned by the library.
+ *  - All device work is issued asynchronously on the CUDA stream given to lbm_create()
+ *    (a cudaStream_t; NULL means the legacy default stream).  Calls that return host data
+ *    synchronise that stream.
+ *  - Node (x, y) of an nx-by-ny lattice has the dense linear index n = y*nx + x in every
+ *    array that crosses this interface; x is periodic.  Arrays of populations hold 9 planes of
+ *    nx*ny values, plane i for lattice velocity e_i in the order of the columns of the
+ *    transformation matrix M (Eq. 2): e_0 = (0,0); e_1..e_4 = (1,0),(0,1),(-1,0),(0,-1);
+ *    e_5..e_8 = (1,1),(-1,1),(-1,-1),(1,-1).
+ *  - Calls out of order (a step before lbm_init, for example) return LBM_ESTATE.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = 1,     /* invalid argument or configuration */
+  LBM_ENOMEM = 2,     /* workspace too small, or a geometry exceeds its link capacity */
+  LBM_ECUDA = 3,      /* a CUDA call failed (message in lbm_last_error) */
+  LBM_ESTATE = 4,     /* call out of order */
+  LBM_EUNSTABLE = 5,  /* a NaN or Inf appeared in the mass audit */
+  LBM_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
+  LBM_EINTERNAL = 7
+} lbm_status;
+
+/* Equation of state of the nonideal fluid (Sec. 2.2). */
+typedef enum {
+  LBM_EOS_NONE = 0,   /* no nonideal force: single-phase fluid, force = rho g only */
+  LBM_EOS_CS = 1,     /* Carnahan-Starling: p0 = rho R T (1+eta+eta^2-eta^3)/(1-eta)^3 - a rho^2,
+                         eta = b rho / 4 */
+  LBM_EOS_PR = 2      /* Peng-Robinson, Eqs. 10-11 */
+} lbm_eos_kind;
+
+typedef enum { LBM_COLL_BGK = 0, LBM_COLL_MRT = 1 } lbm_coll;  /* Eq. 4 */
+
+/* Treatment of each cut fluid-solid link. */
+typedef enum {
+  LBM_BC_PRESENT = 0, /* the paper's scheme: Eqs. 16-17 with the nonideal term, plus Eq. 18 */
+  LBM_BC_IBC = 1,     /* linear interpolation without the nonideal term and without Eq. 18 */
+  LBM_BC_MIBC = 2,    /* IBC plus the mass compensation of Eq. 18 */
+  LBM_BC_HBB = 3      /* halfway bounce-back: f_ibar(x1, t+1) = f~_i(x1, t) */
+} lbm_bc;
+
+typedef enum { LBM_FP32 = 0, LBM_FP64 = 1 } lbm_prec;
+
+/*
+ * Configuration of one lattice.  Geometry: nodes sit at integer (x, y), 0 <= x < nx,
+ * 0 <= y < ny.  A node is solid when it lies inside a cylinder, (x-cx)^2 + (y-cy)^2 <= r^2,
+ * or, with walls = 1, when y <= y_bottom or y >= y_top; walls = 0 makes y periodic.  The
+ * wall lines must satisfy 1 <= y_bottom < 2 and ny-3 < y_top <= ny-2 (two solid rows each,
+ * as the fourth-order stencils need), and each cylinder must keep two nodes from the
+ * periodic edges.
+ *
+ * Wettability (Sec. 2.3): solid nodes carry the chemical potential
+ *     mu^_w = k^2 mu_sat + dmu_w,
+ * where mu_sat is the bulk chemical potential at coexistence; dmu_w = 0 is a neutral wall
+ * (90 degrees), dmu_w < 0 hydrophilic, dmu_w > 0 hydrophobic.
+ */
+typedef struct {
+  int32_t nx, ny;
+  int32_t walls;
+  double y_bottom, y_top;
+  int32_t eos;                 /* lbm_eos_kind */
+  double a, b, R, T_over_Tc;   /* EOS constants; temperature as a fraction of the critical one */
+  double omega;                /* acentric factor (Peng-Robinson alpha(T)) */
+  double k, kappa;             /* Eq. 12: mu^ = k^2 psi'(rho) - kappa^ lap(rho) */
+  int32_t coll;                /* lbm_coll */
+  double tau;                  /* BGK relaxation time */
+  double s_e, s_eps, s_q, s_nu;/* MRT rates of Eq. 3 (s_nu = 1/tau gives nu = (tau-1/2)/3) */
+  double gx, gy;               /* body-force acceleration (force rho g added to Eq. 9) */
+  int32_t bc;                  /* lbm_bc */
+  int32_t precision;           /* lbm_prec: storage and arithmetic type of the populations */
+  double rho_ref;              /* populations are stored as f_i - w_i rho_ref; a negative value
+                                  selects the gas coexistence density in FP32 and 0 in FP64 */
+  int32_t n_cyl;
+  const double* cx;            /* host arrays of n_cyl values, read during lbm_create only */
+  const double* cy;
+  const double* r;
+  const double* dmu_w;
+  double dmu_w_walls;          /* dmu_w of the two flat walls */
+} lbm_config;
+
+/* Initial state, Eq. 19: around each droplet a tanh profile of width `width` between the
+ * Maxwell coexistence densities; velocity (ux0, uy0) weighted by the local liquid fraction;
+ * populations at equilibrium. */
+typedef struct {
+  int32_t n_drop;
+  const double* x0;            /* host arrays of n_drop values */
+  const double* y0;
+  const double* r0;
+  const double* ux0;           /* may be NULL: zero */
+  const double* uy0;           /* may be NULL: zero */
+  double width;
+} lbm_init_spec;
+
+/* Bytes of device workspace one lattice of this configuration needs (populations in two
+ * lattices, density and chemical-potential planes, node flags, boundary-link and solid-layer
+ * lists sized for the geometry's upper bound, reduction scratch). */
+lbm_status lbm_workspace_size(const lbm_config* cfg, size_t* bytes);
+
+/* Validates cfg, solves the EOS set-up on the host (critical point and Maxwell coexistence
+ * densities, Sec. 4), and binds the caller's device workspace (device pointer, 256-byte
+ * aligned, `bytes` >= lbm_workspace_size).  No device work is issued yet.
+ * stream: cudaStream_t of the caller (may be NULL). */
+lbm_status lbm_create(const lbm_config* cfg, void* stream, void* workspace, size_t bytes,
+                      lbm_ctx** out);
+
+/* Classifies nodes (fluid, first and second solid layer of Eq. 15, deeper solid), finds every
+ * cut link (x1 fluid, x1 + e_i solid) with its fraction q (Sec. 3.1; the smaller root of
+ * |x1 + q e_i - c|^2 = r^2 for a cylinder, q = y1 - y_bottom or y_top - y1 for a wall),
+ * builds the link list sorted by (x1, i), and writes the constant chemical potential of the
+ * solid layers.  q is evaluated in FP64 without contractions, so identical inputs give
+ * identical bits on any IEEE host.  Synchronises the stream. */
+lbm_status lbm_build_links(lbm_ctx* ctx);
+
+/* Counts from lbm_build_links: cut links, boundary-fluid nodes, fluid nodes, first- and
+ * second-layer solid nodes. */
+lbm_status lbm_counts(lbm_ctx* ctx, int64_t* n_links, int64_t* n_boundary_nodes,
+                      int64_t* n_fluid, int64_t* n_solid1, int64_t* n_solid2);
+
+/* Copies the link list to caller-owned HOST arrays of at least n_links entries: node x1,
+ * direction i, q (FP64), x2 = x1 - e_i, and whether x2 is fluid. */
+lbm_status lbm_get_links(lbm_ctx* ctx, int64_t capacity, int32_t* x1, int32_t* dir, double* q,
+                         int32_t* x2, int32_t* x2_fluid);
+
+/* Node classes to a caller-owned HOST array of nx*ny bytes: 0 fluid, 1 first solid layer,
+ * 2 second solid layer, 3 deeper solid. */
+lbm_status lbm_get_kind(lbm_ctx* ctx, uint8_t* kind);
+
+/* Eq. 19 initial state on the device, then the initial mass M0 (FP64).  Synchronises. */
+lbm_status lbm_init(lbm_ctx* ctx, const lbm_init_spec* init);
+
+/* Advances n time steps, asynchronously on the context's stream (captured into a CUDA
+ * graph on first use).  Each step: density (Sec. 2.1); solid-node densities (Eq. 15);
+ * chemical potential (Eq. 12); nonideal force (Eq. 9) with exact-difference forcing
+ * (Eqs. 13-14), collision (Eq. 4) and streaming (Eq. 5) fused in one kernel; then every cut
+ * link by Eq. 16 (q < 1/2) or Eq. 17 (q >= 1/2) with the per-node compensation of Eq. 18
+ * accumulated in FP64. */
+lbm_status lbm_step(lbm_ctx* ctx, int64_t n);
+
+/* Density and velocity v = u + F/(2 rho) of the current state (the macroscopic velocity
+ * defined under Eq. 14) into caller-owned arrays of nx*ny values of the context's precision
+ * (float or double); zero at solid nodes.  on_device != 0: device pointers, written
+ * asynchronously; 0: host pointers, the call synchronises. */
+lbm_status lbm_fields(lbm_ctx* ctx, void* rho, void* vx, void* vy, int32_t on_device);
+
+/* Populations f_i (not offset) of the current state, 9 planes of nx*ny values of the
+ * context's precision; zero at solid nodes.  on_device as for lbm_fields. */
+lbm_status lbm_populations(lbm_ctx* ctx, void* f, int32_t on_device);
+
+/* Total mass M = sum over fluid nodes of sum_i f_i (FP64 on the device), the initial mass,
+ * and the domain sum of the Eq. 18 compensation of the last step.  Synchronises.  Returns
+ * LBM_EUNSTABLE when the populations hold a NaN or Inf. */
+lbm_status lbm_mass(lbm_ctx* ctx, double* M, double* M0, double* dM_last);
+
+/* Per-step compensation sums (Eq. 18) of the last min(n, steps taken, 4096) steps, oldest
+ * first, to a caller-owned HOST array; *n_out receives the count.  Synchronises. */
+lbm_status lbm_dM_history(lbm_ctx* ctx, double* out, int64_t n, int64_t* n_out);
+
+/* Domain sum of the Eq. 18 compensation of the last step (8 bytes read back; synchronises). */
+lbm_status lbm_last_dM(lbm_ctx* ctx, double* dM);
+
+/* Advances n steps like lbm_step, launching the five phases one by one with CUDA events on
+ * the context's stream between them, and adds each phase's device time (ms) to ms5:
+ * [0] density, [1] solid layers (Eq. 15), [2] chemical potential, [3] force + collision +
+ * streaming, [4] boundary links (Eqs. 16-18).  Synchronises after every step. */
+lbm_status lbm_profile_steps(lbm_ctx* ctx, int64_t n, double* ms5);
+
+/* EOS summary (host FP64): Tc, rho_c, T, alpha, rho_g, rho_l, mu_sat, p_sat. */
+lbm_status lbm_eos_info(lbm_ctx* ctx, double* out8);
+
+/* Number of kernel launches one lbm_step(ctx, 1) issues. */
+lbm_status lbm_launches_per_step(lbm_ctx* ctx, int64_t* n);
+
+void lbm_destroy(lbm_ctx* ctx);
+const char* lbm_status_str(lbm_status s);
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

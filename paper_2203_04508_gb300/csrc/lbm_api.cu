@@ -1,0 +1,638 @@
+// C ABI of the library (declared in include/lbm.h): context, workspace layout, geometry
+// set-up, graph-captured time stepping and read-outs.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using namespace lbmgb;
+
+namespace {
+
+constexpr int MAX_DROPS = 4096;
+constexpr size_t ALIGN = 256;
+
+size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct Caps {
+  long long links, bnodes, s1, s2;
+};
+
+// Upper bounds of the list sizes.  Nodes of the first / second solid layer and boundary-fluid
+// nodes of a cylinder of radius r lie within sqrt(2) resp. 2 sqrt(2) of its circle; the unit
+// squares around them are disjoint and lie in the annulus r-3.6 < |x-c| < r+3.2, so its area
+// bounds their number.  A node has at most 8 cut links.  Each flat wall has nx nodes per layer
+// and 3 cut links per column.
+Caps list_caps(const lbm_config* c) {
+  Caps k{16, 16, 16, 16};
+  for (int j = 0; j < c->n_cyl; ++j) {
+    double r = c->r[j];
+    double rin = r - 3.6 > 0 ? r - 3.6 : 0.0;
+    long long ann = (long long)std::ceil(M_PI * ((r + 3.2) * (r + 3.2) - rin * rin)) + 16;
+    k.s1 += ann;
+    k.s2 += ann;
+    k.bnodes += ann;
+    k.links += 8 * ann;
+  }
+  if (c->walls) {
+    k.s1 += 2LL * c->nx;
+    k.s2 += 2LL * c->nx;
+    k.bnodes += 2LL * c->nx;
+    k.links += 6LL * c->nx;
+  }
+  return k;
+}
+
+struct Layout {
+  int pitch;
+  long long plane;
+  size_t sz;
+  Caps cap;
+  size_t fA, fB, rho, mu, kind;
+  size_t lq64, lq, ldir, lx2f, bnode, bstart, carry;
+  size_t s1node, s1mask, s1winv, s2node, s2mask, s2winv;
+  size_t cyl, drops, partials, counter, step_ctr, scalars, dm_ring, block_sums, totals;
+  size_t total;
+};
+
+Layout make_layout(const lbm_config* c) {
+  Layout L{};
+  L.sz = c->precision == LBM_FP64 ? 8 : 4;
+  const int per_line = (int)(128 / L.sz);
+  L.pitch = (c->nx + per_line - 1) / per_line * per_line;
+  L.plane = (long long)L.pitch * c->ny;
+  L.cap = list_caps(c);
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return at; };
+  L.fA = take(9 * L.plane * L.sz);
+  L.fB = take(9 * L.plane * L.sz);
+  L.rho = take(L.plane * L.sz);
+  L.mu = take(L.plane * L.sz);
+  L.kind = take(L.plane);
+  L.lq64 = take(L.cap.links * 8);
+  L.lq = take(L.cap.links * L.sz);
+  L.ldir = take(L.cap.links);
+  L.lx2f = take(L.cap.links);
+  L.bnode = take(L.cap.bnodes * 4);
+  L.bstart = take((L.cap.bnodes + 1) * 4);
+  L.carry = take(L.cap.bnodes * 8);
+  L.s1node = take(L.cap.s1 * 4);
+  L.s1mask = take(L.cap.s1);
+  L.s1winv = take(L.cap.s1 * L.sz);
+  L.s2node = take(L.cap.s2 * 4);
+  L.s2mask = take(L.cap.s2);
+  L.s2winv = take(L.cap.s2 * L.sz);
+  L.cyl = take((size_t)(c->n_cyl > 0 ? c->n_cyl : 1) * 4 * 8);
+  L.drops = take((size_t)MAX_DROPS * 5 * 8);
+  size_t nparts = 2 * (size_t)mass_blocks();
+  size_t bparts = (size_t)((L.cap.bnodes + 255) / 256) + 1;
+  L.partials = take(8 * (nparts > bparts ? nparts : bparts));
+  L.counter = take(16);
+  L.step_ctr = take(16);
+  L.scalars = take(4 * 8);
+  L.dm_ring = take((size_t)DM_RING * 8);
+  L.block_sums = take(((size_t)(L.plane + 1023) / 1024 + 1) * 4);
+  L.totals = take(16 * 4);
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+
+struct lbm_ctx {
+  lbm_config cfg{};
+  std::vector<double> cx, cy, r, dmu;
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  Layout lay{};
+  EosSolution eos{};
+  bool fp64 = false;
+  double rho_ref = 0;
+  bool built = false, inited = false;
+  int cur = 0;
+  long long steps = 0;
+  long long n_links = 0, n_bnodes = 0, n_s1 = 0, n_s2 = 0, n_fluid = 0;
+  Lattice<float> Lf{};
+  Lattice<double> Ld{};
+  double mass0 = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  lbm_status sticky = LBM_OK;
+  std::string err;
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx* c, lbm_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) {
+    c->err = buf;
+    if (s == LBM_ECUDA) c->sticky = s;
+  }
+  return s;
+}
+
+#define CUDA_OK(ctx, call)                                                                   \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail(ctx, LBM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));           \
+  } while (0)
+
+template <typename real>
+void fill_lattice(lbm_ctx* c, Lattice<real>& L) {
+  const Layout& y = c->lay;
+  char* w = c->ws;
+  L.nx = c->cfg.nx;
+  L.ny = c->cfg.ny;
+  L.pitch = y.pitch;
+  L.walls = c->cfg.walls;
+  L.plane = y.plane;
+  L.f[0] = (real*)(w + y.fA);
+  L.f[1] = (real*)(w + y.fB);
+  L.rho = (real*)(w + y.rho);
+  L.mu = (real*)(w + y.mu);
+  L.kind = (const uint8_t*)(w + y.kind);
+  const lbm_config& g = c->cfg;
+  L.eos = g.eos;
+  const double RT = g.R * c->eos.T;
+  L.RT = (real)RT;
+  L.a = (real)g.a;
+  L.b = (real)g.b;
+  L.aalpha = (real)(g.a * c->eos.alpha);
+  L.k2 = (real)(g.k * g.k);
+  L.kappa = (real)g.kappa;
+  L.mu_sat = (real)c->eos.mu_sat;
+  {
+    const real rg = (real)c->eos.rho_g, rl = (real)c->eos.rho_l;
+    L.rho_g = rg;
+    L.rho_l = rl;
+    L.rho_split = (real)std::sqrt(c->eos.rho_g * c->eos.rho_l);
+    auto Pof = [&](double r) { double e = g.b * r / 4.0; return 8.0 * e - 9.0 * e * e + 3.0 * e * e * e; };
+    L.P_g = (real)Pof((double)rg);
+    L.P_l = (real)Pof((double)rl);
+    const double aal = g.a * c->eos.alpha;
+    L.c_g = (real)(eos_mu(g.eos, g.a, g.b, RT, aal, (double)rg) - c->eos.mu_sat);
+    L.c_l = (real)(eos_mu(g.eos, g.a, g.b, RT, aal, (double)rl) - c->eos.mu_sat);
+  }
+  L.rho_ref = (real)c->rho_ref;
+  L.coll = g.coll;
+  L.omega = (real)(1.0 / g.tau);
+  L.s_e = (real)g.s_e;
+  L.s_eps = (real)g.s_eps;
+  L.s_q = (real)g.s_q;
+  L.s_nu = (real)g.s_nu;
+  L.gx = (real)g.gx;
+  L.gy = (real)g.gy;
+  L.bc = g.bc;
+  L.n_bnodes = (int)c->n_bnodes;
+  L.bnode = (const int*)(w + y.bnode);
+  L.bstart = (const int*)(w + y.bstart);
+  L.ldir = (const uint8_t*)(w + y.ldir);
+  L.lq = (const real*)(w + y.lq);
+  L.lx2f = (const uint8_t*)(w + y.lx2f);
+  L.carry = (double*)(w + y.carry);
+  L.n_s1 = (int)c->n_s1;
+  L.n_s2 = (int)c->n_s2;
+  L.s1node = (const int*)(w + y.s1node);
+  L.s1mask = (const uint8_t*)(w + y.s1mask);
+  L.s1winv = (const real*)(w + y.s1winv);
+  L.s2node = (const int*)(w + y.s2node);
+  L.s2mask = (const uint8_t*)(w + y.s2mask);
+  L.s2winv = (const real*)(w + y.s2winv);
+  L.partials = (double*)(w + y.partials);
+  L.counter = (unsigned int*)(w + y.counter);
+  L.dM_ring = (double*)(w + y.dm_ring);
+  L.step_ctr = (unsigned long long*)(w + y.step_ctr);
+  L.scalars = (double*)(w + y.scalars);
+}
+
+void refresh(lbm_ctx* c) {
+  if (c->fp64) fill_lattice(c, c->Ld); else fill_lattice(c, c->Lf);
+}
+
+lbm_status validate(const lbm_config* g, char* msg) {
+  auto bad = [&](const char* m) { std::snprintf(msg, 256, "%s", m); return LBM_EINVAL; };
+  if (g->nx < 5 || g->ny < 5) return bad("nx and ny must be at least 5");
+  if ((long long)g->nx * g->ny > (1LL << 30)) return bad("lattice larger than 2^30 nodes");
+  if (g->walls != 0 && g->walls != 1) return bad("walls must be 0 or 1");
+  if (g->walls) {
+    if (!(g->y_bottom >= 1.0 && g->y_bottom < 2.0)) return bad("y_bottom must lie in [1, 2)");
+    if (!(g->y_top > g->ny - 3.0 && g->y_top <= g->ny - 2.0)) return bad("y_top must lie in (ny-3, ny-2]");
+  }
+  if (g->eos < LBM_EOS_NONE || g->eos > LBM_EOS_PR) return bad("unknown EOS");
+  if (g->coll != LBM_COLL_BGK && g->coll != LBM_COLL_MRT) return bad("unknown collision model");
+  if (g->bc < LBM_BC_PRESENT || g->bc > LBM_BC_HBB) return bad("unknown boundary scheme");
+  if (g->precision != LBM_FP32 && g->precision != LBM_FP64) return bad("precision must be LBM_FP32 or LBM_FP64");
+  if (g->coll == LBM_COLL_BGK && !(g->tau > 0.5)) return bad("BGK needs tau > 1/2");
+  if (g->coll == LBM_COLL_MRT) {
+    const double s[4] = {g->s_e, g->s_eps, g->s_q, g->s_nu};
+    for (double v : s)
+      if (!(v > 0.0 && v < 2.0)) return bad("MRT rates must lie in (0, 2)");
+  }
+  if (!(std::isfinite(g->gx) && std::isfinite(g->gy))) return bad("gravity must be finite");
+  if (g->eos != LBM_EOS_NONE && !(g->k > 0 && g->kappa >= 0)) return bad("k must be positive and kappa non-negative");
+  if (g->n_cyl < 0) return bad("n_cyl must be non-negative");
+  if (g->n_cyl > 0 && (!g->cx || !g->cy || !g->r || !g->dmu_w)) return bad("cylinder arrays missing");
+  for (int j = 0; j < g->n_cyl; ++j) {
+    double r = g->r[j];
+    if (!(r > 0)) return bad("cylinder radius must be positive");
+    if (g->cx[j] - r < 2.0 || g->cx[j] + r > g->nx - 3.0) return bad("cylinder must keep two nodes from the periodic x edges");
+    if (!g->walls && (g->cy[j] - r < 2.0 || g->cy[j] + r > g->ny - 3.0))
+      return bad("cylinder must keep two nodes from the periodic y edges");
+    if (!std::isfinite(g->dmu_w[j])) return bad("wall chemical potential must be finite");
+  }
+  return LBM_OK;
+}
+
+template <typename real>
+lbm_status do_step(lbm_ctx* c, const Lattice<real>& L, long long n) {
+  if (n >= 2 && c->stream != nullptr) {
+    int p = c->cur;
+    if (!c->graph[p]) {
+      cudaGraph_t g;
+      CUDA_OK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e1 = launch_step(L, p, c->stream);
+      cudaError_t e2 = launch_step(L, p ^ 1, c->stream);
+      cudaError_t e3 = cudaStreamEndCapture(c->stream, &g);
+      if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+        return fail(c, LBM_ECUDA, "graph capture failed: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3)));
+      cudaError_t e4 = cudaGraphInstantiate(&c->graph[p], g, 0);
+      cudaGraphDestroy(g);
+      if (e4 != cudaSuccess) return fail(c, LBM_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e4));
+    }
+    for (long long k = 0; k < n / 2; ++k) CUDA_OK(c, cudaGraphLaunch(c->graph[p], c->stream));
+    n -= 2 * (n / 2);
+  }
+  for (long long k = 0; k < n; ++k) {
+    CUDA_OK(c, launch_step(L, c->cur, c->stream));
+    c->cur ^= 1;
+  }
+  return LBM_OK;
+}
+
+template <typename real>
+lbm_status profile_steps(lbm_ctx* c, const Lattice<real>& L, long long n, double* ms) {
+  cudaEvent_t ev[6];
+  for (auto& e : ev) CUDA_OK(c, cudaEventCreate(&e));
+  for (int k = 0; k < 5; ++k) ms[k] = 0.0;
+  lbm_status st = LBM_OK;
+  for (long long s = 0; s < n && st == LBM_OK; ++s) {
+    for (int ph = 0; ph < 5; ++ph) {
+      cudaEventRecord(ev[ph], c->stream);
+      cudaError_t e = launch_phase(L, c->cur, ph, c->stream);
+      if (e != cudaSuccess) { st = fail(c, LBM_ECUDA, "launch failed: %s", cudaGetErrorString(e)); break; }
+    }
+    cudaEventRecord(ev[5], c->stream);
+    cudaError_t e = cudaEventSynchronize(ev[5]);
+    if (e != cudaSuccess) { st = fail(c, LBM_ECUDA, "step failed: %s", cudaGetErrorString(e)); break; }
+    for (int ph = 0; ph < 5; ++ph) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[ph], ev[ph + 1]);
+      ms[ph] += t;
+    }
+    c->cur ^= 1;
+    c->steps += 1;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_status_str(lbm_status s) {
+  switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOMEM: return "workspace too small";
+    case LBM_ECUDA: return "CUDA error";
+    case LBM_ESTATE: return "call out of order";
+    case LBM_EUNSTABLE: return "non-finite populations";
+    case LBM_ETIMEOUT: return "device wait timed out";
+    default: return "internal error";
+  }
+}
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+lbm_status lbm_workspace_size(const lbm_config* cfg, size_t* bytes) {
+  if (!cfg || !bytes) return LBM_EINVAL;
+  char msg[256];
+  lbm_status s = validate(cfg, msg);
+  if (s != LBM_OK) return s;
+  *bytes = make_layout(cfg).total;
+  return LBM_OK;
+}
+
+lbm_status lbm_create(const lbm_config* cfg, void* stream, void* workspace, size_t bytes, lbm_ctx** out) {
+  if (!cfg || !out) return LBM_EINVAL;
+  *out = nullptr;
+  lbm_ctx* c = new lbm_ctx();
+  char msg[256] = {0};
+  lbm_status s = validate(cfg, msg);
+  if (s != LBM_OK) {
+    c->err = msg;
+    *out = c;   // returned so that the caller can read lbm_last_error, then destroy
+    return s;
+  }
+  c->cfg = *cfg;
+  c->cx.assign(cfg->cx, cfg->cx + cfg->n_cyl);
+  c->cy.assign(cfg->cy, cfg->cy + cfg->n_cyl);
+  c->r.assign(cfg->r, cfg->r + cfg->n_cyl);
+  c->dmu.assign(cfg->dmu_w, cfg->dmu_w + cfg->n_cyl);
+  c->cfg.cx = c->cx.data();
+  c->cfg.cy = c->cy.data();
+  c->cfg.r = c->r.data();
+  c->cfg.dmu_w = c->dmu.data();
+  c->fp64 = cfg->precision == LBM_FP64;
+  if (eos_solve(cfg->eos, cfg->a, cfg->b, cfg->R, cfg->T_over_Tc, cfg->omega, &c->eos, msg)) {
+    c->err = msg;
+    *out = c;
+    return LBM_EINVAL;
+  }
+  c->rho_ref = cfg->rho_ref >= 0 ? cfg->rho_ref : (c->fp64 ? 0.0 : (cfg->eos == LBM_EOS_NONE ? 1.0 : c->eos.rho_g));
+  c->lay = make_layout(&c->cfg);
+  *out = c;
+  if (!workspace) return fail(c, LBM_EINVAL, "workspace is NULL");
+  if (((uintptr_t)workspace) % ALIGN) return fail(c, LBM_EINVAL, "workspace must be 256-byte aligned");
+  if (bytes < c->lay.total)
+    return fail(c, LBM_ENOMEM, "workspace of %zu bytes, %zu needed", bytes, c->lay.total);
+  c->ws = (char*)workspace;
+  c->ws_bytes = bytes;
+  c->stream = (cudaStream_t)stream;
+  refresh(c);
+  return LBM_OK;
+}
+
+lbm_status lbm_build_links(lbm_ctx* c) {
+  if (!c || !c->ws) return LBM_ESTATE;
+  if (c->sticky != LBM_OK) return c->sticky;
+  for (auto& gr : c->graph)
+    if (gr) { cudaGraphExecDestroy(gr); gr = nullptr; }
+  const Layout& y = c->lay;
+  const lbm_config& g = c->cfg;
+  char* w = c->ws;
+  std::vector<double> cyl(4 * (g.n_cyl > 0 ? g.n_cyl : 1), 0.0);
+  for (int j = 0; j < g.n_cyl; ++j) {
+    cyl[4 * j] = c->cx[j]; cyl[4 * j + 1] = c->cy[j]; cyl[4 * j + 2] = c->r[j]; cyl[4 * j + 3] = c->dmu[j];
+  }
+  CUDA_OK(c, cudaMemcpyAsync(w + y.cyl, cyl.data(), cyl.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  GeomParams gp{};
+  gp.nx = g.nx; gp.ny = g.ny; gp.pitch = y.pitch; gp.walls = g.walls; gp.plane = y.plane;
+  gp.y_bottom = g.y_bottom; gp.y_top = g.y_top; gp.n_cyl = g.n_cyl; gp.cyl = (const double*)(w + y.cyl);
+  gp.dmu_walls = g.dmu_w_walls;
+  // the second lattice is free until lbm_init: it holds the per-node scratch of the set-up
+  GeomScratch sc{};
+  sc.body = (int*)(w + y.fB);
+  sc.cnt = sc.body + y.plane;
+  sc.off = sc.cnt + y.plane;
+  sc.block_sums = (int*)(w + y.block_sums);
+  sc.totals = (int*)(w + y.totals);
+  CUDA_OK(c, geom_classify_and_count(gp, sc, (uint8_t*)(w + y.kind), c->stream));
+  int tot[8];
+  CUDA_OK(c, cudaMemcpyAsync(tot, sc.totals, sizeof(tot), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  c->n_links = tot[0]; c->n_bnodes = tot[1]; c->n_s1 = tot[2]; c->n_s2 = tot[3]; c->n_fluid = tot[4];
+  if (c->n_links > y.cap.links || c->n_bnodes > y.cap.bnodes || c->n_s1 > y.cap.s1 || c->n_s2 > y.cap.s2)
+    return fail(c, LBM_ENOMEM, "geometry exceeds the list capacity (links %lld/%lld)", c->n_links, y.cap.links);
+  GeomOut o{};
+  o.kind = (uint8_t*)(w + y.kind);
+  o.bnode = (int*)(w + y.bnode); o.bstart = (int*)(w + y.bstart); o.ldir = (uint8_t*)(w + y.ldir);
+  o.lq64 = (double*)(w + y.lq64); o.lx2f = (uint8_t*)(w + y.lx2f); o.lq = w + y.lq;
+  o.s1node = (int*)(w + y.s1node); o.s1mask = (uint8_t*)(w + y.s1mask); o.s1winv = w + y.s1winv;
+  o.s2node = (int*)(w + y.s2node); o.s2mask = (uint8_t*)(w + y.s2mask); o.s2winv = w + y.s2winv;
+  o.mu = w + y.mu;
+  o.fp64 = c->fp64;
+  CUDA_OK(c, geom_fill(gp, sc, o, 0.0, c->stream));
+  int last = (int)c->n_links;
+  CUDA_OK(c, cudaMemcpyAsync(o.bstart + c->n_bnodes, &last, 4, cudaMemcpyHostToDevice, c->stream));
+  CUDA_OK(c, cudaMemsetAsync(w + y.counter, 0, 16, c->stream));
+  CUDA_OK(c, cudaMemsetAsync(w + y.step_ctr, 0, 16, c->stream));
+  CUDA_OK(c, cudaMemsetAsync(w + y.dm_ring, 0, (size_t)DM_RING * 8, c->stream));
+  CUDA_OK(c, cudaMemsetAsync(w + y.rho, 0, y.plane * y.sz, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  c->built = true;
+  c->inited = false;
+  refresh(c);
+  return LBM_OK;
+}
+
+lbm_status lbm_counts(lbm_ctx* c, int64_t* nl, int64_t* nb, int64_t* nf, int64_t* n1, int64_t* n2) {
+  if (!c || !c->built) return LBM_ESTATE;
+  if (nl) *nl = c->n_links;
+  if (nb) *nb = c->n_bnodes;
+  if (nf) *nf = c->n_fluid;
+  if (n1) *n1 = c->n_s1;
+  if (n2) *n2 = c->n_s2;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_links(lbm_ctx* c, int64_t capacity, int32_t* x1, int32_t* dir, double* q, int32_t* x2,
+                         int32_t* x2f) {
+  if (!c || !c->built) return LBM_ESTATE;
+  if (c->sticky != LBM_OK) return c->sticky;
+  if (capacity < c->n_links) return fail(c, LBM_EINVAL, "capacity %lld < %lld links", (long long)capacity, c->n_links);
+  const Layout& y = c->lay;
+  const long long L = c->n_links, B = c->n_bnodes;
+  std::vector<int> bnode(B), bstart(B + 1);
+  std::vector<uint8_t> d(L), f2(L);
+  std::vector<double> qq(L);
+  CUDA_OK(c, cudaMemcpy(bnode.data(), c->ws + y.bnode, B * 4, cudaMemcpyDeviceToHost));
+  CUDA_OK(c, cudaMemcpy(bstart.data(), c->ws + y.bstart, (B + 1) * 4, cudaMemcpyDeviceToHost));
+  CUDA_OK(c, cudaMemcpy(d.data(), c->ws + y.ldir, L, cudaMemcpyDeviceToHost));
+  CUDA_OK(c, cudaMemcpy(f2.data(), c->ws + y.lx2f, L, cudaMemcpyDeviceToHost));
+  CUDA_OK(c, cudaMemcpy(qq.data(), c->ws + y.lq64, L * 8, cudaMemcpyDeviceToHost));
+  const int nx = c->cfg.nx, ny = c->cfg.ny;
+  for (long long b = 0; b < B; ++b) {
+    int n = bnode[b];
+    int x = n % y.pitch, yy = n / y.pitch;
+    for (int l = bstart[b]; l < bstart[b + 1]; ++l) {
+      int i = d[l];
+      if (x1) x1[l] = yy * nx + x;
+      if (dir) dir[l] = i;
+      if (q) q[l] = qq[l];
+      int xx = ((x - ex(i)) % nx + nx) % nx;
+      int y2 = yy - ey(i);
+      if (!c->cfg.walls) y2 = (y2 % ny + ny) % ny;
+      if (x2) x2[l] = y2 * nx + xx;
+      if (x2f) x2f[l] = f2[l];
+    }
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_get_kind(lbm_ctx* c, uint8_t* kind) {
+  if (!c || !c->built) return LBM_ESTATE;
+  if (c->sticky != LBM_OK) return c->sticky;
+  const Layout& y = c->lay;
+  CUDA_OK(c, cudaMemcpy2D(kind, c->cfg.nx, c->ws + y.kind, y.pitch, c->cfg.nx, c->cfg.ny, cudaMemcpyDeviceToHost));
+  return LBM_OK;
+}
+
+lbm_status lbm_init(lbm_ctx* c, const lbm_init_spec* s) {
+  if (!c || !c->built) return LBM_ESTATE;
+  if (c->sticky != LBM_OK) return c->sticky;
+  if (!s || s->n_drop < 0 || s->n_drop > MAX_DROPS) return fail(c, LBM_EINVAL, "n_drop must lie in [0, %d]", MAX_DROPS);
+  if (s->n_drop > 0 && (!s->x0 || !s->y0 || !s->r0)) return fail(c, LBM_EINVAL, "droplet arrays missing");
+  if (!(s->width > 0)) return fail(c, LBM_EINVAL, "interface width must be positive");
+  std::vector<double> d(5 * (s->n_drop > 0 ? s->n_drop : 1), 0.0);
+  for (int k = 0; k < s->n_drop; ++k) {
+    d[5 * k] = s->x0[k]; d[5 * k + 1] = s->y0[k]; d[5 * k + 2] = s->r0[k];
+    d[5 * k + 3] = s->ux0 ? s->ux0[k] : 0.0; d[5 * k + 4] = s->uy0 ? s->uy0[k] : 0.0;
+  }
+  const Layout& y = c->lay;
+  CUDA_OK(c, cudaMemcpyAsync(c->ws + y.drops, d.data(), d.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  const double* dd = (const double*)(c->ws + y.drops);
+  if (c->fp64) CUDA_OK(c, launch_init(c->Ld, dd, s->n_drop, s->width, c->eos.rho_g, c->eos.rho_l, c->stream));
+  else CUDA_OK(c, launch_init(c->Lf, dd, s->n_drop, s->width, c->eos.rho_g, c->eos.rho_l, c->stream));
+  CUDA_OK(c, cudaMemsetAsync(c->ws + y.step_ctr, 0, 16, c->stream));
+  CUDA_OK(c, cudaMemsetAsync(c->ws + y.dm_ring, 0, (size_t)DM_RING * 8, c->stream));
+  CUDA_OK(c, cudaMemsetAsync(c->ws + y.carry, 0, (size_t)y.cap.bnodes * 8, c->stream));
+  c->cur = 0;
+  c->steps = 0;
+  if (c->fp64) CUDA_OK(c, launch_mass(c->Ld, 0, c->stream)); else CUDA_OK(c, launch_mass(c->Lf, 0, c->stream));
+  double sc[2];
+  CUDA_OK(c, cudaMemcpyAsync(sc, c->ws + y.scalars, 16, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  c->mass0 = sc[0] + (double)c->n_fluid * c->rho_ref;
+  c->inited = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int64_t n) {
+  if (!c || !c->inited) return LBM_ESTATE;
+  if (c->sticky != LBM_OK) return c->sticky;
+  if (n < 0) return fail(c, LBM_EINVAL, "negative step count");
+  lbm_status s = c->fp64 ? do_step(c, c->Ld, n) : do_step(c, c->Lf, n);
+  if (s == LBM_OK) c->steps += n;
+  return s;
+}
+
+lbm_status lbm_launches_per_step(lbm_ctx* c, int64_t* n) {
+  if (!c || !c->built || !n) return LBM_ESTATE;
+  *n = c->fp64 ? launches_per_step(c->Ld) : launches_per_step(c->Lf);
+  return LBM_OK;
+}
+
+lbm_status lbm_fields(lbm_ctx* c, void* rho, void* vx, void* vy, int32_t on_device) {
+  if (!c || !c->inited) return LBM_ESTATE;
+  if (c->sticky != LBM_OK) return c->sticky;
+  if (!rho || !vx || !vy) return fail(c, LBM_EINVAL, "null output");
+  const long long dn = (long long)c->cfg.nx * c->cfg.ny;
+  const size_t sz = c->lay.sz;
+  // the lattice that the next step overwrites completely serves as staging memory
+  char* stage = c->ws + (c->cur ? c->lay.fA : c->lay.fB);
+  char* r = on_device ? (char*)rho : stage;
+  char* u = on_device ? (char*)vx : stage + dn * sz;
+  char* v = on_device ? (char*)vy : stage + 2 * dn * sz;
+  if (c->fp64) CUDA_OK(c, launch_fields(c->Ld, c->cur, (double*)r, (double*)u, (double*)v, c->stream));
+  else CUDA_OK(c, launch_fields(c->Lf, c->cur, (float*)r, (float*)u, (float*)v, c->stream));
+  if (!on_device) {
+    CUDA_OK(c, cudaMemcpyAsync(rho, r, dn * sz, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(c, cudaMemcpyAsync(vx, u, dn * sz, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(c, cudaMemcpyAsync(vy, v, dn * sz, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_populations(lbm_ctx* c, void* f, int32_t on_device) {
+  if (!c || !c->inited) return LBM_ESTATE;
+  if (c->sticky != LBM_OK) return c->sticky;
+  if (!f) return fail(c, LBM_EINVAL, "null output");
+  const long long dn = (long long)c->cfg.nx * c->cfg.ny;
+  const size_t sz = c->lay.sz;
+  char* stage = c->ws + (c->cur ? c->lay.fA : c->lay.fB);
+  char* out = on_device ? (char*)f : stage;
+  if (c->fp64) CUDA_OK(c, launch_populations(c->Ld, c->cur, (double*)out, c->stream));
+  else CUDA_OK(c, launch_populations(c->Lf, c->cur, (float*)out, c->stream));
+  if (!on_device) {
+    CUDA_OK(c, cudaMemcpyAsync(f, out, 9 * dn * sz, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_mass(lbm_ctx* c, double* M, double* M0, double* dM_last) {
+  if (!c || !c->inited) return LBM_ESTATE;
+  if (c->sticky != LBM_OK) return c->sticky;
+  const Layout& y = c->lay;
+  if (c->fp64) CUDA_OK(c, launch_mass(c->Ld, c->cur, c->stream)); else CUDA_OK(c, launch_mass(c->Lf, c->cur, c->stream));
+  double sc[2];
+  unsigned long long ctr = 0;
+  CUDA_OK(c, cudaMemcpyAsync(sc, c->ws + y.scalars, 16, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaMemcpyAsync(&ctr, c->ws + y.step_ctr, 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  double last = 0.0;
+  if (ctr > 0)
+    CUDA_OK(c, cudaMemcpy(&last, c->ws + y.dm_ring + ((ctr - 1) % DM_RING) * 8, 8, cudaMemcpyDeviceToHost));
+  if (M) *M = sc[0] + (double)c->n_fluid * c->rho_ref;
+  if (M0) *M0 = c->mass0;
+  if (dM_last) *dM_last = last;
+  if (sc[1] != 0.0) return fail(c, LBM_EUNSTABLE, "%.0f non-finite populations", sc[1]);
+  return LBM_OK;
+}
+
+lbm_status lbm_dM_history(lbm_ctx* c, double* out, int64_t n, int64_t* n_out) {
+  if (!c || !c->inited) return LBM_ESTATE;
+  if (c->sticky != LBM_OK) return c->sticky;
+  const Layout& y = c->lay;
+  unsigned long long ctr = 0;
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  CUDA_OK(c, cudaMemcpy(&ctr, c->ws + y.step_ctr, 8, cudaMemcpyDeviceToHost));
+  std::vector<double> ring(DM_RING);
+  CUDA_OK(c, cudaMemcpy(ring.data(), c->ws + y.dm_ring, DM_RING * 8, cudaMemcpyDeviceToHost));
+  long long avail = (long long)ctr < DM_RING ? (long long)ctr : DM_RING;
+  long long k = n < avail ? n : avail;
+  for (long long j = 0; j < k; ++j) out[j] = ring[(ctr - k + j) % DM_RING];
+  if (n_out) *n_out = k;
+  return LBM_OK;
+}
+
+lbm_status lbm_last_dM(lbm_ctx* c, double* dM) {
+  if (!c || !c->inited || !dM) return LBM_ESTATE;
+  if (c->sticky != LBM_OK) return c->sticky;
+  const Layout& y = c->lay;
+  unsigned long long ctr = 0;
+  CUDA_OK(c, cudaMemcpyAsync(&ctr, c->ws + y.step_ctr, 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  *dM = 0.0;
+  if (ctr > 0) {
+    CUDA_OK(c, cudaMemcpyAsync(dM, c->ws + y.dm_ring + ((ctr - 1) % DM_RING) * 8, 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_profile_steps(lbm_ctx* c, int64_t n, double* ms5) {
+  if (!c || !c->inited || !ms5) return LBM_ESTATE;
+  if (c->sticky != LBM_OK) return c->sticky;
+  return c->fp64 ? profile_steps(c, c->Ld, n, ms5) : profile_steps(c, c->Lf, n, ms5);
+}
+
+lbm_status lbm_eos_info(lbm_ctx* c, double* o) {
+  if (!c || !o) return LBM_EINVAL;
+  o[0] = c->eos.Tc; o[1] = c->eos.rho_c; o[2] = c->eos.T; o[3] = c->eos.alpha;
+  o[4] = c->eos.rho_g; o[5] = c->eos.rho_l; o[6] = c->eos.mu_sat; o[7] = c->eos.p_sat;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* c) {
+  if (!c) return;
+  for (auto& g : c->graph)
+    if (g) cudaGraphExecDestroy(g);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,369 @@
+// Device-side building blocks of the multiphase curved-boundary LBM step (sm_103a).
+//
+// Layout in HBM (one lattice): every per-node quantity is a plane of `pitch * ny` elements,
+// node (x, y) at y*pitch + x with pitch = nx rounded up to a 128-byte multiple, so that each
+// row starts on a cache-line boundary and a warp touches whole lines.  Populations are 9
+// such planes (structure of arrays) per lattice, two lattices A/B swapped every step, stored
+// in offset form  f_i - w_i rho_ref.  Padding nodes (x >= nx) carry kind KIND_PAD and are
+// never read as data.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbmgb {
+
+enum : uint8_t { KIND_FLUID = 0, KIND_SOLID1 = 1, KIND_SOLID2 = 2, KIND_DEEP = 3, KIND_PAD = 255 };
+enum { EOS_NONE = 0, EOS_CS = 1, EOS_PR = 2 };
+enum { COLL_BGK = 0, COLL_MRT = 1 };
+enum { BC_PRESENT = 0, BC_IBC = 1, BC_MIBC = 2, BC_HBB = 3 };
+constexpr int DM_RING = 4096;
+
+// D2Q9 velocities in the order of the columns of the transformation matrix M (Eq. 2).
+__host__ __device__ constexpr int ex(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0); }
+__host__ __device__ constexpr int ey(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0); }
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5); }
+__host__ __device__ constexpr double wgt(int i) { return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
+
+// Everything a kernel needs to address one lattice and evaluate its physics.
+template <typename real>
+struct Lattice {
+  int nx, ny, pitch, walls;
+  long long plane;              // pitch * ny
+  real* f[2];                   // the two population lattices (9 planes each)
+  real* rho;                    // density plane (fluid and the two solid layers)
+  real* mu;                     // chemical potential minus k^2 mu_sat (constant at solids)
+  const uint8_t* kind;
+  // equation of state, Eq. 12: mu~ = k^2 (psi'(rho) - mu_sat) - kappa lap(rho)
+  int eos;
+  real RT, a, b, aalpha, k2, kappa, mu_sat;
+  real rho_g, rho_l, rho_split;  // coexistence densities (storage-rounded) and sqrt(rho_g rho_l)
+  real P_g, P_l, c_g, c_l;        // CS: P(eta0) and psi'(rho0) - mu_sat at the rounded rho0
+  real rho_ref;
+  // collision, Eqs. 3-4
+  int coll;
+  real omega;                   // 1 / tau (BGK)
+  real s_e, s_eps, s_q, s_nu;
+  real gx, gy;
+  int bc;
+  // cut links, CSR over boundary-fluid nodes sorted by node
+  int n_bnodes;
+  const int* bnode;
+  const int* bstart;
+  const uint8_t* ldir;
+  const real* lq;
+  const uint8_t* lx2f;
+  // first and second solid layers for Eq. 15
+  int n_s1, n_s2;
+  const int* s1node;
+  const uint8_t* s1mask;         // bit i-1 set: neighbour e_i (i = 1..8) contributes
+  const real* s1winv;
+  const int* s2node;
+  const uint8_t* s2mask;
+  const real* s2winv;
+  double* carry;                // per boundary node: Eq. 18 residual below storage precision
+  // reductions (FP64)
+  double* partials;             // per-block partial sums
+  unsigned int* counter;        // last-block-done counter (returns to 0)
+  double* dM_ring;              // per-step domain sum of the Eq. 18 compensation
+  unsigned long long* step_ctr; // steps taken (device side)
+  double* scalars;              // [0] mass, [1] non-finite count
+};
+
+template <typename real>
+__device__ __forceinline__ int wrap_x(const Lattice<real>& L, int x) {
+  return x < 0 ? x + L.nx : (x >= L.nx ? x - L.nx : x);
+}
+template <typename real>
+__device__ __forceinline__ int wrap_y(const Lattice<real>& L, int y) {
+  if (L.walls) return y;
+  return y < 0 ? y + L.ny : (y >= L.ny ? y - L.ny : y);
+}
+template <typename real>
+__device__ __forceinline__ long long node_at(const Lattice<real>& L, int x, int y) {
+  return (long long)wrap_y(L, y) * L.pitch + wrap_x(L, x);
+}
+
+// ---------------------------------------------------------------------------------------
+// Equation of state: bulk chemical potential psi'(rho) minus its coexistence value.
+//   CS: psi' = RT [ln rho + (8 eta - 9 eta^2 + 3 eta^3)/(1-eta)^3] - 2 a rho,  eta = b rho/4
+//   PR: Eq. 11 without the gradient term.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float dev_log(float x) { return logf(x); }
+__device__ __forceinline__ double dev_log(double x) { return log(x); }
+
+__device__ __forceinline__ float dev_log1p(float x) { return log1pf(x); }
+__device__ __forceinline__ double dev_log1p(double x) { return log1p(x); }
+
+// CS: psi'(rho) - mu_sat evaluated against the nearer coexistence density rho0 (gas below
+// sqrt(rho_g rho_l), liquid above), where psi'(rho0) = mu_sat:
+//   RT ln(rho/rho0) + RT [G(eta) - G(eta0)] - 2a (rho - rho0) + c0,
+//   G(eta) = P(eta)/(1-eta)^3,  P = 8 eta - 9 eta^2 + 3 eta^3,
+// with ln(rho/rho0) = log1p((rho - rho0)/rho0) and the exact factorisation
+//   G(eta) - G(eta0) = h { [8 - 9(eta+eta0) + 3(eta^2 + eta eta0 + eta0^2)] / b^3
+//                          + P(eta0) (a^2 + a b + b^2) / (a^3 b^3) },
+//   h = eta - eta0, a = 1 - eta0, b = 1 - eta,
+// so that every term vanishes with rho - rho0 (which is exact near rho0) instead of cancelling
+// between terms of size RT ln rho.  c0 = psi'(rho0) - mu_sat of the storage-rounded rho0 is
+// computed in FP64 on the host, so both branches meet the same function.
+template <typename real>
+__device__ __forceinline__ real psi_prime_shifted(const Lattice<real>& L, real r) {
+  if (L.eos == EOS_CS) {
+    const bool liquid = r > L.rho_split;
+    const real r0 = liquid ? L.rho_l : L.rho_g;
+    const real P0 = liquid ? L.P_l : L.P_g;
+    const real c0 = liquid ? L.c_l : L.c_g;
+    const real dr = r - r0;
+    const real eta = L.b * r * real(0.25), eta0 = L.b * r0 * real(0.25);
+    const real h = L.b * dr * real(0.25);
+    const real a = real(1) - eta0, bb = real(1) - eta;
+    const real b3 = bb * bb * bb, a3 = a * a * a;
+    const real q1 = (real(8) - real(9) * (eta + eta0) + real(3) * (eta * eta + eta * eta0 + eta0 * eta0)) / b3;
+    const real q2 = P0 * (a * a + a * bb + bb * bb) / (a3 * b3);
+    return L.RT * dev_log1p(dr / r0) + L.RT * h * (q1 + q2) - real(2) * L.a * dr + c0;
+  }
+  // Peng-Robinson, Eq. 11 without the gradient term
+  const real s2 = real(1.4142135623730951);
+  real br = L.b * r;
+  real om = real(1) - br;
+  return L.RT * dev_log(r / om) -
+         L.aalpha / (real(2) * s2 * L.b) * dev_log((s2 - real(1) + br) / (s2 + real(1) - br)) +
+         L.RT / om - L.aalpha * r / (real(1) + real(2) * br - br * br) - L.mu_sat;
+}
+
+// Fourth-order central first derivatives and Laplacian along the lattice axes.
+struct Stencil {
+  long long xm2, xm1, xp1, xp2, ym2, ym1, yp1, yp2;
+};
+template <typename real>
+__device__ __forceinline__ Stencil stencil_at(const Lattice<real>& L, int x, int y) {
+  Stencil s;
+  long long row = (long long)y * L.pitch;
+  s.xm2 = row + wrap_x(L, x - 2);
+  s.xm1 = row + wrap_x(L, x - 1);
+  s.xp1 = row + wrap_x(L, x + 1);
+  s.xp2 = row + wrap_x(L, x + 2);
+  s.ym2 = (long long)wrap_y(L, y - 2) * L.pitch + x;
+  s.ym1 = (long long)wrap_y(L, y - 1) * L.pitch + x;
+  s.yp1 = (long long)wrap_y(L, y + 1) * L.pitch + x;
+  s.yp2 = (long long)wrap_y(L, y + 2) * L.pitch + x;
+  return s;
+}
+
+template <typename real>
+__device__ __forceinline__ void grad4(const real* __restrict__ p, const Stencil& s, real& gx, real& gy) {
+  const real c = real(1.0 / 12.0);
+  gx = (real(8) * (__ldg(p + s.xp1) - __ldg(p + s.xm1)) - (__ldg(p + s.xp2) - __ldg(p + s.xm2))) * c;
+  gy = (real(8) * (__ldg(p + s.yp1) - __ldg(p + s.ym1)) - (__ldg(p + s.yp2) - __ldg(p + s.ym2))) * c;
+}
+
+// Written as differences from the centre value, (-p2 + 16 p1 - 30 c + 16 p-1 - p-2)/12 =
+// (16 [(p1 - c) + (p-1 - c)] - [(p2 - c) + (p-2 - c)])/12: inside a bulk phase the
+// differences are exact (Sterbenz), so FP32 keeps the Laplacian's relative accuracy there
+// instead of losing it to cancellation between terms of size 30 rho.
+template <typename real>
+__device__ __forceinline__ real lap4(const real* __restrict__ p, long long n, const Stencil& s) {
+  const real c = p[n];
+  real lx = real(16) * ((p[s.xp1] - c) + (p[s.xm1] - c)) - ((p[s.xp2] - c) + (p[s.xm2] - c));
+  real ly = real(16) * ((p[s.yp1] - c) + (p[s.ym1] - c)) - ((p[s.yp2] - c) + (p[s.ym2] - c));
+  return (lx + ly) * real(1.0 / 12.0);
+}
+
+// Nonideal force of Eq. 9 in mesh units, F = -rho grad(mu^) + c_s^2 grad(rho), plus rho g.
+template <typename real>
+__device__ __forceinline__ void force_at(const Lattice<real>& L, int x, int y, real r, real& Fx, real& Fy) {
+  Fx = r * L.gx;
+  Fy = r * L.gy;
+  if (L.eos != EOS_NONE) {
+    Stencil s = stencil_at(L, x, y);
+    real gmx, gmy, grx, gry;
+    grad4(L.mu, s, gmx, gmy);
+    grad4(L.rho, s, grx, gry);
+    const real cs2 = real(1.0 / 3.0);
+    Fx += -r * gmx + cs2 * grx;
+    Fy += -r * gmy + cs2 * gry;
+  }
+}
+
+// Exact-difference forcing term of Eq. 13 for direction i,
+//   F_i = f_i^eq(rho, u + du) - f_i^eq(rho, u),  du = F / rho,
+// written as a difference so that FP32 keeps its relative accuracy:
+//   w_i rho [3 e.du + 4.5 (e.du)(e.(2u+du)) - 1.5 du.(2u+du)].
+template <typename real>
+__device__ __forceinline__ real edm_term(int i, real r, real ux, real uy, real dux, real duy) {
+  real edu = real(ex(i)) * dux + real(ey(i)) * duy;
+  real e2u = real(ex(i)) * (real(2) * ux + dux) + real(ey(i)) * (real(2) * uy + duy);
+  real du2u = dux * (real(2) * ux + dux) + duy * (real(2) * uy + duy);
+  return real(wgt(i)) * r * (real(3) * edu + real(4.5) * edu * e2u - real(1.5) * du2u);
+}
+
+// Error-free sum of two numbers (Knuth's TwoSum): a + b = s + err exactly.
+template <typename real>
+__device__ __forceinline__ real two_sum(real a, real b, real& err) {
+  const real s = a + b;
+  const real bb = s - a;
+  err = (a - (s - bb)) + (b - bb);
+  return s;
+}
+
+// Moments of a node's offset populations: delta rho = sum_i (f_i - w_i rho_ref) and
+// j = sum_i f_i e_i.  delta rho is summed with compensation (TwoSum), so it is the correctly
+// rounded sum of the stored populations; j is summed as differences of opposite populations,
+// which are exact near equilibrium (Sterbenz), so the momentum keeps its relative accuracy
+// although it is a small difference of populations of size ~rho/9.
+template <typename real>
+__device__ __forceinline__ real density_sum(const real (&f)[9]) {
+  real s = f[0], c = real(0), e;
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    s = two_sum(s, f[i], e);
+    c += e;
+  }
+  return s + c;
+}
+
+template <typename real>
+__device__ __forceinline__ void moments(const real (&f)[9], real& drho, real& jx, real& jy) {
+  drho = density_sum(f);
+  jx = (f[1] - f[3]) + ((f[5] - f[7]) + (f[8] - f[6]));
+  jy = (f[2] - f[4]) + ((f[5] - f[7]) + (f[6] - f[8]));
+}
+
+// Density as the rho pass stores it (the same sum as moments()).
+template <typename real>
+__device__ __forceinline__ real density_of(const Lattice<real>& L, const real (&f)[9]) {
+  return L.rho_ref + density_sum(f);
+}
+
+// Collision (Eq. 4) of offset populations with the exact-difference term (Eq. 13) added.
+// Written on the non-equilibrium part g = f - f^eq (Eq. 14 equilibrium, offset by w_i rho_ref):
+//   MRT: f~ = f - M^-1 S (m - m_eq) = f^eq + M^-1 (I - S) M g,
+// which is the same map because m_eq = M f^eq (the moment equilibria under Eq. 1, with
+// q_y^eq = -j_y, are the moments of Eq. 14).  The conserved moments of g vanish, the other six
+// are scaled by 1 - s_k (Eq. 3 rates) and mapped back with M^-1 = M^T diag(1/9, 1/36, 1/36,
+// 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).  BGK: f~ = f^eq + (1 - 1/tau) g.
+//
+// FP32 accuracy: the large part of every population, w_i delta rho, is formed as
+// {16, 4, 1} x (delta rho / 36) -- exact multiples of one correctly rounded quotient, so the
+// weights sum to one exactly and no mass bias arises -- and every other (small) term is
+// accumulated before the single final rounding of each post-collision population.
+template <typename real>
+__device__ __forceinline__ void collide_node(const Lattice<real>& L, real (&f)[9], real r, real drho,
+                                             real jx, real jy, real Fx, real Fy) {
+  const real inv_r = real(1) / r;
+  const real ux = jx * inv_r, uy = jy * inv_r;
+  const real dux = Fx * inv_r, duy = Fy * inv_r;
+  const real usq = real(1.5) * (ux * ux + uy * uy);
+  const real q36 = drho / real(36);
+  real big[9], veq[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    big[i] = real(i == 0 ? 16 : (i <= 4 ? 4 : 1)) * q36;
+    real eu = real(ex(i)) * ux + real(ey(i)) * uy;
+    veq[i] = real(wgt(i)) * r * (real(3) * eu + real(4.5) * eu * eu - usq);
+    f[i] = (f[i] - big[i]) - veq[i];   // g_i, the non-equilibrium part
+  }
+  if (L.coll == COLL_MRT) {
+    const real (&g)[9] = f;
+    real e = real(-4) * g[0] - ((g[1] + g[2]) + (g[3] + g[4])) + real(2) * ((g[5] + g[6]) + (g[7] + g[8]));
+    real eps = real(4) * g[0] - real(2) * ((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8]));
+    real qx = real(-2) * (g[1] - g[3]) + ((g[5] - g[7]) + (g[8] - g[6]));
+    real qy = real(-2) * (g[2] - g[4]) + ((g[5] - g[7]) + (g[6] - g[8]));
+    real pxx = (g[1] + g[3]) - (g[2] + g[4]);
+    real pxy = (g[5] + g[7]) - (g[6] + g[8]);
+    e *= real(1) - L.s_e;
+    eps *= real(1) - L.s_eps;
+    qx *= real(1) - L.s_q;
+    qy *= real(1) - L.s_q;
+    pxx *= real(1) - L.s_nu;
+    pxy *= real(1) - L.s_nu;
+    const real e36 = e * real(1.0 / 36.0), e18 = e * real(1.0 / 18.0), e9 = e * real(1.0 / 9.0);
+    const real s36 = eps * real(1.0 / 36.0), s18 = eps * real(1.0 / 18.0), s9 = eps * real(1.0 / 9.0);
+    const real qx6 = qx * real(1.0 / 6.0), qy6 = qy * real(1.0 / 6.0);
+    const real qx12 = qx * real(1.0 / 12.0), qy12 = qy * real(1.0 / 12.0);
+    const real pxx4 = pxx * real(0.25), pxy4 = pxy * real(0.25);
+    f[0] = s9 - e9;
+    f[1] = -e36 - s18 - qx6 + pxx4;
+    f[2] = -e36 - s18 - qy6 - pxx4;
+    f[3] = -e36 - s18 + qx6 + pxx4;
+    f[4] = -e36 - s18 + qy6 - pxx4;
+    f[5] = e18 + s36 + qx12 + qy12 + pxy4;
+    f[6] = e18 + s36 - qx12 + qy12 - pxy4;
+    f[7] = e18 + s36 - qx12 - qy12 + pxy4;
+    f[8] = e18 + s36 + qx12 - qy12 - pxy4;
+  } else {
+    const real keep = real(1) - L.omega;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] *= keep;
+  }
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    f[i] = big[i] + ((veq[i] + f[i]) + edm_term<real>(i, r, ux, uy, dux, duy));
+}
+
+// Eqs. 16-17 (present scheme) and their variants for one link.
+//   a  = f~_i(x1, t)      (parked in the solid node's slot by the push)
+//   b2 = f~_i(x2, t)      (streamed into x1)
+//   c  = f~_ibar(x1, t)   (streamed into x2)
+//   Fi = F_i(x1, t)       (exact-difference term of direction i at x1)
+template <typename real>
+__device__ __forceinline__ real link_rule(int bc, real q, int x2_fluid, real a, real b2, real c, real Fi) {
+  if (bc == BC_HBB) return a;
+  const bool with_force = bc == BC_PRESENT;
+  if (q < real(0.5)) {
+    if (!x2_fluid) return a;
+    real w = real(1) - real(2) * q;
+    real v = real(2) * q * a + w * b2;
+    if (with_force) v += w * Fi;
+    return v;
+  }
+  real inv = real(1) / (real(2) * q);
+  real w = (real(2) * q - real(1)) * inv;
+  real v = a * inv + w * c;
+  if (with_force) v += w * Fi;
+  return v;
+}
+
+// Deterministic block sum of one double per thread (fixed shuffle tree, then warps in order).
+__device__ __forceinline__ double block_sum(double v, double* smem /* >= 32 */) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) smem[warp] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  double t = 0.0;
+  if (warp == 0) {
+    t = lane < nw ? smem[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  }
+  __syncthreads();
+  return t;   // valid in thread 0
+}
+
+// Last-block-done finish of a two-level deterministic reduction: every block stores its
+// partial; the block that arrives last sums all partials in index order.  Returns true in
+// thread 0 of that block, with the total in *total.
+__device__ __forceinline__ bool finish_reduction(double block_total, double* partials, unsigned int* counter,
+                                                 double* total, double* smem) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = block_total;
+    __threadfence();
+    unsigned int prev = atomicAdd(counter, 1u);
+    last = prev == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double v = 0.0;
+  for (unsigned int k = threadIdx.x; k < gridDim.x; k += blockDim.x) v += ((volatile double*)partials)[k];
+  double s = block_sum(v, smem);
+  if (threadIdx.x == 0) {
+    *total = s;
+    *counter = 0u;
+  }
+  return threadIdx.x == 0;
+}
+
+}  // namespace lbmgb

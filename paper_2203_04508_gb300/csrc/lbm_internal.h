@@ -1,0 +1,66 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace lbmgb {
+
+inline unsigned mass_blocks() { return 152 * 4; }
+
+// ---- step kernels (lbm_step.cu)
+template <typename real> cudaError_t launch_step(const Lattice<real>& L, int cur, cudaStream_t s);
+template <typename real> int launches_per_step(const Lattice<real>& L);
+template <typename real> cudaError_t launch_phase(const Lattice<real>& L, int cur, int phase, cudaStream_t s);
+template <typename real> cudaError_t launch_macro(const Lattice<real>& L, int cur, cudaStream_t s);
+template <typename real> cudaError_t launch_fields(const Lattice<real>& L, int cur, real* r, real* vx, real* vy, cudaStream_t s);
+template <typename real> cudaError_t launch_populations(const Lattice<real>& L, int cur, real* out, cudaStream_t s);
+template <typename real> cudaError_t launch_mass(const Lattice<real>& L, int cur, cudaStream_t s);
+template <typename real> cudaError_t launch_init(const Lattice<real>& L, const double* drops, int n_drop, double W,
+                                                 double rho_g, double rho_l, cudaStream_t s);
+
+// ---- geometry (lbm_geometry.cu, compiled without FMA contraction)
+struct GeomParams {
+  int nx, ny, pitch, walls;
+  long long plane;
+  double y_bottom, y_top;
+  int n_cyl;
+  const double* cyl;          // device: n_cyl x {cx, cy, r, dmu}
+  double dmu_walls;
+};
+
+struct GeomScratch {
+  int* body;                  // plane
+  int* cnt;                   // plane
+  int* off;                   // plane
+  int* block_sums;            // ceil(plane / 1024) + 1
+  int* totals;                // 8 ints on the device
+};
+
+struct GeomOut {
+  uint8_t* kind;
+  int* bnode; int* bstart; uint8_t* ldir; double* lq64; uint8_t* lx2f;
+  int* s1node; uint8_t* s1mask; int* s2node; uint8_t* s2mask;
+  void* lq;   void* s1winv; void* s2winv;   // precision-typed
+  void* mu;                                 // precision-typed plane
+  int fp64;
+};
+
+// Classification, layers and counts.  Leaves totals = {n_links, n_bnodes, n_s1, n_s2, n_fluid}
+// on the device (and the per-node link offsets in scratch) for the host to check capacities.
+cudaError_t geom_classify_and_count(const GeomParams& g, const GeomScratch& s, uint8_t* kind, cudaStream_t st);
+// Fills the link CSR, the layer lists and the constant wall chemical potential.
+cudaError_t geom_fill(const GeomParams& g, const GeomScratch& s, const GeomOut& o, double k2_mu_sat_unused,
+                      cudaStream_t st);
+
+// ---- EOS on the host (lbm_eos.cpp)
+struct EosSolution {
+  double Tc, rho_c, T, alpha, rho_g, rho_l, mu_sat, p_sat;
+};
+// returns 0 on success, otherwise writes a message to err (256 bytes)
+int eos_solve(int kind, double a, double b, double R, double Tr, double omega, EosSolution* out, char* err);
+double eos_pressure(int kind, double a, double b, double RT, double aalpha, double rho);
+double eos_mu(int kind, double a, double b, double RT, double aalpha, double rho);
+
+}  // namespace lbmgb

@@ -1,0 +1,395 @@
+// Kernels of one time step and of the state set-up / read-out (sm_103a).
+//
+// One step is five launches on one stream:
+//   k_rho           density of every fluid node from the 9 offset populations   (Sec. 2.1)
+//   k_solid (x2)    densities of the first, then second solid layer             (Eq. 15)
+//   k_mu            chemical potential at fluid nodes                            (Eq. 12)
+//   k_collide       force (Eq. 9) + collision (Eq. 4) + exact-difference forcing (Eq. 13)
+//                   + push streaming (Eq. 5) into the other lattice
+//   k_bc            every cut link by Eq. 16 / Eq. 17, the per-node compensation of Eq. 18
+//                   accumulated in FP64, and the deterministic domain sum of that step
+//
+// Streaming pushes every population, including those leaving a fluid node towards a solid
+// node: they land in the solid node's slot of the destination lattice, where k_bc reads them
+// back as f~_i(x1, t).  Likewise f~_i(x2, t) has streamed into x1 and f~_ibar(x1, t) into x2,
+// so k_bc needs no copy of the post-collision lattice.
+#include <cstdio>
+
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace lbmgb {
+
+constexpr int NODE_BLOCK = 256;
+
+template <typename real>
+__global__ void __launch_bounds__(NODE_BLOCK) k_rho(Lattice<real> L, int cur) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= L.plane) return;
+  if (L.kind[n] != KIND_FLUID) return;
+  const real* __restrict__ f = L.f[cur];
+  real fl[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) fl[i] = f[i * L.plane + n];
+  L.rho[n] = density_of(L, fl);
+}
+
+// Eq. 15: rho(x_s) = sum_i w_i rho(x_s + e_i) s_w / sum_i w_i s_w over the neighbours of the
+// previous layer (fluid for layer 1, layer 1 for layer 2); the mask and 1/sum w_i s_w are
+// geometry and were computed once.
+template <typename real>
+__global__ void __launch_bounds__(NODE_BLOCK) k_solid(Lattice<real> L, int layer) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cnt = layer == 1 ? L.n_s1 : L.n_s2;
+  if (j >= cnt) return;
+  const int n = layer == 1 ? L.s1node[j] : L.s2node[j];
+  const uint8_t m = layer == 1 ? L.s1mask[j] : L.s2mask[j];
+  const real winv = layer == 1 ? L.s1winv[j] : L.s2winv[j];
+  const int x = n % L.pitch, y = n / L.pitch;
+  real acc = real(0);
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    if (m & (1u << (i - 1))) acc += real(wgt(i)) * L.rho[node_at(L, x + ex(i), y + ey(i))];
+  }
+  L.rho[n] = acc * winv;
+}
+
+// Eq. 12 in mesh units, shifted by the constant k^2 mu_sat (only gradients of mu enter
+// Eq. 9): mu~ = k^2 (psi'(rho) - mu_sat) - kappa^ lap(rho).  Solid layers keep their
+// constant wall value.
+template <typename real>
+__global__ void __launch_bounds__(NODE_BLOCK) k_mu(Lattice<real> L) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= L.plane) return;
+  if (L.kind[n] != KIND_FLUID) return;
+  const int x = (int)(n % L.pitch), y = (int)(n / L.pitch);
+  Stencil s = stencil_at(L, x, y);
+  const real r = L.rho[n];
+  L.mu[n] = L.k2 * psi_prime_shifted(L, r) - L.kappa * lap4(L.rho, n, s);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(NODE_BLOCK) k_collide(Lattice<real> L, int cur) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= L.plane) return;
+  if (L.kind[n] != KIND_FLUID) return;
+  const int x = (int)(n % L.pitch), y = (int)(n / L.pitch);
+  const real* __restrict__ fin = L.f[cur];
+  real* __restrict__ fout = L.f[cur ^ 1];
+  real fl[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) fl[i] = fin[i * L.plane + n];
+  real drho, jx, jy;
+  moments(fl, drho, jx, jy);
+  const real r = L.rho_ref + drho;
+  real Fx, Fy;
+  force_at(L, x, y, r, Fx, Fy);
+  collide_node(L, fl, r, drho, jx, jy, Fx, Fy);
+  // push streaming, Eq. 5
+  const int xm = wrap_x(L, x - 1), xp = wrap_x(L, x + 1);
+  const long long rowc = (long long)y * L.pitch;
+  const long long rowm = (long long)wrap_y(L, y - 1) * L.pitch;
+  const long long rowp = (long long)wrap_y(L, y + 1) * L.pitch;
+  fout[0 * L.plane + n] = fl[0];
+  fout[1 * L.plane + rowc + xp] = fl[1];
+  fout[2 * L.plane + rowp + x] = fl[2];
+  fout[3 * L.plane + rowc + xm] = fl[3];
+  fout[4 * L.plane + rowm + x] = fl[4];
+  fout[5 * L.plane + rowp + xp] = fl[5];
+  fout[6 * L.plane + rowp + xm] = fl[6];
+  fout[7 * L.plane + rowm + xm] = fl[7];
+  fout[8 * L.plane + rowm + xp] = fl[8];
+}
+
+// One thread per boundary-fluid node x1: rebuild (rho, u, F) of step t at x1 from the
+// pre-collision lattice and the rho / mu planes (the same arithmetic k_collide used), then
+// apply Eq. 16 or 17 on each of its links and add the FP64 sum of Eq. 18 to f_0.
+template <typename real>
+__global__ void __launch_bounds__(NODE_BLOCK) k_bc(Lattice<real> L, int cur) {
+  __shared__ double red[32];
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  double sum = 0.0;
+  if (b < L.n_bnodes) {
+    const int n = L.bnode[b];
+    const int x = n % L.pitch, y = n / L.pitch;
+    const real* __restrict__ fin = L.f[cur];
+    real* fout = L.f[cur ^ 1];
+    real fl[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fl[i] = fin[i * L.plane + n];
+    real drho, jx, jy;
+    moments(fl, drho, jx, jy);
+    const real r = L.rho_ref + drho;
+    real Fx, Fy;
+    force_at(L, x, y, r, Fx, Fy);
+    const real inv_r = real(1) / r;
+    const real ux = jx * inv_r, uy = jy * inv_r, dux = Fx * inv_r, duy = Fy * inv_r;
+    const int l0 = L.bstart[b], l1 = L.bstart[b + 1];
+    for (int l = l0; l < l1; ++l) {
+      const int i = L.ldir[l];
+      const int ib = opp(i);
+      const long long xs = node_at(L, x + ex(i), y + ey(i));
+      const long long x2 = node_at(L, x - ex(i), y - ey(i));
+      const real a = fout[i * L.plane + xs];
+      const real b2 = fout[i * L.plane + n];
+      const real c = fout[ib * L.plane + x2];
+      // F_i(x1, t) of direction i
+      real Fi = real(0);
+      switch (i) {
+        case 1: Fi = edm_term<real>(1, r, ux, uy, dux, duy); break;
+        case 2: Fi = edm_term<real>(2, r, ux, uy, dux, duy); break;
+        case 3: Fi = edm_term<real>(3, r, ux, uy, dux, duy); break;
+        case 4: Fi = edm_term<real>(4, r, ux, uy, dux, duy); break;
+        case 5: Fi = edm_term<real>(5, r, ux, uy, dux, duy); break;
+        case 6: Fi = edm_term<real>(6, r, ux, uy, dux, duy); break;
+        case 7: Fi = edm_term<real>(7, r, ux, uy, dux, duy); break;
+        default: Fi = edm_term<real>(8, r, ux, uy, dux, duy); break;
+      }
+      const real v = link_rule<real>(L.bc, L.lq[l], L.lx2f[l], a, b2, c, Fi);
+      fout[ib * L.plane + n] = v;
+      sum += (double)a - (double)v;
+    }
+    if (L.bc == BC_PRESENT || L.bc == BC_MIBC) {
+      // Eq. 18 on f_0, accumulated in FP64.  The part of the sum that the storage precision
+      // cannot hold is carried to the node's next step instead of being dropped, so that the
+      // mass stays conserved to FP64 accuracy over any number of steps.
+      const double t = (double)fout[n] + sum + L.carry[b];
+      const real stored = (real)t;
+      L.carry[b] = t - (double)stored;
+      fout[n] = stored;
+    } else {
+      sum = 0.0;
+    }
+  }
+  double bt = block_sum(sum, red);
+  double total;
+  if (finish_reduction(bt, L.partials, L.counter, &total, red)) {
+    unsigned long long s = *L.step_ctr;
+    L.dM_ring[s % DM_RING] = total;
+    *L.step_ctr = s + 1;
+  }
+}
+
+// FP64 mass audit: sum over fluid nodes of sum_i (f_i - w_i rho_ref), plus a count of
+// non-finite populations.  The host adds n_fluid * rho_ref.
+template <typename real>
+__global__ void __launch_bounds__(NODE_BLOCK) k_mass(Lattice<real> L, int cur) {
+  __shared__ double red[32];
+  __shared__ double red2[32];
+  double s = 0.0, bad = 0.0;
+  const real* __restrict__ f = L.f[cur];
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < L.plane;
+       n += (long long)gridDim.x * blockDim.x) {
+    if (L.kind[n] != KIND_FLUID) continue;
+    double t = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      real v = f[i * L.plane + n];
+      if (!isfinite(v)) bad += 1.0;
+      t += (double)v;
+    }
+    s += t;
+  }
+  double bs = block_sum(s, red);
+  double bb = block_sum(bad, red2);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    L.partials[2 * blockIdx.x] = bs;
+    L.partials[2 * blockIdx.x + 1] = bb;
+    __threadfence();
+    unsigned int prev = atomicAdd(L.counter, 1u);
+    last = prev == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double a = 0.0, c = 0.0;
+  for (unsigned int k = threadIdx.x; k < gridDim.x; k += blockDim.x) {
+    a += ((volatile double*)L.partials)[2 * k];
+    c += ((volatile double*)L.partials)[2 * k + 1];
+  }
+  double ta = block_sum(a, red);
+  double tc = block_sum(c, red2);
+  if (threadIdx.x == 0) {
+    L.scalars[0] = ta;
+    L.scalars[1] = tc;
+    *L.counter = 0u;
+  }
+}
+
+// Density and v = u + F/(2 rho) of the current state into dense nx*ny arrays.
+template <typename real>
+__global__ void __launch_bounds__(NODE_BLOCK) k_fields(Lattice<real> L, int cur, real* rho_out, real* vx_out,
+                                                       real* vy_out) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= L.plane) return;
+  const int x = (int)(n % L.pitch), y = (int)(n / L.pitch);
+  if (x >= L.nx) return;
+  const long long d = (long long)y * L.nx + x;
+  if (L.kind[n] != KIND_FLUID) {
+    rho_out[d] = real(0);
+    vx_out[d] = real(0);
+    vy_out[d] = real(0);
+    return;
+  }
+  const real* __restrict__ f = L.f[cur];
+  real fl[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) fl[i] = f[i * L.plane + n];
+  real drho, jx, jy;
+  moments(fl, drho, jx, jy);
+  const real r = L.rho_ref + drho;
+  real Fx, Fy;
+  force_at(L, x, y, r, Fx, Fy);
+  rho_out[d] = r;
+  vx_out[d] = (jx + real(0.5) * Fx) / r;
+  vy_out[d] = (jy + real(0.5) * Fy) / r;
+}
+
+template <typename real>
+__global__ void k_populations(Lattice<real> L, int cur, real* out) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= L.plane) return;
+  const int x = (int)(n % L.pitch), y = (int)(n / L.pitch);
+  if (x >= L.nx) return;
+  const long long d = (long long)y * L.nx + x;
+  const long long dn = (long long)L.nx * L.ny;
+  const bool fluid = L.kind[n] == KIND_FLUID;
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    out[i * dn + d] = fluid ? L.f[cur][i * L.plane + n] + real(wgt(i)) * L.rho_ref : real(0);
+}
+
+// Eq. 19 initial state: rho = (rho_g + rho_l)/2 + (rho_g - rho_l)/2 tanh(2(r - r0)/W) around
+// the droplet with the largest liquid fraction phi at the node, u = phi u0, f = f^eq.
+template <typename real>
+__global__ void k_init(Lattice<real> L, const double* __restrict__ drops, int n_drop, double W,
+                       double rho_g, double rho_l) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= L.plane) return;
+  const int x = (int)(n % L.pitch), y = (int)(n / L.pitch);
+  real* f0 = L.f[0];
+  real* f1 = L.f[1];
+  if (x >= L.nx || L.kind[n] != KIND_FLUID) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) { f0[i * L.plane + n] = real(0); f1[i * L.plane + n] = real(0); }
+    return;
+  }
+  double phi = 0.0, u0 = 0.0, v0 = 0.0;
+  for (int d = 0; d < n_drop; ++d) {
+    const double* p = drops + 5 * d;
+    double dx = x - p[0], dy = y - p[1];
+    double rr = sqrt(dx * dx + dy * dy);
+    double ph = 0.5 - 0.5 * tanh(2.0 * (rr - p[2]) / W);
+    if (ph > phi) { phi = ph; u0 = p[3]; v0 = p[4]; }
+  }
+  const double r = 0.5 * (rho_g + rho_l) + 0.5 * (rho_g - rho_l) * (1.0 - 2.0 * phi);
+  const double ux = u0 * phi, uy = v0 * phi;
+  const double usq = 1.5 * (ux * ux + uy * uy);
+  const double rref = (double)L.rho_ref;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    double eu = ex(i) * ux + ey(i) * uy;
+    double feq = wgt(i) * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - usq);
+    f0[i * L.plane + n] = (real)(feq - wgt(i) * rref);
+    f1[i * L.plane + n] = real(0);
+  }
+  L.rho[n] = (real)r;
+}
+
+// ---------------------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------------------
+static inline unsigned grid_for(long long n, int block) { return (unsigned)((n + block - 1) / block); }
+
+template <typename real>
+cudaError_t launch_step(const Lattice<real>& L, int cur, cudaStream_t s) {
+  const unsigned gn = grid_for(L.plane, NODE_BLOCK);
+  k_rho<real><<<gn, NODE_BLOCK, 0, s>>>(L, cur);
+  if (L.n_s1 > 0) k_solid<real><<<grid_for(L.n_s1, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 1);
+  if (L.n_s2 > 0) k_solid<real><<<grid_for(L.n_s2, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 2);
+  if (L.eos != EOS_NONE) k_mu<real><<<gn, NODE_BLOCK, 0, s>>>(L);
+  k_collide<real><<<gn, NODE_BLOCK, 0, s>>>(L, cur);
+  unsigned gb = grid_for(L.n_bnodes, NODE_BLOCK);
+  k_bc<real><<<gb > 0 ? gb : 1, NODE_BLOCK, 0, s>>>(L, cur);
+  return cudaGetLastError();
+}
+
+// one phase of a step: 0 density, 1 solid layers, 2 chemical potential, 3 force+collide+stream,
+// 4 boundary links
+template <typename real>
+cudaError_t launch_phase(const Lattice<real>& L, int cur, int phase, cudaStream_t s) {
+  const unsigned gn = grid_for(L.plane, NODE_BLOCK);
+  switch (phase) {
+    case 0: k_rho<real><<<gn, NODE_BLOCK, 0, s>>>(L, cur); break;
+    case 1:
+      if (L.n_s1 > 0) k_solid<real><<<grid_for(L.n_s1, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 1);
+      if (L.n_s2 > 0) k_solid<real><<<grid_for(L.n_s2, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 2);
+      break;
+    case 2: if (L.eos != EOS_NONE) k_mu<real><<<gn, NODE_BLOCK, 0, s>>>(L); break;
+    case 3: k_collide<real><<<gn, NODE_BLOCK, 0, s>>>(L, cur); break;
+    default: {
+      unsigned gb = grid_for(L.n_bnodes, NODE_BLOCK);
+      k_bc<real><<<gb > 0 ? gb : 1, NODE_BLOCK, 0, s>>>(L, cur);
+    }
+  }
+  return cudaGetLastError();
+}
+
+template <typename real>
+int launches_per_step(const Lattice<real>& L) {
+  return 3 + (L.n_s1 > 0) + (L.n_s2 > 0) + (L.eos != EOS_NONE);
+}
+
+// density / solid layers / chemical potential of the current state (for the read-outs)
+template <typename real>
+cudaError_t launch_macro(const Lattice<real>& L, int cur, cudaStream_t s) {
+  const unsigned gn = grid_for(L.plane, NODE_BLOCK);
+  k_rho<real><<<gn, NODE_BLOCK, 0, s>>>(L, cur);
+  if (L.n_s1 > 0) k_solid<real><<<grid_for(L.n_s1, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 1);
+  if (L.n_s2 > 0) k_solid<real><<<grid_for(L.n_s2, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 2);
+  if (L.eos != EOS_NONE) k_mu<real><<<gn, NODE_BLOCK, 0, s>>>(L);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_fields(const Lattice<real>& L, int cur, real* r, real* vx, real* vy, cudaStream_t s) {
+  cudaError_t e = launch_macro(L, cur, s);
+  if (e != cudaSuccess) return e;
+  k_fields<real><<<grid_for(L.plane, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, cur, r, vx, vy);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_populations(const Lattice<real>& L, int cur, real* out, cudaStream_t s) {
+  k_populations<real><<<grid_for(L.plane, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, cur, out);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_mass(const Lattice<real>& L, int cur, cudaStream_t s) {
+  k_mass<real><<<mass_blocks(), NODE_BLOCK, 0, s>>>(L, cur);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_init(const Lattice<real>& L, const double* drops, int n_drop, double W, double rho_g,
+                        double rho_l, cudaStream_t s) {
+  k_init<real><<<grid_for(L.plane, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, drops, n_drop, W, rho_g, rho_l);
+  return cudaGetLastError();
+}
+
+#define LBMGB_INSTANTIATE(real)                                                                          \
+  template cudaError_t launch_step<real>(const Lattice<real>&, int, cudaStream_t);                      \
+  template int launches_per_step<real>(const Lattice<real>&);                                           \
+  template cudaError_t launch_phase<real>(const Lattice<real>&, int, int, cudaStream_t);                \
+  template cudaError_t launch_macro<real>(const Lattice<real>&, int, cudaStream_t);                     \
+  template cudaError_t launch_fields<real>(const Lattice<real>&, int, real*, real*, real*, cudaStream_t); \
+  template cudaError_t launch_populations<real>(const Lattice<real>&, int, real*, cudaStream_t);        \
+  template cudaError_t launch_mass<real>(const Lattice<real>&, int, cudaStream_t);                      \
+  template cudaError_t launch_init<real>(const Lattice<real>&, const double*, int, double, double,      \
+                                         double, cudaStream_t);
+LBMGB_INSTANTIATE(float)
+LBMGB_INSTANTIATE(double)
+
+}  // namespace lbmgb

@@ -1,0 +1,166 @@
+"""Python front end of one lattice: device workspace and stream from PyTorch, every step of
+the method in the CUDA library (through the C ABI of include/lbm.h)."""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional
+
+import numpy as np
+
+from . import _abi
+from ._abi import check, lbm_config, lbm_init_spec
+
+_PHYS_KEYS = ("nx", "ny", "walls", "y_bottom", "y_top", "eos", "a", "b", "R", "T_over_Tc", "omega", "k",
+              "kappa", "coll", "tau", "s_e", "s_eps", "s_q", "s_nu", "gx", "gy", "bc", "dmu_w_walls")
+
+
+def make_config(phys: dict, precision: int, rho_ref: float = -1.0):
+    """lbm_config from a plain dict of physical parameters; returns (struct, keep-alive arrays)."""
+    keep = {k: np.ascontiguousarray(np.asarray(phys.get(k, []), dtype=np.float64).reshape(-1))
+            for k in ("cx", "cy", "r", "dmu_w")}
+    c = lbm_config()
+    for k in _PHYS_KEYS:
+        setattr(c, k, phys[k])
+    c.precision = precision
+    c.rho_ref = rho_ref
+    c.n_cyl = len(keep["r"])
+    for k, a in keep.items():
+        setattr(c, k, a.ctypes.data_as(C.POINTER(C.c_double)))
+    return c, keep
+
+
+def workspace_size(phys: dict, precision: int) -> int:
+    c, keep = make_config(phys, precision)
+    n = C.c_size_t()
+    check(_abi.load().lbm_workspace_size(C.byref(c), C.byref(n)))
+    return n.value
+
+
+class Lattice:
+    """One lattice on the current CUDA device."""
+
+    def __init__(self, phys: dict, precision: int = _abi.LBM_FP32, rho_ref: float = -1.0,
+                 stream=None, build: bool = True):
+        import torch
+        lib = _abi.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.lib = lib
+        self.nx, self.ny = int(phys["nx"]), int(phys["ny"])
+        self.precision = precision
+        self.dtype = np.float64 if precision == _abi.LBM_FP64 else np.float32
+        self.tdtype = torch.float64 if precision == _abi.LBM_FP64 else torch.float32
+        self._cfg, self._keep = make_config(phys, precision, rho_ref)
+        n = C.c_size_t()
+        check(lib.lbm_workspace_size(C.byref(self._cfg), C.byref(n)))
+        self.workspace = torch.empty(n.value, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        ctx = C.c_void_p()
+        st = lib.lbm_create(C.byref(self._cfg), C.c_void_p(self.stream.cuda_stream),
+                            C.c_void_p(self.workspace.data_ptr()), n.value, C.byref(ctx))
+        self.ctx = ctx
+        if st != _abi.LBM_OK:
+            msg = lib.lbm_last_error(ctx).decode() if ctx else ""
+            if ctx:
+                lib.lbm_destroy(ctx)
+                self.ctx = None
+            raise _abi.LbmError(st, msg)
+        if build:
+            self.build_links()
+
+    def __del__(self):
+        if getattr(self, "ctx", None):
+            self.lib.lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def _c(self, st):
+        check(st, self.ctx)
+
+    # ---- set-up
+    def build_links(self):
+        self._c(self.lib.lbm_build_links(self.ctx))
+
+    def counts(self):
+        v = [C.c_int64() for _ in range(5)]
+        self._c(self.lib.lbm_counts(self.ctx, *[C.byref(x) for x in v]))
+        return dict(zip(("links", "boundary_nodes", "fluid", "solid1", "solid2"), [x.value for x in v]))
+
+    def links(self):
+        n = self.counts()["links"]
+        x1 = np.zeros(n, np.int32); d = np.zeros(n, np.int32); q = np.zeros(n, np.float64)
+        x2 = np.zeros(n, np.int32); f2 = np.zeros(n, np.int32)
+        self._c(self.lib.lbm_get_links(self.ctx, n, x1.ctypes.data, d.ctypes.data, q.ctypes.data,
+                                       x2.ctypes.data, f2.ctypes.data))
+        return {"x1": x1, "dir": d, "q": q, "x2": x2, "x2_fluid": f2}
+
+    def kind(self):
+        k = np.zeros((self.ny, self.nx), np.uint8)
+        self._c(self.lib.lbm_get_kind(self.ctx, k.ctypes.data))
+        return k
+
+    def init(self, x0, y0, r0, width, ux0=None, uy0=None):
+        n = len(r0)
+        arrs = [np.ascontiguousarray(np.asarray(v if v is not None else np.zeros(n), np.float64))
+                for v in (x0, y0, r0, ux0, uy0)]
+        self._init_keep = arrs
+        s = lbm_init_spec(n, *[a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrs], float(width))
+        self._c(self.lib.lbm_init(self.ctx, C.byref(s)))
+
+    def init_droplets(self, d: dict):
+        self.init(d["x0"], d["y0"], d["r0"], d["width"], d.get("ux0"), d.get("uy0"))
+
+    # ---- time stepping
+    def step(self, n: int = 1):
+        self._c(self.lib.lbm_step(self.ctx, int(n)))
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    # ---- read-outs
+    def fields(self, on_device: bool = False):
+        """(rho, vx, vy) of the current state, as numpy arrays (host) or torch tensors."""
+        import torch
+        if on_device:
+            out = [torch.empty((self.ny, self.nx), dtype=self.tdtype, device="cuda") for _ in range(3)]
+            self._c(self.lib.lbm_fields(self.ctx, *[C.c_void_p(t.data_ptr()) for t in out], 1))
+            return tuple(out)
+        out = [np.zeros((self.ny, self.nx), self.dtype) for _ in range(3)]
+        self._c(self.lib.lbm_fields(self.ctx, *[o.ctypes.data for o in out], 0))
+        return tuple(out)
+
+    def populations(self):
+        f = np.zeros((9, self.ny, self.nx), self.dtype)
+        self._c(self.lib.lbm_populations(self.ctx, f.ctypes.data, 0))
+        return f
+
+    def mass(self):
+        m, m0, dm = C.c_double(), C.c_double(), C.c_double()
+        self._c(self.lib.lbm_mass(self.ctx, C.byref(m), C.byref(m0), C.byref(dm)))
+        return m.value, m0.value, dm.value
+
+    def dM_history(self, n: int = 4096):
+        out = np.zeros(n)
+        k = C.c_int64()
+        self._c(self.lib.lbm_dM_history(self.ctx, out.ctypes.data, n, C.byref(k)))
+        return out[:k.value]
+
+    def last_dM(self) -> float:
+        d = C.c_double()
+        self._c(self.lib.lbm_last_dM(self.ctx, C.byref(d)))
+        return d.value
+
+    def profile_steps(self, n: int):
+        """Per-phase device time (ms) summed over n steps: rho, solid, mu, collide, bc."""
+        ms = np.zeros(5)
+        self._c(self.lib.lbm_profile_steps(self.ctx, int(n), ms.ctypes.data))
+        return ms
+
+    def eos_info(self):
+        o = np.zeros(8)
+        self._c(self.lib.lbm_eos_info(self.ctx, o.ctypes.data))
+        return dict(zip(("Tc", "rho_c", "T", "alpha", "rho_g", "rho_l", "mu_sat", "p_sat"), o.tolist()))
+
+    def launches_per_step(self) -> int:
+        n = C.c_int64()
+        self._c(self.lib.lbm_launches_per_step(self.ctx, C.byref(n)))
+        return n.value
