@@ -194,6 +194,27 @@ lbm_status lbm_eos_info(lbm_ctx* ctx, double* out8);
 /* Number of kernel launches one lbm_step(ctx, 1) issues. */
 lbm_status lbm_launches_per_step(lbm_ctx* ctx, int64_t* n);
 
+/* Mass audit that allocates no device memory (the paper has no counterpart: this serves
+ * callers that may not call cudaMalloc -- a host callback, a monitor, or a process whose device
+ * memory budget belongs to another allocator -- but already hold populations on the device).
+ *
+ * f:       device pointer to 9 planes of n_nodes values each (plane i at f + i*n_nodes), of
+ *          type float (precision LBM_FP32) or double (LBM_FP64), e.g. from lbm_populations;
+ * kind:    device pointer to n_nodes bytes; nodes with kind 0 (fluid) are summed;
+ * n_nodes: 1 .. LBM_NOALLOC_MAX_NODES, otherwise LBM_EINVAL and nothing is launched;
+ * stream:  cudaStream_t the work is issued on (may be NULL);
+ * out2:    HOST pointer to 2 doubles: sum over fluid nodes of sum_i f_i (FP64, deterministic
+ *          order), and the number of non-finite values.  The call synchronises the stream.
+ *
+ * Scratch: a fixed 16.6 kB array in the library's own device memory (a static __device__
+ * variable, present on every GPU the library is loaded on until the process exits), looked up
+ * with cudaGetSymbolAddress by the first call on each device -- make that first call before
+ * any stream capture.  Every call reuses the array; calls whose kernels overlap on the GPU
+ * race on it and must be serialised by the caller. */
+#define LBM_NOALLOC_MAX_NODES (1LL << 30)
+lbm_status lbm_mass_noalloc(const void* f, const uint8_t* kind, int64_t n_nodes, int32_t precision,
+                            void* stream, double* out2);
+
 void lbm_destroy(lbm_ctx* ctx);
 const char* lbm_status_str(lbm_status s);
 const char* lbm_last_error(const lbm_ctx* ctx);

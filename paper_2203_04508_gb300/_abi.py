@@ -57,6 +57,7 @@ _SIGS = {
     "lbm_last_dM": (I32, [P, C.POINTER(D)]),
     "lbm_profile_steps": (I32, [P, I64, P]),
     "lbm_launches_per_step": (I32, [P, C.POINTER(I64)]),
+    "lbm_mass_noalloc": (I32, [P, P, I64, I32, P, P]),
     "lbm_destroy": (None, [P]),
     "lbm_status_str": (C.c_char_p, [I32]),
     "lbm_last_error": (C.c_char_p, [P]),

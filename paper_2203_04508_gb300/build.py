@@ -24,6 +24,7 @@ UNITS = [
     ("lbm_step.cu", []),
     ("lbm_geometry.cu", ["-fmad=false"]),
     ("lbm_eos.cpp", ["-x", "cu"]),
+    ("lbm_noalloc.cu", []),
 ]
 
 
