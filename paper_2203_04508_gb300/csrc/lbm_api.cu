@@ -172,17 +172,20 @@ void fill_lattice(lbm_ctx* c, Lattice<real>& L) {
   L.k2 = (real)(g.k * g.k);
   L.kappa = (real)g.kappa;
   L.mu_sat = (real)c->eos.mu_sat;
-  {
-    const real rg = (real)c->eos.rho_g, rl = (real)c->eos.rho_l;
-    L.rho_g = rg;
-    L.rho_l = rl;
-    L.rho_split = (real)std::sqrt(c->eos.rho_g * c->eos.rho_l);
-    auto Pof = [&](double r) { double e = g.b * r / 4.0; return 8.0 * e - 9.0 * e * e + 3.0 * e * e * e; };
-    L.P_g = (real)Pof((double)rg);
-    L.P_l = (real)Pof((double)rl);
-    const double aal = g.a * c->eos.alpha;
-    L.c_g = (real)(eos_mu(g.eos, g.a, g.b, RT, aal, (double)rg) - c->eos.mu_sat);
-    L.c_l = (real)(eos_mu(g.eos, g.a, g.b, RT, aal, (double)rl) - c->eos.mu_sat);
+  L.rho_split = (real)std::sqrt(c->eos.rho_g * c->eos.rho_l);
+  for (int k = 0; k < 2; ++k) {
+    // reference densities of the CS chemical potential, rounded to the storage type first so
+    // that every constant below belongs to the value the kernel actually subtracts
+    const real r0 = (real)(k == 0 ? c->eos.rho_g : c->eos.rho_l);
+    const double r0d = (double)r0;
+    const double eta0 = g.b * r0d / 4.0, a0 = 1.0 - eta0;
+    const double P0 = 8.0 * eta0 - 9.0 * eta0 * eta0 + 3.0 * eta0 * eta0 * eta0;
+    L.cs_r0[k] = r0;
+    L.cs_inv_r0[k] = (real)(1.0 / r0d);
+    L.cs_eta0[k] = (real)eta0;
+    L.cs_a0[k] = (real)a0;
+    L.cs_p0a3[k] = (real)(P0 / (a0 * a0 * a0));
+    L.cs_c0[k] = (real)(eos_mu(g.eos, g.a, g.b, RT, g.a * c->eos.alpha, r0d) - c->eos.mu_sat);
   }
   L.rho_ref = (real)c->rho_ref;
   L.coll = g.coll;
@@ -223,7 +226,7 @@ void refresh(lbm_ctx* c) {
 lbm_status validate(const lbm_config* g, char* msg) {
   auto bad = [&](const char* m) { std::snprintf(msg, 256, "%s", m); return LBM_EINVAL; };
   if (g->nx < 5 || g->ny < 5) return bad("nx and ny must be at least 5");
-  if ((long long)g->nx * g->ny > (1LL << 30)) return bad("lattice larger than 2^30 nodes");
+  if ((long long)g->nx * g->ny > 200000000LL) return bad("lattice larger than 2e8 nodes (32-bit plane offsets)");
   if (g->walls != 0 && g->walls != 1) return bad("walls must be 0 or 1");
   if (g->walls) {
     if (!(g->y_bottom >= 1.0 && g->y_bottom < 2.0)) return bad("y_bottom must lie in [1, 2)");

@@ -28,7 +28,7 @@ __host__ __device__ constexpr double wgt(int i) { return i == 0 ? 4.0 / 9.0 : (i
 template <typename real>
 struct Lattice {
   int nx, ny, pitch, walls;
-  long long plane;              // pitch * ny
+  int plane;                    // pitch * ny (9 * plane < 2^31)
   real* f[2];                   // the two population lattices (9 planes each)
   real* rho;                    // density plane (fluid and the two solid layers)
   real* mu;                     // chemical potential minus k^2 mu_sat (constant at solids)
@@ -36,8 +36,10 @@ struct Lattice {
   // equation of state, Eq. 12: mu~ = k^2 (psi'(rho) - mu_sat) - kappa lap(rho)
   int eos;
   real RT, a, b, aalpha, k2, kappa, mu_sat;
-  real rho_g, rho_l, rho_split;  // coexistence densities (storage-rounded) and sqrt(rho_g rho_l)
-  real P_g, P_l, c_g, c_l;        // CS: P(eta0) and psi'(rho0) - mu_sat at the rounded rho0
+  real rho_split;                // sqrt(rho_g rho_l): below it mu is evaluated against rho_g
+  // CS, per reference density rho0 in {rho_g, rho_l} (index 0 gas, 1 liquid), storage-rounded:
+  // rho0, 1/rho0, eta0 = b rho0/4, a0 = 1 - eta0, P(eta0)/a0^3, psi'(rho0) - mu_sat (FP64 on host)
+  real cs_r0[2], cs_inv_r0[2], cs_eta0[2], cs_a0[2], cs_p0a3[2], cs_c0[2];
   real rho_ref;
   // collision, Eqs. 3-4
   int coll;
@@ -79,8 +81,8 @@ __device__ __forceinline__ int wrap_y(const Lattice<real>& L, int y) {
   return y < 0 ? y + L.ny : (y >= L.ny ? y - L.ny : y);
 }
 template <typename real>
-__device__ __forceinline__ long long node_at(const Lattice<real>& L, int x, int y) {
-  return (long long)wrap_y(L, y) * L.pitch + wrap_x(L, x);
+__device__ __forceinline__ int node_at(const Lattice<real>& L, int x, int y) {
+  return wrap_y(L, y) * L.pitch + wrap_x(L, x);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -104,22 +106,21 @@ __device__ __forceinline__ double dev_log1p(double x) { return log1p(x); }
 //   h = eta - eta0, a = 1 - eta0, b = 1 - eta,
 // so that every term vanishes with rho - rho0 (which is exact near rho0) instead of cancelling
 // between terms of size RT ln rho.  c0 = psi'(rho0) - mu_sat of the storage-rounded rho0 is
-// computed in FP64 on the host, so both branches meet the same function.
+// computed in FP64 on the host, so both branches meet the same function.  One division.
 template <typename real>
 __device__ __forceinline__ real psi_prime_shifted(const Lattice<real>& L, real r) {
   if (L.eos == EOS_CS) {
-    const bool liquid = r > L.rho_split;
-    const real r0 = liquid ? L.rho_l : L.rho_g;
-    const real P0 = liquid ? L.P_l : L.P_g;
-    const real c0 = liquid ? L.c_l : L.c_g;
-    const real dr = r - r0;
-    const real eta = L.b * r * real(0.25), eta0 = L.b * r0 * real(0.25);
+    const int k = r > L.rho_split ? 1 : 0;
+    const real dr = r - L.cs_r0[k];
+    const real eta0 = L.cs_eta0[k], a = L.cs_a0[k];
+    const real eta = L.b * r * real(0.25);
     const real h = L.b * dr * real(0.25);
-    const real a = real(1) - eta0, bb = real(1) - eta;
-    const real b3 = bb * bb * bb, a3 = a * a * a;
-    const real q1 = (real(8) - real(9) * (eta + eta0) + real(3) * (eta * eta + eta * eta0 + eta0 * eta0)) / b3;
-    const real q2 = P0 * (a * a + a * bb + bb * bb) / (a3 * b3);
-    return L.RT * dev_log1p(dr / r0) + L.RT * h * (q1 + q2) - real(2) * L.a * dr + c0;
+    const real bb = real(1) - eta;
+    const real ib = real(1) / bb;
+    const real ib3 = ib * ib * ib;
+    const real q1 = real(8) - real(9) * (eta + eta0) + real(3) * (eta * eta + eta * eta0 + eta0 * eta0);
+    const real q2 = L.cs_p0a3[k] * (a * a + a * bb + bb * bb);
+    return L.RT * dev_log1p(dr * L.cs_inv_r0[k]) + L.RT * h * ((q1 + q2) * ib3) - real(2) * L.a * dr + L.cs_c0[k];
   }
   // Peng-Robinson, Eq. 11 without the gradient term
   const real s2 = real(1.4142135623730951);
@@ -132,20 +133,20 @@ __device__ __forceinline__ real psi_prime_shifted(const Lattice<real>& L, real r
 
 // Fourth-order central first derivatives and Laplacian along the lattice axes.
 struct Stencil {
-  long long xm2, xm1, xp1, xp2, ym2, ym1, yp1, yp2;
+  int xm2, xm1, xp1, xp2, ym2, ym1, yp1, yp2;
 };
 template <typename real>
 __device__ __forceinline__ Stencil stencil_at(const Lattice<real>& L, int x, int y) {
   Stencil s;
-  long long row = (long long)y * L.pitch;
+  const int row = y * L.pitch;
   s.xm2 = row + wrap_x(L, x - 2);
   s.xm1 = row + wrap_x(L, x - 1);
   s.xp1 = row + wrap_x(L, x + 1);
   s.xp2 = row + wrap_x(L, x + 2);
-  s.ym2 = (long long)wrap_y(L, y - 2) * L.pitch + x;
-  s.ym1 = (long long)wrap_y(L, y - 1) * L.pitch + x;
-  s.yp1 = (long long)wrap_y(L, y + 1) * L.pitch + x;
-  s.yp2 = (long long)wrap_y(L, y + 2) * L.pitch + x;
+  s.ym2 = wrap_y(L, y - 2) * L.pitch + x;
+  s.ym1 = wrap_y(L, y - 1) * L.pitch + x;
+  s.yp1 = wrap_y(L, y + 1) * L.pitch + x;
+  s.yp2 = wrap_y(L, y + 2) * L.pitch + x;
   return s;
 }
 
@@ -161,7 +162,7 @@ __device__ __forceinline__ void grad4(const real* __restrict__ p, const Stencil&
 // differences are exact (Sterbenz), so FP32 keeps the Laplacian's relative accuracy there
 // instead of losing it to cancellation between terms of size 30 rho.
 template <typename real>
-__device__ __forceinline__ real lap4(const real* __restrict__ p, long long n, const Stencil& s) {
+__device__ __forceinline__ real lap4(const real* __restrict__ p, int n, const Stencil& s) {
   const real c = p[n];
   real lx = real(16) * ((p[s.xp1] - c) + (p[s.xm1] - c)) - ((p[s.xp2] - c) + (p[s.xm2] - c));
   real ly = real(16) * ((p[s.yp1] - c) + (p[s.ym1] - c)) - ((p[s.yp2] - c) + (p[s.ym2] - c));
@@ -245,22 +246,28 @@ __device__ __forceinline__ real density_of(const Lattice<real>& L, const real (&
 // FP32 accuracy: the large part of every population, w_i delta rho, is formed as
 // {16, 4, 1} x (delta rho / 36) -- exact multiples of one correctly rounded quotient, so the
 // weights sum to one exactly and no mass bias arises -- and every other (small) term is
-// accumulated before the single final rounding of each post-collision population.
+// accumulated before the single final rounding of each post-collision population.  The
+// exact-difference forcing enters through the equilibrium at u' = u + F/rho.
 template <typename real>
 __device__ __forceinline__ void collide_node(const Lattice<real>& L, real (&f)[9], real r, real drho,
                                              real jx, real jy, real Fx, real Fy) {
   const real inv_r = real(1) / r;
   const real ux = jx * inv_r, uy = jy * inv_r;
-  const real dux = Fx * inv_r, duy = Fy * inv_r;
+  // u' = u + F/rho: the exact-difference term of Eq. 13 is f^eq(rho, u') - f^eq(rho, u), so the
+  // equilibrium part of the post-collision populations is f^eq(rho, u') itself
+  const real vx = ux + Fx * inv_r, vy = uy + Fy * inv_r;
   const real usq = real(1.5) * (ux * ux + uy * uy);
+  const real vsq = real(1.5) * (vx * vx + vy * vy);
   const real q36 = drho / real(36);
   real big[9], veq[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     big[i] = real(i == 0 ? 16 : (i <= 4 ? 4 : 1)) * q36;
-    real eu = real(ex(i)) * ux + real(ey(i)) * uy;
-    veq[i] = real(wgt(i)) * r * (real(3) * eu + real(4.5) * eu * eu - usq);
-    f[i] = (f[i] - big[i]) - veq[i];   // g_i, the non-equilibrium part
+    const real wr = real(wgt(i)) * r;
+    const real eu = real(ex(i)) * ux + real(ey(i)) * uy;
+    const real ev = real(ex(i)) * vx + real(ey(i)) * vy;
+    f[i] = (f[i] - big[i]) - wr * (real(3) * eu + real(4.5) * eu * eu - usq);   // g_i
+    veq[i] = wr * (real(3) * ev + real(4.5) * ev * ev - vsq);
   }
   if (L.coll == COLL_MRT) {
     const real (&g)[9] = f;
@@ -296,8 +303,7 @@ __device__ __forceinline__ void collide_node(const Lattice<real>& L, real (&f)[9
     for (int i = 0; i < 9; ++i) f[i] *= keep;
   }
 #pragma unroll
-  for (int i = 0; i < 9; ++i)
-    f[i] = big[i] + ((veq[i] + f[i]) + edm_term<real>(i, r, ux, uy, dux, duy));
+  for (int i = 0; i < 9; ++i) f[i] = big[i] + (veq[i] + f[i]);
 }
 
 // Eqs. 16-17 (present scheme) and their variants for one link.

@@ -22,10 +22,21 @@ namespace lbmgb {
 
 constexpr int NODE_BLOCK = 256;
 
+// node kernels run on a 2D grid of TILE_X x TILE_Y blocks: x along the row, y across rows
+constexpr int TILE_X = 128, TILE_Y = 2;
+
+template <typename real>
+__device__ __forceinline__ bool node_of_thread(const Lattice<real>& L, int& x, int& y, int& n) {
+  x = blockIdx.x * TILE_X + threadIdx.x;
+  y = blockIdx.y * TILE_Y + threadIdx.y;
+  n = y * L.pitch + x;
+  return x < L.nx && y < L.ny;
+}
+
 template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_rho(Lattice<real> L, int cur) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= L.plane) return;
+  int x, y, n;
+  if (!node_of_thread(L, x, y, n)) return;
   if (L.kind[n] != KIND_FLUID) return;
   const real* __restrict__ f = L.f[cur];
   real fl[9];
@@ -59,10 +70,9 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_solid(Lattice<real> L, int layer
 // constant wall value.
 template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_mu(Lattice<real> L) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= L.plane) return;
+  int x, y, n;
+  if (!node_of_thread(L, x, y, n)) return;
   if (L.kind[n] != KIND_FLUID) return;
-  const int x = (int)(n % L.pitch), y = (int)(n / L.pitch);
   Stencil s = stencil_at(L, x, y);
   const real r = L.rho[n];
   L.mu[n] = L.k2 * psi_prime_shifted(L, r) - L.kappa * lap4(L.rho, n, s);
@@ -70,10 +80,9 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_mu(Lattice<real> L) {
 
 template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_collide(Lattice<real> L, int cur) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= L.plane) return;
+  int x, y, n;
+  if (!node_of_thread(L, x, y, n)) return;
   if (L.kind[n] != KIND_FLUID) return;
-  const int x = (int)(n % L.pitch), y = (int)(n / L.pitch);
   const real* __restrict__ fin = L.f[cur];
   real* __restrict__ fout = L.f[cur ^ 1];
   real fl[9];
@@ -87,9 +96,9 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide(Lattice<real> L, int cur
   collide_node(L, fl, r, drho, jx, jy, Fx, Fy);
   // push streaming, Eq. 5
   const int xm = wrap_x(L, x - 1), xp = wrap_x(L, x + 1);
-  const long long rowc = (long long)y * L.pitch;
-  const long long rowm = (long long)wrap_y(L, y - 1) * L.pitch;
-  const long long rowp = (long long)wrap_y(L, y + 1) * L.pitch;
+  const int rowc = y * L.pitch;
+  const int rowm = wrap_y(L, y - 1) * L.pitch;
+  const int rowp = wrap_y(L, y + 1) * L.pitch;
   fout[0 * L.plane + n] = fl[0];
   fout[1 * L.plane + rowc + xp] = fl[1];
   fout[2 * L.plane + rowp + x] = fl[2];
@@ -128,8 +137,8 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_bc(Lattice<real> L, int cur) {
     for (int l = l0; l < l1; ++l) {
       const int i = L.ldir[l];
       const int ib = opp(i);
-      const long long xs = node_at(L, x + ex(i), y + ey(i));
-      const long long x2 = node_at(L, x - ex(i), y - ey(i));
+      const int xs = node_at(L, x + ex(i), y + ey(i));
+      const int x2 = node_at(L, x - ex(i), y - ey(i));
       const real a = fout[i * L.plane + xs];
       const real b2 = fout[i * L.plane + n];
       const real c = fout[ib * L.plane + x2];
@@ -301,15 +310,20 @@ __global__ void k_init(Lattice<real> L, const double* __restrict__ drops, int n_
 // host launchers
 // ---------------------------------------------------------------------------------------
 static inline unsigned grid_for(long long n, int block) { return (unsigned)((n + block - 1) / block); }
+template <typename real>
+static inline dim3 node_grid(const Lattice<real>& L) {
+  return dim3((unsigned)((L.nx + TILE_X - 1) / TILE_X), (unsigned)((L.ny + TILE_Y - 1) / TILE_Y));
+}
+static inline dim3 node_block() { return dim3(TILE_X, TILE_Y); }
 
 template <typename real>
 cudaError_t launch_step(const Lattice<real>& L, int cur, cudaStream_t s) {
   const unsigned gn = grid_for(L.plane, NODE_BLOCK);
-  k_rho<real><<<gn, NODE_BLOCK, 0, s>>>(L, cur);
+  k_rho<real><<<node_grid(L), node_block(), 0, s>>>(L, cur);
   if (L.n_s1 > 0) k_solid<real><<<grid_for(L.n_s1, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 1);
   if (L.n_s2 > 0) k_solid<real><<<grid_for(L.n_s2, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 2);
-  if (L.eos != EOS_NONE) k_mu<real><<<gn, NODE_BLOCK, 0, s>>>(L);
-  k_collide<real><<<gn, NODE_BLOCK, 0, s>>>(L, cur);
+  if (L.eos != EOS_NONE) k_mu<real><<<node_grid(L), node_block(), 0, s>>>(L);
+  k_collide<real><<<node_grid(L), node_block(), 0, s>>>(L, cur);
   unsigned gb = grid_for(L.n_bnodes, NODE_BLOCK);
   k_bc<real><<<gb > 0 ? gb : 1, NODE_BLOCK, 0, s>>>(L, cur);
   return cudaGetLastError();
@@ -321,13 +335,13 @@ template <typename real>
 cudaError_t launch_phase(const Lattice<real>& L, int cur, int phase, cudaStream_t s) {
   const unsigned gn = grid_for(L.plane, NODE_BLOCK);
   switch (phase) {
-    case 0: k_rho<real><<<gn, NODE_BLOCK, 0, s>>>(L, cur); break;
+    case 0: k_rho<real><<<node_grid(L), node_block(), 0, s>>>(L, cur); break;
     case 1:
       if (L.n_s1 > 0) k_solid<real><<<grid_for(L.n_s1, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 1);
       if (L.n_s2 > 0) k_solid<real><<<grid_for(L.n_s2, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 2);
       break;
-    case 2: if (L.eos != EOS_NONE) k_mu<real><<<gn, NODE_BLOCK, 0, s>>>(L); break;
-    case 3: k_collide<real><<<gn, NODE_BLOCK, 0, s>>>(L, cur); break;
+    case 2: if (L.eos != EOS_NONE) k_mu<real><<<node_grid(L), node_block(), 0, s>>>(L); break;
+    case 3: k_collide<real><<<node_grid(L), node_block(), 0, s>>>(L, cur); break;
     default: {
       unsigned gb = grid_for(L.n_bnodes, NODE_BLOCK);
       k_bc<real><<<gb > 0 ? gb : 1, NODE_BLOCK, 0, s>>>(L, cur);
@@ -345,10 +359,10 @@ int launches_per_step(const Lattice<real>& L) {
 template <typename real>
 cudaError_t launch_macro(const Lattice<real>& L, int cur, cudaStream_t s) {
   const unsigned gn = grid_for(L.plane, NODE_BLOCK);
-  k_rho<real><<<gn, NODE_BLOCK, 0, s>>>(L, cur);
+  k_rho<real><<<node_grid(L), node_block(), 0, s>>>(L, cur);
   if (L.n_s1 > 0) k_solid<real><<<grid_for(L.n_s1, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 1);
   if (L.n_s2 > 0) k_solid<real><<<grid_for(L.n_s2, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 2);
-  if (L.eos != EOS_NONE) k_mu<real><<<gn, NODE_BLOCK, 0, s>>>(L);
+  if (L.eos != EOS_NONE) k_mu<real><<<node_grid(L), node_block(), 0, s>>>(L);
   return cudaGetLastError();
 }
 
