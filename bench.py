@@ -32,9 +32,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS & % HBM roofline, FP32 vs FP64 oracle; batched and adjoint cost ratio"
 UNIT = "MLUPS"
-# algorithmic bytes of the fused force + collide + stream kernel per fluid node: read 9 and
-# write 9 FP32 populations (72 B) plus the density and chemical-potential planes (8 B)
+# algorithmic bytes of the fused force + collision + streaming kernel: per fluid node read 9
+# and write 9 FP32 populations (72 B) and read rho and mu (8 B); per lattice node its class
+# byte (1 B)
 COLLIDE_BYTES_PER_FLUID_NODE = 80
+COLLIDE_BYTES_PER_NODE = 1
 STEP_BYTES_PER_NODE = 72
 FALLBACK_HBM_GBS = 6800.0
 
@@ -253,7 +255,7 @@ def main():
     phase_ms = lat.profile_steps(n_prof) / n_prof
     collide_ms = float(phase_ms[3])
     peak, peak_src = measured_peak()
-    coll_bytes = COLLIDE_BYTES_PER_FLUID_NODE * counts["fluid"]
+    coll_bytes = COLLIDE_BYTES_PER_FLUID_NODE * counts["fluid"] + COLLIDE_BYTES_PER_NODE * sc.nodes
     achieved = coll_bytes / (collide_ms / 1e3) / 1e9
     traffic = recorded_traffic(args.workload)
     step_eff = STEP_BYTES_PER_NODE * sc.nodes / (ms_step / 1e3) / 1e9

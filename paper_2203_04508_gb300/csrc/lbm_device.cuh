@@ -197,29 +197,13 @@ __device__ __forceinline__ real edm_term(int i, real r, real ux, real uy, real d
   return real(wgt(i)) * r * (real(3) * edu + real(4.5) * edu * e2u - real(1.5) * du2u);
 }
 
-// Error-free sum of two numbers (Knuth's TwoSum): a + b = s + err exactly.
-template <typename real>
-__device__ __forceinline__ real two_sum(real a, real b, real& err) {
-  const real s = a + b;
-  const real bb = s - a;
-  err = (a - (s - bb)) + (b - bb);
-  return s;
-}
-
 // Moments of a node's offset populations: delta rho = sum_i (f_i - w_i rho_ref) and
-// j = sum_i f_i e_i.  delta rho is summed with compensation (TwoSum), so it is the correctly
-// rounded sum of the stored populations; j is summed as differences of opposite populations,
-// which are exact near equilibrium (Sterbenz), so the momentum keeps its relative accuracy
+// j = sum_i f_i e_i.  j is summed as differences of opposite populations, which are exact in
+// floating point near equilibrium (Sterbenz), so the momentum keeps its relative accuracy
 // although it is a small difference of populations of size ~rho/9.
 template <typename real>
 __device__ __forceinline__ real density_sum(const real (&f)[9]) {
-  real s = f[0], c = real(0), e;
-#pragma unroll
-  for (int i = 1; i < 9; ++i) {
-    s = two_sum(s, f[i], e);
-    c += e;
-  }
-  return s + c;
+  return f[0] + (((f[1] + f[3]) + (f[2] + f[4])) + ((f[5] + f[7]) + (f[6] + f[8])));
 }
 
 template <typename real>
@@ -229,81 +213,102 @@ __device__ __forceinline__ void moments(const real (&f)[9], real& drho, real& jx
   jy = (f[2] - f[4]) + ((f[5] - f[7]) + (f[6] - f[8]));
 }
 
-// Density as the rho pass stores it (the same sum as moments()).
+// Density as the read-out pass and the sweep store it (the same sum, in the same order).
 template <typename real>
 __device__ __forceinline__ real density_of(const Lattice<real>& L, const real (&f)[9]) {
   return L.rho_ref + density_sum(f);
 }
 
-// Collision (Eq. 4) of offset populations with the exact-difference term (Eq. 13) added.
-// Written on the non-equilibrium part g = f - f^eq (Eq. 14 equilibrium, offset by w_i rho_ref):
-//   MRT: f~ = f - M^-1 S (m - m_eq) = f^eq + M^-1 (I - S) M g,
-// which is the same map because m_eq = M f^eq (the moment equilibria under Eq. 1, with
-// q_y^eq = -j_y, are the moments of Eq. 14).  The conserved moments of g vanish, the other six
-// are scaled by 1 - s_k (Eq. 3 rates) and mapped back with M^-1 = M^T diag(1/9, 1/36, 1/36,
-// 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).  BGK: f~ = f^eq + (1 - 1/tau) g.
-//
-// FP32 accuracy: the large part of every population, w_i delta rho, is formed as
-// {16, 4, 1} x (delta rho / 36) -- exact multiples of one correctly rounded quotient, so the
-// weights sum to one exactly and no mass bias arises -- and every other (small) term is
-// accumulated before the single final rounding of each post-collision population.  The
-// exact-difference forcing enters through the equilibrium at u' = u + F/rho.
+// delta rho / 36 to within an ulp: the product with the rounded reciprocal, corrected once
+// with its FMA residual
+__device__ __forceinline__ float div36(float d) {
+  const float c = 1.0f / 36.0f;
+  const float q = d * c;
+  return fmaf(fmaf(-36.0f, q, d), c, q);
+}
+__device__ __forceinline__ double div36(double d) { return d / 36.0; }
+
+// Collision (Eq. 4) of offset populations with the exact-difference term (Eq. 13).
+//   MRT: f~ = f - M^-1 S (m - m_eq) + F_i,  M of Eq. 2, S of Eq. 3, m_eq listed under Eq. 1
+//        (q_y^eq = -j_y), all offset by the moments of w_i rho_ref (= m_eq(rho_ref, 0));
+//   BGK: f~ = f - (f - f^eq)/tau + F_i.
+// The exact-difference term is f^eq(rho, u') - f^eq(rho, u) with u' = u + F/rho, so the
+// post-collision populations are f^eq(rho, u') plus the relaxed non-equilibrium part:
+//   f~_i = f^eq_i(rho, u') + [M^-1 (I - S) (m - m_eq)]_i,
+// M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4); the conserved moments
+// drop out.  FP32: the large part of f^eq, w_i delta rho, is formed as {16, 4, 1} x
+// (delta rho / 36) -- exact multiples of one quotient, so the weights sum to one exactly and
+// no mass bias arises -- and the small terms are added before the final rounding.
 template <typename real>
 __device__ __forceinline__ void collide_node(const Lattice<real>& L, real (&f)[9], real r, real drho,
                                              real jx, real jy, real Fx, real Fy) {
   const real inv_r = real(1) / r;
   const real ux = jx * inv_r, uy = jy * inv_r;
-  // u' = u + F/rho: the exact-difference term of Eq. 13 is f^eq(rho, u') - f^eq(rho, u), so the
-  // equilibrium part of the post-collision populations is f^eq(rho, u') itself
   const real vx = ux + Fx * inv_r, vy = uy + Fy * inv_r;
-  const real usq = real(1.5) * (ux * ux + uy * uy);
-  const real vsq = real(1.5) * (vx * vx + vy * vy);
-  const real q36 = drho / real(36);
-  real big[9], veq[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    big[i] = real(i == 0 ? 16 : (i <= 4 ? 4 : 1)) * q36;
-    const real wr = real(wgt(i)) * r;
-    const real eu = real(ex(i)) * ux + real(ey(i)) * uy;
-    const real ev = real(ex(i)) * vx + real(ey(i)) * vy;
-    f[i] = (f[i] - big[i]) - wr * (real(3) * eu + real(4.5) * eu * eu - usq);   // g_i
-    veq[i] = wr * (real(3) * ev + real(4.5) * ev * ev - vsq);
-  }
+  const real q36 = div36(drho);
+  real neq[9];
   if (L.coll == COLL_MRT) {
-    const real (&g)[9] = f;
-    real e = real(-4) * g[0] - ((g[1] + g[2]) + (g[3] + g[4])) + real(2) * ((g[5] + g[6]) + (g[7] + g[8]));
-    real eps = real(4) * g[0] - real(2) * ((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8]));
-    real qx = real(-2) * (g[1] - g[3]) + ((g[5] - g[7]) + (g[8] - g[6]));
-    real qy = real(-2) * (g[2] - g[4]) + ((g[5] - g[7]) + (g[6] - g[8]));
-    real pxx = (g[1] + g[3]) - (g[2] + g[4]);
-    real pxy = (g[5] + g[7]) - (g[6] + g[8]);
-    e *= real(1) - L.s_e;
-    eps *= real(1) - L.s_eps;
-    qx *= real(1) - L.s_q;
-    qy *= real(1) - L.s_q;
-    pxx *= real(1) - L.s_nu;
-    pxy *= real(1) - L.s_nu;
-    const real e36 = e * real(1.0 / 36.0), e18 = e * real(1.0 / 18.0), e9 = e * real(1.0 / 9.0);
-    const real s36 = eps * real(1.0 / 36.0), s18 = eps * real(1.0 / 18.0), s9 = eps * real(1.0 / 9.0);
+    const real s13 = f[1] + f[3], s24 = f[2] + f[4], s57 = f[5] + f[7], s68 = f[6] + f[8];
+    const real s1234 = s13 + s24, s5678 = s57 + s68;
+    const real d13 = f[1] - f[3], d24 = f[2] - f[4];
+    const real j2r = (jx * jx + jy * jy) * inv_r;
+    // non-equilibrium moments, scaled by 1 - s_k
+    const real e = ((real(-4) * f[0] - s1234 + real(2) * s5678) + (real(2) * drho - real(3) * j2r)) * (real(1) - L.s_e);
+    const real eps = ((real(4) * f[0] - real(2) * s1234 + s5678) - (drho - real(3) * j2r)) * (real(1) - L.s_eps);
+    const real qx = ((jx - real(3) * d13) + jx) * (real(1) - L.s_q);
+    const real qy = ((jy - real(3) * d24) + jy) * (real(1) - L.s_q);
+    const real pxx = ((s13 - s24) - (jx * jx - jy * jy) * inv_r) * (real(1) - L.s_nu);
+    const real pxy = ((s57 - s68) - jx * jy * inv_r) * (real(1) - L.s_nu);
+    const real e36 = e * real(1.0 / 36.0), e18 = e * real(1.0 / 18.0);
+    const real s36 = eps * real(1.0 / 36.0), s18 = eps * real(1.0 / 18.0);
     const real qx6 = qx * real(1.0 / 6.0), qy6 = qy * real(1.0 / 6.0);
     const real qx12 = qx * real(1.0 / 12.0), qy12 = qy * real(1.0 / 12.0);
     const real pxx4 = pxx * real(0.25), pxy4 = pxy * real(0.25);
-    f[0] = s9 - e9;
-    f[1] = -e36 - s18 - qx6 + pxx4;
-    f[2] = -e36 - s18 - qy6 - pxx4;
-    f[3] = -e36 - s18 + qx6 + pxx4;
-    f[4] = -e36 - s18 + qy6 - pxx4;
-    f[5] = e18 + s36 + qx12 + qy12 + pxy4;
-    f[6] = e18 + s36 - qx12 + qy12 - pxy4;
-    f[7] = e18 + s36 - qx12 - qy12 + pxy4;
-    f[8] = e18 + s36 + qx12 - qy12 - pxy4;
+    const real a14 = -e36 - s18, a58 = e18 + s36;
+    neq[0] = real(4) * (s36 - e36);
+    neq[1] = a14 - qx6 + pxx4;
+    neq[2] = a14 - qy6 - pxx4;
+    neq[3] = a14 + qx6 + pxx4;
+    neq[4] = a14 + qy6 - pxx4;
+    neq[5] = a58 + qx12 + qy12 + pxy4;
+    neq[6] = a58 - qx12 + qy12 - pxy4;
+    neq[7] = a58 - qx12 - qy12 + pxy4;
+    neq[8] = a58 + qx12 - qy12 - pxy4;
   } else {
     const real keep = real(1) - L.omega;
+    const real usq = real(1.5) * (ux * ux + uy * uy);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] *= keep;
+    for (int i = 0; i < 9; ++i) {
+      const real eu = real(ex(i)) * ux + real(ey(i)) * uy;
+      const real big = real(i == 0 ? 16 : (i <= 4 ? 4 : 1)) * q36;
+      neq[i] = keep * ((f[i] - big) - real(wgt(i)) * r * (real(3) * eu + real(4.5) * eu * eu - usq));
+    }
   }
-#pragma unroll
-  for (int i = 0; i < 9; ++i) f[i] = big[i] + (veq[i] + f[i]);
+  // f~_i = w_i delta rho + w_i rho (3 e.u' + 4.5 (e.u')^2 - 1.5 u'^2) + neq_i, opposite
+  // directions sharing the even part
+  const real vsq = real(1.5) * (vx * vx + vy * vy);
+  const real r9 = r * real(1.0 / 9.0), r36 = r * real(1.0 / 36.0);
+  f[0] = real(16) * q36 + (real(4) * r9 * (-vsq) + neq[0]);
+  {
+    const real ev = vx, even = real(4.5) * ev * ev - vsq, odd = real(3) * ev;
+    f[1] = real(4) * q36 + (r9 * (even + odd) + neq[1]);
+    f[3] = real(4) * q36 + (r9 * (even - odd) + neq[3]);
+  }
+  {
+    const real ev = vy, even = real(4.5) * ev * ev - vsq, odd = real(3) * ev;
+    f[2] = real(4) * q36 + (r9 * (even + odd) + neq[2]);
+    f[4] = real(4) * q36 + (r9 * (even - odd) + neq[4]);
+  }
+  {
+    const real ev = vx + vy, even = real(4.5) * ev * ev - vsq, odd = real(3) * ev;
+    f[5] = q36 + (r36 * (even + odd) + neq[5]);
+    f[7] = q36 + (r36 * (even - odd) + neq[7]);
+  }
+  {
+    const real ev = vy - vx, even = real(4.5) * ev * ev - vsq, odd = real(3) * ev;
+    f[6] = q36 + (r36 * (even + odd) + neq[6]);
+    f[8] = q36 + (r36 * (even - odd) + neq[8]);
+  }
 }
 
 // Eqs. 16-17 (present scheme) and their variants for one link.
