@@ -48,6 +48,65 @@ def workload(name):
     return S.c3_impact(), "c3 drop impact on a cylinder 2048x4096 D2Q9 MRT CS T=0.6Tc gravity FP32"
 
 
+def shard_instances(sizes, world):
+    """Greedy bin packing of independent instances (largest first) onto `world` ranks; returns
+    one index list per rank (each sorted).  No data moves between ranks: each advances its own."""
+    order = sorted(range(len(sizes)), key=lambda k: (-sizes[k], k))
+    load = [0] * world
+    out = [[] for _ in range(world)]
+    for k in order:
+        r = min(range(world), key=lambda j: (load[j], j))
+        out[r].append(k)
+        load[r] += sizes[k]
+    return [sorted(v) for v in out]
+
+
+def run_batched(G, torch, rank, world, steps):
+    """Batched workload: seed-random droplet-on-cylinder instances of 128^2..768^2, advanced
+    together by the persistent kernel (one launch for all steps), against the same instances
+    each advanced by its own lbm_step graph launches one after another."""
+    import scenarios as S
+    scs = S.c4_batch()
+    mine = shard_instances([sc.nodes for sc in scs], world)[rank]
+    scs = [scs[k] for k in mine]
+    nodes = sum(sc.nodes for sc in scs)
+    b = G.Batch([sc.physics() for sc in scs], precision=G.LBM_FP32)
+    b.init([sc.droplets() for sc in scs])
+    b.step(2)
+    b.check()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    b.step(steps)
+    e1.record(b.stream)
+    e1.synchronize()
+    b.check()
+    ms_b = e0.elapsed_time(e1)
+    info = b.info()
+    del b
+    torch.cuda.empty_cache()
+    # looping single-instance launches, same instances, same steps
+    lats = []
+    for sc in scs:
+        lat = G.Lattice(sc.physics(), precision=G.LBM_FP32)
+        lat.init_droplets(sc.droplets())
+        lat.step(2)
+        lats.append(lat)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for lat in lats:
+        lat.step(steps)
+    for lat in lats:
+        lat.synchronize()
+    ms_l = (time.perf_counter() - t0) * 1e3
+    del lats
+    torch.cuda.empty_cache()
+    return {"instances": len(scs), "nodes": nodes, "steps": steps, "ms_batched": round(ms_b, 3),
+            "mlups_batched": round(nodes * steps / ms_b / 1e3, 1), "ms_looped": round(ms_l, 3),
+            "mlups_looped": round(nodes * steps / ms_l / 1e3, 1), "speedup": round(ms_l / ms_b, 3),
+            "persistent_grid": info["grid"], "graph_captured": info["graph"],
+            "looped_timing": "host wall clock around all instances' lbm_step calls, synchronised"}
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -172,6 +231,8 @@ def main():
     ap.add_argument("--workload", default="c3", choices=["c3", "c2"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=200,
+                    help="steps of the batched-instances comparison (0: skip it)")
     ap.add_argument("--mode", default="full", choices=["full", "kernels"],
                     help="kernels: only warm-up and timed steps (for profiler captures)")
     args = ap.parse_args()
@@ -284,6 +345,20 @@ def main():
                "d2h_bytes_per_step": round(16 + d2h_fields / n_e2e, 2), "steps": n_e2e}
         del lat2
 
+    batched = None
+    if args.batch_steps > 0:
+        batched = run_batched(G, torch, rank, world, args.batch_steps)
+        if world > 1:
+            t = torch.tensor([batched["ms_batched"], batched["ms_looped"]], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            nn = torch.tensor([batched["nodes"]], device="cuda", dtype=torch.float64)
+            dist.all_reduce(nn)
+            steps_b = args.batch_steps
+            batched.update(ms_batched=float(t[0]), ms_looped=float(t[1]), nodes=int(nn.item()),
+                           mlups_batched=round(float(nn.item()) * steps_b / float(t[0]) / 1e3, 1),
+                           mlups_looped=round(float(nn.item()) * steps_b / float(t[1]) / 1e3, 1),
+                           speedup=round(float(t[1]) / float(t[0]), 3), instances=256)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, n, cores = oracle_rate(sc, max_seconds=20.0, max_steps=50)
@@ -308,6 +383,7 @@ def main():
                          "phase_ms": {k: round(float(v), 5) for k, v in
                                       zip(("rho", "solid", "mu", "collide", "bc"), phase_ms)}},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": lps * args.steps,
+            "batched": batched,
             "mass_drift": M / M0 - 1,
         }
         print(json.dumps(line), flush=True)

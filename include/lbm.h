@@ -194,6 +194,52 @@ lbm_status lbm_eos_info(lbm_ctx* ctx, double* out8);
 /* Number of kernel launches one lbm_step(ctx, 1) issues. */
 lbm_status lbm_launches_per_step(lbm_ctx* ctx, int64_t* n);
 
+/* ---- Batches: many independent lattices advanced together -------------------------------
+ * All instances share one precision; sizes, physics, geometry and initial states may differ.
+ * Each instance is an ordinary lbm_ctx inside the batch (lbm_batch_instance), so lbm_fields,
+ * lbm_mass, lbm_dM_history ... work on it; lbm_step on a single instance is not allowed while it
+ * belongs to a batch (lbm_batch_step then returns LBM_ESTATE). */
+typedef struct lbm_batch lbm_batch;
+
+/* Device workspace for n instances: their own workspaces plus the batch's work lists. */
+lbm_status lbm_batch_workspace_size(int32_t n, const lbm_config* cfgs, size_t* bytes);
+
+/* Creates the n instances (lbm_create each, on sub-ranges of the one workspace). */
+lbm_status lbm_batch_create(int32_t n, const lbm_config* cfgs, void* stream, void* workspace, size_t bytes,
+                            lbm_batch** out);
+
+/* lbm_build_links for every instance, then the flat work lists of the persistent kernel: tiles
+ * of 256 consecutive nodes and chunks of 256 solid-layer / boundary entries across all
+ * instances.  Synchronises. */
+lbm_status lbm_batch_build_links(lbm_batch* b);
+
+/* lbm_init for every instance with specs[k] (n specs).  Synchronises. */
+lbm_status lbm_batch_init(lbm_batch* b, const lbm_init_spec* specs);
+
+/* Advances every instance n steps in ONE cooperative launch of a persistent kernel (captured
+ * into a CUDA graph on first use for this n): each step runs the phases of lbm_step over all
+ * instances' work, separated by grid barriers; per-instance compensation sums go to each
+ * instance's ring as with lbm_step.  Asynchronous; lbm_batch_check reports a barrier timeout. */
+lbm_status lbm_batch_step(lbm_batch* b, int64_t n);
+
+/* Synchronises and returns LBM_ETIMEOUT if a grid-barrier wait of the last launches gave up
+ * (the kernel then left without finishing its steps). */
+lbm_status lbm_batch_check(lbm_batch* b);
+
+/* Polls before a grid-barrier wait gives up (default 2^22, about a second or more); 0 makes
+ * every wait give up at once (used to test the timeout path).  Clears the error flag. */
+lbm_status lbm_batch_set_spin_limit(lbm_batch* b, int64_t polls);
+
+/* Instance k of the batch (owned by the batch). */
+lbm_status lbm_batch_instance(lbm_batch* b, int32_t k, lbm_ctx** ctx);
+
+/* [0] blocks of the persistent grid, [1] node tiles per phase, [2] 1 if the launch is graph-
+ * captured, [3] boundary chunks. */
+lbm_status lbm_batch_info(lbm_batch* b, int64_t* out4);
+
+const char* lbm_batch_last_error(const lbm_batch* b);
+void lbm_batch_destroy(lbm_batch* b);
+
 /* Mass audit that allocates no device memory (the paper has no counterpart: this serves
  * callers that may not call cudaMalloc -- a host callback, a monitor, or a process whose device
  * memory budget belongs to another allocator -- but already hold populations on the device).

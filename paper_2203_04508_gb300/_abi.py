@@ -57,6 +57,17 @@ _SIGS = {
     "lbm_last_dM": (I32, [P, C.POINTER(D)]),
     "lbm_profile_steps": (I32, [P, I64, P]),
     "lbm_launches_per_step": (I32, [P, C.POINTER(I64)]),
+    "lbm_batch_workspace_size": (I32, [I32, P, C.POINTER(SZ)]),
+    "lbm_batch_create": (I32, [I32, P, P, P, SZ, C.POINTER(P)]),
+    "lbm_batch_build_links": (I32, [P]),
+    "lbm_batch_init": (I32, [P, P]),
+    "lbm_batch_step": (I32, [P, I64]),
+    "lbm_batch_check": (I32, [P]),
+    "lbm_batch_set_spin_limit": (I32, [P, I64]),
+    "lbm_batch_instance": (I32, [P, I32, C.POINTER(P)]),
+    "lbm_batch_info": (I32, [P, P]),
+    "lbm_batch_last_error": (C.c_char_p, [P]),
+    "lbm_batch_destroy": (None, [P]),
     "lbm_mass_noalloc": (I32, [P, P, I64, I32, P, P]),
     "lbm_destroy": (None, [P]),
     "lbm_status_str": (C.c_char_p, [I32]),

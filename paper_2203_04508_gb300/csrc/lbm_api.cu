@@ -639,3 +639,292 @@ void lbm_destroy(lbm_ctx* c) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Batched lattices
+// ---------------------------------------------------------------------------------------
+struct lbm_batch {
+  int n = 0;
+  bool fp64 = false;
+  std::vector<lbm_ctx*> ctx;
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  std::vector<size_t> inst_off, inst_bytes;
+  size_t tab_off = 0;
+  // table offsets inside the tables region
+  size_t t_lat = 0, t_tiles = 0, t_s1 = 0, t_s2 = 0, t_bc = 0, t_first = 0, t_part = 0, t_bar = 0, t_err = 0;
+  long long cap_tiles = 0, cap_s1 = 0, cap_s2 = 0, cap_bc = 0;
+  BatchDev dev{};
+  bool tables = false;
+  int grid = 0;
+  bool use_graph = true;
+  cudaGraphExec_t graph = nullptr;
+  long long graph_steps = -1;
+  int graph_cur = -1;
+  long long spin_limit = 1LL << 22;
+  int cur = 0;
+  std::string err;
+};
+
+namespace {
+
+struct BatchPlan {
+  std::vector<size_t> off, bytes;
+  size_t tab_off, total;
+  size_t t_lat, t_tiles, t_s1, t_s2, t_bc, t_first, t_part, t_bar, t_err;
+  long long cap_tiles, cap_s1, cap_s2, cap_bc;
+};
+
+lbm_status plan_batch(int n, const lbm_config* cfgs, BatchPlan* P, char* msg) {
+  if (n < 1 || !cfgs) { std::snprintf(msg, 256, "batch needs at least one configuration"); return LBM_EINVAL; }
+  P->off.resize(n);
+  P->bytes.resize(n);
+  size_t o = 0;
+  P->cap_tiles = P->cap_s1 = P->cap_s2 = P->cap_bc = 0;
+  for (int k = 0; k < n; ++k) {
+    lbm_status s = validate(&cfgs[k], msg);
+    if (s != LBM_OK) return s;
+    if (cfgs[k].precision != cfgs[0].precision) { std::snprintf(msg, 256, "all instances of a batch share one precision"); return LBM_EINVAL; }
+    Layout L = make_layout(&cfgs[k]);
+    P->off[k] = o;
+    P->bytes[k] = L.total;
+    o = align_up(o + L.total);
+    const int bb = batch_block_size();
+    P->cap_tiles += (L.plane + bb - 1) / bb;
+    P->cap_s1 += (L.cap.s1 + bb - 1) / bb;
+    P->cap_s2 += (L.cap.s2 + bb - 1) / bb;
+    P->cap_bc += (L.cap.bnodes + bb - 1) / bb;
+  }
+  P->tab_off = o;
+  size_t t = 0;
+  auto take = [&](size_t bytes) { size_t at = t; t = align_up(t + bytes); return at; };
+  const size_t lat_sz = cfgs[0].precision == LBM_FP64 ? sizeof(Lattice<double>) : sizeof(Lattice<float>);
+  P->t_lat = take((size_t)n * lat_sz);
+  P->t_tiles = take((size_t)P->cap_tiles * sizeof(int2));
+  P->t_s1 = take((size_t)(P->cap_s1 + 1) * sizeof(int2));
+  P->t_s2 = take((size_t)(P->cap_s2 + 1) * sizeof(int2));
+  P->t_bc = take((size_t)(P->cap_bc + 1) * sizeof(int2));
+  P->t_first = take((size_t)(n + 1) * sizeof(int));
+  P->t_part = take((size_t)(P->cap_bc + 1) * sizeof(double));
+  P->t_bar = take(16);
+  P->t_err = take(16);
+  P->total = P->tab_off + t;
+  return LBM_OK;
+}
+
+lbm_status bfail(lbm_batch* b, lbm_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (b) b->err = buf;
+  return s;
+}
+
+#define BCUDA(b, call)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) return bfail(b, LBM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename real>
+lbm_status batch_tables(lbm_batch* b) {
+  const int bb = batch_block_size();
+  std::vector<Lattice<real>> lats(b->n);
+  std::vector<int2> tiles, s1, s2, bc;
+  std::vector<int> first(b->n + 1, 0);
+  for (int k = 0; k < b->n; ++k) {
+    const Lattice<real>& L = b->fp64 ? *reinterpret_cast<const Lattice<real>*>(&b->ctx[k]->Ld)
+                                     : *reinterpret_cast<const Lattice<real>*>(&b->ctx[k]->Lf);
+    lats[k] = L;
+    for (long long n0 = 0; n0 < L.plane; n0 += bb) tiles.push_back(make_int2(k, (int)n0));
+    for (int j = 0; j < L.n_s1; j += bb) s1.push_back(make_int2(k, j));
+    for (int j = 0; j < L.n_s2; j += bb) s2.push_back(make_int2(k, j));
+    first[k] = (int)bc.size();
+    for (int j = 0; j < L.n_bnodes; j += bb) bc.push_back(make_int2(k, j));
+  }
+  first[b->n] = (int)bc.size();
+  if ((long long)tiles.size() > b->cap_tiles || (long long)s1.size() > b->cap_s1 + 1 ||
+      (long long)s2.size() > b->cap_s2 + 1 || (long long)bc.size() > b->cap_bc + 1)
+    return bfail(b, LBM_ENOMEM, "batch work lists exceed their capacity");
+  char* t = b->ws + b->tab_off;
+  BCUDA(b, cudaMemcpyAsync(t + b->t_lat, lats.data(), lats.size() * sizeof(Lattice<real>), cudaMemcpyHostToDevice, b->stream));
+  BCUDA(b, cudaMemcpyAsync(t + b->t_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+  if (!s1.empty()) BCUDA(b, cudaMemcpyAsync(t + b->t_s1, s1.data(), s1.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+  if (!s2.empty()) BCUDA(b, cudaMemcpyAsync(t + b->t_s2, s2.data(), s2.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+  if (!bc.empty()) BCUDA(b, cudaMemcpyAsync(t + b->t_bc, bc.data(), bc.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+  BCUDA(b, cudaMemcpyAsync(t + b->t_first, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+  BCUDA(b, cudaMemsetAsync(t + b->t_err, 0, 16, b->stream));
+  BCUDA(b, cudaStreamSynchronize(b->stream));
+  BatchDev& d = b->dev;
+  d.n_inst = b->n;
+  d.lat = t + b->t_lat;
+  d.n_node_tiles = (int)tiles.size();
+  d.node_tiles = (const int2*)(t + b->t_tiles);
+  d.n_s1_items = (int)s1.size();
+  d.n_s2_items = (int)s2.size();
+  d.n_bc_items = (int)bc.size();
+  d.s1_items = (const int2*)(t + b->t_s1);
+  d.s2_items = (const int2*)(t + b->t_s2);
+  d.bc_items = (const int2*)(t + b->t_bc);
+  d.inst_bc_first = (const int*)(t + b->t_first);
+  d.bc_partials = (double*)(t + b->t_part);
+  d.bar = (unsigned int*)(t + b->t_bar);
+  d.err = (int*)(t + b->t_err);
+  d.spin_limit = b->spin_limit;
+  b->grid = batch_grid_size(b->fp64);
+  b->tables = true;
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_workspace_size(int32_t n, const lbm_config* cfgs, size_t* bytes) {
+  if (!bytes) return LBM_EINVAL;
+  BatchPlan P;
+  char msg[256];
+  lbm_status s = plan_batch(n, cfgs, &P, msg);
+  if (s != LBM_OK) return s;
+  *bytes = P.total;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_create(int32_t n, const lbm_config* cfgs, void* stream, void* workspace, size_t bytes,
+                            lbm_batch** out) {
+  if (!out) return LBM_EINVAL;
+  lbm_batch* b = new lbm_batch();
+  *out = b;
+  BatchPlan P;
+  char msg[256] = {0};
+  lbm_status s = plan_batch(n, cfgs, &P, msg);
+  if (s != LBM_OK) { b->err = msg; return s; }
+  if (!workspace || ((uintptr_t)workspace) % ALIGN) return bfail(b, LBM_EINVAL, "workspace must be a 256-byte aligned device pointer");
+  if (bytes < P.total) return bfail(b, LBM_ENOMEM, "batch workspace of %zu bytes, %zu needed", bytes, P.total);
+  b->n = n;
+  b->fp64 = cfgs[0].precision == LBM_FP64;
+  b->stream = (cudaStream_t)stream;
+  b->ws = (char*)workspace;
+  b->inst_off = P.off;
+  b->inst_bytes = P.bytes;
+  b->tab_off = P.tab_off;
+  b->t_lat = P.t_lat; b->t_tiles = P.t_tiles; b->t_s1 = P.t_s1; b->t_s2 = P.t_s2; b->t_bc = P.t_bc;
+  b->t_first = P.t_first; b->t_part = P.t_part; b->t_bar = P.t_bar; b->t_err = P.t_err;
+  b->cap_tiles = P.cap_tiles; b->cap_s1 = P.cap_s1; b->cap_s2 = P.cap_s2; b->cap_bc = P.cap_bc;
+  b->ctx.assign(n, nullptr);
+  for (int k = 0; k < n; ++k) {
+    lbm_status st = lbm_create(&cfgs[k], stream, b->ws + P.off[k], P.bytes[k], &b->ctx[k]);
+    if (st != LBM_OK) return bfail(b, st, "instance %d: %s", k, b->ctx[k] ? b->ctx[k]->err.c_str() : "");
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_build_links(lbm_batch* b) {
+  if (!b || b->ctx.empty()) return LBM_ESTATE;
+  for (int k = 0; k < b->n; ++k) {
+    lbm_status st = lbm_build_links(b->ctx[k]);
+    if (st != LBM_OK) return bfail(b, st, "instance %d: %s", k, b->ctx[k]->err.c_str());
+  }
+  if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+  return b->fp64 ? batch_tables<double>(b) : batch_tables<float>(b);
+}
+
+lbm_status lbm_batch_init(lbm_batch* b, const lbm_init_spec* specs) {
+  if (!b || !b->tables || !specs) return LBM_ESTATE;
+  for (int k = 0; k < b->n; ++k) {
+    lbm_status st = lbm_init(b->ctx[k], &specs[k]);
+    if (st != LBM_OK) return bfail(b, st, "instance %d: %s", k, b->ctx[k]->err.c_str());
+  }
+  b->cur = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int64_t n) {
+  if (!b || !b->tables) return LBM_ESTATE;
+  for (int k = 0; k < b->n; ++k) {
+    if (!b->ctx[k]->inited) return bfail(b, LBM_ESTATE, "instance %d not initialised", k);
+    if (b->ctx[k]->cur != b->cur) return bfail(b, LBM_ESTATE, "instance %d was stepped on its own", k);
+  }
+  if (n <= 0) return n == 0 ? LBM_OK : LBM_EINVAL;
+  if (n > (1LL << 30)) return bfail(b, LBM_EINVAL, "too many steps in one launch");
+  b->dev.spin_limit = b->spin_limit;
+  if (b->use_graph && (b->graph_steps != n || b->graph_cur != b->cur || !b->graph)) {
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = launch_batch(b->dev, b->fp64, b->grid, (int)n, b->cur, b->stream);
+      cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+      e = e1 != cudaSuccess ? e1 : e2;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+      if (g) cudaGraphDestroy(g);
+    }
+    if (e != cudaSuccess) {
+      // a cooperative launch that cannot be captured is issued directly instead
+      cudaGetLastError();
+      b->use_graph = false;
+      b->graph = nullptr;
+    } else {
+      b->graph_steps = n;
+      b->graph_cur = b->cur;
+    }
+  }
+  if (b->use_graph && b->graph) BCUDA(b, cudaGraphLaunch(b->graph, b->stream));
+  else BCUDA(b, launch_batch(b->dev, b->fp64, b->grid, (int)n, b->cur, b->stream));
+  const int flip = (int)(n & 1);
+  b->cur ^= flip;
+  for (int k = 0; k < b->n; ++k) {
+    b->ctx[k]->cur ^= flip;
+    b->ctx[k]->steps += n;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_check(lbm_batch* b) {
+  if (!b || !b->tables) return LBM_ESTATE;
+  int e = 0;
+  BCUDA(b, cudaMemcpyAsync(&e, b->dev.err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  BCUDA(b, cudaStreamSynchronize(b->stream));
+  if (e) return bfail(b, LBM_ETIMEOUT, "a grid barrier wait gave up");
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_set_spin_limit(lbm_batch* b, int64_t polls) {
+  if (!b || polls < 0) return LBM_EINVAL;
+  b->spin_limit = polls;
+  if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+  b->graph_steps = -1;
+  if (b->tables) {
+    BCUDA(b, cudaMemsetAsync(b->dev.err, 0, sizeof(int), b->stream));
+    BCUDA(b, cudaStreamSynchronize(b->stream));
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_instance(lbm_batch* b, int32_t k, lbm_ctx** ctx) {
+  if (!b || !ctx || k < 0 || k >= b->n) return LBM_EINVAL;
+  *ctx = b->ctx[k];
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_info(lbm_batch* b, int64_t* out4) {
+  if (!b || !out4) return LBM_EINVAL;
+  out4[0] = b->grid;
+  out4[1] = b->dev.n_node_tiles;
+  out4[2] = b->use_graph ? 1 : 0;
+  out4[3] = b->dev.n_bc_items;
+  return LBM_OK;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+void lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (auto* c : b->ctx) lbm_destroy(c);
+  delete b;
+}
+
+}  // extern "C"

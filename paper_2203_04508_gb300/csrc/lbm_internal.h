@@ -54,6 +54,26 @@ cudaError_t geom_classify_and_count(const GeomParams& g, const GeomScratch& s, u
 cudaError_t geom_fill(const GeomParams& g, const GeomScratch& s, const GeomOut& o, double k2_mu_sat_unused,
                       cudaStream_t st);
 
+// ---- batched persistent step (lbm_batch.cu)
+struct BatchDev {
+  int n_inst;
+  const void* lat;              // device array of n_inst Lattice<real> descriptors
+  int n_node_tiles;             // (instance, first node) of 256 consecutive nodes
+  const int2* node_tiles;
+  int n_s1_items, n_s2_items, n_bc_items;   // (instance, first entry) of 256 list entries
+  const int2* s1_items;
+  const int2* s2_items;
+  const int2* bc_items;
+  const int* inst_bc_first;     // bc items of instance k: [first[k], first[k+1])
+  double* bc_partials;          // one compensation sum per bc item
+  unsigned int* bar;            // grid barrier: arrivals, completed barriers
+  int* err;                     // set when a barrier wait gave up
+  long long spin_limit;         // polls before a barrier wait gives up
+};
+int batch_block_size();
+int batch_grid_size(int fp64);
+cudaError_t launch_batch(const BatchDev& B, int fp64, int grid, int n_steps, int cur0, cudaStream_t s);
+
 // ---- EOS on the host (lbm_eos.cpp)
 struct EosSolution {
   double Tc, rho_c, T, alpha, rho_g, rho_l, mu_sat, p_sat;

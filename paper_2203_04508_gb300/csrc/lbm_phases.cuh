@@ -1,0 +1,146 @@
+// Per-node (and per-list-entry) bodies of the phases of one time step, shared by the
+// single-lattice kernels (lbm_step.cu) and the batched persistent kernel (lbm_batch.cu), so
+// that both run the same arithmetic.
+//
+// Streaming pushes every population, including those leaving a fluid node towards a solid
+// node: they land in the solid node's slot of the destination lattice, where the boundary
+// phase reads them back as f~_i(x1, t).  Likewise f~_i(x2, t) has streamed into x1 and
+// f~_ibar(x1, t) into x2, so the boundary phase needs no copy of the post-collision lattice.
+#pragma once
+#include "lbm_device.cuh"
+
+namespace lbmgb {
+
+// density of fluid node (x, y) from its 9 offset populations (Sec. 2.1)
+template <typename real>
+__device__ __forceinline__ void phase_rho(const Lattice<real>& L, int cur, int x, int y) {
+  const int n = y * L.pitch + x;
+  if (L.kind[n] != KIND_FLUID) return;
+  const real* __restrict__ f = L.f[cur];
+  real fl[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) fl[i] = f[i * L.plane + n];
+  L.rho[n] = density_of(L, fl);
+}
+
+// Eq. 15: rho(x_s) = sum_i w_i rho(x_s + e_i) s_w / sum_i w_i s_w over the neighbours of the
+// previous layer (fluid for layer 1, layer 1 for layer 2); the mask and 1/sum w_i s_w are
+// geometry and were computed once.
+template <typename real>
+__device__ __forceinline__ void phase_solid(const Lattice<real>& L, int layer, int j) {
+  const int n = layer == 1 ? L.s1node[j] : L.s2node[j];
+  const uint8_t m = layer == 1 ? L.s1mask[j] : L.s2mask[j];
+  const real winv = layer == 1 ? L.s1winv[j] : L.s2winv[j];
+  const int x = n % L.pitch, y = n / L.pitch;
+  real acc = real(0);
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    if (m & (1u << (i - 1))) acc += real(wgt(i)) * L.rho[node_at(L, x + ex(i), y + ey(i))];
+  }
+  L.rho[n] = acc * winv;
+}
+
+// Eq. 12 in mesh units, shifted by the constant k^2 mu_sat (only gradients of mu enter
+// Eq. 9): mu~ = k^2 (psi'(rho) - mu_sat) - kappa^ lap(rho).  Solid layers keep their
+// constant wall value.
+template <typename real>
+__device__ __forceinline__ void phase_mu(const Lattice<real>& L, int x, int y) {
+  const int n = y * L.pitch + x;
+  if (L.kind[n] != KIND_FLUID) return;
+  Stencil s = stencil_at(L, x, y);
+  const real r = L.rho[n];
+  L.mu[n] = L.k2 * psi_prime_shifted(L, r) - L.kappa * lap4(L.rho, n, s);
+}
+
+// force (Eq. 9) + collision (Eq. 4) with exact-difference forcing (Eq. 13) + push streaming
+// (Eq. 5) of fluid node (x, y) into the other lattice
+template <typename real>
+__device__ __forceinline__ void phase_collide(const Lattice<real>& L, int cur, int x, int y) {
+  const int n = y * L.pitch + x;
+  if (L.kind[n] != KIND_FLUID) return;
+  const real* __restrict__ fin = L.f[cur];
+  real* __restrict__ fout = L.f[cur ^ 1];
+  real fl[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) fl[i] = fin[i * L.plane + n];
+  real drho, jx, jy;
+  moments(fl, drho, jx, jy);
+  const real r = L.rho_ref + drho;
+  real Fx, Fy;
+  force_at(L, x, y, r, Fx, Fy);
+  collide_node(L, fl, r, drho, jx, jy, Fx, Fy);
+  const int xm = wrap_x(L, x - 1), xp = wrap_x(L, x + 1);
+  const int rowc = y * L.pitch;
+  const int rowm = wrap_y(L, y - 1) * L.pitch;
+  const int rowp = wrap_y(L, y + 1) * L.pitch;
+  fout[0 * L.plane + n] = fl[0];
+  fout[1 * L.plane + rowc + xp] = fl[1];
+  fout[2 * L.plane + rowp + x] = fl[2];
+  fout[3 * L.plane + rowc + xm] = fl[3];
+  fout[4 * L.plane + rowm + x] = fl[4];
+  fout[5 * L.plane + rowp + xp] = fl[5];
+  fout[6 * L.plane + rowp + xm] = fl[6];
+  fout[7 * L.plane + rowm + xm] = fl[7];
+  fout[8 * L.plane + rowm + xp] = fl[8];
+}
+
+// Boundary node b (one per thread): rebuild (rho, u, F) of step t at x1 from the
+// pre-collision lattice and the rho / mu planes (the arithmetic of the collide phase), apply
+// Eq. 16 or 17 on each of its links, and add the FP64 sum of Eq. 18 to f_0.  Returns that sum
+// (0 for the schemes without compensation).
+template <typename real>
+__device__ __forceinline__ double phase_bc(const Lattice<real>& L, int cur, int b) {
+  const int n = L.bnode[b];
+  const int x = n % L.pitch, y = n / L.pitch;
+  const real* __restrict__ fin = L.f[cur];
+  real* fout = L.f[cur ^ 1];
+  real fl[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) fl[i] = fin[i * L.plane + n];
+  real drho, jx, jy;
+  moments(fl, drho, jx, jy);
+  const real r = L.rho_ref + drho;
+  real Fx, Fy;
+  force_at(L, x, y, r, Fx, Fy);
+  const real inv_r = real(1) / r;
+  const real ux = jx * inv_r, uy = jy * inv_r, dux = Fx * inv_r, duy = Fy * inv_r;
+  double sum = 0.0;
+  const int l0 = L.bstart[b], l1 = L.bstart[b + 1];
+  for (int l = l0; l < l1; ++l) {
+    const int i = L.ldir[l];
+    const int ib = opp(i);
+    const int xs = node_at(L, x + ex(i), y + ey(i));
+    const int x2 = node_at(L, x - ex(i), y - ey(i));
+    const real a = fout[i * L.plane + xs];
+    const real b2 = fout[i * L.plane + n];
+    const real c = fout[ib * L.plane + x2];
+    // F_i(x1, t) of direction i
+    real Fi = real(0);
+    switch (i) {
+      case 1: Fi = edm_term<real>(1, r, ux, uy, dux, duy); break;
+      case 2: Fi = edm_term<real>(2, r, ux, uy, dux, duy); break;
+      case 3: Fi = edm_term<real>(3, r, ux, uy, dux, duy); break;
+      case 4: Fi = edm_term<real>(4, r, ux, uy, dux, duy); break;
+      case 5: Fi = edm_term<real>(5, r, ux, uy, dux, duy); break;
+      case 6: Fi = edm_term<real>(6, r, ux, uy, dux, duy); break;
+      case 7: Fi = edm_term<real>(7, r, ux, uy, dux, duy); break;
+      default: Fi = edm_term<real>(8, r, ux, uy, dux, duy); break;
+    }
+    const real v = link_rule<real>(L.bc, L.lq[l], L.lx2f[l], a, b2, c, Fi);
+    fout[ib * L.plane + n] = v;
+    sum += (double)a - (double)v;
+  }
+  if (L.bc == BC_PRESENT || L.bc == BC_MIBC) {
+    // Eq. 18 on f_0, accumulated in FP64.  The part of the sum that the storage precision
+    // cannot hold is carried to the node's next step instead of being dropped, so that the
+    // mass stays conserved to FP64 accuracy over any number of steps.
+    const double t = (double)fout[n] + sum + L.carry[b];
+    const real stored = (real)t;
+    L.carry[b] = t - (double)stored;
+    fout[n] = stored;
+    return sum;
+  }
+  return 0.0;
+}
+
+}  // namespace lbmgb

@@ -8,15 +8,12 @@
 //                   + push streaming (Eq. 5) into the other lattice
 //   k_bc            every cut link by Eq. 16 / Eq. 17, the per-node compensation of Eq. 18
 //                   accumulated in FP64, and the deterministic domain sum of that step
-//
-// Streaming pushes every population, including those leaving a fluid node towards a solid
-// node: they land in the solid node's slot of the destination lattice, where k_bc reads them
-// back as f~_i(x1, t).  Likewise f~_i(x2, t) has streamed into x1 and f~_ibar(x1, t) into x2,
-// so k_bc needs no copy of the post-collision lattice.
+// The per-node bodies of the phases live in lbm_phases.cuh.
 #include <cstdio>
 
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
+#include "lbm_phases.cuh"
 
 namespace lbmgb {
 
@@ -37,145 +34,43 @@ template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_rho(Lattice<real> L, int cur) {
   int x, y, n;
   if (!node_of_thread(L, x, y, n)) return;
-  if (L.kind[n] != KIND_FLUID) return;
-  const real* __restrict__ f = L.f[cur];
-  real fl[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) fl[i] = f[i * L.plane + n];
-  L.rho[n] = density_of(L, fl);
+  phase_rho(L, cur, x, y);
 }
 
-// Eq. 15: rho(x_s) = sum_i w_i rho(x_s + e_i) s_w / sum_i w_i s_w over the neighbours of the
-// previous layer (fluid for layer 1, layer 1 for layer 2); the mask and 1/sum w_i s_w are
-// geometry and were computed once.
 template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_solid(Lattice<real> L, int layer) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int cnt = layer == 1 ? L.n_s1 : L.n_s2;
-  if (j >= cnt) return;
-  const int n = layer == 1 ? L.s1node[j] : L.s2node[j];
-  const uint8_t m = layer == 1 ? L.s1mask[j] : L.s2mask[j];
-  const real winv = layer == 1 ? L.s1winv[j] : L.s2winv[j];
-  const int x = n % L.pitch, y = n / L.pitch;
-  real acc = real(0);
-#pragma unroll
-  for (int i = 1; i < 9; ++i) {
-    if (m & (1u << (i - 1))) acc += real(wgt(i)) * L.rho[node_at(L, x + ex(i), y + ey(i))];
-  }
-  L.rho[n] = acc * winv;
+  if (j >= (layer == 1 ? L.n_s1 : L.n_s2)) return;
+  phase_solid(L, layer, j);
 }
 
-// Eq. 12 in mesh units, shifted by the constant k^2 mu_sat (only gradients of mu enter
-// Eq. 9): mu~ = k^2 (psi'(rho) - mu_sat) - kappa^ lap(rho).  Solid layers keep their
-// constant wall value.
 template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_mu(Lattice<real> L) {
   int x, y, n;
   if (!node_of_thread(L, x, y, n)) return;
-  if (L.kind[n] != KIND_FLUID) return;
-  Stencil s = stencil_at(L, x, y);
-  const real r = L.rho[n];
-  L.mu[n] = L.k2 * psi_prime_shifted(L, r) - L.kappa * lap4(L.rho, n, s);
+  phase_mu(L, x, y);
 }
 
 template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_collide(Lattice<real> L, int cur) {
   int x, y, n;
   if (!node_of_thread(L, x, y, n)) return;
-  if (L.kind[n] != KIND_FLUID) return;
-  const real* __restrict__ fin = L.f[cur];
-  real* __restrict__ fout = L.f[cur ^ 1];
-  real fl[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) fl[i] = fin[i * L.plane + n];
-  real drho, jx, jy;
-  moments(fl, drho, jx, jy);
-  const real r = L.rho_ref + drho;
-  real Fx, Fy;
-  force_at(L, x, y, r, Fx, Fy);
-  collide_node(L, fl, r, drho, jx, jy, Fx, Fy);
-  // push streaming, Eq. 5
-  const int xm = wrap_x(L, x - 1), xp = wrap_x(L, x + 1);
-  const int rowc = y * L.pitch;
-  const int rowm = wrap_y(L, y - 1) * L.pitch;
-  const int rowp = wrap_y(L, y + 1) * L.pitch;
-  fout[0 * L.plane + n] = fl[0];
-  fout[1 * L.plane + rowc + xp] = fl[1];
-  fout[2 * L.plane + rowp + x] = fl[2];
-  fout[3 * L.plane + rowc + xm] = fl[3];
-  fout[4 * L.plane + rowm + x] = fl[4];
-  fout[5 * L.plane + rowp + xp] = fl[5];
-  fout[6 * L.plane + rowp + xm] = fl[6];
-  fout[7 * L.plane + rowm + xm] = fl[7];
-  fout[8 * L.plane + rowm + xp] = fl[8];
+  phase_collide(L, cur, x, y);
 }
 
-// One thread per boundary-fluid node x1: rebuild (rho, u, F) of step t at x1 from the
-// pre-collision lattice and the rho / mu planes (the same arithmetic k_collide used), then
-// apply Eq. 16 or 17 on each of its links and add the FP64 sum of Eq. 18 to f_0.
+// Boundary links, then the deterministic domain sum of this step's Eq. 18 compensation into
+// the per-step ring (two-level reduction, the last block to finish sums the partials).
 template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_bc(Lattice<real> L, int cur) {
   __shared__ double red[32];
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  double sum = 0.0;
-  if (b < L.n_bnodes) {
-    const int n = L.bnode[b];
-    const int x = n % L.pitch, y = n / L.pitch;
-    const real* __restrict__ fin = L.f[cur];
-    real* fout = L.f[cur ^ 1];
-    real fl[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) fl[i] = fin[i * L.plane + n];
-    real drho, jx, jy;
-    moments(fl, drho, jx, jy);
-    const real r = L.rho_ref + drho;
-    real Fx, Fy;
-    force_at(L, x, y, r, Fx, Fy);
-    const real inv_r = real(1) / r;
-    const real ux = jx * inv_r, uy = jy * inv_r, dux = Fx * inv_r, duy = Fy * inv_r;
-    const int l0 = L.bstart[b], l1 = L.bstart[b + 1];
-    for (int l = l0; l < l1; ++l) {
-      const int i = L.ldir[l];
-      const int ib = opp(i);
-      const int xs = node_at(L, x + ex(i), y + ey(i));
-      const int x2 = node_at(L, x - ex(i), y - ey(i));
-      const real a = fout[i * L.plane + xs];
-      const real b2 = fout[i * L.plane + n];
-      const real c = fout[ib * L.plane + x2];
-      // F_i(x1, t) of direction i
-      real Fi = real(0);
-      switch (i) {
-        case 1: Fi = edm_term<real>(1, r, ux, uy, dux, duy); break;
-        case 2: Fi = edm_term<real>(2, r, ux, uy, dux, duy); break;
-        case 3: Fi = edm_term<real>(3, r, ux, uy, dux, duy); break;
-        case 4: Fi = edm_term<real>(4, r, ux, uy, dux, duy); break;
-        case 5: Fi = edm_term<real>(5, r, ux, uy, dux, duy); break;
-        case 6: Fi = edm_term<real>(6, r, ux, uy, dux, duy); break;
-        case 7: Fi = edm_term<real>(7, r, ux, uy, dux, duy); break;
-        default: Fi = edm_term<real>(8, r, ux, uy, dux, duy); break;
-      }
-      const real v = link_rule<real>(L.bc, L.lq[l], L.lx2f[l], a, b2, c, Fi);
-      fout[ib * L.plane + n] = v;
-      sum += (double)a - (double)v;
-    }
-    if (L.bc == BC_PRESENT || L.bc == BC_MIBC) {
-      // Eq. 18 on f_0, accumulated in FP64.  The part of the sum that the storage precision
-      // cannot hold is carried to the node's next step instead of being dropped, so that the
-      // mass stays conserved to FP64 accuracy over any number of steps.
-      const double t = (double)fout[n] + sum + L.carry[b];
-      const real stored = (real)t;
-      L.carry[b] = t - (double)stored;
-      fout[n] = stored;
-    } else {
-      sum = 0.0;
-    }
-  }
+  const double sum = b < L.n_bnodes ? phase_bc(L, cur, b) : 0.0;
   double bt = block_sum(sum, red);
   double total;
   if (finish_reduction(bt, L.partials, L.counter, &total, red)) {
-    unsigned long long s = *L.step_ctr;
-    L.dM_ring[s % DM_RING] = total;
-    *L.step_ctr = s + 1;
+    unsigned long long st = *L.step_ctr;
+    L.dM_ring[st % DM_RING] = total;
+    *L.step_ctr = st + 1;
   }
 }
 

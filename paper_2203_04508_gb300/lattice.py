@@ -164,3 +164,94 @@ class Lattice:
         n = C.c_int64()
         self._c(self.lib.lbm_launches_per_step(self.ctx, C.byref(n)))
         return n.value
+
+
+class _InstanceView(Lattice):
+    """An instance of a Batch: an ordinary lattice context owned by the batch."""
+
+    def __init__(self, batch, k, ctx, phys, precision):
+        self.lib = batch.lib
+        self.nx, self.ny = int(phys["nx"]), int(phys["ny"])
+        self.precision = precision
+        import torch
+        self.dtype = np.float64 if precision == _abi.LBM_FP64 else np.float32
+        self.tdtype = torch.float64 if precision == _abi.LBM_FP64 else torch.float32
+        self.stream = batch.stream
+        self.ctx = ctx
+        self._batch = batch   # keeps the batch (and its workspace) alive
+
+    def __del__(self):
+        pass   # the batch owns the context
+
+    def step(self, n: int = 1):
+        raise RuntimeError("instances of a batch advance with Batch.step")
+
+
+class Batch:
+    """Many independent lattices advanced together by the persistent batched kernel."""
+
+    def __init__(self, physics: list, precision: int = _abi.LBM_FP32, stream=None):
+        import torch
+        lib = _abi.load()
+        self.lib = lib
+        self.n = len(physics)
+        self.precision = precision
+        made = [make_config(p, precision) for p in physics]
+        self._keep = made
+        arr = (lbm_config * self.n)(*[m[0] for m in made])
+        self._cfgs = arr
+        n = C.c_size_t()
+        check(lib.lbm_batch_workspace_size(self.n, arr, C.byref(n)))
+        self.workspace = torch.empty(n.value, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        b = C.c_void_p()
+        st = lib.lbm_batch_create(self.n, arr, C.c_void_p(self.stream.cuda_stream),
+                                  C.c_void_p(self.workspace.data_ptr()), n.value, C.byref(b))
+        self.b = b
+        self._check(st)
+        self._check(lib.lbm_batch_build_links(self.b))
+        self.instances = []
+        for k in range(self.n):
+            ctx = C.c_void_p()
+            self._check(lib.lbm_batch_instance(self.b, k, C.byref(ctx)))
+            self.instances.append(_InstanceView(self, k, ctx, physics[k], precision))
+
+    def __del__(self):
+        if getattr(self, "b", None):
+            self.instances = []
+            self.lib.lbm_batch_destroy(self.b)
+            self.b = None
+
+    def _check(self, st):
+        if st != _abi.LBM_OK:
+            msg = self.lib.lbm_batch_last_error(self.b).decode() if getattr(self, "b", None) else ""
+            raise _abi.LbmError(st, msg)
+
+    def init(self, droplets: list):
+        self._init_keep = []
+        specs = (lbm_init_spec * self.n)()
+        for k, d in enumerate(droplets):
+            m = len(d["r0"])
+            arrs = [np.ascontiguousarray(np.asarray(d.get(key) if d.get(key) is not None else np.zeros(m), np.float64))
+                    for key in ("x0", "y0", "r0", "ux0", "uy0")]
+            self._init_keep.append(arrs)
+            specs[k] = lbm_init_spec(m, *[a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrs], float(d["width"]))
+        self._check(self.lib.lbm_batch_init(self.b, specs))
+
+    def step(self, n: int = 1):
+        self._check(self.lib.lbm_batch_step(self.b, int(n)))
+
+    def check(self):
+        """Synchronises; raises LbmError(LBM_ETIMEOUT) if a grid-barrier wait gave up."""
+        self._check(self.lib.lbm_batch_check(self.b))
+
+    def set_spin_limit(self, polls: int):
+        self._check(self.lib.lbm_batch_set_spin_limit(self.b, int(polls)))
+
+    def info(self):
+        o = np.zeros(4, np.int64)
+        self._check(self.lib.lbm_batch_info(self.b, o.ctypes.data))
+        return {"grid": int(o[0]), "node_tiles": int(o[1]), "graph": bool(o[2]), "bc_chunks": int(o[3])}
+
+    def synchronize(self):
+        self.stream.synchronize()

@@ -1,0 +1,103 @@
+"""The batched persistent step: many lattices of different sizes and physics advanced by one
+cooperative kernel per call must reproduce each lattice stepped on its own, match the oracle,
+and report a grid-barrier timeout instead of hanging."""
+import numpy as np
+import pytest
+
+import scenarios as S
+from harness import compare, make_lattice, make_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_04508_gb300 import build
+    build.build()
+
+
+def _mixed(fp64=False):
+    """Four unlike instances: ragged sizes, two temperatures, MRT and BGK, walls and a periodic
+    box, one to two cylinders."""
+    return [
+        S.small_parity(seed=7, fp64=fp64),
+        S.small_parity(seed=11, nx=97, ny=83, fp64=fp64, T_over_Tc=0.7),
+        S.c1_plain_fp64().with_(fp64=fp64, dmu_w=[-0.03]),
+        S.Scenario(name="free", nx=61, ny=53, walls=0, T_over_Tc=0.8, coll=S.COLL_BGK, tau=1.0,
+                   cx=[30.41], cy=[26.77], r=[9.3], dmu_w=[0.02], x0=[30.41], y0=[38.0], r0=[6.0], fp64=fp64),
+    ]
+
+
+def _batch(scs, fp64):
+    import paper_2203_04508_gb300 as G
+    b = G.Batch([sc.physics() for sc in scs], precision=G.LBM_FP64 if fp64 else G.LBM_FP32)
+    b.init([sc.droplets() for sc in scs])
+    return b
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_batch_equals_each_lattice_stepped_alone(fp64):
+    scs = _mixed(fp64)
+    b = _batch(scs, fp64)
+    b.step(57)
+    b.check()
+    tol = 0.0 if fp64 else 1e-6
+    for k, sc in enumerate(scs):
+        single = make_lattice(sc, fp64=fp64)
+        single.step(57)
+        fb, fs = b.instances[k].populations(), single.populations()
+        scale = np.abs(fs).max()
+        assert np.abs(fb.astype(np.float64) - fs).max() <= max(tol, 1e-13) * scale, sc.name
+        # the per-step compensation sums are cancelling sums of (f~ - f) over links: in FP32 the
+        # two kernels' roundings (contracted differently by the compiler) show at 1e-6 there
+        hb, hs = b.instances[k].dM_history(57), single.dM_history(57)
+        assert np.allclose(hb, hs, rtol=1e-9 if fp64 else 1e-4, atol=1e-12 if fp64 else 1e-7), sc.name
+        Mb, M0b, _ = b.instances[k].mass()
+        assert abs(Mb / M0b - 1) < (1e-12 if fp64 else 1e-6)
+
+
+def test_fp64_batch_matches_the_oracle():
+    scs = _mixed(True)
+    b = _batch(scs, True)
+    b.step(40)
+    b.check()
+    for k, sc in enumerate(scs):
+        orc = make_oracle(sc)
+        orc.step(40)
+        er, ev, ef = compare(b.instances[k], orc)
+        assert ef < 1e-11 and er < 1e-11, (sc.name, er, ev, ef)
+
+
+def test_consecutive_calls_and_odd_step_counts():
+    scs = _mixed(False)[:2]
+    a, c = _batch(scs, False), _batch(scs, False)
+    a.step(7)
+    a.step(6)
+    c.step(13)
+    a.check()
+    c.check()
+    for k in range(2):
+        assert np.array_equal(a.instances[k].populations(), c.instances[k].populations())
+
+
+def test_grid_barrier_timeout_is_reported_not_hung():
+    """With a zero poll budget every barrier wait gives up at once: the kernel leaves early and
+    the host sees LBM_ETIMEOUT; restoring the budget and re-initialising works again."""
+    from paper_2203_04508_gb300 import LbmError
+    scs = _mixed(False)[:2]
+    b = _batch(scs, False)
+    info = b.info()
+    if info["grid"] < 2:
+        pytest.skip("a one-block grid never waits")
+    b.set_spin_limit(0)
+    b.step(3)
+    with pytest.raises(LbmError) as e:
+        b.check()
+    assert e.value.status == 6
+    b.set_spin_limit(1 << 22)
+    b.init([sc.droplets() for sc in scs])
+    b.step(3)
+    b.check()
