@@ -107,6 +107,50 @@ def run_batched(G, torch, rank, world, steps):
             "looped_timing": "host wall clock around all instances' lbm_step calls, synchronised"}
 
 
+def run_adjoint(G, torch, steps, every):
+    """Gradient workload: droplet r = 40 on a cylinder r = 80 in a 512 x 512 channel (FP32).
+    Times a plain forward pass, the checkpointed forward pass and the reverse sweep (segment
+    recomputation included) with CUDA events on the library's stream."""
+    import scenarios as S
+    sc = S.c5_adjoint()
+    mk = lambda: G.Lattice(sc.physics(), precision=G.LBM_FP32)
+
+    def timed(lat, fn):
+        s = lat.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        out = fn()
+        e1.record(s)
+        e1.synchronize()
+        return e0.elapsed_time(e1), out
+
+    plain = mk()
+    plain.init_droplets(sc.droplets())
+    plain.step(20)                       # warm-up (graph capture)
+    plain.init_droplets(sc.droplets())
+    ms_fwd, _ = timed(plain, lambda: plain.step(steps))
+    del plain
+    lat = mk()
+    lat.init_droplets(sc.droplets())
+    lat.forward_checkpointed(2 * every, every)   # warm-up of both passes
+    _, seed = lat.objective(0, seed=True)
+    lat.adjoint(drho=seed)
+    lat.init_droplets(sc.droplets())
+    ms_ckpt, _ = timed(lat, lambda: lat.forward_checkpointed(steps, every))
+    J, seed = lat.objective(0, seed=True)
+    ms_adj, grad = timed(lat, lambda: lat.adjoint(drho=seed))
+    ws = lat.adjoint_workspace_size(steps, every)
+    del lat, seed
+    torch.cuda.empty_cache()
+    return {"workload": f"{sc.name}: {sc.nx}x{sc.ny}, cylinder r={sc.r[0]:g}, droplet r={sc.r0[0]:g}, FP32",
+            "steps": steps, "checkpoint_every": every, "workspace_GB": round(ws / 1e9, 3),
+            "ms_forward": round(ms_fwd, 3), "ms_forward_checkpointed": round(ms_ckpt, 3),
+            "ms_reverse": round(ms_adj, 3),
+            "cost_ratio": round((ms_ckpt + ms_adj) / ms_fwd, 3),
+            "reverse_MLUPS": round(sc.nodes * steps / ms_adj / 1e3, 1),
+            "J": J, "dJ_ddmu_w": float(grad[0]), "dJ_dcx": float(grad[2]), "dJ_dcy": float(grad[3])}
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -233,6 +277,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=200,
                     help="steps of the batched-instances comparison (0: skip it)")
+    ap.add_argument("--adjoint-steps", type=int, default=4000,
+                    help="steps of the gradient workload (0: skip it)")
+    ap.add_argument("--adjoint-every", type=int, default=200)
     ap.add_argument("--mode", default="full", choices=["full", "kernels"],
                     help="kernels: only warm-up and timed steps (for profiler captures)")
     args = ap.parse_args()
@@ -359,6 +406,10 @@ def main():
                            mlups_looped=round(float(nn.item()) * steps_b / float(t[1]) / 1e3, 1),
                            speedup=round(float(t[1]) / float(t[0]), 3), instances=256)
 
+    adjoint = None
+    if args.adjoint_steps > 0:
+        adjoint = run_adjoint(G, torch, args.adjoint_steps, args.adjoint_every)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, n, cores = oracle_rate(sc, max_seconds=20.0, max_steps=50)
@@ -384,6 +435,7 @@ def main():
                                       zip(("rho", "solid", "mu", "collide", "bc"), phase_ms)}},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": lps * args.steps,
             "batched": batched,
+            "adjoint": adjoint,
             "mass_drift": M / M0 - 1,
         }
         print(json.dumps(line), flush=True)

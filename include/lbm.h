@@ -194,6 +194,59 @@ lbm_status lbm_eos_info(lbm_ctx* ctx, double* out8);
 /* Number of kernel launches one lbm_step(ctx, 1) issues. */
 lbm_status lbm_launches_per_step(lbm_ctx* ctx, int64_t* n);
 
+/* Sets the state (a new initial state, in place of lbm_init) from 9 arrays of ny x nx
+ * absolute populations in the context's precision, population i at offset i*nx*ny (the layout
+ * lbm_populations writes); values at non-fluid nodes are ignored.  Clears the step counter,
+ * the compensation history and the Eq. 18 carries, and takes the state's mass as the new M0.
+ * on_device: 1 if f is a device pointer, 0 for host memory.  Synchronises the stream.  With
+ * FP32 offset storage the values are stored as f_i - w_i rho_ref, so a state read out by
+ * lbm_populations comes back to within an ulp of each offset population. */
+lbm_status lbm_set_populations(lbm_ctx* ctx, const void* f, int32_t on_device);
+
+/* ---- Objective and reverse mode (gradients through the time integration) ----------------
+ * The step (Eqs. 9, 12, 13, 15-18) is differentiable in the populations and in the parameters
+ * of the wall: the wall chemical potential offset dmu_w of every cylinder and of the
+ * flat walls, and the centre (cx, cy) of every cylinder, which enters only through the cut
+ * fractions q of Eqs. 16-17 (the set of cut links stays fixed under an infinitesimal change).
+ * lbm_forward_checkpointed advances the lattice and keeps checkpoints in a caller-owned device
+ * workspace; lbm_adjoint then runs the step's transpose backwards through those steps
+ * (recomputing each segment of `every` steps from its checkpoint) and returns dJ/d(parameters)
+ * for a seed dJ/d(final state).  Every step of both passes runs in CUDA kernels.
+ *
+ * Parameter-gradient layout (3 n_cyl + 1 doubles): [0, n_cyl) dJ/d dmu_w of each cylinder,
+ * [n_cyl] dJ/d dmu_w_walls, then dJ/dcx_k, dJ/dcy_k at [n_cyl + 1 + 2k], [n_cyl + 2 + 2k]. */
+
+/* Bytes of device workspace for a checkpointed forward pass of n_steps steps with a
+ * checkpoint every `every` steps (0: ceil(sqrt(n_steps))).  The workspace holds
+ * ceil(n_steps/every) + every - 1 population lattices plus 27 planes of adjoint state. */
+lbm_status lbm_adjoint_workspace_size(lbm_ctx* ctx, int64_t n_steps, int64_t every, size_t* bytes);
+
+/* Advances n_steps like lbm_step, storing a checkpoint (populations and Eq. 18 carries) at
+ * the start of every segment in `workspace` (device, 256-byte aligned, caller-owned, at least
+ * lbm_adjoint_workspace_size bytes; it must stay untouched until lbm_adjoint).  Asynchronous.
+ * Any later lbm_step / lbm_init / lbm_build_links invalidates the checkpoints. */
+lbm_status lbm_forward_checkpointed(lbm_ctx* ctx, int64_t n_steps, int64_t every, void* workspace, size_t bytes);
+
+/* Droplet objective of the current state for cylinder `body` (0 <= body < n_cyl):
+ *   J = y_cm + L_wet,  y_cm = sum (rho - rho_g) y / sum (rho - rho_g) over fluid nodes,
+ *   L_wet = (2 pi r_body / N) sum phi over the N fluid nodes with a cut link into the body,
+ *   phi = (rho - rho_g)/(rho_l - rho_g)  (the liquid fraction beside the wall).
+ * Writes J (host double); if dJ_drho is not NULL also writes dJ/drho, row-major ny x nx in the
+ * context's precision (zero off the fluid), to device (on_device = 1) or host memory.
+ * Synchronises the stream. */
+lbm_status lbm_objective(lbm_ctx* ctx, int32_t body, double* J, void* dJ_drho, int32_t on_device);
+
+/* Reverse sweep through the steps of the last lbm_forward_checkpointed, which must end at the
+ * current state (LBM_ESTATE otherwise).  Seeds: dJ_drho (ny x nx, row-major) and dJ_df (9
+ * arrays of ny x nx, population i at offset i*nx*ny), both of the final state, in the context's
+ * precision; either may be NULL (zero).  Writes the parameter gradient (host, 3 n_cyl + 1
+ * doubles, layout above; FP64 accumulation) if grad is not NULL, and dJ/df of the first state
+ * (same layout as dJ_df) if dJ_df0 is not NULL.  on_device applies to the three arrays.  The
+ * lattice state, step counter, compensation history and carries are those after the forward
+ * pass again when it returns; the call may be repeated.  Synchronises the stream. */
+lbm_status lbm_adjoint(lbm_ctx* ctx, const void* dJ_drho, const void* dJ_df, int32_t on_device, double* grad,
+                       void* dJ_df0);
+
 /* ---- Batches: many independent lattices advanced together -------------------------------
  * All instances share one precision; sizes, physics, geometry and initial states may differ.
  * Each instance is an ordinary lbm_ctx inside the batch (lbm_batch_instance), so lbm_fields,

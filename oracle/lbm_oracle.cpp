@@ -310,6 +310,25 @@ int orc_eos_eval(const orc_config* cfg, int n, const double* rho, double* p, dou
   });
 }
 
+// droplet objective J = y_cm + L_wet of cylinder `body` for the current state (real and
+// imaginary parts; the imaginary part / h is the complex-step derivative)
+int orc_objective(void* p, int body, double* J_re, double* J_im) {
+  return guarded([&] {
+    if (H(p)->mode == 0) {
+      auto& s = *H(p)->d;
+      if (body < 0 || body >= (int)s.rad.size()) throw std::runtime_error("objective: no such cylinder");
+      *J_re = s.objective(body);
+      if (J_im) *J_im = 0.0;
+    } else {
+      auto& s = *H(p)->c;
+      if (body < 0 || body >= (int)s.rad.size()) throw std::runtime_error("objective: no such cylinder");
+      cplx J = s.objective(body);
+      *J_re = J.real();
+      if (J_im) *J_im = J.imag();
+    }
+  });
+}
+
 // ---- single-node pieces, for the algebraic pins ----
 void orc_mrt_matrices(double* M81, double* Minv81) {
   double inv[9][9];

@@ -722,6 +722,40 @@ struct Sim {
     ++steps_done;
   }
 
+  // Droplet objective of the current state (the gradient target; the paper has none):
+  //   J = y_cm + L_wet,
+  //   y_cm  = sum_fluid (rho - rho_g) y / sum_fluid (rho - rho_g),  rho = sum_i f_i,
+  //   L_wet = (2 pi r_b / N_b) sum over the N_b fluid nodes with a link into body b of
+  //           phi(rho) = (rho - rho_g) / (rho_l - rho_g),
+  // i.e. the centre-of-mass height of the excess density plus the wetted arc length of the
+  // cylinder b estimated from the liquid fraction next to its wall.
+  T objective(int b) const {
+    const int n_all = N();
+    const double rg = eos.rho_g, rl = eos.rho_l;
+    T num = 0.0, den = 0.0, wet = 0.0;
+    int n_touch = 0;
+    for (int n = 0; n < n_all; ++n) {
+      if (kind[n] != KIND_FLUID) continue;
+      T r = 0.0;
+      for (int i = 0; i < 9; ++i) r += f[(size_t)i * n_all + n];
+      num += (r - rg) * double(n / nx);
+      den += r - rg;
+      bool touches = false;
+      for (int l = link_start[n]; l < link_start[n + 1]; ++l) {
+        int m;
+        nb(n, links[l].dir, &m);
+        if (body[m] == b) touches = true;
+      }
+      if (touches) {
+        wet += (r - rg) / (rl - rg);
+        ++n_touch;
+      }
+    }
+    const double pi = 3.14159265358979323846;
+    T Lw = n_touch > 0 ? (2.0 * pi * rad[b] / double(n_touch)) * wet : T(0.0);
+    return num / den + Lw;
+  }
+
   // Macroscopic fields of the current state: rho, and v = u + F/(2 rho) (below Eq. 14).
   void fields(std::vector<T>& r, std::vector<T>& vx, std::vector<T>& vy) {
     moments();

@@ -72,6 +72,7 @@ def _load():
         "orc_dM_history": (I, [P, dp, I]),
         "orc_eos_info": (I, [P, dp]),
         "orc_eos_eval": (I, [P, I, dp, dp, dp, dp]),
+        "orc_objective": (I, [P, I, dp, dp]),
         "orc_mrt_matrices": (None, [dp, dp]),
         "orc_lattice": (None, [ip, ip, dp, ip]),
         "orc_feq": (None, [D, D, D, dp]),
@@ -256,6 +257,12 @@ class Oracle:
         out = np.zeros(n)
         _check(self._lib.orc_dM_history(self._h, _dptr(out), int(n)))
         return out
+
+    def objective(self, body: int = 0):
+        """(J, imaginary part of J) of the droplet objective for cylinder `body`."""
+        re, im = C.c_double(), C.c_double()
+        _check(self._lib.orc_objective(self._h, int(body), C.byref(re), C.byref(im)))
+        return re.value, im.value
 
     def eos_info(self):
         out = np.zeros(8)

@@ -8,6 +8,7 @@ PyTorch.  There is no CPU fallback: without the built library every call raises.
 from . import _abi  # noqa: F401
 from ._abi import LBM_FP32, LBM_FP64, LbmError, declared_symbols, load  # noqa: F401
 from .lattice import Batch, Lattice, make_config, workspace_size  # noqa: F401
+from .autograd import params_vector, rollout, with_params  # noqa: F401
 
 EOS_NONE, EOS_CS, EOS_PR = 0, 1, 2
 COLL_BGK, COLL_MRT = 0, 1

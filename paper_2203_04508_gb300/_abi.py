@@ -51,6 +51,7 @@ _SIGS = {
     "lbm_step": (I32, [P, I64]),
     "lbm_fields": (I32, [P, P, P, P, I32]),
     "lbm_populations": (I32, [P, P, I32]),
+    "lbm_set_populations": (I32, [P, P, I32]),
     "lbm_mass": (I32, [P, C.POINTER(D), C.POINTER(D), C.POINTER(D)]),
     "lbm_dM_history": (I32, [P, P, I64, C.POINTER(I64)]),
     "lbm_eos_info": (I32, [P, P]),
@@ -69,6 +70,10 @@ _SIGS = {
     "lbm_batch_last_error": (C.c_char_p, [P]),
     "lbm_batch_destroy": (None, [P]),
     "lbm_mass_noalloc": (I32, [P, P, I64, I32, P, P]),
+    "lbm_adjoint_workspace_size": (I32, [P, I64, I64, C.POINTER(SZ)]),
+    "lbm_forward_checkpointed": (I32, [P, I64, I64, P, SZ]),
+    "lbm_objective": (I32, [P, I32, C.POINTER(D), P, I32]),
+    "lbm_adjoint": (I32, [P, P, P, I32, P, P]),
     "lbm_destroy": (None, [P]),
     "lbm_status_str": (C.c_char_p, [I32]),
     "lbm_last_error": (C.c_char_p, [P]),

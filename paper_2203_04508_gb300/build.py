@@ -1,6 +1,6 @@
 """Builds the CUDA library liblbm_gb300.so in-tree for sm_103a (GB300).
 
-Four translation units are compiled in parallel with nvcc and linked into one shared
+The translation units are compiled in parallel with nvcc and linked into one shared
 library with the static CUDA runtime.  lbm_geometry.cu is compiled with -fmad=false so that
 the cut fractions q are rounded operation by operation (bit-reproducible on any IEEE host).
 """
@@ -26,6 +26,7 @@ UNITS = [
     ("lbm_eos.cpp", ["-x", "cu"]),
     ("lbm_noalloc.cu", []),
     ("lbm_batch.cu", []),
+    ("lbm_adjoint.cu", []),
 ]
 
 

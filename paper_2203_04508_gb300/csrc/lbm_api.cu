@@ -53,7 +53,7 @@ struct Layout {
   long long plane;
   size_t sz;
   Caps cap;
-  size_t fA, fB, rho, mu, kind;
+  size_t fA, fB, rho, mu, kind, body;
   size_t lq64, lq, ldir, lx2f, bnode, bstart, carry;
   size_t s1node, s1mask, s1winv, s2node, s2mask, s2winv;
   size_t cyl, drops, partials, counter, step_ctr, scalars, dm_ring, block_sums, totals;
@@ -74,6 +74,7 @@ Layout make_layout(const lbm_config* c) {
   L.rho = take(L.plane * L.sz);
   L.mu = take(L.plane * L.sz);
   L.kind = take(L.plane);
+  L.body = take(L.plane * 4);
   L.lq64 = take(L.cap.links * 8);
   L.lq = take(L.cap.links * L.sz);
   L.ldir = take(L.cap.links);
@@ -124,6 +125,15 @@ struct lbm_ctx {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   lbm_status sticky = LBM_OK;
   std::string err;
+  // the last checkpointed forward pass (lbm_forward_checkpointed), for lbm_adjoint
+  struct Tape {
+    bool valid = false;
+    char* ws = nullptr;
+    size_t bytes = 0;
+    long long n = 0, every = 0, nseg = 0;
+    long long steps_end = 0;
+    int cur_end = 0;
+  } tape;
 };
 
 namespace {
@@ -162,6 +172,8 @@ void fill_lattice(lbm_ctx* c, Lattice<real>& L) {
   L.rho = (real*)(w + y.rho);
   L.mu = (real*)(w + y.mu);
   L.kind = (const uint8_t*)(w + y.kind);
+  L.body = (const int*)(w + y.body);
+  L.cyl = (const double*)(w + y.cyl);
   const lbm_config& g = c->cfg;
   L.eos = g.eos;
   const double RT = g.R * c->eos.T;
@@ -397,8 +409,8 @@ lbm_status lbm_build_links(lbm_ctx* c) {
   gp.dmu_walls = g.dmu_w_walls;
   // the second lattice is free until lbm_init: it holds the per-node scratch of the set-up
   GeomScratch sc{};
-  sc.body = (int*)(w + y.fB);
-  sc.cnt = sc.body + y.plane;
+  sc.body = (int*)(w + y.body);
+  sc.cnt = (int*)(w + y.fB);
   sc.off = sc.cnt + y.plane;
   sc.block_sums = (int*)(w + y.block_sums);
   sc.totals = (int*)(w + y.totals);
@@ -427,6 +439,7 @@ lbm_status lbm_build_links(lbm_ctx* c) {
   CUDA_OK(c, cudaStreamSynchronize(c->stream));
   c->built = true;
   c->inited = false;
+  c->tape.valid = false;
   refresh(c);
   return LBM_OK;
 }
@@ -510,6 +523,7 @@ lbm_status lbm_init(lbm_ctx* c, const lbm_init_spec* s) {
   CUDA_OK(c, cudaStreamSynchronize(c->stream));
   c->mass0 = sc[0] + (double)c->n_fluid * c->rho_ref;
   c->inited = true;
+  c->tape.valid = false;
   return LBM_OK;
 }
 
@@ -519,6 +533,7 @@ lbm_status lbm_step(lbm_ctx* c, int64_t n) {
   if (n < 0) return fail(c, LBM_EINVAL, "negative step count");
   lbm_status s = c->fp64 ? do_step(c, c->Ld, n) : do_step(c, c->Lf, n);
   if (s == LBM_OK) c->steps += n;
+  if (n > 0) c->tape.valid = false;
   return s;
 }
 
@@ -564,6 +579,34 @@ lbm_status lbm_populations(lbm_ctx* c, void* f, int32_t on_device) {
     CUDA_OK(c, cudaMemcpyAsync(f, out, 9 * dn * sz, cudaMemcpyDeviceToHost, c->stream));
     CUDA_OK(c, cudaStreamSynchronize(c->stream));
   }
+  return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_ctx* c, const void* f, int32_t on_device) {
+  if (!c || !c->built) return LBM_ESTATE;
+  if (c->sticky != LBM_OK) return c->sticky;
+  if (!f) return fail(c, LBM_EINVAL, "null input");
+  const Layout& y = c->lay;
+  const long long dn = (long long)c->cfg.nx * c->cfg.ny;
+  c->cur = 0;
+  const void* src = f;
+  if (!on_device) {
+    CUDA_OK(c, cudaMemcpyAsync(c->ws + y.fB, f, 9 * dn * y.sz, cudaMemcpyHostToDevice, c->stream));
+    src = c->ws + y.fB;
+  }
+  if (c->fp64) CUDA_OK(c, launch_set_populations(c->Ld, 0, (const double*)src, c->stream));
+  else CUDA_OK(c, launch_set_populations(c->Lf, 0, (const float*)src, c->stream));
+  CUDA_OK(c, cudaMemsetAsync(c->ws + y.step_ctr, 0, 16, c->stream));
+  CUDA_OK(c, cudaMemsetAsync(c->ws + y.dm_ring, 0, (size_t)DM_RING * 8, c->stream));
+  CUDA_OK(c, cudaMemsetAsync(c->ws + y.carry, 0, (size_t)y.cap.bnodes * 8, c->stream));
+  c->steps = 0;
+  if (c->fp64) CUDA_OK(c, launch_mass(c->Ld, 0, c->stream)); else CUDA_OK(c, launch_mass(c->Lf, 0, c->stream));
+  double sc[2];
+  CUDA_OK(c, cudaMemcpyAsync(sc, c->ws + y.scalars, 16, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  c->mass0 = sc[0] + (double)c->n_fluid * c->rho_ref;
+  c->inited = true;
+  c->tape.valid = false;
   return LBM_OK;
 }
 
@@ -925,6 +968,237 @@ void lbm_batch_destroy(lbm_batch* b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
   for (auto* c : b->ctx) lbm_destroy(c);
   delete b;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Objective and reverse mode
+// ---------------------------------------------------------------------------------------
+namespace {
+
+// Adjoint workspace: checkpoints of the populations and of the Eq. 18 carries at the start of
+// every segment of `every` steps, the recomputed states inside one segment, the adjoint
+// planes, and the snapshots that restore the forward state afterwards.
+struct AdjLayout {
+  long long n, every, nseg;
+  size_t ckpt, ckcarry, seg, lam0, lam1, lam_bc, lrj, lamF, Lmu, Lrho, bct, ring, ctr, carry, grad;
+  size_t state;   // bytes of one population lattice (9 planes)
+  size_t total;
+};
+
+AdjLayout make_adj_layout(const lbm_ctx* c, long long n, long long every) {
+  AdjLayout A{};
+  const Layout& y = c->lay;
+  if (every <= 0) every = (long long)std::ceil(std::sqrt((double)n));
+  if (every < 1) every = 1;
+  if (every > n) every = n;
+  A.n = n;
+  A.every = every;
+  A.nseg = (n + every - 1) / every;
+  A.state = align_up(9 * (size_t)y.plane * y.sz);
+  const size_t pl = (size_t)y.plane * y.sz;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return at; };
+  A.ckpt = take((size_t)A.nseg * A.state);
+  A.ckcarry = take((size_t)A.nseg * (size_t)y.cap.bnodes * 8);
+  A.seg = take((size_t)(every - 1) * A.state);
+  A.lam0 = take(9 * pl);
+  A.lam1 = take(9 * pl);
+  A.lam_bc = take(9 * pl);
+  A.lrj = take(3 * pl);
+  A.lamF = take(2 * pl);
+  A.Lmu = take(pl);
+  A.Lrho = take(pl);
+  A.bct = take((size_t)y.plane);
+  A.ring = take((size_t)DM_RING * 8);
+  A.ctr = take(16);
+  A.carry = take((size_t)y.cap.bnodes * 8);
+  A.grad = take((size_t)(3 * c->cfg.n_cyl + 1) * 8);
+  A.total = o;
+  return A;
+}
+
+template <typename real>
+lbm_status forward_checkpointed(lbm_ctx* c, const Lattice<real>& L, const AdjLayout& A) {
+  const Layout& y = c->lay;
+  char* w = c->tape.ws;
+  for (long long s = 0; s < A.nseg; ++s) {
+    const long long k = s + 1 < A.nseg ? A.every : A.n - s * A.every;
+    CUDA_OK(c, cudaMemcpyAsync(w + A.ckpt + s * A.state, L.f[c->cur], 9 * (size_t)y.plane * y.sz,
+                               cudaMemcpyDeviceToDevice, c->stream));
+    if (c->n_bnodes > 0)
+      CUDA_OK(c, cudaMemcpyAsync(w + A.ckcarry + s * (size_t)y.cap.bnodes * 8, L.carry, (size_t)c->n_bnodes * 8,
+                                 cudaMemcpyDeviceToDevice, c->stream));
+    lbm_status st = do_step(c, L, k);
+    if (st != LBM_OK) return st;
+    c->steps += k;
+  }
+  return LBM_OK;
+}
+
+template <typename real>
+lbm_status objective(lbm_ctx* c, const Lattice<real>& L, int body, double* J, void* seed, int on_device) {
+  const Layout& y = c->lay;
+  // the lattice that the next step overwrites completely holds the scratch
+  char* stage = c->ws + (c->cur ? y.fA : y.fB);
+  uint8_t* touch = (uint8_t*)stage;
+  double* red = (double*)(stage + align_up((size_t)y.plane));
+  real* out = (real*)(stage + align_up((size_t)y.plane) + ALIGN);
+  CUDA_OK(c, objective_sums(L, c->cur, body, touch, red, c->eos.rho_g, c->eos.rho_l, c->stream));
+  double h[4];
+  CUDA_OK(c, cudaMemcpyAsync(h, red, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  if (!(h[0] != 0.0)) return fail(c, LBM_EINVAL, "no excess density: the objective is undefined");
+  const double y_cm = h[1] / h[0];
+  const double dphi = c->eos.rho_l - c->eos.rho_g;
+  const double arc = h[3] > 0 ? 2.0 * M_PI * c->r[body] / h[3] : 0.0;
+  *J = y_cm + arc * h[2];
+  if (seed) {
+    const long long dn = (long long)c->cfg.nx * c->cfg.ny;
+    real* dst = on_device ? (real*)seed : out;
+    CUDA_OK(c, objective_seed(L, touch, y_cm, h[0], arc / dphi, dst, c->stream));
+    if (!on_device) {
+      CUDA_OK(c, cudaMemcpyAsync(seed, dst, dn * y.sz, cudaMemcpyDeviceToHost, c->stream));
+      CUDA_OK(c, cudaStreamSynchronize(c->stream));
+    }
+  }
+  return LBM_OK;
+}
+
+template <typename real>
+lbm_status adjoint(lbm_ctx* c, const Lattice<real>& L, const void* drho, const void* df, int on_device, double* grad,
+                   void* df0) {
+  const Layout& y = c->lay;
+  const AdjLayout A = make_adj_layout(c, c->tape.n, c->tape.every);
+  char* w = c->tape.ws;
+  cudaStream_t st = c->stream;
+  const long long dn = (long long)c->cfg.nx * c->cfg.ny;
+  const size_t pl = (size_t)y.plane * y.sz;
+  // snapshots of the forward state that the recomputation overwrites
+  CUDA_OK(c, cudaMemcpyAsync(w + A.ring, L.dM_ring, (size_t)DM_RING * 8, cudaMemcpyDeviceToDevice, st));
+  CUDA_OK(c, cudaMemcpyAsync(w + A.ctr, L.step_ctr, 8, cudaMemcpyDeviceToDevice, st));
+  if (c->n_bnodes > 0)
+    CUDA_OK(c, cudaMemcpyAsync(w + A.carry, L.carry, (size_t)c->n_bnodes * 8, cudaMemcpyDeviceToDevice, st));
+  // seeds (host seeds are staged in planes that are overwritten before they are read)
+  const real* s_rho = (const real*)drho;
+  const real* s_f = (const real*)df;
+  if (!on_device) {
+    if (drho) {
+      CUDA_OK(c, cudaMemcpyAsync(w + A.Lmu, drho, dn * y.sz, cudaMemcpyHostToDevice, st));
+      s_rho = (const real*)(w + A.Lmu);
+    }
+    if (df) {
+      CUDA_OK(c, cudaMemcpyAsync(w + A.lam_bc, df, 9 * dn * y.sz, cudaMemcpyHostToDevice, st));
+      s_f = (const real*)(w + A.lam_bc);
+    }
+  }
+  real* lam[2] = {(real*)(w + A.lam0), (real*)(w + A.lam1)};
+  CUDA_OK(c, adj_seed(L, lam[0], s_rho, s_f, st));
+  CUDA_OK(c, cudaMemsetAsync(lam[1], 0, 9 * pl, st));
+  CUDA_OK(c, cudaMemsetAsync(w + A.lam_bc, 0, 9 * pl, st));
+  CUDA_OK(c, cudaMemsetAsync(w + A.lamF, 0, 2 * pl, st));
+  CUDA_OK(c, cudaMemsetAsync(w + A.grad, 0, (size_t)(3 * c->cfg.n_cyl + 1) * 8, st));
+  CUDA_OK(c, adj_flags(L, (uint8_t*)(w + A.bct), st));
+  AdjBuffers B{};
+  B.lam_bc = w + A.lam_bc;
+  B.lrj = w + A.lrj;
+  B.lamF = w + A.lamF;
+  B.Lmu = w + A.Lmu;
+  B.Lrho = w + A.Lrho;
+  B.bct = (const uint8_t*)(w + A.bct);
+  B.grad = (double*)(w + A.grad);
+  B.n_cyl = c->cfg.n_cyl;
+  int p = 0;
+  auto state = [&](long long s, long long i) -> real* {
+    return (real*)(i == 0 ? w + A.ckpt + s * A.state : w + A.seg + (i - 1) * A.state);
+  };
+  for (long long s = A.nseg - 1; s >= 0; --s) {
+    const long long k = s + 1 < A.nseg ? A.every : A.n - s * A.every;
+    // recompute the states of the segment from its checkpoint, carries included
+    if (c->n_bnodes > 0)
+      CUDA_OK(c, cudaMemcpyAsync(L.carry, w + A.ckcarry + s * (size_t)y.cap.bnodes * 8, (size_t)c->n_bnodes * 8,
+                                 cudaMemcpyDeviceToDevice, st));
+    Lattice<real> Lc = L;
+    for (long long i = 0; i + 1 < k; ++i) {
+      Lc.f[0] = state(s, i);
+      Lc.f[1] = state(s, i + 1);
+      CUDA_OK(c, launch_step(Lc, 0, st));
+    }
+    for (long long i = k - 1; i >= 0; --i) {
+      Lc.f[0] = state(s, i);
+      Lc.f[1] = nullptr;
+      B.lam_in = lam[p];
+      B.lam_out = lam[p ^ 1];
+      CUDA_OK(c, adj_step(Lc, B, st));
+      p ^= 1;
+    }
+  }
+  if (df0) {
+    real* dst = on_device ? (real*)df0 : (real*)(w + A.lam_bc);
+    CUDA_OK(c, adj_export(L, lam[p], dst, st));
+    if (!on_device) CUDA_OK(c, cudaMemcpyAsync(df0, dst, 9 * dn * y.sz, cudaMemcpyDeviceToHost, st));
+  }
+  std::vector<double> g(3 * c->cfg.n_cyl + 1);
+  CUDA_OK(c, cudaMemcpyAsync(g.data(), w + A.grad, g.size() * 8, cudaMemcpyDeviceToHost, st));
+  // the forward state as it was after lbm_forward_checkpointed
+  CUDA_OK(c, cudaMemcpyAsync(L.dM_ring, w + A.ring, (size_t)DM_RING * 8, cudaMemcpyDeviceToDevice, st));
+  CUDA_OK(c, cudaMemcpyAsync(L.step_ctr, w + A.ctr, 8, cudaMemcpyDeviceToDevice, st));
+  if (c->n_bnodes > 0)
+    CUDA_OK(c, cudaMemcpyAsync(L.carry, w + A.carry, (size_t)c->n_bnodes * 8, cudaMemcpyDeviceToDevice, st));
+  CUDA_OK(c, cudaStreamSynchronize(st));
+  if (grad) std::memcpy(grad, g.data(), g.size() * 8);
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_adjoint_workspace_size(lbm_ctx* c, int64_t n_steps, int64_t every, size_t* bytes) {
+  if (!c || !c->built || !bytes) return LBM_ESTATE;
+  if (n_steps < 1 || every < 0) return fail(c, LBM_EINVAL, "n_steps must be positive and every non-negative");
+  *bytes = make_adj_layout(c, n_steps, every).total;
+  return LBM_OK;
+}
+
+lbm_status lbm_forward_checkpointed(lbm_ctx* c, int64_t n_steps, int64_t every, void* workspace, size_t bytes) {
+  if (!c || !c->inited) return LBM_ESTATE;
+  if (c->sticky != LBM_OK) return c->sticky;
+  if (n_steps < 1 || every < 0) return fail(c, LBM_EINVAL, "n_steps must be positive and every non-negative");
+  const AdjLayout A = make_adj_layout(c, n_steps, every);
+  if (!workspace || ((uintptr_t)workspace) % ALIGN) return fail(c, LBM_EINVAL, "adjoint workspace must be 256-byte aligned");
+  if (bytes < A.total) return fail(c, LBM_ENOMEM, "adjoint workspace of %zu bytes, %zu needed", bytes, A.total);
+  c->tape = lbm_ctx::Tape{};
+  c->tape.ws = (char*)workspace;
+  c->tape.bytes = bytes;
+  c->tape.n = A.n;
+  c->tape.every = A.every;
+  c->tape.nseg = A.nseg;
+  lbm_status s = c->fp64 ? forward_checkpointed(c, c->Ld, A) : forward_checkpointed(c, c->Lf, A);
+  if (s != LBM_OK) return s;
+  c->tape.steps_end = c->steps;
+  c->tape.cur_end = c->cur;
+  c->tape.valid = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_objective(lbm_ctx* c, int32_t body, double* J, void* dJ_drho, int32_t on_device) {
+  if (!c || !c->inited) return LBM_ESTATE;
+  if (c->sticky != LBM_OK) return c->sticky;
+  if (!J) return fail(c, LBM_EINVAL, "null output");
+  if (body < 0 || body >= c->cfg.n_cyl) return fail(c, LBM_EINVAL, "body %d is not a cylinder", body);
+  return c->fp64 ? objective(c, c->Ld, body, J, dJ_drho, on_device) : objective(c, c->Lf, body, J, dJ_drho, on_device);
+}
+
+lbm_status lbm_adjoint(lbm_ctx* c, const void* dJ_drho, const void* dJ_df, int32_t on_device, double* grad,
+                       void* dJ_df0) {
+  if (!c || !c->inited) return LBM_ESTATE;
+  if (c->sticky != LBM_OK) return c->sticky;
+  if (!c->tape.valid || c->tape.steps_end != c->steps || c->tape.cur_end != c->cur)
+    return fail(c, LBM_ESTATE, "no checkpointed forward pass ends at the current state");
+  return c->fp64 ? adjoint(c, c->Ld, dJ_drho, dJ_df, on_device, grad, dJ_df0)
+                 : adjoint(c, c->Lf, dJ_drho, dJ_df, on_device, grad, dJ_df0);
 }
 
 }  // extern "C"

@@ -33,6 +33,8 @@ struct Lattice {
   real* rho;                    // density plane (fluid and the two solid layers)
   real* mu;                     // chemical potential minus k^2 mu_sat (constant at solids)
   const uint8_t* kind;
+  const int* body;              // body of each solid node (cylinders 0.., then bottom, top wall)
+  const double* cyl;            // per cylinder: cx, cy, r, wall chemical-potential offset
   // equation of state, Eq. 12: mu~ = k^2 (psi'(rho) - mu_sat) - kappa lap(rho)
   int eos;
   real RT, a, b, aalpha, k2, kappa, mu_sat;

@@ -16,6 +16,7 @@ template <typename real> cudaError_t launch_phase(const Lattice<real>& L, int cu
 template <typename real> cudaError_t launch_macro(const Lattice<real>& L, int cur, cudaStream_t s);
 template <typename real> cudaError_t launch_fields(const Lattice<real>& L, int cur, real* r, real* vx, real* vy, cudaStream_t s);
 template <typename real> cudaError_t launch_populations(const Lattice<real>& L, int cur, real* out, cudaStream_t s);
+template <typename real> cudaError_t launch_set_populations(const Lattice<real>& L, int cur, const real* in, cudaStream_t s);
 template <typename real> cudaError_t launch_mass(const Lattice<real>& L, int cur, cudaStream_t s);
 template <typename real> cudaError_t launch_init(const Lattice<real>& L, const double* drops, int n_drop, double W,
                                                  double rho_g, double rho_l, cudaStream_t s);
@@ -31,7 +32,7 @@ struct GeomParams {
 };
 
 struct GeomScratch {
-  int* body;                  // plane
+  int* body;                  // plane (kept: the body of every solid node)
   int* cnt;                   // plane
   int* off;                   // plane
   int* block_sums;            // ceil(plane / 1024) + 1
@@ -73,6 +74,32 @@ struct BatchDev {
 int batch_block_size();
 int batch_grid_size(int fp64);
 cudaError_t launch_batch(const BatchDev& B, int fp64, int grid, int n_steps, int cur0, cudaStream_t s);
+
+// ---- reverse mode of the step (lbm_adjoint.cu)
+// Precision-typed planes (pitch * ny elements each) of one reverse step.
+struct AdjBuffers {
+  const void* lam_in;   // 9 planes: dJ/df^{t+1}
+  void* lam_out;        // 9 planes: dJ/df^t
+  void* lam_bc;         // 9 planes: boundary contributions to dJ/d(post-collision f), zero between steps
+  void* lrj;            // 3 planes: dJ/d(delta rho, jx, jy) of the link rule at boundary nodes
+  void* lamF;           // 2 planes: dJ/dF (zero off the fluid)
+  void* Lmu;            // dJ/dmu
+  void* Lrho;           // dJ/drho (the density plane)
+  const uint8_t* bct;   // per node: bit 0 lam_bc may be non-zero, bit 1 boundary node
+  double* grad;         // dJ/d dmu per cylinder, dJ/d dmu of the walls, dJ/d(cx, cy) per cylinder
+  int n_cyl;
+};
+template <typename real> cudaError_t adj_flags(const Lattice<real>& L, uint8_t* bct, cudaStream_t s);
+template <typename real>
+cudaError_t objective_sums(const Lattice<real>& L, int cur, int body, uint8_t* touch, double* red, double rg,
+                           double rl, cudaStream_t s);
+template <typename real>
+cudaError_t objective_seed(const Lattice<real>& L, const uint8_t* touch, double y_cm, double S, double wcoef,
+                           real* out, cudaStream_t s);
+template <typename real>
+cudaError_t adj_seed(const Lattice<real>& L, real* lam, const real* drho, const real* df, cudaStream_t s);
+template <typename real> cudaError_t adj_export(const Lattice<real>& L, const real* lam, real* out, cudaStream_t s);
+template <typename real> cudaError_t adj_step(const Lattice<real>& L, const AdjBuffers& A, cudaStream_t s);
 
 // ---- EOS on the host (lbm_eos.cpp)
 struct EosSolution {

@@ -164,6 +164,20 @@ __global__ void k_populations(Lattice<real> L, int cur, real* out) {
     out[i * dn + d] = fluid ? L.f[cur][i * L.plane + n] + real(wgt(i)) * L.rho_ref : real(0);
 }
 
+// inverse of k_populations: fluid nodes of lattice `cur` from 9 row-major arrays of absolute
+// populations (other nodes keep their values)
+template <typename real>
+__global__ void k_set_populations(Lattice<real> L, int cur, const real* in) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= L.plane) return;
+  const int x = (int)(n % L.pitch), y = (int)(n / L.pitch);
+  if (x >= L.nx || L.kind[n] != KIND_FLUID) return;
+  const long long d = (long long)y * L.nx + x;
+  const long long dn = (long long)L.nx * L.ny;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) L.f[cur][i * L.plane + n] = in[i * dn + d] - real(wgt(i)) * L.rho_ref;
+}
+
 // Eq. 19 initial state: rho = (rho_g + rho_l)/2 + (rho_g - rho_l)/2 tanh(2(r - r0)/W) around
 // the droplet with the largest liquid fraction phi at the node, u = phi u0, f = f^eq.
 template <typename real>
@@ -276,6 +290,12 @@ cudaError_t launch_populations(const Lattice<real>& L, int cur, real* out, cudaS
 }
 
 template <typename real>
+cudaError_t launch_set_populations(const Lattice<real>& L, int cur, const real* in, cudaStream_t s) {
+  k_set_populations<real><<<grid_for(L.plane, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, cur, in);
+  return cudaGetLastError();
+}
+
+template <typename real>
 cudaError_t launch_mass(const Lattice<real>& L, int cur, cudaStream_t s) {
   k_mass<real><<<mass_blocks(), NODE_BLOCK, 0, s>>>(L, cur);
   return cudaGetLastError();
@@ -295,6 +315,7 @@ cudaError_t launch_init(const Lattice<real>& L, const double* drops, int n_drop,
   template cudaError_t launch_macro<real>(const Lattice<real>&, int, cudaStream_t);                     \
   template cudaError_t launch_fields<real>(const Lattice<real>&, int, real*, real*, real*, cudaStream_t); \
   template cudaError_t launch_populations<real>(const Lattice<real>&, int, real*, cudaStream_t);        \
+  template cudaError_t launch_set_populations<real>(const Lattice<real>&, int, const real*, cudaStream_t); \
   template cudaError_t launch_mass<real>(const Lattice<real>&, int, cudaStream_t);                      \
   template cudaError_t launch_init<real>(const Lattice<real>&, const double*, int, double, double,      \
                                          double, cudaStream_t);

@@ -122,7 +122,9 @@ class Lattice:
         import torch
         if on_device:
             out = [torch.empty((self.ny, self.nx), dtype=self.tdtype, device="cuda") for _ in range(3)]
+            self.stream.wait_stream(torch.cuda.current_stream())
             self._c(self.lib.lbm_fields(self.ctx, *[C.c_void_p(t.data_ptr()) for t in out], 1))
+            torch.cuda.current_stream().wait_stream(self.stream)
             return tuple(out)
         out = [np.zeros((self.ny, self.nx), self.dtype) for _ in range(3)]
         self._c(self.lib.lbm_fields(self.ctx, *[o.ctypes.data for o in out], 0))
@@ -132,6 +134,18 @@ class Lattice:
         f = np.zeros((9, self.ny, self.nx), self.dtype)
         self._c(self.lib.lbm_populations(self.ctx, f.ctypes.data, 0))
         return f
+
+    def set_populations(self, f):
+        """New initial state from absolute populations (9 x ny x nx, numpy array or torch
+        tensor on the device)."""
+        import torch
+        if isinstance(f, torch.Tensor):
+            t = f.detach().to(device="cuda", dtype=self.tdtype).contiguous()
+            self.stream.wait_stream(torch.cuda.current_stream())
+            self._c(self.lib.lbm_set_populations(self.ctx, C.c_void_p(t.data_ptr()), 1))
+        else:
+            a = np.ascontiguousarray(np.asarray(f, self.dtype))
+            self._c(self.lib.lbm_set_populations(self.ctx, a.ctypes.data, 0))
 
     def mass(self):
         m, m0, dm = C.c_double(), C.c_double(), C.c_double()
@@ -164,6 +178,65 @@ class Lattice:
         n = C.c_int64()
         self._c(self.lib.lbm_launches_per_step(self.ctx, C.byref(n)))
         return n.value
+
+    # ---- objective and reverse mode
+    @property
+    def n_params(self) -> int:
+        """Length of the parameter gradient: dmu_w per cylinder, dmu_w of the walls, (cx, cy)
+        per cylinder."""
+        return 3 * int(self._cfg.n_cyl) + 1
+
+    def objective(self, body: int = 0, seed: bool = False):
+        """Droplet objective J of the current state for cylinder `body`; with seed=True also
+        dJ/drho (ny x nx torch tensor on the device, zero off the fluid)."""
+        import torch
+        J = C.c_double()
+        out = None
+        if seed:
+            out = torch.empty((self.ny, self.nx), dtype=self.tdtype, device="cuda")
+            self.stream.wait_stream(torch.cuda.current_stream())
+        self._c(self.lib.lbm_objective(self.ctx, int(body), C.byref(J),
+                                       C.c_void_p(out.data_ptr()) if seed else None, 1))
+        return (J.value, out) if seed else J.value
+
+    def adjoint_workspace_size(self, n: int, every: int = 0) -> int:
+        b = C.c_size_t()
+        self._c(self.lib.lbm_adjoint_workspace_size(self.ctx, int(n), int(every), C.byref(b)))
+        return b.value
+
+    def forward_checkpointed(self, n: int, every: int = 0):
+        """Advances n steps keeping checkpoints every `every` steps (0: about sqrt(n)) in a
+        device workspace held by this object until the next call."""
+        import torch
+        size = self.adjoint_workspace_size(n, every)
+        if getattr(self, "_tape", None) is None or self._tape.numel() < size:
+            self._tape = None
+            self._tape = torch.empty(size, dtype=torch.uint8, device="cuda")
+        self.stream.wait_stream(torch.cuda.current_stream())
+        self._c(self.lib.lbm_forward_checkpointed(self.ctx, int(n), int(every),
+                                                  C.c_void_p(self._tape.data_ptr()), self._tape.numel()))
+
+    def adjoint(self, drho=None, df=None, want_df0: bool = False):
+        """Reverse sweep through the last forward_checkpointed.  drho (ny x nx) and df
+        (9 x ny x nx) are torch tensors of dJ/d(final state), either may be None.  Returns the
+        parameter gradient (numpy, n_params) and, with want_df0, dJ/df of the first state."""
+        import torch
+
+        def dev(t, shape):
+            if t is None:
+                return None
+            t = t.detach().to(device="cuda", dtype=self.tdtype).contiguous()
+            if tuple(t.shape) != shape:
+                raise ValueError(f"seed of shape {tuple(t.shape)}, expected {shape}")
+            return t
+        drho = dev(drho, (self.ny, self.nx))
+        df = dev(df, (9, self.ny, self.nx))
+        df0 = torch.empty((9, self.ny, self.nx), dtype=self.tdtype, device="cuda") if want_df0 else None
+        grad = np.zeros(self.n_params)
+        self.stream.wait_stream(torch.cuda.current_stream())
+        ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+        self._c(self.lib.lbm_adjoint(self.ctx, ptr(drho), ptr(df), 1, grad.ctypes.data, ptr(df0)))
+        return (grad, df0) if want_df0 else grad
 
 
 class _InstanceView(Lattice):
