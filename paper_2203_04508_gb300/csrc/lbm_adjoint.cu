@@ -12,8 +12,10 @@
 //   adj_force   Eq. 9: the force's dependence on mu and rho at the stencil neighbours (gather)
 //   adj_mu      Eq. 12: mu's dependence on rho (gather); wall mu -> dJ/d(offset)
 //   adj_solid   Eq. 15, second layer then first layer (scatter, atomics)
-//   adj_final   the density's share added to every population
-// The forward quantities of step t (rho, solid rho, mu) are recomputed from the stored f^t.
+// The density's share of lambda^t, Lrho (one value per node, the same for all nine
+// populations), is not added to the nine planes: lambda^t is kept as (nine planes, Lrho) and the
+// next reverse step adds Lrho where it reads lambda.  The forward quantities of step t (rho,
+// solid rho, mu) are those the recomputation of the segment stored for that step.
 #include "lbm_internal.h"
 #include "lbm_phases.cuh"
 
@@ -132,6 +134,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adj_bc(Lattice<real> L, AdjBuffer
   const int n = L.bnode[b];
   const int x = n % L.pitch, y = n / L.pitch;
   const real* lin = static_cast<const real*>(A.lam_in);
+  const real lrn = static_cast<const real*>(A.Lrho)[n];   // density share of lambda^{t+1} at x1
   real* lbc = static_cast<real*>(A.lam_bc);
   real f[9], r, drho, jx, jy, Fx, Fy;
   node_state(L, x, y, f, r, drho, jx, jy, Fx, Fy);
@@ -141,7 +144,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adj_bc(Lattice<real> L, AdjBuffer
   collide_node(L, ft, r, drho, jx, jy, Fx, Fy);
   const bool comp = L.bc == BC_PRESENT || L.bc == BC_MIBC;
   const real wF = L.bc == BC_PRESENT ? real(1) : real(0);
-  const real l0 = comp ? lin[n] : real(0);
+  const real l0 = comp ? lin[n] + lrn : real(0);
   const real ir = real(1) / r;
   real lrho = 0, ljx = 0, ljy = 0, lFx = 0, lFy = 0;
   for (int l = L.bstart[b]; l < L.bstart[b + 1]; ++l) {
@@ -155,7 +158,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adj_bc(Lattice<real> L, AdjBuffer
     const real Jx = jx + Fx, Jy = jy + Fy;
     const real Fi = real(wgt(i)) * (real(3) * eF + real(4.5) * (eJ * eJ - ej * ej) * ir -
                                     real(1.5) * ((Jx * Jx + Jy * Jy) - (jx * jx + jy * jy)) * ir);
-    const real lR = lin[ib * L.plane + n] - l0;
+    const real lR = (lin[ib * L.plane + n] + lrn) - l0;
     real dA = 0, dB = 0, dC = 0, dF = 0, dQ = 0;
     if (L.bc == BC_HBB || (q < real(0.5) && !L.lx2f[l])) {
       dA = 1;
@@ -222,6 +225,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adj_collide(Lattice<real> L, AdjB
   const int n = y * L.pitch + x;
   if (L.kind[n] != KIND_FLUID) return;
   const real* lin = static_cast<const real*>(A.lam_in);
+  const real* lrp = static_cast<const real*>(A.Lrho);   // density share of lambda^{t+1}
   real* lout = static_cast<real*>(A.lam_out);
   real* lbc = static_cast<real*>(A.lam_bc);
   real* lrj = static_cast<real*>(A.lrj);
@@ -236,7 +240,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adj_collide(Lattice<real> L, AdjB
     real v = real(0);
     if (!L.walls || (yy >= 0 && yy < L.ny)) {
       const int m = node_at(L, x + ex(i), yy);
-      if (L.kind[m] == KIND_FLUID) v = lin[i * L.plane + m];
+      if (L.kind[m] == KIND_FLUID) v = lin[i * L.plane + m] + lrp[m];
     }
     lt[i] = v;
   }
@@ -356,19 +360,6 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adj_solid(Lattice<real> L, AdjBuf
     if (m & (1u << (i - 1))) atomicAdd(&Lrho[node_at(L, x + ex(i), y + ey(i))], real(wgt(i)) * v);
 }
 
-// ---- adj_final: the density's adjoint joins every population -------------------------------
-template <typename real>
-__global__ void __launch_bounds__(ADJ_BLOCK) k_adj_final(Lattice<real> L, AdjBuffers A) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-  if (x >= L.nx) return;
-  const int n = y * L.pitch + x;
-  if (L.kind[n] != KIND_FLUID) return;
-  real* lout = static_cast<real*>(A.lam_out);
-  const real lr = static_cast<const real*>(A.Lrho)[n];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) lout[i * L.plane + n] += lr;
-}
-
 // ---- set-up, objective, seeds ------------------------------------------------------------
 // bct bit 0: node may receive boundary contributions to its post-collision adjoint (x1 or x2 of
 // a cut link); bit 1: boundary node (local moment and force adjoints from its links)
@@ -406,9 +397,10 @@ __global__ void k_touch(Lattice<real> L, uint8_t* touch, int body) {
   touch[n] = t;
 }
 
-// Sums of the droplet objective over the fluid nodes of lattice `cur`:
-//   red[0] = sum (rho - rho_g), red[1] = sum (rho - rho_g) y,
-//   red[2] = sum over touching nodes of (rho - rho_g)/(rho_l - rho_g), red[3] = their number.
+// Sums of the droplet objective over the fluid nodes of lattice `cur`, one set per block
+// (red[4 b + k]; the host adds the blocks in order, so the result does not depend on timing):
+//   k = 0: sum (rho - rho_g), 1: sum (rho - rho_g) y,
+//   2: sum over touching nodes of (rho - rho_g)/(rho_l - rho_g), 3: their number.
 template <typename real>
 __global__ void k_objective_sums(Lattice<real> L, int cur, const uint8_t* touch, double* red, double rg, double rl) {
   __shared__ double sm[32];
@@ -427,11 +419,12 @@ __global__ void k_objective_sums(Lattice<real> L, int cur, const uint8_t* touch,
       s3 += 1.0;
     }
   }
+  double* out = red + 4 * blockIdx.x;
   double t;
-  t = block_sum(s0, sm); if (threadIdx.x == 0) atomicAdd(&red[0], t);
-  t = block_sum(s1, sm); if (threadIdx.x == 0) atomicAdd(&red[1], t);
-  t = block_sum(s2, sm); if (threadIdx.x == 0) atomicAdd(&red[2], t);
-  t = block_sum(s3, sm); if (threadIdx.x == 0) atomicAdd(&red[3], t);
+  t = block_sum(s0, sm); if (threadIdx.x == 0) out[0] = t;
+  t = block_sum(s1, sm); if (threadIdx.x == 0) out[1] = t;
+  t = block_sum(s2, sm); if (threadIdx.x == 0) out[2] = t;
+  t = block_sum(s3, sm); if (threadIdx.x == 0) out[3] = t;
 }
 
 // dJ/drho of the objective at every node (row-major nx x ny; zero off the fluid)
@@ -459,16 +452,18 @@ __global__ void k_adj_seed(Lattice<real> L, real* lam, const real* drho, const r
   for (int i = 0; i < 9; ++i) lam[i * L.plane + n] = fl ? g + (df ? df[i * dn + c] : real(0)) : real(0);
 }
 
-// lambda of the first state, row-major (9 arrays of nx x ny; zero off the fluid)
+// lambda of the first state (nine planes plus the density share), row-major (9 arrays of
+// nx x ny; zero off the fluid)
 template <typename real>
-__global__ void k_adj_export(Lattice<real> L, const real* lam, real* out) {
+__global__ void k_adj_export(Lattice<real> L, const real* lam, const real* Lrho, real* out) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x >= L.nx) return;
   const int n = y * L.pitch + x;
   const long long c = (long long)y * L.nx + x, dn = (long long)L.nx * L.ny;
   const bool fl = L.kind[n] == KIND_FLUID;
+  const real lr = fl ? Lrho[n] : real(0);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) out[i * dn + c] = fl ? lam[i * L.plane + n] : real(0);
+  for (int i = 0; i < 9; ++i) out[i * dn + c] = fl ? lam[i * L.plane + n] + lr : real(0);
 }
 
 // ---- launchers -------------------------------------------------------------------------------
@@ -485,14 +480,18 @@ cudaError_t adj_flags(const Lattice<real>& L, uint8_t* bct, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+unsigned objective_blocks(long long plane) {
+  const long long b = (plane + ADJ_BLOCK - 1) / ADJ_BLOCK;
+  return (unsigned)(b < (long long)mass_blocks() ? b : (long long)mass_blocks());
+}
+
 template <typename real>
 cudaError_t objective_sums(const Lattice<real>& L, int cur, int body, uint8_t* touch, double* red, double rg,
                            double rl, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(touch, 0, (size_t)L.plane, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(red, 0, 4 * sizeof(double), s);
   if (e != cudaSuccess) return e;
   if (L.n_bnodes > 0) k_touch<real><<<list_grid(L.n_bnodes), ADJ_BLOCK, 0, s>>>(L, touch, body);
-  k_objective_sums<real><<<mass_blocks(), ADJ_BLOCK, 0, s>>>(L, cur, touch, red, rg, rl);
+  k_objective_sums<real><<<objective_blocks(L.plane), ADJ_BLOCK, 0, s>>>(L, cur, touch, red, rg, rl);
   return cudaGetLastError();
 }
 
@@ -510,23 +509,21 @@ cudaError_t adj_seed(const Lattice<real>& L, real* lam, const real* drho, const 
 }
 
 template <typename real>
-cudaError_t adj_export(const Lattice<real>& L, const real* lam, real* out, cudaStream_t s) {
-  k_adj_export<real><<<adj_grid(L), ADJ_BLOCK, 0, s>>>(L, lam, out);
+cudaError_t adj_export(const Lattice<real>& L, const real* lam, const real* Lrho, real* out, cudaStream_t s) {
+  k_adj_export<real><<<adj_grid(L), ADJ_BLOCK, 0, s>>>(L, lam, Lrho, out);
   return cudaGetLastError();
 }
 
-// one reverse step: L.f[0] holds f^t; A.lam_in holds lambda^{t+1}; writes lambda^t to A.lam_out
+// One reverse step.  L.f[0] holds f^t and L.rho / L.mu the density and chemical potential of
+// step t; lambda^{t+1} is (A.lam_in, A.Lrho); leaves lambda^t as (A.lam_out, A.Lrho).
 template <typename real>
 cudaError_t adj_step(const Lattice<real>& L, const AdjBuffers& A, cudaStream_t s) {
-  cudaError_t e = launch_macro(L, 0, s);   // rho, solid rho, mu of step t
-  if (e != cudaSuccess) return e;
   if (L.n_bnodes > 0) k_adj_bc<real><<<list_grid(L.n_bnodes), ADJ_BLOCK, 0, s>>>(L, A);
   k_adj_collide<real><<<adj_grid(L), ADJ_BLOCK, 0, s>>>(L, A);
   k_adj_force<real><<<adj_grid(L), ADJ_BLOCK, 0, s>>>(L, A);
   k_adj_mu<real><<<adj_grid(L), ADJ_BLOCK, 0, s>>>(L, A);
   if (L.n_s2 > 0) k_adj_solid<real><<<list_grid(L.n_s2), ADJ_BLOCK, 0, s>>>(L, A, 2);
   if (L.n_s1 > 0) k_adj_solid<real><<<list_grid(L.n_s1), ADJ_BLOCK, 0, s>>>(L, A, 1);
-  k_adj_final<real><<<adj_grid(L), ADJ_BLOCK, 0, s>>>(L, A);
   return cudaGetLastError();
 }
 
@@ -537,7 +534,7 @@ cudaError_t adj_step(const Lattice<real>& L, const AdjBuffers& A, cudaStream_t s
   template cudaError_t objective_seed<real>(const Lattice<real>&, const uint8_t*, double, double, double, \
                                             real*, cudaStream_t);                                         \
   template cudaError_t adj_seed<real>(const Lattice<real>&, real*, const real*, const real*, cudaStream_t); \
-  template cudaError_t adj_export<real>(const Lattice<real>&, const real*, real*, cudaStream_t);          \
+  template cudaError_t adj_export<real>(const Lattice<real>&, const real*, const real*, real*, cudaStream_t); \
   template cudaError_t adj_step<real>(const Lattice<real>&, const AdjBuffers&, cudaStream_t);
 LBMGB_ADJ_INSTANTIATE(float)
 LBMGB_ADJ_INSTANTIATE(double)

@@ -125,6 +125,14 @@ struct lbm_ctx {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   lbm_status sticky = LBM_OK;
   std::string err;
+  // reverse sweeps of one segment, captured once per (workspace, spacing, length, parity)
+  struct AdjGraph {
+    const char* ws;
+    long long n, every, k;
+    int parity;
+    cudaGraphExec_t exec;
+  };
+  std::vector<AdjGraph> adj_graphs;
   // the last checkpointed forward pass (lbm_forward_checkpointed), for lbm_adjoint
   struct Tape {
     bool valid = false;
@@ -395,6 +403,8 @@ lbm_status lbm_build_links(lbm_ctx* c) {
   if (c->sticky != LBM_OK) return c->sticky;
   for (auto& gr : c->graph)
     if (gr) { cudaGraphExecDestroy(gr); gr = nullptr; }
+  for (auto& a : c->adj_graphs) cudaGraphExecDestroy(a.exec);
+  c->adj_graphs.clear();
   const Layout& y = c->lay;
   const lbm_config& g = c->cfg;
   char* w = c->ws;
@@ -678,6 +688,7 @@ void lbm_destroy(lbm_ctx* c) {
   if (!c) return;
   for (auto& g : c->graph)
     if (g) cudaGraphExecDestroy(g);
+  for (auto& a : c->adj_graphs) cudaGraphExecDestroy(a.exec);
   delete c;
 }
 
@@ -978,11 +989,12 @@ void lbm_batch_destroy(lbm_batch* b) {
 namespace {
 
 // Adjoint workspace: checkpoints of the populations and of the Eq. 18 carries at the start of
-// every segment of `every` steps, the recomputed states inside one segment, the adjoint
-// planes, and the snapshots that restore the forward state afterwards.
+// every segment of `every` steps; the states of one segment (its checkpoint copied to slot 0,
+// the recomputed ones after it) with the density and chemical-potential planes of each of its
+// steps; the adjoint planes; and the snapshots that restore the forward state afterwards.
 struct AdjLayout {
   long long n, every, nseg;
-  size_t ckpt, ckcarry, seg, lam0, lam1, lam_bc, lrj, lamF, Lmu, Lrho, bct, ring, ctr, carry, grad;
+  size_t ckpt, ckcarry, seg, segrho, segmu, lam0, lam1, lam_bc, lrj, lamF, Lmu, Lrho, bct, ring, ctr, carry, grad;
   size_t state;   // bytes of one population lattice (9 planes)
   size_t total;
 };
@@ -1002,7 +1014,9 @@ AdjLayout make_adj_layout(const lbm_ctx* c, long long n, long long every) {
   auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return at; };
   A.ckpt = take((size_t)A.nseg * A.state);
   A.ckcarry = take((size_t)A.nseg * (size_t)y.cap.bnodes * 8);
-  A.seg = take((size_t)(every - 1) * A.state);
+  A.seg = take((size_t)every * A.state);
+  A.segrho = take((size_t)every * pl);
+  A.segmu = take((size_t)every * pl);
   A.lam0 = take(9 * pl);
   A.lam1 = take(9 * pl);
   A.lam_bc = take(9 * pl);
@@ -1042,13 +1056,18 @@ lbm_status objective(lbm_ctx* c, const Lattice<real>& L, int body, double* J, vo
   const Layout& y = c->lay;
   // the lattice that the next step overwrites completely holds the scratch
   char* stage = c->ws + (c->cur ? y.fA : y.fB);
+  // touch flags, 4 partial sums per block and the seed fit in the 9 planes for any plane size
+  const size_t nred = 4 * (size_t)objective_blocks(y.plane);
   uint8_t* touch = (uint8_t*)stage;
   double* red = (double*)(stage + align_up((size_t)y.plane));
-  real* out = (real*)(stage + align_up((size_t)y.plane) + ALIGN);
+  real* out = (real*)(stage + align_up((size_t)y.plane) + align_up(nred * 8));
   CUDA_OK(c, objective_sums(L, c->cur, body, touch, red, c->eos.rho_g, c->eos.rho_l, c->stream));
-  double h[4];
-  CUDA_OK(c, cudaMemcpyAsync(h, red, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  std::vector<double> part(nred);
+  CUDA_OK(c, cudaMemcpyAsync(part.data(), red, nred * 8, cudaMemcpyDeviceToHost, c->stream));
   CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  double h[4] = {0, 0, 0, 0};
+  for (size_t b = 0; b < nred; b += 4)
+    for (int k = 0; k < 4; ++k) h[k] += part[b + k];
   if (!(h[0] != 0.0)) return fail(c, LBM_EINVAL, "no excess density: the objective is undefined");
   const double y_cm = h[1] / h[0];
   const double dphi = c->eos.rho_l - c->eos.rho_g;
@@ -1109,34 +1128,65 @@ lbm_status adjoint(lbm_ctx* c, const Lattice<real>& L, const void* drho, const v
   B.bct = (const uint8_t*)(w + A.bct);
   B.grad = (double*)(w + A.grad);
   B.n_cyl = c->cfg.n_cyl;
+  // the chemical potential of the solid layers is constant: every step's plane starts as a
+  // copy of the lattice's own plane, whose fluid values the recomputation overwrites
+  for (long long i = 0; i < A.every; ++i)
+    CUDA_OK(c, cudaMemcpyAsync(w + A.segmu + i * pl, L.mu, pl, cudaMemcpyDeviceToDevice, st));
+  CUDA_OK(c, cudaMemsetAsync(w + A.Lrho, 0, pl, st));
   int p = 0;
-  auto state = [&](long long s, long long i) -> real* {
-    return (real*)(i == 0 ? w + A.ckpt + s * A.state : w + A.seg + (i - 1) * A.state);
-  };
   for (long long s = A.nseg - 1; s >= 0; --s) {
     const long long k = s + 1 < A.nseg ? A.every : A.n - s * A.every;
-    // recompute the states of the segment from its checkpoint, carries included
+    CUDA_OK(c, cudaMemcpyAsync(w + A.seg, w + A.ckpt + s * A.state, 9 * pl, cudaMemcpyDeviceToDevice, st));
     if (c->n_bnodes > 0)
       CUDA_OK(c, cudaMemcpyAsync(L.carry, w + A.ckcarry + s * (size_t)y.cap.bnodes * 8, (size_t)c->n_bnodes * 8,
                                  cudaMemcpyDeviceToDevice, st));
-    Lattice<real> Lc = L;
-    for (long long i = 0; i + 1 < k; ++i) {
-      Lc.f[0] = state(s, i);
-      Lc.f[1] = state(s, i + 1);
-      CUDA_OK(c, launch_step(Lc, 0, st));
+    cudaGraphExec_t g = nullptr;
+    for (auto& a : c->adj_graphs)
+      if (a.ws == w && a.n == A.n && a.every == A.every && a.k == k && a.parity == p) g = a.exec;
+    if (!g) {
+      // recompute the segment's states (and each step's rho, mu) from slot 0, then run its
+      // reverse steps; captured once and replayed for every segment of this length and parity
+      cudaGraph_t gr;
+      CUDA_OK(c, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = cudaSuccess;
+      Lattice<real> Lc = L;
+      auto at = [&](long long i) {
+        Lc.f[0] = (real*)(w + A.seg + i * A.state);
+        Lc.f[1] = i + 1 < A.every ? (real*)(w + A.seg + (i + 1) * A.state) : nullptr;
+        Lc.rho = (real*)(w + A.segrho + i * pl);
+        Lc.mu = (real*)(w + A.segmu + i * pl);
+      };
+      for (long long i = 0; i + 1 < k && e == cudaSuccess; ++i) {
+        at(i);
+        e = launch_step(Lc, 0, st);
+      }
+      if (e == cudaSuccess) {
+        at(k - 1);
+        e = launch_macro(Lc, 0, st);
+      }
+      int pp = p;
+      for (long long i = k - 1; i >= 0 && e == cudaSuccess; --i) {
+        at(i);
+        Lc.f[1] = nullptr;
+        B.lam_in = lam[pp];
+        B.lam_out = lam[pp ^ 1];
+        e = adj_step(Lc, B, st);
+        pp ^= 1;
+      }
+      cudaError_t e2 = cudaStreamEndCapture(st, &gr);
+      if (e != cudaSuccess || e2 != cudaSuccess)
+        return fail(c, LBM_ECUDA, "reverse-sweep capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+      cudaError_t e3 = cudaGraphInstantiate(&g, gr, 0);
+      cudaGraphDestroy(gr);
+      if (e3 != cudaSuccess) return fail(c, LBM_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e3));
+      c->adj_graphs.push_back({w, A.n, A.every, k, p, g});
     }
-    for (long long i = k - 1; i >= 0; --i) {
-      Lc.f[0] = state(s, i);
-      Lc.f[1] = nullptr;
-      B.lam_in = lam[p];
-      B.lam_out = lam[p ^ 1];
-      CUDA_OK(c, adj_step(Lc, B, st));
-      p ^= 1;
-    }
+    CUDA_OK(c, cudaGraphLaunch(g, st));
+    p ^= (int)(k & 1);
   }
   if (df0) {
     real* dst = on_device ? (real*)df0 : (real*)(w + A.lam_bc);
-    CUDA_OK(c, adj_export(L, lam[p], dst, st));
+    CUDA_OK(c, adj_export(L, lam[p], (const real*)(w + A.Lrho), dst, st));
     if (!on_device) CUDA_OK(c, cudaMemcpyAsync(df0, dst, 9 * dn * y.sz, cudaMemcpyDeviceToHost, st));
   }
   std::vector<double> g(3 * c->cfg.n_cyl + 1);

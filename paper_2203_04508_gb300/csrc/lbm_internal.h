@@ -84,11 +84,14 @@ struct AdjBuffers {
   void* lrj;            // 3 planes: dJ/d(delta rho, jx, jy) of the link rule at boundary nodes
   void* lamF;           // 2 planes: dJ/dF (zero off the fluid)
   void* Lmu;            // dJ/dmu
-  void* Lrho;           // dJ/drho (the density plane)
+  void* Lrho;           // dJ/drho (the density plane); between steps the density share of lambda
   const uint8_t* bct;   // per node: bit 0 lam_bc may be non-zero, bit 1 boundary node
   double* grad;         // dJ/d dmu per cylinder, dJ/d dmu of the walls, dJ/d(cx, cy) per cylinder
   int n_cyl;
 };
+// blocks of the objective's reduction over a plane of `plane` nodes (at most one per 256
+// nodes): it leaves 4 partial sums per block in `red`
+unsigned objective_blocks(long long plane);
 template <typename real> cudaError_t adj_flags(const Lattice<real>& L, uint8_t* bct, cudaStream_t s);
 template <typename real>
 cudaError_t objective_sums(const Lattice<real>& L, int cur, int body, uint8_t* touch, double* red, double rg,
@@ -98,7 +101,8 @@ cudaError_t objective_seed(const Lattice<real>& L, const uint8_t* touch, double 
                            real* out, cudaStream_t s);
 template <typename real>
 cudaError_t adj_seed(const Lattice<real>& L, real* lam, const real* drho, const real* df, cudaStream_t s);
-template <typename real> cudaError_t adj_export(const Lattice<real>& L, const real* lam, real* out, cudaStream_t s);
+template <typename real>
+cudaError_t adj_export(const Lattice<real>& L, const real* lam, const real* Lrho, real* out, cudaStream_t s);
 template <typename real> cudaError_t adj_step(const Lattice<real>& L, const AdjBuffers& A, cudaStream_t s);
 
 // ---- EOS on the host (lbm_eos.cpp)
