@@ -162,7 +162,7 @@ def measured_peak():
 
 def collide_source_hash():
     h = hashlib.sha256()
-    for f in ("lbm_step.cu", "lbm_device.cuh"):
+    for f in ("lbm_step.cu", "lbm_device.cuh", "lbm_phases.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2203_04508_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

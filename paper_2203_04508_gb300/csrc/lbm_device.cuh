@@ -138,8 +138,21 @@ struct Stencil {
   int xm2, xm1, xp1, xp2, ym2, ym1, yp1, yp2;
 };
 template <typename real>
+__device__ __forceinline__ bool interior(const Lattice<real>& L, int x, int y) {
+  // no periodic wrap within two nodes (with walls the rows never wrap: fluid nodes keep two
+  // solid rows below and above them)
+  return x >= 2 && x < L.nx - 2 && (L.walls || (y >= 2 && y < L.ny - 2));
+}
+
+template <typename real>
 __device__ __forceinline__ Stencil stencil_at(const Lattice<real>& L, int x, int y) {
   Stencil s;
+  if (interior(L, x, y)) {
+    const int n = y * L.pitch + x, p = L.pitch;
+    s.xm2 = n - 2; s.xm1 = n - 1; s.xp1 = n + 1; s.xp2 = n + 2;
+    s.ym2 = n - 2 * p; s.ym1 = n - p; s.yp1 = n + p; s.yp2 = n + 2 * p;
+    return s;
+  }
   const int row = y * L.pitch;
   s.xm2 = row + wrap_x(L, x - 2);
   s.xm1 = row + wrap_x(L, x - 1);

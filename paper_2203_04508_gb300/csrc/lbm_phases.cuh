@@ -69,10 +69,13 @@ __device__ __forceinline__ void phase_collide(const Lattice<real>& L, int cur, i
   real Fx, Fy;
   force_at(L, x, y, r, Fx, Fy);
   collide_node(L, fl, r, drho, jx, jy, Fx, Fy);
-  const int xm = wrap_x(L, x - 1), xp = wrap_x(L, x + 1);
-  const int rowc = y * L.pitch;
-  const int rowm = wrap_y(L, y - 1) * L.pitch;
-  const int rowp = wrap_y(L, y + 1) * L.pitch;
+  int xm = x - 1, xp = x + 1, rowc = y * L.pitch, rowm = rowc - L.pitch, rowp = rowc + L.pitch;
+  if (!interior(L, x, y)) {
+    xm = wrap_x(L, x - 1);
+    xp = wrap_x(L, x + 1);
+    rowm = wrap_y(L, y - 1) * L.pitch;
+    rowp = wrap_y(L, y + 1) * L.pitch;
+  }
   fout[0 * L.plane + n] = fl[0];
   fout[1 * L.plane + rowc + xp] = fl[1];
   fout[2 * L.plane + rowp + x] = fl[2];
