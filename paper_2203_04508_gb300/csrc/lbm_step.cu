@@ -1,7 +1,7 @@
 // Kernels of one time step and of the state set-up / read-out (sm_103a).
 //
 // One step is five launches on one stream:
-//   k_rho           density of every fluid node from the 9 offset populations   (Sec. 2.1)
+//   k_rho_vec       density of every fluid node from the 9 offset populations   (Sec. 2.1)
 //   k_solid (x2)    densities of the first, then second solid layer             (Eq. 15)
 //   k_mu            chemical potential at fluid nodes                            (Eq. 12)
 //   k_collide       force (Eq. 9) + collision (Eq. 4) + exact-difference forcing (Eq. 13)
@@ -30,11 +30,40 @@ __device__ __forceinline__ bool node_of_thread(const Lattice<real>& L, int& x, i
   return x < L.nx && y < L.ny;
 }
 
+// Density pass with 16-byte loads: each thread takes V = 16/sizeof(real) consecutive nodes of
+// a row (rows start on 128-byte boundaries, so every vector is aligned) and stores density_of
+// of each fluid node -- the values phase_rho stores, with more bytes in flight per thread.
+template <typename real> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int V = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int V = 2; };
+
 template <typename real>
-__global__ void __launch_bounds__(NODE_BLOCK) k_rho(Lattice<real> L, int cur) {
-  int x, y, n;
-  if (!node_of_thread(L, x, y, n)) return;
-  phase_rho(L, cur, x, y);
+__device__ __forceinline__ real lane_of(const typename Vec16<real>::type& v, int k);
+template <> __device__ __forceinline__ float lane_of<float>(const float4& v, int k) {
+  return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+template <> __device__ __forceinline__ double lane_of<double>(const double2& v, int k) { return k == 0 ? v.x : v.y; }
+
+template <typename real>
+__global__ void __launch_bounds__(NODE_BLOCK) k_rho_vec(Lattice<real> L, int cur) {
+  using VT = typename Vec16<real>::type;
+  constexpr int V = Vec16<real>::V;
+  const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * V, y = blockIdx.y;
+  if (x0 >= L.nx) return;
+  const int n0 = y * L.pitch + x0;
+  const real* __restrict__ f = L.f[cur];
+  VT fv[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) fv[i] = __ldg(reinterpret_cast<const VT*>(f + i * L.plane + n0));
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    if (x0 + k < L.nx && L.kind[n0 + k] == KIND_FLUID) {
+      real fl[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) fl[i] = lane_of<real>(fv[i], k);
+      L.rho[n0 + k] = density_of(L, fl);
+    }
+  }
 }
 
 template <typename real>
@@ -224,11 +253,16 @@ static inline dim3 node_grid(const Lattice<real>& L) {
   return dim3((unsigned)((L.nx + TILE_X - 1) / TILE_X), (unsigned)((L.ny + TILE_Y - 1) / TILE_Y));
 }
 static inline dim3 node_block() { return dim3(TILE_X, TILE_Y); }
+template <typename real>
+static inline dim3 rho_grid(const Lattice<real>& L) {
+  const int nv = (L.nx + Vec16<real>::V - 1) / Vec16<real>::V;
+  return dim3((unsigned)((nv + NODE_BLOCK - 1) / NODE_BLOCK), (unsigned)L.ny);
+}
 
 template <typename real>
 cudaError_t launch_step(const Lattice<real>& L, int cur, cudaStream_t s) {
   const unsigned gn = grid_for(L.plane, NODE_BLOCK);
-  k_rho<real><<<node_grid(L), node_block(), 0, s>>>(L, cur);
+  k_rho_vec<real><<<rho_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
   if (L.n_s1 > 0) k_solid<real><<<grid_for(L.n_s1, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 1);
   if (L.n_s2 > 0) k_solid<real><<<grid_for(L.n_s2, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 2);
   if (L.eos != EOS_NONE) k_mu<real><<<node_grid(L), node_block(), 0, s>>>(L);
@@ -244,7 +278,7 @@ template <typename real>
 cudaError_t launch_phase(const Lattice<real>& L, int cur, int phase, cudaStream_t s) {
   const unsigned gn = grid_for(L.plane, NODE_BLOCK);
   switch (phase) {
-    case 0: k_rho<real><<<node_grid(L), node_block(), 0, s>>>(L, cur); break;
+    case 0: k_rho_vec<real><<<rho_grid(L), NODE_BLOCK, 0, s>>>(L, cur); break;
     case 1:
       if (L.n_s1 > 0) k_solid<real><<<grid_for(L.n_s1, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 1);
       if (L.n_s2 > 0) k_solid<real><<<grid_for(L.n_s2, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 2);
@@ -268,7 +302,7 @@ int launches_per_step(const Lattice<real>& L) {
 template <typename real>
 cudaError_t launch_macro(const Lattice<real>& L, int cur, cudaStream_t s) {
   const unsigned gn = grid_for(L.plane, NODE_BLOCK);
-  k_rho<real><<<node_grid(L), node_block(), 0, s>>>(L, cur);
+  k_rho_vec<real><<<rho_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
   if (L.n_s1 > 0) k_solid<real><<<grid_for(L.n_s1, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 1);
   if (L.n_s2 > 0) k_solid<real><<<grid_for(L.n_s2, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 2);
   if (L.eos != EOS_NONE) k_mu<real><<<node_grid(L), node_block(), 0, s>>>(L);
