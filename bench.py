@@ -280,8 +280,9 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=4000,
                     help="steps of the gradient workload (0: skip it)")
     ap.add_argument("--adjoint-every", type=int, default=200)
-    ap.add_argument("--mode", default="full", choices=["full", "kernels"],
-                    help="kernels: only warm-up and timed steps (for profiler captures)")
+    ap.add_argument("--mode", default="full", choices=["full", "kernels", "adjoint"],
+                    help="kernels: only warm-up and timed steps; adjoint: only the gradient "
+                         "workload (both for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -303,6 +304,9 @@ def main():
     if world > 1:
         dist.barrier()
     G.load()
+    if args.mode == "adjoint":
+        print(json.dumps({"mode": "adjoint", **run_adjoint(G, torch, args.adjoint_steps, args.adjoint_every)}))
+        return
 
     sc, wname = workload(args.workload)
     lat = G.Lattice(sc.physics(), precision=G.LBM_FP32)

@@ -218,7 +218,8 @@ lbm_status lbm_set_populations(lbm_ctx* ctx, const void* f, int32_t on_device);
 
 /* Bytes of device workspace for a checkpointed forward pass of n_steps steps with a
  * checkpoint every `every` steps (0: ceil(sqrt(n_steps))).  The workspace holds
- * ceil(n_steps/every) + every - 1 population lattices plus 27 planes of adjoint state. */
+ * ceil(n_steps/every) + every + 1 population lattices plus 2 every + 34 planes (the density
+ * and chemical potential of each step of a segment, and the adjoint state). */
 lbm_status lbm_adjoint_workspace_size(lbm_ctx* ctx, int64_t n_steps, int64_t every, size_t* bytes);
 
 /* Advances n_steps like lbm_step, storing a checkpoint (populations and Eq. 18 carries) at

@@ -7,7 +7,8 @@
 // share of dJ/d(wall chemical potential) and dJ/d(cylinder centre) (the centre enters only
 // through the cut fractions q: |x1 + q e - c|^2 = r^2 gives dq/dc = p / (p . e) with
 // p = x1 + q e - c).  The reverse phases run in the opposite order of the forward ones:
-//   adj_bc      links and Eq. 18 (per boundary node; recomputes the collisions it needs)
+//   adj_bc      links and Eq. 18 (per boundary node; the post-collision values a, b2, c the
+//               links used are read back from f^{t+1}, where the step left them)
 //   adj_collide streaming (pulled) + collision + forcing, per fluid node
 //   adj_force   Eq. 9: the force's dependence on mu and rho at the stencil neighbours (gather)
 //   adj_mu      Eq. 12: mu's dependence on rho (gather); wall mu -> dJ/d(offset)
@@ -26,14 +27,6 @@ constexpr int ADJ_BLOCK = 256;
 template <typename real>
 __device__ __forceinline__ bool is_field_node(uint8_t k) {
   return k == KIND_FLUID || k == KIND_SOLID1 || k == KIND_SOLID2;
-}
-
-// value of a plane at (x + dx, y + dy), zero outside a walled domain
-template <typename real, typename T>
-__device__ __forceinline__ T plane_at(const Lattice<real>& L, const T* p, int x, int y, int dx, int dy) {
-  int yy = y + dy;
-  if (L.walls && (yy < 0 || yy >= L.ny)) return T(0);
-  return p[node_at(L, x + dx, yy)];
 }
 
 // dpsi'/drho = (dp0/drho) / rho (Eq. 7)
@@ -138,10 +131,10 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adj_bc(Lattice<real> L, AdjBuffer
   real* lbc = static_cast<real*>(A.lam_bc);
   real f[9], r, drho, jx, jy, Fx, Fy;
   node_state(L, x, y, f, r, drho, jx, jy, Fx, Fy);
-  real ft[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) ft[i] = f[i];
-  collide_node(L, ft, r, drho, jx, jy, Fx, Fy);
+  // f^{t+1} holds the post-collision values the links used: a = f~_i(x1) parked in the solid
+  // node's slot, b2 = f~_i(x2) streamed into x1, c = f~_ibar(x1) streamed into x2 (the link
+  // phase overwrites none of them where they are used)
+  const real* __restrict__ fn = L.f[1];
   const bool comp = L.bc == BC_PRESENT || L.bc == BC_MIBC;
   const real wF = L.bc == BC_PRESENT ? real(1) : real(0);
   const real l0 = comp ? lin[n] + lrn : real(0);
@@ -152,7 +145,8 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adj_bc(Lattice<real> L, AdjBuffer
     const int ib = opp(i);
     const real q = L.lq[l];
     const int x2 = node_at(L, x - ex(i), y - ey(i));
-    const real a = ft[i], c = ft[ib];
+    const int xs = node_at(L, x + ex(i), y + ey(i));
+    const real a = fn[i * L.plane + xs], c = fn[ib * L.plane + x2];
     const real exi = real(ex(i)), eyi = real(ey(i));
     const real eF = exi * Fx + eyi * Fy, ej = exi * jx + eyi * jy, eJ = ej + eF;
     const real Jx = jx + Fx, Jy = jy + Fy;
@@ -163,15 +157,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adj_bc(Lattice<real> L, AdjBuffer
     if (L.bc == BC_HBB || (q < real(0.5) && !L.lx2f[l])) {
       dA = 1;
     } else if (q < real(0.5)) {
-      // f~_i(x2): the collision at x2
-      real g[9], r2, d2, jx2, jy2, Fx2, Fy2;
-      const int xx2 = x2 % L.pitch, yy2 = x2 / L.pitch;
-      node_state(L, xx2, yy2, g, r2, d2, jx2, jy2, Fx2, Fy2);
-      collide_node(L, g, r2, d2, jx2, jy2, Fx2, Fy2);
-      real b2 = g[0];
-#pragma unroll
-      for (int k = 1; k < 9; ++k)
-        if (k == i) b2 = g[k];
+      const real b2 = fn[i * L.plane + n];
       dA = real(2) * q;
       dB = real(1) - real(2) * q;
       dF = wF * (real(1) - real(2) * q);
@@ -197,7 +183,6 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adj_bc(Lattice<real> L, AdjBuffer
       lrho -= w * (real(4.5) * (eJ * eJ - ej * ej) - real(1.5) * ((Jx * Jx + Jy * Jy) - (jx * jx + jy * jy))) * ir * ir;
     }
     // dJ/dq -> dJ/dc of the cylinder this link cuts
-    const int xs = node_at(L, x + ex(i), y + ey(i));
     const int bd = L.body[xs];
     if (bd >= 0 && bd < A.n_cyl && dQ != real(0)) {
       const double gq = (double)dQ * (double)lR;
@@ -285,16 +270,29 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adj_force(Lattice<real> L, AdjBuf
   real lm = 0, lr = 0;
   if (L.eos != EOS_NONE) {
     // gradient coefficients c_{+1} = 8/12, c_{+2} = -1/12, c_{-d} = -c_d; the neighbour m - d
-    // sees this node at offset +d
+    // sees this node at offset +d.  Only fluid neighbours carry a force (and so dJ/dF); the
+    // density plane holds no value at deep solid nodes, so they are skipped, not multiplied
+    // by zero.
     const real c1 = real(8.0 / 12.0), c2 = real(-1.0 / 12.0), cs2 = real(1.0 / 3.0);
     const int dd[4] = {1, -1, 2, -2};
     const real cc[4] = {c1, -c1, c2, -c2};
 #pragma unroll
     for (int k2 = 0; k2 < 4; ++k2) {
-      const real lx = plane_at(L, lF, x, y, -dd[k2], 0), rx = plane_at(L, L.rho, x, y, -dd[k2], 0);
-      const real ly = plane_at(L, lFy, x, y, 0, -dd[k2]), ry = plane_at(L, L.rho, x, y, 0, -dd[k2]);
-      lm -= cc[k2] * (rx * lx + ry * ly);
-      lr += cs2 * cc[k2] * (lx + ly);
+      const int yy = y - dd[k2];
+      if (!L.walls || (yy >= 0 && yy < L.ny)) {
+        const int m = node_at(L, x, yy);
+        if (L.kind[m] == KIND_FLUID) {
+          const real ly = lFy[m];
+          lm -= cc[k2] * (L.rho[m] * ly);
+          lr += cs2 * cc[k2] * ly;
+        }
+      }
+      const int mx = node_at(L, x - dd[k2], y);
+      if (L.kind[mx] == KIND_FLUID) {
+        const real lx = lF[mx];
+        lm -= cc[k2] * (L.rho[mx] * lx);
+        lr += cs2 * cc[k2] * lx;
+      }
     }
   }
   if (k == KIND_FLUID) {

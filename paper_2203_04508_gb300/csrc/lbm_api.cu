@@ -125,14 +125,18 @@ struct lbm_ctx {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   lbm_status sticky = LBM_OK;
   std::string err;
-  // reverse sweeps of one segment, captured once per (workspace, spacing, length, parity)
+  // one segment's recomputation (kind 0) or reverse steps (kind 1), captured once per
+  // (workspace, steps, spacing, kind, buffer, length, parity)
   struct AdjGraph {
     const char* ws;
     long long n, every, k;
-    int parity;
+    int kind, buf, parity;
     cudaGraphExec_t exec;
   };
   std::vector<AdjGraph> adj_graphs;
+  // second stream and events of the reverse sweep (created on its first use)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_rec[2] = {nullptr, nullptr}, ev_rev[2] = {nullptr, nullptr};
   // the last checkpointed forward pass (lbm_forward_checkpointed), for lbm_adjoint
   struct Tape {
     bool valid = false;
@@ -689,6 +693,9 @@ void lbm_destroy(lbm_ctx* c) {
   for (auto& g : c->graph)
     if (g) cudaGraphExecDestroy(g);
   for (auto& a : c->adj_graphs) cudaGraphExecDestroy(a.exec);
+  for (cudaEvent_t e : {c->ev_start, c->ev_rec[0], c->ev_rec[1], c->ev_rev[0], c->ev_rev[1]})
+    if (e) cudaEventDestroy(e);
+  if (c->aux) cudaStreamDestroy(c->aux);
   delete c;
 }
 
@@ -989,9 +996,10 @@ void lbm_batch_destroy(lbm_batch* b) {
 namespace {
 
 // Adjoint workspace: checkpoints of the populations and of the Eq. 18 carries at the start of
-// every segment of `every` steps; the states of one segment (its checkpoint copied to slot 0,
-// the recomputed ones after it) with the density and chemical-potential planes of each of its
-// steps; the adjoint planes; and the snapshots that restore the forward state afterwards.
+// every segment of `every` steps; two sets of segment buffers -- the states of one segment
+// (its checkpoint copied to slot 0, the k recomputed ones in slots 1..k) with the density and
+// chemical-potential planes of each of its steps; the adjoint planes; and the snapshots that
+// restore the forward state afterwards.
 struct AdjLayout {
   long long n, every, nseg;
   size_t ckpt, ckcarry, seg, segrho, segmu, lam0, lam1, lam_bc, lrj, lamF, Lmu, Lrho, bct, ring, ctr, carry, grad;
@@ -1014,9 +1022,10 @@ AdjLayout make_adj_layout(const lbm_ctx* c, long long n, long long every) {
   auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return at; };
   A.ckpt = take((size_t)A.nseg * A.state);
   A.ckcarry = take((size_t)A.nseg * (size_t)y.cap.bnodes * 8);
-  A.seg = take((size_t)every * A.state);
-  A.segrho = take((size_t)every * pl);
-  A.segmu = take((size_t)every * pl);
+  // two sets of segment buffers: one is recomputed while the other is swept backwards
+  A.seg = take(2 * (size_t)(every + 1) * A.state);
+  A.segrho = take(2 * (size_t)every * pl);
+  A.segmu = take(2 * (size_t)every * pl);
   A.lam0 = take(9 * pl);
   A.lam1 = take(9 * pl);
   A.lam_bc = take(9 * pl);
@@ -1128,60 +1137,114 @@ lbm_status adjoint(lbm_ctx* c, const Lattice<real>& L, const void* drho, const v
   B.bct = (const uint8_t*)(w + A.bct);
   B.grad = (double*)(w + A.grad);
   B.n_cyl = c->cfg.n_cyl;
+  // Pipeline: the recomputation of segment s-1 (second stream) overlaps the reverse steps of
+  // segment s (the context's stream); the two use alternate buffer sets.  Events order each
+  // buffer's reuse: a set is recomputed only after the reverse steps that read it are done.
+  if (!c->aux) {
+    CUDA_OK(c, cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+    for (cudaEvent_t* e : {&c->ev_start, &c->ev_rec[0], &c->ev_rec[1], &c->ev_rev[0], &c->ev_rev[1]})
+      CUDA_OK(c, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  }
+  cudaStream_t aux = c->aux;
+  auto seg_at = [&](int buf, long long i) { return w + A.seg + ((size_t)buf * (A.every + 1) + i) * A.state; };
+  auto rho_at = [&](int buf, long long i) { return w + A.segrho + ((size_t)buf * A.every + i) * pl; };
+  auto mu_at = [&](int buf, long long i) { return w + A.segmu + ((size_t)buf * A.every + i) * pl; };
+  auto seg_len = [&](long long s) { return s + 1 < A.nseg ? A.every : A.n - s * A.every; };
   // the chemical potential of the solid layers is constant: every step's plane starts as a
   // copy of the lattice's own plane, whose fluid values the recomputation overwrites
-  for (long long i = 0; i < A.every; ++i)
-    CUDA_OK(c, cudaMemcpyAsync(w + A.segmu + i * pl, L.mu, pl, cudaMemcpyDeviceToDevice, st));
+  for (int buf = 0; buf < 2; ++buf)
+    for (long long i = 0; i < A.every; ++i)
+      CUDA_OK(c, cudaMemcpyAsync(mu_at(buf, i), L.mu, pl, cudaMemcpyDeviceToDevice, st));
   CUDA_OK(c, cudaMemsetAsync(w + A.Lrho, 0, pl, st));
-  int p = 0;
-  for (long long s = A.nseg - 1; s >= 0; --s) {
-    const long long k = s + 1 < A.nseg ? A.every : A.n - s * A.every;
-    CUDA_OK(c, cudaMemcpyAsync(w + A.seg, w + A.ckpt + s * A.state, 9 * pl, cudaMemcpyDeviceToDevice, st));
-    if (c->n_bnodes > 0)
-      CUDA_OK(c, cudaMemcpyAsync(L.carry, w + A.ckcarry + s * (size_t)y.cap.bnodes * 8, (size_t)c->n_bnodes * 8,
-                                 cudaMemcpyDeviceToDevice, st));
-    cudaGraphExec_t g = nullptr;
+
+  // the graphs the sweep needs, captured before any of them runs
+  auto find = [&](int kind, int buf, long long k, int par) -> cudaGraphExec_t {
     for (auto& a : c->adj_graphs)
-      if (a.ws == w && a.n == A.n && a.every == A.every && a.k == k && a.parity == p) g = a.exec;
-    if (!g) {
-      // recompute the segment's states (and each step's rho, mu) from slot 0, then run its
-      // reverse steps; captured once and replayed for every segment of this length and parity
-      cudaGraph_t gr;
-      CUDA_OK(c, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e = cudaSuccess;
-      Lattice<real> Lc = L;
-      auto at = [&](long long i) {
-        Lc.f[0] = (real*)(w + A.seg + i * A.state);
-        Lc.f[1] = i + 1 < A.every ? (real*)(w + A.seg + (i + 1) * A.state) : nullptr;
-        Lc.rho = (real*)(w + A.segrho + i * pl);
-        Lc.mu = (real*)(w + A.segmu + i * pl);
-      };
-      for (long long i = 0; i + 1 < k && e == cudaSuccess; ++i) {
+      if (a.ws == w && a.n == A.n && a.every == A.every && a.kind == kind && a.buf == buf && a.k == k &&
+          a.parity == par)
+        return a.exec;
+    return nullptr;
+  };
+  auto capture = [&](int kind, int buf, long long k, int par) -> lbm_status {
+    if (find(kind, buf, k, par)) return LBM_OK;
+    cudaGraph_t gr;
+    CUDA_OK(c, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    Lattice<real> Lc = L;
+    auto at = [&](long long i) {
+      Lc.f[0] = (real*)seg_at(buf, i);
+      Lc.f[1] = (real*)seg_at(buf, i + 1);
+      Lc.rho = (real*)rho_at(buf, i);
+      Lc.mu = (real*)mu_at(buf, i);
+    };
+    if (kind == 0) {
+      // the segment's states (and each step's rho, mu) from slot 0
+      for (long long i = 0; i < k && e == cudaSuccess; ++i) {
         at(i);
         e = launch_step(Lc, 0, st);
       }
-      if (e == cudaSuccess) {
-        at(k - 1);
-        e = launch_macro(Lc, 0, st);
-      }
-      int pp = p;
+    } else {
+      // its reverse steps: step i reads f^i from slot i and the values its links used from
+      // slot i+1
+      int pp = par;
       for (long long i = k - 1; i >= 0 && e == cudaSuccess; --i) {
         at(i);
-        Lc.f[1] = nullptr;
-        B.lam_in = lam[pp];
-        B.lam_out = lam[pp ^ 1];
-        e = adj_step(Lc, B, st);
+        AdjBuffers Bi = B;
+        Bi.lam_in = lam[pp];
+        Bi.lam_out = lam[pp ^ 1];
+        e = adj_step(Lc, Bi, st);
         pp ^= 1;
       }
-      cudaError_t e2 = cudaStreamEndCapture(st, &gr);
-      if (e != cudaSuccess || e2 != cudaSuccess)
-        return fail(c, LBM_ECUDA, "reverse-sweep capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
-      cudaError_t e3 = cudaGraphInstantiate(&g, gr, 0);
-      cudaGraphDestroy(gr);
-      if (e3 != cudaSuccess) return fail(c, LBM_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e3));
-      c->adj_graphs.push_back({w, A.n, A.every, k, p, g});
     }
-    CUDA_OK(c, cudaGraphLaunch(g, st));
+    cudaError_t e2 = cudaStreamEndCapture(st, &gr);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+      return fail(c, LBM_ECUDA, "reverse-sweep capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    cudaGraphExec_t g = nullptr;
+    cudaError_t e3 = cudaGraphInstantiate(&g, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e3 != cudaSuccess) return fail(c, LBM_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e3));
+    c->adj_graphs.push_back({w, A.n, A.every, k, kind, buf, par, g});
+    return LBM_OK;
+  };
+  {
+    int p = 0;
+    for (long long s = A.nseg - 1; s >= 0; --s) {
+      const long long k = seg_len(s);
+      lbm_status r1 = capture(0, (int)(s & 1), k, 0);
+      if (r1 != LBM_OK) return r1;
+      lbm_status r2 = capture(1, (int)(s & 1), k, p);
+      if (r2 != LBM_OK) return r2;
+      p ^= (int)(k & 1);
+    }
+  }
+  // recomputation of segment s into buffer set s & 1, on the second stream
+  auto recompute = [&](long long s) -> lbm_status {
+    const int buf = (int)(s & 1);
+    CUDA_OK(c, cudaMemcpyAsync(seg_at(buf, 0), w + A.ckpt + s * A.state, 9 * pl, cudaMemcpyDeviceToDevice, aux));
+    if (c->n_bnodes > 0)
+      CUDA_OK(c, cudaMemcpyAsync(L.carry, w + A.ckcarry + s * (size_t)y.cap.bnodes * 8, (size_t)c->n_bnodes * 8,
+                                 cudaMemcpyDeviceToDevice, aux));
+    CUDA_OK(c, cudaGraphLaunch(find(0, buf, seg_len(s), 0), aux));
+    CUDA_OK(c, cudaEventRecord(c->ev_rec[buf], aux));
+    return LBM_OK;
+  };
+  CUDA_OK(c, cudaEventRecord(c->ev_start, st));
+  CUDA_OK(c, cudaStreamWaitEvent(aux, c->ev_start, 0));
+  lbm_status rs = recompute(A.nseg - 1);
+  if (rs != LBM_OK) return rs;
+  int p = 0;
+  for (long long s = A.nseg - 1; s >= 0; --s) {
+    const int buf = (int)(s & 1);
+    const long long k = seg_len(s);
+    if (s >= 1) {
+      // buffer set buf^1 was last read by the reverse steps of segment s+1
+      if (s + 1 < A.nseg) CUDA_OK(c, cudaStreamWaitEvent(aux, c->ev_rev[buf ^ 1], 0));
+      rs = recompute(s - 1);
+      if (rs != LBM_OK) return rs;
+    }
+    CUDA_OK(c, cudaStreamWaitEvent(st, c->ev_rec[buf], 0));
+    CUDA_OK(c, cudaGraphLaunch(find(1, buf, k, p), st));
+    CUDA_OK(c, cudaEventRecord(c->ev_rev[buf], st));
     p ^= (int)(k & 1);
   }
   if (df0) {
