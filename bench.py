@@ -61,12 +61,13 @@ def shard_instances(sizes, world):
     return [sorted(v) for v in out]
 
 
-def run_batched(G, torch, rank, world, steps):
-    """Batched workload: seed-random droplet-on-cylinder instances of 128^2..768^2, advanced
-    together by the persistent kernel (one launch for all steps), against the same instances
-    each advanced by its own lbm_step graph launches one after another."""
+def run_batched(G, torch, rank, world, steps, small=False):
+    """Batched workload: seed-random droplet-on-cylinder instances of 128^2..768^2 (small:
+    1024 instances of 64^2..128^2), advanced together by the persistent kernel (one launch for
+    all steps), against the same instances each advanced by its own lbm_step graph launches,
+    issued one lattice after another (each lattice has its own stream)."""
     import scenarios as S
-    scs = S.c4_batch()
+    scs = S.c4_batch(seed=5, n=1024, nmin=64, nmax=128) if small else S.c4_batch()
     mine = shard_instances([sc.nodes for sc in scs], world)[rank]
     scs = [scs[k] for k in mine]
     nodes = sum(sc.nodes for sc in scs)
@@ -399,6 +400,8 @@ def main():
     batched = None
     if args.batch_steps > 0:
         batched = run_batched(G, torch, rank, world, args.batch_steps)
+        # many small lattices, where one persistent launch replaces thousands of launches
+        small = run_batched(G, torch, rank, world, args.batch_steps, small=True) if world == 1 else None
         if world > 1:
             t = torch.tensor([batched["ms_batched"], batched["ms_looped"]], device="cuda", dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -409,6 +412,10 @@ def main():
                            mlups_batched=round(float(nn.item()) * steps_b / float(t[0]) / 1e3, 1),
                            mlups_looped=round(float(nn.item()) * steps_b / float(t[1]) / 1e3, 1),
                            speedup=round(float(t[1]) / float(t[0]), 3), instances=256)
+        if small is not None:
+            batched["small_instances"] = {k: small[k] for k in ("instances", "nodes", "ms_batched", "mlups_batched",
+                                                                 "ms_looped", "mlups_looped", "speedup")}
+            batched["small_instances"]["sizes"] = "64^2..128^2"
 
     adjoint = None
     if args.adjoint_steps > 0:

@@ -751,7 +751,7 @@ lbm_status plan_batch(int n, const lbm_config* cfgs, BatchPlan* P, char* msg) {
     P->bytes[k] = L.total;
     o = align_up(o + L.total);
     const int bb = batch_block_size();
-    P->cap_tiles += (L.plane + bb - 1) / bb;
+    P->cap_tiles += batch_node_tiles(cfgs[k].nx, cfgs[k].ny);
     P->cap_s1 += (L.cap.s1 + bb - 1) / bb;
     P->cap_s2 += (L.cap.s2 + bb - 1) / bb;
     P->cap_bc += (L.cap.bnodes + bb - 1) / bb;
@@ -799,7 +799,8 @@ lbm_status batch_tables(lbm_batch* b) {
     const Lattice<real>& L = b->fp64 ? *reinterpret_cast<const Lattice<real>*>(&b->ctx[k]->Ld)
                                      : *reinterpret_cast<const Lattice<real>*>(&b->ctx[k]->Lf);
     lats[k] = L;
-    for (long long n0 = 0; n0 < L.plane; n0 += bb) tiles.push_back(make_int2(k, (int)n0));
+    const long long nt = batch_node_tiles(L.nx, L.ny);
+    for (long long t = 0; t < nt; ++t) tiles.push_back(make_int2(k, (int)t));
     for (int j = 0; j < L.n_s1; j += bb) s1.push_back(make_int2(k, j));
     for (int j = 0; j < L.n_s2; j += bb) s2.push_back(make_int2(k, j));
     first[k] = (int)bc.size();

@@ -1,8 +1,8 @@
 // Batched persistent step: many independent lattices (of different sizes and physics) advanced
 // together, n steps in one cooperative launch.
 //
-// Every phase of a step runs over a flat work list that spans all instances -- tiles of 256
-// consecutive nodes for the node phases, chunks of 256 entries for the solid-layer lists and
+// Every phase of a step runs over a flat work list that spans all instances -- 2D tiles of 256
+// nodes for the node phases, chunks of 256 entries for the solid-layer lists and
 // the boundary nodes -- so that small and large lattices share the GPU evenly.  Between phases
 // all blocks meet at a grid barrier (the blocks are co-resident: cooperative launch).  The
 // barrier's wait is bounded: after `spin_limit` polls it sets an error flag and every block
@@ -71,16 +71,21 @@ __device__ __forceinline__ void block_range(int n, int& w0, int& w1) {
   w1 = (int)(((long long)n * (blockIdx.x + 1)) / gridDim.x);
 }
 
-// node (x, y) of thread t in the tile that starts at plane index n0; false past the plane or in
-// the row padding
+// Node tiles are BTILE_X x BTILE_Y blocks of an instance's lattice, row-major over the tiles
+// of each instance: tile t of an instance with tiles_x tiles per row band covers
+// x in [BTILE_X (t % tiles_x), +BTILE_X), y in [BTILE_Y (t / tiles_x), +BTILE_Y).  A warp reads
+// whole row segments and the stencils' nearby rows lie in the same block.  False outside the
+// lattice.
+constexpr int BTILE_X = 32, BTILE_Y = 8;
+static_assert(BTILE_X * BTILE_Y == BATCH_BLOCK, "one node per thread");
+
 template <typename real>
-__device__ __forceinline__ bool tile_node(const Lattice<real>& L, int n0, int& x, int& y) {
-  const int n = n0 + (int)threadIdx.x;
-  if (n >= L.plane) return false;
-  y = n0 / L.pitch;   // block-uniform division
-  x = n - y * L.pitch;
-  while (x >= L.pitch) { x -= L.pitch; ++y; }
-  return x < L.nx;
+__device__ __forceinline__ bool tile_node(const Lattice<real>& L, int t, int& x, int& y) {
+  const int tiles_x = (L.nx + BTILE_X - 1) / BTILE_X;   // block-uniform
+  const int ty = t / tiles_x, tx = t - ty * tiles_x;
+  x = tx * BTILE_X + (int)(threadIdx.x % BTILE_X);
+  y = ty * BTILE_Y + (int)(threadIdx.x / BTILE_X);
+  return x < L.nx && y < L.ny;
 }
 
 template <typename real>
@@ -157,6 +162,10 @@ __global__ void __launch_bounds__(BATCH_BLOCK, 6) k_batch(BatchDev B, int n_step
 }
 
 int batch_block_size() { return BATCH_BLOCK; }
+
+long long batch_node_tiles(int nx, int ny) {
+  return (long long)((nx + BTILE_X - 1) / BTILE_X) * ((ny + BTILE_Y - 1) / BTILE_Y);
+}
 
 int batch_grid_size(int fp64) {
   int dev = 0, sms = 0, per_sm = 0;

@@ -59,7 +59,7 @@ cudaError_t geom_fill(const GeomParams& g, const GeomScratch& s, const GeomOut& 
 struct BatchDev {
   int n_inst;
   const void* lat;              // device array of n_inst Lattice<real> descriptors
-  int n_node_tiles;             // (instance, first node) of 256 consecutive nodes
+  int n_node_tiles;             // (instance, tile) of 256 nodes, row-major over the tiles
   const int2* node_tiles;
   int n_s1_items, n_s2_items, n_bc_items;   // (instance, first entry) of 256 list entries
   const int2* s1_items;
@@ -72,6 +72,7 @@ struct BatchDev {
   long long spin_limit;         // polls before a barrier wait gives up
 };
 int batch_block_size();
+long long batch_node_tiles(int nx, int ny);   // 2D node tiles of one instance
 int batch_grid_size(int fp64);
 cudaError_t launch_batch(const BatchDev& B, int fp64, int grid, int n_steps, int cur0, cudaStream_t s);
 
