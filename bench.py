@@ -148,6 +148,8 @@ def run_adjoint(G, torch, steps, every):
             "ms_forward": round(ms_fwd, 3), "ms_forward_checkpointed": round(ms_ckpt, 3),
             "ms_reverse": round(ms_adj, 3),
             "cost_ratio": round((ms_ckpt + ms_adj) / ms_fwd, 3),
+            # one reverse step (its share of the recomputation included) against one forward step
+            "adjoint_step_over_forward_step": round(ms_adj / ms_fwd, 3),
             "reverse_MLUPS": round(sc.nodes * steps / ms_adj / 1e3, 1),
             "J": J, "dJ_ddmu_w": float(grad[0]), "dJ_dcx": float(grad[2]), "dJ_dcy": float(grad[3])}
 
