@@ -91,12 +91,58 @@ __device__ __forceinline__ void phase_collide(const Lattice<real>& L, int cur, i
 // pre-collision lattice and the rho / mu planes (the arithmetic of the collide phase), apply
 // Eq. 16 or 17 on each of its links, and add the FP64 sum of Eq. 18 to f_0.  Returns that sum
 // (0 for the schemes without compensation).
+//
+// PREFETCH > 0 (the single-lattice kernel): the data of the node's first PREFETCH links --
+// direction, q, x2 flag, then a, b2, c -- are loaded before the node's own state, so that the
+// thread waits on two rounds of loads instead of two per link.  Loading early changes nothing:
+// no link reads a value an earlier link of the node writes (a link writes f_ibar(x1) only where
+// x1 - e_ibar is solid, and then no other link of x1 reads that slot).  PREFETCH = 0 keeps the
+// register count low for the batched kernel.  Both produce identical values.
 template <typename real>
+__device__ __forceinline__ real edm_dir(int i, real r, real ux, real uy, real dux, real duy) {
+  switch (i) {
+    case 1: return edm_term<real>(1, r, ux, uy, dux, duy);
+    case 2: return edm_term<real>(2, r, ux, uy, dux, duy);
+    case 3: return edm_term<real>(3, r, ux, uy, dux, duy);
+    case 4: return edm_term<real>(4, r, ux, uy, dux, duy);
+    case 5: return edm_term<real>(5, r, ux, uy, dux, duy);
+    case 6: return edm_term<real>(6, r, ux, uy, dux, duy);
+    case 7: return edm_term<real>(7, r, ux, uy, dux, duy);
+    default: return edm_term<real>(8, r, ux, uy, dux, duy);
+  }
+}
+
+template <typename real, int PREFETCH = 0>
 __device__ __forceinline__ double phase_bc(const Lattice<real>& L, int cur, int b) {
   const int n = L.bnode[b];
   const int x = n % L.pitch, y = n / L.pitch;
   const real* __restrict__ fin = L.f[cur];
   real* fout = L.f[cur ^ 1];
+  const int l0 = L.bstart[b], l1 = L.bstart[b + 1];
+  constexpr int P = PREFETCH > 0 ? PREFETCH : 1;
+  int pd[P];
+  real pq[P], pa[P], pb[P], pc[P];
+  uint8_t pf[P];
+  if (PREFETCH > 0) {
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      pd[k] = 1;
+      if (l0 + k < l1) {
+        pd[k] = L.ldir[l0 + k];
+        pq[k] = L.lq[l0 + k];
+        pf[k] = L.lx2f[l0 + k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      if (l0 + k < l1) {
+        const int i = pd[k];
+        pa[k] = fout[i * L.plane + node_at(L, x + ex(i), y + ey(i))];
+        pb[k] = fout[i * L.plane + n];
+        pc[k] = fout[opp(i) * L.plane + node_at(L, x - ex(i), y - ey(i))];
+      }
+    }
+  }
   real fl[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) fl[i] = fin[i * L.plane + n];
@@ -108,28 +154,29 @@ __device__ __forceinline__ double phase_bc(const Lattice<real>& L, int cur, int 
   const real inv_r = real(1) / r;
   const real ux = jx * inv_r, uy = jy * inv_r, dux = Fx * inv_r, duy = Fy * inv_r;
   double sum = 0.0;
-  const int l0 = L.bstart[b], l1 = L.bstart[b + 1];
   for (int l = l0; l < l1; ++l) {
-    const int i = L.ldir[l];
-    const int ib = opp(i);
-    const int xs = node_at(L, x + ex(i), y + ey(i));
-    const int x2 = node_at(L, x - ex(i), y - ey(i));
-    const real a = fout[i * L.plane + xs];
-    const real b2 = fout[i * L.plane + n];
-    const real c = fout[ib * L.plane + x2];
-    // F_i(x1, t) of direction i
-    real Fi = real(0);
-    switch (i) {
-      case 1: Fi = edm_term<real>(1, r, ux, uy, dux, duy); break;
-      case 2: Fi = edm_term<real>(2, r, ux, uy, dux, duy); break;
-      case 3: Fi = edm_term<real>(3, r, ux, uy, dux, duy); break;
-      case 4: Fi = edm_term<real>(4, r, ux, uy, dux, duy); break;
-      case 5: Fi = edm_term<real>(5, r, ux, uy, dux, duy); break;
-      case 6: Fi = edm_term<real>(6, r, ux, uy, dux, duy); break;
-      case 7: Fi = edm_term<real>(7, r, ux, uy, dux, duy); break;
-      default: Fi = edm_term<real>(8, r, ux, uy, dux, duy); break;
+    const int k = l - l0;
+    int i;
+    real q, a, b2, c;
+    int x2f;
+    if (PREFETCH > 0 && k < P) {
+      // registers indexed by a loop counter: select among the unrolled slots
+      i = pd[0]; q = pq[0]; a = pa[0]; b2 = pb[0]; c = pc[0]; x2f = pf[0];
+#pragma unroll
+      for (int s = 1; s < P; ++s)
+        if (k == s) { i = pd[s]; q = pq[s]; a = pa[s]; b2 = pb[s]; c = pc[s]; x2f = pf[s]; }
+    } else {
+      i = L.ldir[l];
+      q = L.lq[l];
+      x2f = L.lx2f[l];
+      a = fout[i * L.plane + node_at(L, x + ex(i), y + ey(i))];
+      b2 = fout[i * L.plane + n];
+      c = fout[opp(i) * L.plane + node_at(L, x - ex(i), y - ey(i))];
     }
-    const real v = link_rule<real>(L.bc, L.lq[l], L.lx2f[l], a, b2, c, Fi);
+    const int ib = opp(i);
+    // F_i(x1, t) of direction i
+    const real Fi = edm_dir<real>(i, r, ux, uy, dux, duy);
+    const real v = link_rule<real>(L.bc, q, x2f, a, b2, c, Fi);
     fout[ib * L.plane + n] = v;
     sum += (double)a - (double)v;
   }

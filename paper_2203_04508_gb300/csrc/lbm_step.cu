@@ -93,7 +93,7 @@ template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_bc(Lattice<real> L, int cur) {
   __shared__ double red[32];
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  const double sum = b < L.n_bnodes ? phase_bc(L, cur, b) : 0.0;
+  const double sum = b < L.n_bnodes ? phase_bc<real, 4>(L, cur, b) : 0.0;
   double bt = block_sum(sum, red);
   double total;
   if (finish_reduction(bt, L.partials, L.counter, &total, red)) {
