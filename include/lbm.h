@@ -284,6 +284,19 @@ lbm_status lbm_batch_check(lbm_batch* b);
  * every wait give up at once (used to test the timeout path).  Clears the error flag. */
 lbm_status lbm_batch_set_spin_limit(lbm_batch* b, int64_t polls);
 
+/* Shape of the node tiles of the persistent kernel: 2^log2w nodes wide and 256 / 2^log2w
+ * rows high, log2w in 4 .. 8 (16x16, 32x8, 64x4, 128x2, 256x1; default 5).  Every shape gives
+ * identical results; only the speed differs (how well a warp's row segment and the stencils'
+ * nearby rows fit the instances' widths).  LBM_EINVAL outside the range.  Synchronises. */
+lbm_status lbm_batch_set_tile(lbm_batch* b, int32_t log2w);
+
+/* Tile-shape autotuner: times `steps` steps of the batch with each tile shape (CUDA events on
+ * the batch's stream, after one untimed launch of the same length per shape), keeps the fastest
+ * and writes its log2w to *chosen and the five times (ms, log2w = 4 .. 8) to ms (either may be
+ * NULL).  The trials are real steps: every instance advances 10 * steps steps, so call it on a
+ * representative state and re-initialise afterwards if the state matters. */
+lbm_status lbm_batch_autotune(lbm_batch* b, int64_t steps, int32_t* chosen, double* ms);
+
 /* Instance k of the batch (owned by the batch). */
 lbm_status lbm_batch_instance(lbm_batch* b, int32_t k, lbm_ctx** ctx);
 

@@ -723,6 +723,7 @@ struct lbm_batch {
   long long graph_steps = -1;
   int graph_cur = -1;
   long long spin_limit = 1LL << 22;
+  int tile_log2w = BATCH_TILE_LOG2W_DEFAULT;
   int cur = 0;
   std::string err;
 };
@@ -751,7 +752,12 @@ lbm_status plan_batch(int n, const lbm_config* cfgs, BatchPlan* P, char* msg) {
     P->bytes[k] = L.total;
     o = align_up(o + L.total);
     const int bb = batch_block_size();
-    P->cap_tiles += batch_node_tiles(cfgs[k].nx, cfgs[k].ny);
+    long long most = 0;   // room for the tile list of any shape
+    for (int lw = BATCH_TILE_LOG2W_MIN; lw <= BATCH_TILE_LOG2W_MAX; ++lw) {
+      const long long t = batch_node_tiles(cfgs[k].nx, cfgs[k].ny, lw);
+      most = t > most ? t : most;
+    }
+    P->cap_tiles += most;
     P->cap_s1 += (L.cap.s1 + bb - 1) / bb;
     P->cap_s2 += (L.cap.s2 + bb - 1) / bb;
     P->cap_bc += (L.cap.bnodes + bb - 1) / bb;
@@ -799,7 +805,7 @@ lbm_status batch_tables(lbm_batch* b) {
     const Lattice<real>& L = b->fp64 ? *reinterpret_cast<const Lattice<real>*>(&b->ctx[k]->Ld)
                                      : *reinterpret_cast<const Lattice<real>*>(&b->ctx[k]->Lf);
     lats[k] = L;
-    const long long nt = batch_node_tiles(L.nx, L.ny);
+    const long long nt = batch_node_tiles(L.nx, L.ny, b->tile_log2w);
     for (long long t = 0; t < nt; ++t) tiles.push_back(make_int2(k, (int)t));
     for (int j = 0; j < L.n_s1; j += bb) s1.push_back(make_int2(k, j));
     for (int j = 0; j < L.n_s2; j += bb) s2.push_back(make_int2(k, j));
@@ -823,6 +829,7 @@ lbm_status batch_tables(lbm_batch* b) {
   d.n_inst = b->n;
   d.lat = t + b->t_lat;
   d.n_node_tiles = (int)tiles.size();
+  d.tile_log2w = b->tile_log2w;
   d.node_tiles = (const int2*)(t + b->t_tiles);
   d.n_s1_items = (int)s1.size();
   d.n_s2_items = (int)s2.size();
@@ -963,6 +970,48 @@ lbm_status lbm_batch_set_spin_limit(lbm_batch* b, int64_t polls) {
     BCUDA(b, cudaStreamSynchronize(b->stream));
   }
   return LBM_OK;
+}
+
+lbm_status lbm_batch_set_tile(lbm_batch* b, int32_t log2w) {
+  if (!b || b->ctx.empty()) return LBM_ESTATE;
+  if (log2w < BATCH_TILE_LOG2W_MIN || log2w > BATCH_TILE_LOG2W_MAX)
+    return bfail(b, LBM_EINVAL, "tile width 2^%d outside 2^%d .. 2^%d", log2w, BATCH_TILE_LOG2W_MIN,
+                 BATCH_TILE_LOG2W_MAX);
+  b->tile_log2w = log2w;
+  if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+  b->graph_steps = -1;
+  if (!b->tables) return LBM_OK;
+  return b->fp64 ? batch_tables<double>(b) : batch_tables<float>(b);
+}
+
+lbm_status lbm_batch_autotune(lbm_batch* b, int64_t steps, int32_t* chosen, double* ms) {
+  if (!b || !b->tables) return LBM_ESTATE;
+  if (steps < 1 || steps > (1LL << 20)) return bfail(b, LBM_EINVAL, "trial steps must lie in [1, 2^20]");
+  cudaEvent_t e0, e1;
+  BCUDA(b, cudaEventCreate(&e0));
+  BCUDA(b, cudaEventCreate(&e1));
+  int best = b->tile_log2w;
+  double best_ms = 1e300;
+  lbm_status st = LBM_OK;
+  for (int lw = BATCH_TILE_LOG2W_MIN; lw <= BATCH_TILE_LOG2W_MAX && st == LBM_OK; ++lw) {
+    st = lbm_batch_set_tile(b, lw);
+    if (st == LBM_OK) st = lbm_batch_step(b, steps);   // first launch of this shape: captures its graph
+    if (st != LBM_OK) break;
+    cudaEventRecord(e0, b->stream);
+    st = lbm_batch_step(b, steps);
+    cudaEventRecord(e1, b->stream);
+    if (st != LBM_OK) break;
+    st = lbm_batch_check(b);
+    float t = 0.f;
+    if (st == LBM_OK && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) st = bfail(b, LBM_ECUDA, "event timing failed");
+    if (ms) ms[lw - BATCH_TILE_LOG2W_MIN] = t;
+    if (st == LBM_OK && t < best_ms) { best_ms = t; best = lw; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != LBM_OK) return st;
+  if (chosen) *chosen = best;
+  return lbm_batch_set_tile(b, best);
 }
 
 lbm_status lbm_batch_instance(lbm_batch* b, int32_t k, lbm_ctx** ctx) {

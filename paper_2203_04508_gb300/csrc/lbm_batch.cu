@@ -71,20 +71,18 @@ __device__ __forceinline__ void block_range(int n, int& w0, int& w1) {
   w1 = (int)(((long long)n * (blockIdx.x + 1)) / gridDim.x);
 }
 
-// Node tiles are BTILE_X x BTILE_Y blocks of an instance's lattice, row-major over the tiles
-// of each instance: tile t of an instance with tiles_x tiles per row band covers
-// x in [BTILE_X (t % tiles_x), +BTILE_X), y in [BTILE_Y (t / tiles_x), +BTILE_Y).  A warp reads
-// whole row segments and the stencils' nearby rows lie in the same block.  False outside the
-// lattice.
-constexpr int BTILE_X = 32, BTILE_Y = 8;
-static_assert(BTILE_X * BTILE_Y == BATCH_BLOCK, "one node per thread");
-
+// Node tiles are 2D blocks of 2^tile_log2w x (256 / 2^tile_log2w) nodes of an instance's
+// lattice, row-major over the tiles of each instance: tile t of an instance with tiles_x tiles
+// per row band covers x in [w (t % tiles_x), +w), y in [h (t / tiles_x), +h).  The shape is a
+// run-time choice (lbm_batch_set_tile, lbm_batch_autotune); every shape gives the same values,
+// since each node's arithmetic does not depend on it.  False outside the lattice.
 template <typename real>
-__device__ __forceinline__ bool tile_node(const Lattice<real>& L, int t, int& x, int& y) {
-  const int tiles_x = (L.nx + BTILE_X - 1) / BTILE_X;   // block-uniform
+__device__ __forceinline__ bool tile_node(const Lattice<real>& L, int log2w, int t, int& x, int& y) {
+  const int w = 1 << log2w, h = BATCH_BLOCK >> log2w;
+  const int tiles_x = (L.nx + w - 1) >> log2w;   // block-uniform
   const int ty = t / tiles_x, tx = t - ty * tiles_x;
-  x = tx * BTILE_X + (int)(threadIdx.x % BTILE_X);
-  y = ty * BTILE_Y + (int)(threadIdx.x / BTILE_X);
+  x = (tx << log2w) + (int)(threadIdx.x & (w - 1));
+  y = ty * h + (int)(threadIdx.x >> log2w);
   return x < L.nx && y < L.ny;
 }
 
@@ -104,7 +102,7 @@ __global__ void __launch_bounds__(BATCH_BLOCK, 6) k_batch(BatchDev B, int n_step
       const int2 t = B.node_tiles[w];
       load_lattice(L, lat, t.x, loaded);
       int x, y;
-      if (tile_node(L, t.y, x, y)) phase_rho(L, cur, x, y);
+      if (tile_node(L, B.tile_log2w, t.y, x, y)) phase_rho(L, cur, x, y);
     }
     if (!grid_sync(B, ++target)) return;
     // solid layers (Eq. 15), the second after the first
@@ -125,7 +123,7 @@ __global__ void __launch_bounds__(BATCH_BLOCK, 6) k_batch(BatchDev B, int n_step
       const int2 t = B.node_tiles[w];
       load_lattice(L, lat, t.x, loaded);
       int x, y;
-      if (L.eos != EOS_NONE && tile_node(L, t.y, x, y)) phase_mu(L, x, y);
+      if (L.eos != EOS_NONE && tile_node(L, B.tile_log2w, t.y, x, y)) phase_mu(L, x, y);
     }
     if (!grid_sync(B, ++target)) return;
     // force + collision + streaming
@@ -133,7 +131,7 @@ __global__ void __launch_bounds__(BATCH_BLOCK, 6) k_batch(BatchDev B, int n_step
       const int2 t = B.node_tiles[w];
       load_lattice(L, lat, t.x, loaded);
       int x, y;
-      if (tile_node(L, t.y, x, y)) phase_collide(L, cur, x, y);
+      if (tile_node(L, B.tile_log2w, t.y, x, y)) phase_collide(L, cur, x, y);
     }
     if (!grid_sync(B, ++target)) return;
     // boundary links (Eqs. 16-18); each chunk's compensation sum, in a fixed order
@@ -163,8 +161,9 @@ __global__ void __launch_bounds__(BATCH_BLOCK, 6) k_batch(BatchDev B, int n_step
 
 int batch_block_size() { return BATCH_BLOCK; }
 
-long long batch_node_tiles(int nx, int ny) {
-  return (long long)((nx + BTILE_X - 1) / BTILE_X) * ((ny + BTILE_Y - 1) / BTILE_Y);
+long long batch_node_tiles(int nx, int ny, int log2w) {
+  const int w = 1 << log2w, h = BATCH_BLOCK >> log2w;
+  return (long long)((nx + w - 1) / w) * ((ny + h - 1) / h);
 }
 
 int batch_grid_size(int fp64) {

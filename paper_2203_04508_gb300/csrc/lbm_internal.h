@@ -60,6 +60,7 @@ struct BatchDev {
   int n_inst;
   const void* lat;              // device array of n_inst Lattice<real> descriptors
   int n_node_tiles;             // (instance, tile) of 256 nodes, row-major over the tiles
+  int tile_log2w;               // tile width 2^tile_log2w, height 256 / 2^tile_log2w
   const int2* node_tiles;
   int n_s1_items, n_s2_items, n_bc_items;   // (instance, first entry) of 256 list entries
   const int2* s1_items;
@@ -72,7 +73,10 @@ struct BatchDev {
   long long spin_limit;         // polls before a barrier wait gives up
 };
 int batch_block_size();
-long long batch_node_tiles(int nx, int ny);   // 2D node tiles of one instance
+// node tiles of width 2^log2w (and height 256 / 2^log2w) of one instance; the shapes a batch
+// may use are log2w = BATCH_TILE_LOG2W_MIN .. BATCH_TILE_LOG2W_MAX (16x16 .. 256x1)
+constexpr int BATCH_TILE_LOG2W_MIN = 4, BATCH_TILE_LOG2W_MAX = 8, BATCH_TILE_LOG2W_DEFAULT = 5;
+long long batch_node_tiles(int nx, int ny, int log2w);
 int batch_grid_size(int fp64);
 cudaError_t launch_batch(const BatchDev& B, int fp64, int grid, int n_steps, int cur0, cudaStream_t s);
 

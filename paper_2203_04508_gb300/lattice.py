@@ -321,6 +321,20 @@ class Batch:
     def set_spin_limit(self, polls: int):
         self._check(self.lib.lbm_batch_set_spin_limit(self.b, int(polls)))
 
+    def set_tile(self, log2w: int):
+        """Node-tile shape of the persistent kernel: 2^log2w x 256/2^log2w (log2w in 4..8)."""
+        self._check(self.lib.lbm_batch_set_tile(self.b, int(log2w)))
+
+    def autotune(self, steps: int = 20):
+        """Times every tile shape over `steps` steps (the instances advance 10 * steps steps)
+        and keeps the fastest; returns {"log2w": chosen, "ms": {shape: ms}}."""
+        chosen = C.c_int32()
+        ms = np.zeros(5)
+        self._check(self.lib.lbm_batch_autotune(self.b, int(steps), C.byref(chosen), ms.ctypes.data))
+        shapes = [f"{1 << w}x{256 >> w}" for w in range(4, 9)]
+        return {"log2w": chosen.value, "tile": shapes[chosen.value - 4],
+                "ms": {sh: round(float(t), 3) for sh, t in zip(shapes, ms)}}
+
     def info(self):
         o = np.zeros(4, np.int64)
         self._check(self.lib.lbm_batch_info(self.b, o.ctypes.data))

@@ -101,3 +101,42 @@ def test_grid_barrier_timeout_is_reported_not_hung():
     b.init([sc.droplets() for sc in scs])
     b.step(3)
     b.check()
+
+
+def test_every_tile_shape_gives_identical_results():
+    """The node-tile shape is a scheduling choice only: FP64 populations after 23 steps are the
+    same bits for every shape."""
+    scs = _mixed(True)
+    b = _batch(scs, True)
+    ref = None
+    for log2w in (5, 4, 6, 7, 8):
+        b.set_tile(log2w)
+        b.init([sc.droplets() for sc in scs])
+        b.step(23)
+        b.check()
+        pops = [inst.populations() for inst in b.instances]
+        if ref is None:
+            ref = pops
+        else:
+            for k in range(len(scs)):
+                assert np.array_equal(pops[k], ref[k]), (log2w, k)
+
+
+def test_autotune_picks_a_shape_and_the_batch_stays_correct():
+    from paper_2203_04508_gb300 import LbmError
+    scs = _mixed(False)
+    b = _batch(scs, False)
+    r = b.autotune(3)
+    assert 4 <= r["log2w"] <= 8
+    assert all(v > 0 for v in r["ms"].values())
+    assert r["ms"][r["tile"]] == min(r["ms"].values())
+    b.init([sc.droplets() for sc in scs])
+    b.step(17)
+    b.check()
+    for k, sc in enumerate(scs):
+        single = make_lattice(sc, fp64=False)
+        single.step(17)
+        fb, fs = b.instances[k].populations(), single.populations()
+        assert np.abs(fb.astype(np.float64) - fs).max() <= 1e-6 * np.abs(fs).max(), sc.name
+    with pytest.raises(LbmError):
+        b.set_tile(3)
