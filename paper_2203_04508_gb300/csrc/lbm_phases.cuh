@@ -53,21 +53,20 @@ __device__ __forceinline__ void phase_mu(const Lattice<real>& L, int x, int y) {
 }
 
 // force (Eq. 9) + collision (Eq. 4) with exact-difference forcing (Eq. 13) + push streaming
-// (Eq. 5) of fluid node (x, y) into the other lattice
-template <typename real>
-__device__ __forceinline__ void phase_collide(const Lattice<real>& L, int cur, int x, int y) {
+// (Eq. 5) of fluid node (x, y) into the other lattice.  Force(r, Fx, Fy) evaluates Eq. 9 at
+// the node: from the density and chemical-potential planes (force_at), or from a tile of them
+// staged in shared memory -- the same values in the same order of operations.
+// The second half of the phase, for populations fl already loaded from lattice `cur`.
+template <typename real, typename Force>
+__device__ __forceinline__ void collide_loaded(const Lattice<real>& L, int cur, int x, int y, real (&fl)[9],
+                                               Force&& force) {
   const int n = y * L.pitch + x;
-  if (L.kind[n] != KIND_FLUID) return;
-  const real* __restrict__ fin = L.f[cur];
   real* __restrict__ fout = L.f[cur ^ 1];
-  real fl[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) fl[i] = fin[i * L.plane + n];
   real drho, jx, jy;
   moments(fl, drho, jx, jy);
   const real r = L.rho_ref + drho;
   real Fx, Fy;
-  force_at(L, x, y, r, Fx, Fy);
+  force(r, Fx, Fy);
   collide_node(L, fl, r, drho, jx, jy, Fx, Fy);
   int xm = x - 1, xp = x + 1, rowc = y * L.pitch, rowm = rowc - L.pitch, rowp = rowc + L.pitch;
   if (!interior(L, x, y)) {
@@ -85,6 +84,22 @@ __device__ __forceinline__ void phase_collide(const Lattice<real>& L, int cur, i
   fout[6 * L.plane + rowp + xm] = fl[6];
   fout[7 * L.plane + rowm + xm] = fl[7];
   fout[8 * L.plane + rowm + xp] = fl[8];
+}
+
+template <typename real, typename Force>
+__device__ __forceinline__ void phase_collide_with(const Lattice<real>& L, int cur, int x, int y, Force&& force) {
+  const int n = y * L.pitch + x;
+  if (L.kind[n] != KIND_FLUID) return;
+  const real* __restrict__ fin = L.f[cur];
+  real fl[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) fl[i] = fin[i * L.plane + n];
+  collide_loaded(L, cur, x, y, fl, force);
+}
+
+template <typename real>
+__device__ __forceinline__ void phase_collide(const Lattice<real>& L, int cur, int x, int y) {
+  phase_collide_with(L, cur, x, y, [&](real r, real& Fx, real& Fy) { force_at(L, x, y, r, Fx, Fy); });
 }
 
 // Boundary node b (one per thread): rebuild (rho, u, F) of step t at x1 from the
