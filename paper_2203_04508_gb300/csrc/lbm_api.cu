@@ -53,8 +53,8 @@ struct Layout {
   long long plane;
   size_t sz;
   Caps cap;
-  size_t fA, fB, rho, mu, kind, body;
-  size_t lq64, lq, ldir, lx2f, bnode, bstart, carry;
+  size_t fA, fB, rho, rho2, mu, kind, body;
+  size_t lq64, lq, ldir, lx2f, bnode, bstart, carry, rhob;
   size_t s1node, s1mask, s1winv, s2node, s2mask, s2winv;
   size_t cyl, drops, partials, counter, step_ctr, scalars, dm_ring, block_sums, totals;
   size_t total;
@@ -72,6 +72,7 @@ Layout make_layout(const lbm_config* c) {
   L.fA = take(9 * L.plane * L.sz);
   L.fB = take(9 * L.plane * L.sz);
   L.rho = take(L.plane * L.sz);
+  L.rho2 = take(L.plane * L.sz);
   L.mu = take(L.plane * L.sz);
   L.kind = take(L.plane);
   L.body = take(L.plane * 4);
@@ -82,6 +83,7 @@ Layout make_layout(const lbm_config* c) {
   L.bnode = take(L.cap.bnodes * 4);
   L.bstart = take((L.cap.bnodes + 1) * 4);
   L.carry = take(L.cap.bnodes * 8);
+  L.rhob = take(L.cap.bnodes * L.sz);
   L.s1node = take(L.cap.s1 * 4);
   L.s1mask = take(L.cap.s1);
   L.s1winv = take(L.cap.s1 * L.sz);
@@ -117,6 +119,12 @@ struct lbm_ctx {
   double rho_ref = 0;
   bool built = false, inited = false;
   int cur = 0;
+  // lbm_step keeps the density of lattice `cur` in density plane `cur` (planes rho, rho2),
+  // computing the next one while the boundary phase runs; false until a step or an explicit
+  // density pass has put it there
+  bool rho_ok = false;
+  cudaStream_t side = nullptr;                      // second stream of the overlapped step
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   long long steps = 0;
   long long n_links = 0, n_bnodes = 0, n_s1 = 0, n_s2 = 0, n_fluid = 0;
   Lattice<float> Lf{};
@@ -182,6 +190,7 @@ void fill_lattice(lbm_ctx* c, Lattice<real>& L) {
   L.f[0] = (real*)(w + y.fA);
   L.f[1] = (real*)(w + y.fB);
   L.rho = (real*)(w + y.rho);
+  L.rho_b = nullptr;
   L.mu = (real*)(w + y.mu);
   L.kind = (const uint8_t*)(w + y.kind);
   L.body = (const int*)(w + y.body);
@@ -281,15 +290,41 @@ lbm_status validate(const lbm_config* g, char* msg) {
   return LBM_OK;
 }
 
+// descriptors of a step from lattice `cur`: its density in plane `cur`, the boundary densities
+// into rho_b, and the next state's density plane
+template <typename real>
+void step_lattices(const lbm_ctx* c, const Lattice<real>& L, int cur, Lattice<real>& Lt, Lattice<real>& Ln) {
+  real* planes[2] = {(real*)(c->ws + c->lay.rho), (real*)(c->ws + c->lay.rho2)};
+  Lt = L;
+  Lt.rho = planes[cur];
+  Lt.rho_b = (real*)(c->ws + c->lay.rhob);
+  Ln = Lt;
+  Ln.rho = planes[cur ^ 1];
+}
+
 template <typename real>
 lbm_status do_step(lbm_ctx* c, const Lattice<real>& L, long long n) {
+  if (n <= 0) return LBM_OK;
+  if (!c->side) {
+    CUDA_OK(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    CUDA_OK(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    CUDA_OK(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  }
+  Lattice<real> Lt, Ln;
+  if (!c->rho_ok) {
+    step_lattices(c, L, c->cur, Lt, Ln);
+    CUDA_OK(c, launch_phase(Lt, c->cur, 0, c->stream));   // density of the current lattice
+    c->rho_ok = true;
+  }
   if (n >= 2 && c->stream != nullptr) {
     int p = c->cur;
     if (!c->graph[p]) {
       cudaGraph_t g;
       CUDA_OK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e1 = launch_step(L, p, c->stream);
-      cudaError_t e2 = launch_step(L, p ^ 1, c->stream);
+      step_lattices(c, L, p, Lt, Ln);
+      cudaError_t e1 = launch_step_overlap(Lt, Ln, p, c->stream, c->side, c->ev_fork, c->ev_join);
+      step_lattices(c, L, p ^ 1, Lt, Ln);
+      cudaError_t e2 = e1 == cudaSuccess ? launch_step_overlap(Lt, Ln, p ^ 1, c->stream, c->side, c->ev_fork, c->ev_join) : e1;
       cudaError_t e3 = cudaStreamEndCapture(c->stream, &g);
       if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
         return fail(c, LBM_ECUDA, "graph capture failed: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3)));
@@ -301,7 +336,8 @@ lbm_status do_step(lbm_ctx* c, const Lattice<real>& L, long long n) {
     n -= 2 * (n / 2);
   }
   for (long long k = 0; k < n; ++k) {
-    CUDA_OK(c, launch_step(L, c->cur, c->stream));
+    step_lattices(c, L, c->cur, Lt, Ln);
+    CUDA_OK(c, launch_step_overlap(Lt, Ln, c->cur, c->stream, c->side, c->ev_fork, c->ev_join));
     c->cur ^= 1;
   }
   return LBM_OK;
@@ -331,6 +367,7 @@ lbm_status profile_steps(lbm_ctx* c, const Lattice<real>& L, long long n, double
     c->steps += 1;
   }
   for (auto& e : ev) cudaEventDestroy(e);
+  c->rho_ok = false;   // the phases kept the density in the first plane only
   return st;
 }
 
@@ -453,6 +490,7 @@ lbm_status lbm_build_links(lbm_ctx* c) {
   CUDA_OK(c, cudaStreamSynchronize(c->stream));
   c->built = true;
   c->inited = false;
+  c->rho_ok = false;
   c->tape.valid = false;
   refresh(c);
   return LBM_OK;
@@ -537,6 +575,7 @@ lbm_status lbm_init(lbm_ctx* c, const lbm_init_spec* s) {
   CUDA_OK(c, cudaStreamSynchronize(c->stream));
   c->mass0 = sc[0] + (double)c->n_fluid * c->rho_ref;
   c->inited = true;
+  c->rho_ok = false;
   c->tape.valid = false;
   return LBM_OK;
 }
@@ -553,7 +592,7 @@ lbm_status lbm_step(lbm_ctx* c, int64_t n) {
 
 lbm_status lbm_launches_per_step(lbm_ctx* c, int64_t* n) {
   if (!c || !c->built || !n) return LBM_ESTATE;
-  *n = c->fp64 ? launches_per_step(c->Ld) : launches_per_step(c->Lf);
+  *n = c->fp64 ? launches_per_step_overlap(c->Ld) : launches_per_step_overlap(c->Lf);
   return LBM_OK;
 }
 
@@ -620,6 +659,7 @@ lbm_status lbm_set_populations(lbm_ctx* c, const void* f, int32_t on_device) {
   CUDA_OK(c, cudaStreamSynchronize(c->stream));
   c->mass0 = sc[0] + (double)c->n_fluid * c->rho_ref;
   c->inited = true;
+  c->rho_ok = false;
   c->tape.valid = false;
   return LBM_OK;
 }
@@ -693,9 +733,10 @@ void lbm_destroy(lbm_ctx* c) {
   for (auto& g : c->graph)
     if (g) cudaGraphExecDestroy(g);
   for (auto& a : c->adj_graphs) cudaGraphExecDestroy(a.exec);
-  for (cudaEvent_t e : {c->ev_start, c->ev_rec[0], c->ev_rec[1], c->ev_rev[0], c->ev_rev[1]})
+  for (cudaEvent_t e : {c->ev_start, c->ev_rec[0], c->ev_rec[1], c->ev_rev[0], c->ev_rev[1], c->ev_fork, c->ev_join})
     if (e) cudaEventDestroy(e);
   if (c->aux) cudaStreamDestroy(c->aux);
+  if (c->side) cudaStreamDestroy(c->side);
   delete c;
 }
 
@@ -947,6 +988,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t n) {
   for (int k = 0; k < b->n; ++k) {
     b->ctx[k]->cur ^= flip;
     b->ctx[k]->steps += n;
+    b->ctx[k]->rho_ok = false;
   }
   return LBM_OK;
 }

@@ -31,6 +31,8 @@ struct Lattice {
   int plane;                    // pitch * ny (9 * plane < 2^31)
   real* f[2];                   // the two population lattices (9 planes each)
   real* rho;                    // density plane (fluid and the two solid layers)
+  real* rho_b;                  // if set: the boundary phase leaves the density of each
+                                // boundary node's final populations here (one per node)
   real* mu;                     // chemical potential minus k^2 mu_sat (constant at solids)
   const uint8_t* kind;
   const int* body;              // body of each solid node (cylinders 0.., then bottom, top wall)

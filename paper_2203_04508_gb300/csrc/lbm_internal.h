@@ -14,6 +14,12 @@ template <typename real> cudaError_t launch_step(const Lattice<real>& L, int cur
 template <typename real> int launches_per_step(const Lattice<real>& L);
 template <typename real> cudaError_t launch_phase(const Lattice<real>& L, int cur, int phase, cudaStream_t s);
 template <typename real> cudaError_t launch_macro(const Lattice<real>& L, int cur, cudaStream_t s);
+// step t with its boundary phase overlapping the density pass of step t+1 on stream s2 (Lt:
+// rho = density of lattice cur, rho_b set; Ln: rho = the plane receiving lattice cur^1's)
+template <typename real>
+cudaError_t launch_step_overlap(const Lattice<real>& Lt, const Lattice<real>& Ln, int cur, cudaStream_t s,
+                                cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join);
+template <typename real> int launches_per_step_overlap(const Lattice<real>& L);
 template <typename real> cudaError_t launch_fields(const Lattice<real>& L, int cur, real* r, real* vx, real* vy, cudaStream_t s);
 template <typename real> cudaError_t launch_populations(const Lattice<real>& L, int cur, real* out, cudaStream_t s);
 template <typename real> cudaError_t launch_set_populations(const Lattice<real>& L, int cur, const real* in, cudaStream_t s);

@@ -203,9 +203,16 @@ __device__ __forceinline__ double phase_bc(const Lattice<real>& L, int cur, int 
     const real stored = (real)t;
     L.carry[b] = t - (double)stored;
     fout[n] = stored;
-    return sum;
   }
-  return 0.0;
+  if (L.rho_b) {
+    // the node's populations are final only now: its density for the next step (the sum and
+    // order of density_of, as the density pass would take it)
+    real g[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = fout[i * L.plane + n];
+    L.rho_b[b] = density_of(L, g);
+  }
+  return (L.bc == BC_PRESENT || L.bc == BC_MIBC) ? sum : 0.0;
 }
 
 }  // namespace lbmgb

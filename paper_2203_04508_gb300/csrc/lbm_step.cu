@@ -155,6 +155,13 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_bc(Lattice<real> L, int cur) {
   }
 }
 
+// Boundary nodes' densities, left by the boundary phase in rho_b, into the density plane.
+template <typename real>
+__global__ void __launch_bounds__(NODE_BLOCK) k_rho_scatter(Lattice<real> L) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < L.n_bnodes) L.rho[L.bnode[b]] = L.rho_b[b];
+}
+
 // FP64 mass audit: sum over fluid nodes of sum_i (f_i - w_i rho_ref), plus a count of
 // non-finite populations.  The host adds n_fluid * rho_ref.
 template <typename real>
@@ -328,6 +335,38 @@ cudaError_t launch_step(const Lattice<real>& L, int cur, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// One step whose boundary phase overlaps the density pass of the next step.  Lt describes
+// step t (rho = the density plane of lattice cur, holding its density; rho_b set), Ln the next
+// state (rho = the other density plane).  After the collide the work forks: k_bc on s, the
+// density of every node of lattice cur^1 on s2 -- final everywhere but at boundary nodes, whose
+// populations k_bc is still completing and whose densities it leaves in rho_b -- then joins,
+// and k_rho_scatter puts those in place.  Sequence and values are those of launch_step.
+template <typename real>
+cudaError_t launch_step_overlap(const Lattice<real>& Lt, const Lattice<real>& Ln, int cur, cudaStream_t s,
+                                cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join) {
+  const Lattice<real>& L = Lt;
+  if (L.n_s1 > 0) k_solid<real><<<grid_for(L.n_s1, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 1);
+  if (L.n_s2 > 0) k_solid<real><<<grid_for(L.n_s2, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 2);
+  if (L.eos != EOS_NONE) k_mu<real><<<node_grid(L), node_block(), 0, s>>>(L);
+  k_collide<real><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
+  cudaError_t e = cudaEventRecord(fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, fork, 0);
+  if (e != cudaSuccess) return e;
+  const unsigned gb = grid_for(L.n_bnodes, NODE_BLOCK);
+  k_bc<real><<<gb > 0 ? gb : 1, NODE_BLOCK, 0, s>>>(L, cur);
+  k_rho_vec<real><<<rho_grid(Ln), NODE_BLOCK, 0, s2>>>(Ln, cur ^ 1);
+  e = cudaEventRecord(join, s2);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join, 0);
+  if (e != cudaSuccess) return e;
+  if (L.n_bnodes > 0) k_rho_scatter<real><<<gb, NODE_BLOCK, 0, s>>>(Ln);
+  return cudaGetLastError();
+}
+
+template <typename real>
+int launches_per_step_overlap(const Lattice<real>& L) {
+  return launches_per_step(L) + (L.n_bnodes > 0);
+}
+
 // one phase of a step: 0 density, 1 solid layers, 2 chemical potential, 3 force+collide+stream,
 // 4 boundary links
 template <typename real>
@@ -403,6 +442,9 @@ cudaError_t launch_init(const Lattice<real>& L, const double* drops, int n_drop,
   template int launches_per_step<real>(const Lattice<real>&);                                           \
   template cudaError_t launch_phase<real>(const Lattice<real>&, int, int, cudaStream_t);                \
   template cudaError_t launch_macro<real>(const Lattice<real>&, int, cudaStream_t);                     \
+  template cudaError_t launch_step_overlap<real>(const Lattice<real>&, const Lattice<real>&, int, cudaStream_t, \
+                                                 cudaStream_t, cudaEvent_t, cudaEvent_t);                  \
+  template int launches_per_step_overlap<real>(const Lattice<real>&);                                   \
   template cudaError_t launch_fields<real>(const Lattice<real>&, int, real*, real*, real*, cudaStream_t); \
   template cudaError_t launch_populations<real>(const Lattice<real>&, int, real*, cudaStream_t);        \
   template cudaError_t launch_set_populations<real>(const Lattice<real>&, int, const real*, cudaStream_t); \
