@@ -55,7 +55,7 @@ struct Layout {
   Caps cap;
   size_t fA, fB, rho, rho2, mu, kind, body;
   size_t lq64, lq, ldir, lx2f, bnode, bstart, carry, rhob;
-  size_t s1node, s1mask, s1winv, s2node, s2mask, s2winv;
+  size_t s1node, s1mask, s1winv, s1nb, s2node, s2mask, s2winv;
   size_t cyl, drops, partials, counter, step_ctr, scalars, dm_ring, block_sums, totals;
   size_t total;
 };
@@ -87,6 +87,7 @@ Layout make_layout(const lbm_config* c) {
   L.s1node = take(L.cap.s1 * 4);
   L.s1mask = take(L.cap.s1);
   L.s1winv = take(L.cap.s1 * L.sz);
+  L.s1nb = take(L.cap.s1 * 8 * 4);
   L.s2node = take(L.cap.s2 * 4);
   L.s2mask = take(L.cap.s2);
   L.s2winv = take(L.cap.s2 * L.sz);
@@ -119,9 +120,9 @@ struct lbm_ctx {
   double rho_ref = 0;
   bool built = false, inited = false;
   int cur = 0;
-  // lbm_step keeps the density of lattice `cur` in density plane `cur` (planes rho, rho2),
-  // computing the next one while the boundary phase runs; false until a step or an explicit
-  // density pass has put it there
+  // lbm_step keeps the density of lattice `cur` (fluid and solid layers) in density plane `cur`
+  // (planes rho, rho2), computing the next one while the boundary phase runs; false until a
+  // step or an explicit density pass has put it there
   bool rho_ok = false;
   cudaStream_t side = nullptr;                      // second stream of the overlapped step
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -242,6 +243,7 @@ void fill_lattice(lbm_ctx* c, Lattice<real>& L) {
   L.s1node = (const int*)(w + y.s1node);
   L.s1mask = (const uint8_t*)(w + y.s1mask);
   L.s1winv = (const real*)(w + y.s1winv);
+  L.s1nb = (const int*)(w + y.s1nb);
   L.s2node = (const int*)(w + y.s2node);
   L.s2mask = (const uint8_t*)(w + y.s2mask);
   L.s2winv = (const real*)(w + y.s2winv);
@@ -312,8 +314,10 @@ lbm_status do_step(lbm_ctx* c, const Lattice<real>& L, long long n) {
   }
   Lattice<real> Lt, Ln;
   if (!c->rho_ok) {
+    // density of the current lattice and its solid layers, which the overlapped step expects
     step_lattices(c, L, c->cur, Lt, Ln);
-    CUDA_OK(c, launch_phase(Lt, c->cur, 0, c->stream));   // density of the current lattice
+    CUDA_OK(c, launch_phase(Lt, c->cur, 0, c->stream));
+    CUDA_OK(c, launch_phase(Lt, c->cur, 1, c->stream));
     c->rho_ok = true;
   }
   if (n >= 2 && c->stream != nullptr) {
@@ -477,6 +481,7 @@ lbm_status lbm_build_links(lbm_ctx* c) {
   o.bnode = (int*)(w + y.bnode); o.bstart = (int*)(w + y.bstart); o.ldir = (uint8_t*)(w + y.ldir);
   o.lq64 = (double*)(w + y.lq64); o.lx2f = (uint8_t*)(w + y.lx2f); o.lq = w + y.lq;
   o.s1node = (int*)(w + y.s1node); o.s1mask = (uint8_t*)(w + y.s1mask); o.s1winv = w + y.s1winv;
+  o.s1nb = (int*)(w + y.s1nb);
   o.s2node = (int*)(w + y.s2node); o.s2mask = (uint8_t*)(w + y.s2mask); o.s2winv = w + y.s2winv;
   o.mu = w + y.mu;
   o.fp64 = c->fp64;

@@ -62,6 +62,8 @@ struct Lattice {
   int n_s1, n_s2;
   const int* s1node;
   const uint8_t* s1mask;         // bit i-1 set: neighbour e_i (i = 1..8) contributes
+  const int* s1nb;              // per first-layer entry, 8 ints: the boundary-node index of each
+                                // contributing neighbour (-1 elsewhere)
   const real* s1winv;
   const int* s2node;
   const uint8_t* s2mask;

@@ -225,9 +225,12 @@ __global__ void k_fill_links(GeomParams g, const uint8_t* kind, const int* link_
   }
 }
 
+// bidx, nb (first layer only): for each contributing neighbour (all of them are boundary-fluid
+// nodes) its index in the boundary-node list, nb[8 j + i - 1], -1 where bit i-1 of the mask is
+// clear
 template <typename real>
 __global__ void k_fill_layer(GeomParams g, const uint8_t* kind, const int* off, uint8_t cls, uint8_t from,
-                             int* node, uint8_t* mask, real* winv) {
+                             int* node, uint8_t* mask, real* winv, const int* bidx, int* nb) {
   long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.plane) return;
   if (kind[n] != cls) return;
@@ -242,6 +245,12 @@ __global__ void k_fill_layer(GeomParams g, const uint8_t* kind, const int* off, 
   node[j] = (int)n;
   mask[j] = (uint8_t)msk;
   winv[j] = (real)(1.0 / wsum);
+  if (nb) {
+    for (int i = 1; i < 9; ++i) {
+      int m;
+      nb[8 * j + i - 1] = (msk & (1u << (i - 1))) && gnb(g, x, y, i, &m) ? bidx[m] : -1;
+    }
+  }
 }
 
 // chemical potential plane (shifted by k^2 mu_sat): 0 at fluid and deep solid nodes, the
@@ -272,18 +281,23 @@ static cudaError_t fill_typed(const GeomParams& g, const GeomScratch& s, const G
   e = excl_scan(s.cnt, s.cnt, s.block_sums, s.totals + 6, g.plane, st);
   if (e != cudaSuccess) return e;
   k_fill_links<real><<<gn, 256, 0, st>>>(g, o.kind, link_off, s.cnt, o);
+  // the boundary-node index of every boundary node (the scan just used) outlives the link
+  // offsets: keep it for the first layer's neighbour table
+  int* bidx = s.off;
+  e = cudaMemcpyAsync(bidx, s.cnt, (size_t)g.plane * sizeof(int), cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
   // layer 1 list
   k_count<<<gn, 256, 0, st>>>(g, o.kind, s.cnt, 2);
   e = excl_scan(s.cnt, s.cnt, s.block_sums, s.totals + 7, g.plane, st);
   if (e != cudaSuccess) return e;
   k_fill_layer<real><<<gn, 256, 0, st>>>(g, o.kind, s.cnt, KIND_SOLID1, KIND_FLUID, o.s1node, o.s1mask,
-                                         (real*)o.s1winv);
+                                         (real*)o.s1winv, bidx, o.s1nb);
   // layer 2 list
   k_count<<<gn, 256, 0, st>>>(g, o.kind, s.cnt, 3);
   e = excl_scan(s.cnt, s.cnt, s.block_sums, s.totals + 7, g.plane, st);
   if (e != cudaSuccess) return e;
   k_fill_layer<real><<<gn, 256, 0, st>>>(g, o.kind, s.cnt, KIND_SOLID2, KIND_SOLID1, o.s2node, o.s2mask,
-                                         (real*)o.s2winv);
+                                         (real*)o.s2winv, nullptr, nullptr);
   k_wall_mu<real><<<gn, 256, 0, st>>>(g, o.kind, s.body, (real*)o.mu);
   return cudaGetLastError();
 }

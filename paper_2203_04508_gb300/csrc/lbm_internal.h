@@ -14,8 +14,9 @@ template <typename real> cudaError_t launch_step(const Lattice<real>& L, int cur
 template <typename real> int launches_per_step(const Lattice<real>& L);
 template <typename real> cudaError_t launch_phase(const Lattice<real>& L, int cur, int phase, cudaStream_t s);
 template <typename real> cudaError_t launch_macro(const Lattice<real>& L, int cur, cudaStream_t s);
-// step t with its boundary phase overlapping the density pass of step t+1 on stream s2 (Lt:
-// rho = density of lattice cur, rho_b set; Ln: rho = the plane receiving lattice cur^1's)
+// step t with its boundary phase and the next state's solid layers overlapping the density
+// pass of step t+1 on stream s2 (Lt: rho = fluid and solid-layer densities of lattice cur,
+// rho_b set; Ln: rho = the plane receiving lattice cur^1's).  Starts at the chemical potential.
 template <typename real>
 cudaError_t launch_step_overlap(const Lattice<real>& Lt, const Lattice<real>& Ln, int cur, cudaStream_t s,
                                 cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join);
@@ -49,6 +50,7 @@ struct GeomOut {
   uint8_t* kind;
   int* bnode; int* bstart; uint8_t* ldir; double* lq64; uint8_t* lx2f;
   int* s1node; uint8_t* s1mask; int* s2node; uint8_t* s2mask;
+  int* s1nb;                                // 8 per first-layer entry: neighbours' boundary index
   void* lq;   void* s1winv; void* s2winv;   // precision-typed
   void* mu;                                 // precision-typed plane
   int fp64;

@@ -155,6 +155,22 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_bc(Lattice<real> L, int cur) {
   }
 }
 
+// Eq. 15 for the first solid layer from the boundary nodes' densities in rho_b (every fluid
+// neighbour of a solid node is a boundary node): the sum phase_solid forms, in its order, so
+// the first layer can be done before the density plane of the new state is complete.
+template <typename real>
+__global__ void __launch_bounds__(NODE_BLOCK) k_solid1_b(Lattice<real> L) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= L.n_s1) return;
+  const uint8_t m = L.s1mask[j];
+  real acc = real(0);
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    if (m & (1u << (i - 1))) acc += real(wgt(i)) * L.rho_b[L.s1nb[8 * j + i - 1]];
+  }
+  L.rho[L.s1node[j]] = acc * L.s1winv[j];
+}
+
 // Boundary nodes' densities, left by the boundary phase in rho_b, into the density plane.
 template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_rho_scatter(Lattice<real> L) {
@@ -336,17 +352,17 @@ cudaError_t launch_step(const Lattice<real>& L, int cur, cudaStream_t s) {
 }
 
 // One step whose boundary phase overlaps the density pass of the next step.  Lt describes
-// step t (rho = the density plane of lattice cur, holding its density; rho_b set), Ln the next
-// state (rho = the other density plane).  After the collide the work forks: k_bc on s, the
-// density of every node of lattice cur^1 on s2 -- final everywhere but at boundary nodes, whose
-// populations k_bc is still completing and whose densities it leaves in rho_b -- then joins,
-// and k_rho_scatter puts those in place.  Sequence and values are those of launch_step.
+// step t (rho = the density plane of lattice cur, holding its fluid AND solid-layer densities;
+// rho_b set), Ln the next state (rho = the other density plane).  After the collide the work
+// forks.  On s: k_bc, which completes the boundary nodes' populations and leaves their
+// densities in rho_b; then the two solid layers of the next state (the first from rho_b, the
+// second from the first).  On s2: the density of every fluid node of lattice cur^1 -- final
+// everywhere but at boundary nodes.  After the join k_rho_scatter puts the boundary densities
+// in place.  The values are those of launch_step; only the order of independent work differs.
 template <typename real>
 cudaError_t launch_step_overlap(const Lattice<real>& Lt, const Lattice<real>& Ln, int cur, cudaStream_t s,
                                 cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join) {
   const Lattice<real>& L = Lt;
-  if (L.n_s1 > 0) k_solid<real><<<grid_for(L.n_s1, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 1);
-  if (L.n_s2 > 0) k_solid<real><<<grid_for(L.n_s2, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 2);
   if (L.eos != EOS_NONE) k_mu<real><<<node_grid(L), node_block(), 0, s>>>(L);
   k_collide<real><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
   cudaError_t e = cudaEventRecord(fork, s);
@@ -354,6 +370,8 @@ cudaError_t launch_step_overlap(const Lattice<real>& Lt, const Lattice<real>& Ln
   if (e != cudaSuccess) return e;
   const unsigned gb = grid_for(L.n_bnodes, NODE_BLOCK);
   k_bc<real><<<gb > 0 ? gb : 1, NODE_BLOCK, 0, s>>>(L, cur);
+  if (Ln.n_s1 > 0) k_solid1_b<real><<<grid_for(Ln.n_s1, NODE_BLOCK), NODE_BLOCK, 0, s>>>(Ln);
+  if (Ln.n_s2 > 0) k_solid<real><<<grid_for(Ln.n_s2, NODE_BLOCK), NODE_BLOCK, 0, s>>>(Ln, 2);
   k_rho_vec<real><<<rho_grid(Ln), NODE_BLOCK, 0, s2>>>(Ln, cur ^ 1);
   e = cudaEventRecord(join, s2);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join, 0);
