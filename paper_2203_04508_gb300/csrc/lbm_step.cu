@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_mu(Lattice<real> L) {
 // through the L1/L2 path; the arithmetic is force_at's, operation for operation.
 constexpr int CT_X = 32, CT_Y = NODE_BLOCK / CT_X, CT_H = 2;
 constexpr int CT_SX = CT_X + 2 * CT_H, CT_SY = CT_Y + 2 * CT_H;
+static_assert(CT_X == 32 && CT_SX - 32 <= 32, "one warp stages a row of the tile and its halo");
 
 template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_collide(Lattice<real> L, int cur) {
@@ -106,19 +107,34 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide(Lattice<real> L, int cur
     for (int i = 0; i < 9; ++i) fl[i] = fin[i * L.plane + y * L.pitch + x];
   }
   if (stencils) {
-    for (int e = threadIdx.x; e < CT_SX * CT_SY; e += NODE_BLOCK) {
-      const int ly = e / CT_SX, lx = e - ly * CT_SX;
-      const int x = x0 + lx - CT_H, y = y0 + ly - CT_H;
-      real r = real(0), m = real(0);
-      // a fluid node's stencil reaches x in [-2, nx+1] (wrapped) and, with walls, stays inside
-      // the rows; other slots are never read
-      if (x <= L.nx + 1 && (L.walls ? (y >= 0 && y < L.ny) : (y <= L.ny + 1))) {
-        const int n = node_at(L, x, y);
-        r = L.rho[n];
-        m = L.mu[n];
+    if (x0 >= CT_H && x0 + CT_X + CT_H <= L.nx && y0 >= CT_H && y0 + CT_Y + CT_H <= L.ny) {
+      // tile and halo inside the lattice (block-uniform): one warp per staged row, plain offsets
+      const int lane = threadIdx.x & 31, wr = threadIdx.x >> 5;
+      const int base = (y0 - CT_H) * L.pitch + (x0 - CT_H);
+      for (int r = wr; r < CT_SY; r += NODE_BLOCK / 32) {
+        const int row = base + r * L.pitch;
+        s_rho[r][lane] = L.rho[row + lane];
+        s_mu[r][lane] = L.mu[row + lane];
+        if (lane < CT_SX - 32) {
+          s_rho[r][32 + lane] = L.rho[row + 32 + lane];
+          s_mu[r][32 + lane] = L.mu[row + 32 + lane];
+        }
       }
-      s_rho[ly][lx] = r;
-      s_mu[ly][lx] = m;
+    } else {
+      for (int e = threadIdx.x; e < CT_SX * CT_SY; e += NODE_BLOCK) {
+        const int ly = e / CT_SX, lx = e - ly * CT_SX;
+        const int x = x0 + lx - CT_H, y = y0 + ly - CT_H;
+        real r = real(0), m = real(0);
+        // a fluid node's stencil reaches x in [-2, nx+1] (wrapped) and, with walls, stays
+        // inside the rows; other slots are never read
+        if (x <= L.nx + 1 && (L.walls ? (y >= 0 && y < L.ny) : (y <= L.ny + 1))) {
+          const int n = node_at(L, x, y);
+          r = L.rho[n];
+          m = L.mu[n];
+        }
+        s_rho[ly][lx] = r;
+        s_mu[ly][lx] = m;
+      }
     }
     __syncthreads();
   }
