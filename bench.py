@@ -16,6 +16,16 @@ instead, flushing L2 before every timed step.
 Under torchrun each rank advances its own replica of the workload (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.  `--impl reference` times the FP64
 reference oracle on the host cores instead (rank 0 only).
+
+Besides the contract keys the line carries: `roofline` (the collide kernel's algorithmic bytes
+over its CUDA-event time, against the measured HBM copy bandwidth, with the per-phase times),
+`cpu_baseline` (the oracle on the host cores), `e2e` (through the C-ABI with host buffers),
+`clocks`, `batched` (256 instances of 128^2..768^2 in one persistent launch against the same
+instances stepped one by one; the autotuned tile shape; the same comparison on 1024 instances
+of 64^2..128^2), and `adjoint` (512 x 512, 4000 steps, checkpoint every 200: forward,
+checkpointed forward and reverse-sweep times, one reverse step against one forward step, and
+the gradient).  `--mode kernels` / `--mode adjoint` run only the timed step loop / only the
+gradient workload (for profiler captures).
 """
 from __future__ import annotations
 
