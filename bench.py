@@ -118,7 +118,8 @@ def run_batched(G, torch, rank, world, steps, small=False):
             "mlups_batched": round(nodes * steps / ms_b / 1e3, 1), "ms_looped": round(ms_l, 3),
             "mlups_looped": round(nodes * steps / ms_l / 1e3, 1), "speedup": round(ms_l / ms_b, 3),
             "persistent_grid": info["grid"], "graph_captured": info["graph"],
-            "tile": tuned["tile"], "autotune_ms_per_10_steps": tuned["ms"],
+            "tile": tuned["tile"], "schedule": "two groups" if tuned["groups"] == 2 else "lockstep",
+            "autotune_ms_per_10_steps": tuned["ms"],
             "looped_timing": "host wall clock around all instances' lbm_step calls, synchronised"}
 
 
@@ -430,7 +431,8 @@ def main():
                            speedup=round(float(t[1]) / float(t[0]), 3), instances=256)
         if small is not None:
             batched["small_instances"] = {k: small[k] for k in ("instances", "nodes", "ms_batched", "mlups_batched",
-                                                                 "ms_looped", "mlups_looped", "speedup", "tile")}
+                                                                 "ms_looped", "mlups_looped", "speedup", "tile",
+                                                                 "schedule")}
             batched["small_instances"]["sizes"] = "64^2..128^2"
 
     adjoint = None

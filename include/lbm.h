@@ -290,12 +290,24 @@ lbm_status lbm_batch_set_spin_limit(lbm_batch* b, int64_t polls);
  * nearby rows fit the instances' widths).  LBM_EINVAL outside the range.  Synchronises. */
 lbm_status lbm_batch_set_tile(lbm_batch* b, int32_t log2w);
 
-/* Tile-shape autotuner: times `steps` steps of the batch with each tile shape (CUDA events on
- * the batch's stream, after one untimed launch of the same length per shape), keeps the fastest
- * and writes its log2w to *chosen and the five times (ms, log2w = 4 .. 8) to ms (either may be
- * NULL).  The trials are real steps: every instance advances 10 * steps steps, so call it on a
- * representative state and re-initialise afterwards if the state matters. */
-lbm_status lbm_batch_autotune(lbm_batch* b, int64_t steps, int32_t* chosen, double* ms);
+/* Schedule of the persistent kernel.  groups = 1: every instance runs the same phase between
+ * two grid barriers (lockstep).  groups = 2: the instances are split into two groups of about
+ * equal node counts and the second runs three phases behind the first, so that each barrier
+ * interval pairs the memory-bound density pass of one group with the instruction-bound chemical
+ * potential of the other (and the collision with a solid layer, the boundary links with the
+ * other solid layer).  Each instance still runs its phases in order: both schedules give
+ * identical results.  Default 2.  LBM_EINVAL for other values.  Synchronises. */
+lbm_status lbm_batch_set_schedule(lbm_batch* b, int32_t groups);
+
+/* Autotuner of tile shape and schedule: times `steps` steps of the batch with each tile shape
+ * under the current schedule, then with the fastest shape under both schedules (CUDA events on
+ * the batch's stream, each after one untimed launch of the same length), and keeps the fastest
+ * combination.  Writes the chosen log2w and groups (either pointer may be NULL) and the seven
+ * times in ms (tile log2w = 4 .. 8, then groups 1 and 2) to ms (may be NULL).  The trials are
+ * real steps: every instance advances 14 * steps steps, so call it on a representative state
+ * and re-initialise afterwards if the state matters. */
+lbm_status lbm_batch_autotune(lbm_batch* b, int64_t steps, int32_t* chosen_log2w, int32_t* chosen_groups,
+                              double* ms);
 
 /* Instance k of the batch (owned by the batch). */
 lbm_status lbm_batch_instance(lbm_batch* b, int32_t k, lbm_ctx** ctx);

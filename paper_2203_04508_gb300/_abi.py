@@ -67,7 +67,8 @@ _SIGS = {
     "lbm_batch_set_spin_limit": (I32, [P, I64]),
     "lbm_batch_instance": (I32, [P, I32, C.POINTER(P)]),
     "lbm_batch_set_tile": (I32, [P, I32]),
-    "lbm_batch_autotune": (I32, [P, I64, C.POINTER(I32), P]),
+    "lbm_batch_set_schedule": (I32, [P, I32]),
+    "lbm_batch_autotune": (I32, [P, I64, C.POINTER(I32), C.POINTER(I32), P]),
     "lbm_batch_info": (I32, [P, P]),
     "lbm_batch_last_error": (C.c_char_p, [P]),
     "lbm_batch_destroy": (None, [P]),

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -759,7 +760,9 @@ struct lbm_batch {
   std::vector<size_t> inst_off, inst_bytes;
   size_t tab_off = 0;
   // table offsets inside the tables region
-  size_t t_lat = 0, t_tiles = 0, t_s1 = 0, t_s2 = 0, t_bc = 0, t_first = 0, t_part = 0, t_bar = 0, t_err = 0;
+  size_t t_lat = 0, t_tiles = 0, t_s1 = 0, t_s2 = 0, t_bc = 0, t_first = 0, t_group = 0, t_part = 0, t_bar = 0,
+         t_err = 0;
+  int groups = 2;
   long long cap_tiles = 0, cap_s1 = 0, cap_s2 = 0, cap_bc = 0;
   BatchDev dev{};
   bool tables = false;
@@ -779,7 +782,7 @@ namespace {
 struct BatchPlan {
   std::vector<size_t> off, bytes;
   size_t tab_off, total;
-  size_t t_lat, t_tiles, t_s1, t_s2, t_bc, t_first, t_part, t_bar, t_err;
+  size_t t_lat, t_tiles, t_s1, t_s2, t_bc, t_first, t_group, t_part, t_bar, t_err;
   long long cap_tiles, cap_s1, cap_s2, cap_bc;
 };
 
@@ -817,7 +820,8 @@ lbm_status plan_batch(int n, const lbm_config* cfgs, BatchPlan* P, char* msg) {
   P->t_s1 = take((size_t)(P->cap_s1 + 1) * sizeof(int2));
   P->t_s2 = take((size_t)(P->cap_s2 + 1) * sizeof(int2));
   P->t_bc = take((size_t)(P->cap_bc + 1) * sizeof(int2));
-  P->t_first = take((size_t)(n + 1) * sizeof(int));
+  P->t_first = take((size_t)n * sizeof(int2));
+  P->t_group = take((size_t)n);
   P->t_part = take((size_t)(P->cap_bc + 1) * sizeof(double));
   P->t_bar = take(16);
   P->t_err = take(16);
@@ -844,21 +848,47 @@ lbm_status bfail(lbm_batch* b, lbm_status s, const char* fmt, ...) {
 template <typename real>
 lbm_status batch_tables(lbm_batch* b) {
   const int bb = batch_block_size();
+  const int G = b->groups;
   std::vector<Lattice<real>> lats(b->n);
-  std::vector<int2> tiles, s1, s2, bc;
-  std::vector<int> first(b->n + 1, 0);
-  for (int k = 0; k < b->n; ++k) {
-    const Lattice<real>& L = b->fp64 ? *reinterpret_cast<const Lattice<real>*>(&b->ctx[k]->Ld)
-                                     : *reinterpret_cast<const Lattice<real>*>(&b->ctx[k]->Lf);
-    lats[k] = L;
-    const long long nt = batch_node_tiles(L.nx, L.ny, b->tile_log2w);
-    for (long long t = 0; t < nt; ++t) tiles.push_back(make_int2(k, (int)t));
-    for (int j = 0; j < L.n_s1; j += bb) s1.push_back(make_int2(k, j));
-    for (int j = 0; j < L.n_s2; j += bb) s2.push_back(make_int2(k, j));
-    first[k] = (int)bc.size();
-    for (int j = 0; j < L.n_bnodes; j += bb) bc.push_back(make_int2(k, j));
+  // groups of about equal node counts: largest instances first, each to the lighter group
+  std::vector<uint8_t> group(b->n, 0);
+  if (G == 2) {
+    std::vector<int> order(b->n);
+    for (int k = 0; k < b->n; ++k) order[k] = k;
+    auto nodes = [&](int k) { return (long long)b->ctx[k]->cfg.nx * b->ctx[k]->cfg.ny; };
+    std::stable_sort(order.begin(), order.end(), [&](int u, int v) { return nodes(u) > nodes(v); });
+    long long load[2] = {0, 0};
+    for (int k : order) {
+      const int g = load[1] < load[0] ? 1 : 0;
+      group[k] = (uint8_t)g;
+      load[g] += nodes(k);
+    }
   }
-  first[b->n] = (int)bc.size();
+  std::vector<int2> tiles, s1, s2, bc, inst_bc(b->n);
+  BatchDev& d = b->dev;
+  for (int g = 0; g < 2; ++g) {
+    d.tile_start[g] = (int)tiles.size();
+    d.s1_start[g] = (int)s1.size();
+    d.s2_start[g] = (int)s2.size();
+    d.bc_start[g] = (int)bc.size();
+    for (int k = 0; k < b->n; ++k) {
+      if (group[k] != g) continue;
+      const Lattice<real>& L = b->fp64 ? *reinterpret_cast<const Lattice<real>*>(&b->ctx[k]->Ld)
+                                       : *reinterpret_cast<const Lattice<real>*>(&b->ctx[k]->Lf);
+      lats[k] = L;
+      const long long nt = batch_node_tiles(L.nx, L.ny, b->tile_log2w);
+      for (long long t = 0; t < nt; ++t) tiles.push_back(make_int2(k, (int)t));
+      for (int j = 0; j < L.n_s1; j += bb) s1.push_back(make_int2(k, j));
+      for (int j = 0; j < L.n_s2; j += bb) s2.push_back(make_int2(k, j));
+      inst_bc[k].x = (int)bc.size();
+      for (int j = 0; j < L.n_bnodes; j += bb) bc.push_back(make_int2(k, j));
+      inst_bc[k].y = (int)bc.size();
+    }
+  }
+  d.tile_start[2] = (int)tiles.size();
+  d.s1_start[2] = (int)s1.size();
+  d.s2_start[2] = (int)s2.size();
+  d.bc_start[2] = (int)bc.size();
   if ((long long)tiles.size() > b->cap_tiles || (long long)s1.size() > b->cap_s1 + 1 ||
       (long long)s2.size() > b->cap_s2 + 1 || (long long)bc.size() > b->cap_bc + 1)
     return bfail(b, LBM_ENOMEM, "batch work lists exceed their capacity");
@@ -868,22 +898,20 @@ lbm_status batch_tables(lbm_batch* b) {
   if (!s1.empty()) BCUDA(b, cudaMemcpyAsync(t + b->t_s1, s1.data(), s1.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
   if (!s2.empty()) BCUDA(b, cudaMemcpyAsync(t + b->t_s2, s2.data(), s2.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
   if (!bc.empty()) BCUDA(b, cudaMemcpyAsync(t + b->t_bc, bc.data(), bc.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
-  BCUDA(b, cudaMemcpyAsync(t + b->t_first, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+  BCUDA(b, cudaMemcpyAsync(t + b->t_first, inst_bc.data(), inst_bc.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+  BCUDA(b, cudaMemcpyAsync(t + b->t_group, group.data(), group.size(), cudaMemcpyHostToDevice, b->stream));
   BCUDA(b, cudaMemsetAsync(t + b->t_err, 0, 16, b->stream));
   BCUDA(b, cudaStreamSynchronize(b->stream));
-  BatchDev& d = b->dev;
   d.n_inst = b->n;
+  d.groups = G;
   d.lat = t + b->t_lat;
-  d.n_node_tiles = (int)tiles.size();
+  d.inst_group = (const uint8_t*)(t + b->t_group);
   d.tile_log2w = b->tile_log2w;
   d.node_tiles = (const int2*)(t + b->t_tiles);
-  d.n_s1_items = (int)s1.size();
-  d.n_s2_items = (int)s2.size();
-  d.n_bc_items = (int)bc.size();
   d.s1_items = (const int2*)(t + b->t_s1);
   d.s2_items = (const int2*)(t + b->t_s2);
   d.bc_items = (const int2*)(t + b->t_bc);
-  d.inst_bc_first = (const int*)(t + b->t_first);
+  d.inst_bc = (const int2*)(t + b->t_first);
   d.bc_partials = (double*)(t + b->t_part);
   d.bar = (unsigned int*)(t + b->t_bar);
   d.err = (int*)(t + b->t_err);
@@ -926,7 +954,7 @@ lbm_status lbm_batch_create(int32_t n, const lbm_config* cfgs, void* stream, voi
   b->inst_bytes = P.bytes;
   b->tab_off = P.tab_off;
   b->t_lat = P.t_lat; b->t_tiles = P.t_tiles; b->t_s1 = P.t_s1; b->t_s2 = P.t_s2; b->t_bc = P.t_bc;
-  b->t_first = P.t_first; b->t_part = P.t_part; b->t_bar = P.t_bar; b->t_err = P.t_err;
+  b->t_first = P.t_first; b->t_group = P.t_group; b->t_part = P.t_part; b->t_bar = P.t_bar; b->t_err = P.t_err;
   b->cap_tiles = P.cap_tiles; b->cap_s1 = P.cap_s1; b->cap_s2 = P.cap_s2; b->cap_bc = P.cap_bc;
   b->ctx.assign(n, nullptr);
   for (int k = 0; k < n; ++k) {
@@ -1031,34 +1059,65 @@ lbm_status lbm_batch_set_tile(lbm_batch* b, int32_t log2w) {
   return b->fp64 ? batch_tables<double>(b) : batch_tables<float>(b);
 }
 
-lbm_status lbm_batch_autotune(lbm_batch* b, int64_t steps, int32_t* chosen, double* ms) {
+lbm_status lbm_batch_set_schedule(lbm_batch* b, int32_t groups) {
+  if (!b || b->ctx.empty()) return LBM_ESTATE;
+  if (groups != 1 && groups != 2) return bfail(b, LBM_EINVAL, "groups must be 1 or 2, not %d", groups);
+  b->groups = groups;
+  if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+  b->graph_steps = -1;
+  if (!b->tables) return LBM_OK;
+  return b->fp64 ? batch_tables<double>(b) : batch_tables<float>(b);
+}
+
+namespace {
+// device time (ms) of `steps` steps of the batch as it is set up, after one untimed launch of
+// the same length (which also captures its graph)
+lbm_status time_batch(lbm_batch* b, int64_t steps, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+  lbm_status st = lbm_batch_step(b, steps);
+  if (st != LBM_OK) return st;
+  cudaEventRecord(e0, b->stream);
+  st = lbm_batch_step(b, steps);
+  cudaEventRecord(e1, b->stream);
+  if (st != LBM_OK) return st;
+  st = lbm_batch_check(b);
+  if (st == LBM_OK && cudaEventElapsedTime(ms, e0, e1) != cudaSuccess) st = bfail(b, LBM_ECUDA, "event timing failed");
+  return st;
+}
+}  // namespace
+
+lbm_status lbm_batch_autotune(lbm_batch* b, int64_t steps, int32_t* chosen_log2w, int32_t* chosen_groups,
+                              double* ms) {
   if (!b || !b->tables) return LBM_ESTATE;
   if (steps < 1 || steps > (1LL << 20)) return bfail(b, LBM_EINVAL, "trial steps must lie in [1, 2^20]");
   cudaEvent_t e0, e1;
   BCUDA(b, cudaEventCreate(&e0));
   BCUDA(b, cudaEventCreate(&e1));
-  int best = b->tile_log2w;
+  int best = b->tile_log2w, best_g = b->groups;
   double best_ms = 1e300;
   lbm_status st = LBM_OK;
+  // tile shapes under the current schedule, then both schedules with the fastest shape
   for (int lw = BATCH_TILE_LOG2W_MIN; lw <= BATCH_TILE_LOG2W_MAX && st == LBM_OK; ++lw) {
-    st = lbm_batch_set_tile(b, lw);
-    if (st == LBM_OK) st = lbm_batch_step(b, steps);   // first launch of this shape: captures its graph
-    if (st != LBM_OK) break;
-    cudaEventRecord(e0, b->stream);
-    st = lbm_batch_step(b, steps);
-    cudaEventRecord(e1, b->stream);
-    if (st != LBM_OK) break;
-    st = lbm_batch_check(b);
     float t = 0.f;
-    if (st == LBM_OK && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) st = bfail(b, LBM_ECUDA, "event timing failed");
+    st = lbm_batch_set_tile(b, lw);
+    if (st == LBM_OK) st = time_batch(b, steps, e0, e1, &t);
     if (ms) ms[lw - BATCH_TILE_LOG2W_MIN] = t;
     if (st == LBM_OK && t < best_ms) { best_ms = t; best = lw; }
+  }
+  if (st == LBM_OK) st = lbm_batch_set_tile(b, best);
+  best_ms = 1e300;
+  for (int g = 1; g <= 2 && st == LBM_OK; ++g) {
+    float t = 0.f;
+    st = lbm_batch_set_schedule(b, g);
+    if (st == LBM_OK) st = time_batch(b, steps, e0, e1, &t);
+    if (ms) ms[5 + g - 1] = t;
+    if (st == LBM_OK && t < best_ms) { best_ms = t; best_g = g; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != LBM_OK) return st;
-  if (chosen) *chosen = best;
-  return lbm_batch_set_tile(b, best);
+  if (chosen_log2w) *chosen_log2w = best;
+  if (chosen_groups) *chosen_groups = best_g;
+  return lbm_batch_set_schedule(b, best_g);
 }
 
 lbm_status lbm_batch_instance(lbm_batch* b, int32_t k, lbm_ctx** ctx) {
@@ -1070,9 +1129,9 @@ lbm_status lbm_batch_instance(lbm_batch* b, int32_t k, lbm_ctx** ctx) {
 lbm_status lbm_batch_info(lbm_batch* b, int64_t* out4) {
   if (!b || !out4) return LBM_EINVAL;
   out4[0] = b->grid;
-  out4[1] = b->dev.n_node_tiles;
+  out4[1] = b->dev.tile_start[2];
   out4[2] = b->use_graph ? 1 : 0;
-  out4[3] = b->dev.n_bc_items;
+  out4[3] = b->dev.bc_start[2];
   return LBM_OK;
 }
 

@@ -86,75 +86,128 @@ __device__ __forceinline__ bool tile_node(const Lattice<real>& L, int log2w, int
   return x < L.nx && y < L.ny;
 }
 
+// The six phases of a step, in order; the compensation sums of a step follow its boundary
+// phase after a barrier.
+enum { PH_RHO = 0, PH_S1, PH_S2, PH_MU, PH_COLLIDE, PH_BC, N_PHASES };
+// Group 1 runs this many phases behind group 0, so that the memory-bound density pass of one
+// group shares a barrier interval with the instruction-bound chemical potential of the other
+// (and the collide with the first solid layer, the boundary phase with the second).
+constexpr int SKEW = 3;
+
+// work list of phase p for group g: [first, last) of the node-tile, solid-layer or
+// boundary-chunk list
+__device__ __forceinline__ void phase_list(const BatchDev& B, int p, int g, const int2*& items, int& first,
+                                           int& last) {
+  if (p == PH_S1) { items = B.s1_items; first = B.s1_start[g]; last = B.s1_start[g + 1]; }
+  else if (p == PH_S2) { items = B.s2_items; first = B.s2_start[g]; last = B.s2_start[g + 1]; }
+  else if (p == PH_BC) { items = B.bc_items; first = B.bc_start[g]; last = B.bc_start[g + 1]; }
+  else { items = B.node_tiles; first = B.tile_start[g]; last = B.tile_start[g + 1]; }
+}
+
+// This block's share [w0, w1) of the list of phase p, for one group (block-uniform).
 template <typename real>
-__global__ void __launch_bounds__(BATCH_BLOCK, 6) k_batch(BatchDev B, int n_steps, int cur0) {
-  __shared__ __align__(16) Lattice<real> L;
-  __shared__ double red[32];
-  const Lattice<real>* lat = static_cast<const Lattice<real>*>(B.lat);
-  unsigned int target = 0;
-  int loaded = -1;
-  int w0, w1;
-  for (int s = 0; s < n_steps; ++s) {
-    const int cur = cur0 ^ (s & 1);
-    // density
-    block_range(B.n_node_tiles, w0, w1);
-    for (int w = w0; w < w1; ++w) {
-      const int2 t = B.node_tiles[w];
-      load_lattice(L, lat, t.x, loaded);
-      int x, y;
-      if (tile_node(L, B.tile_log2w, t.y, x, y)) phase_rho(L, cur, x, y);
-    }
-    if (!grid_sync(B, ++target)) return;
-    // solid layers (Eq. 15), the second after the first
-    for (int layer = 1; layer <= 2; ++layer) {
-      const int2* items = layer == 1 ? B.s1_items : B.s2_items;
-      block_range(layer == 1 ? B.n_s1_items : B.n_s2_items, w0, w1);
+__device__ __forceinline__ void run_phase(const BatchDev& B, const Lattice<real>* lat, Lattice<real>& L,
+                                          int& loaded, int p, int cur, const int2* items, int w0, int w1,
+                                          double* red) {
+  int x, y;
+  switch (p) {
+    case PH_RHO:
+      for (int w = w0; w < w1; ++w) {
+        const int2 t = items[w];
+        load_lattice(L, lat, t.x, loaded);
+        if (tile_node(L, B.tile_log2w, t.y, x, y)) phase_rho(L, cur, x, y);
+      }
+      break;
+    case PH_S1:
+    case PH_S2: {
+      const int layer = p == PH_S1 ? 1 : 2;
       for (int w = w0; w < w1; ++w) {
         const int2 t = items[w];
         load_lattice(L, lat, t.x, loaded);
         const int j = t.y + threadIdx.x;
         if (j < (layer == 1 ? L.n_s1 : L.n_s2)) phase_solid(L, layer, j);
       }
-      if (!grid_sync(B, ++target)) return;
+      break;
     }
-    // chemical potential (Eq. 12)
-    block_range(B.n_node_tiles, w0, w1);
-    for (int w = w0; w < w1; ++w) {
-      const int2 t = B.node_tiles[w];
-      load_lattice(L, lat, t.x, loaded);
-      int x, y;
-      if (L.eos != EOS_NONE && tile_node(L, B.tile_log2w, t.y, x, y)) phase_mu(L, x, y);
-    }
-    if (!grid_sync(B, ++target)) return;
-    // force + collision + streaming
-    for (int w = w0; w < w1; ++w) {
-      const int2 t = B.node_tiles[w];
-      load_lattice(L, lat, t.x, loaded);
-      int x, y;
-      if (tile_node(L, B.tile_log2w, t.y, x, y)) phase_collide(L, cur, x, y);
-    }
-    if (!grid_sync(B, ++target)) return;
-    // boundary links (Eqs. 16-18); each chunk's compensation sum, in a fixed order
-    block_range(B.n_bc_items, w0, w1);
-    for (int w = w0; w < w1; ++w) {
-      const int2 t = B.bc_items[w];
-      load_lattice(L, lat, t.x, loaded);
-      const int b = t.y + threadIdx.x;
-      const double sum = b < L.n_bnodes ? phase_bc(L, cur, b) : 0.0;
-      const double bs = block_sum(sum, red);
-      if (threadIdx.x == 0) B.bc_partials[w] = bs;
-    }
-    if (!grid_sync(B, ++target)) return;
-    // per-instance domain sum of the step's compensation, chunks in order
-    if (threadIdx.x == 0) {
-      for (int k = blockIdx.x; k < B.n_inst; k += gridDim.x) {
-        double total = 0.0;
-        for (int w = B.inst_bc_first[k]; w < B.inst_bc_first[k + 1]; ++w) total += B.bc_partials[w];
-        const Lattice<real>& Lk = lat[k];
-        const unsigned long long st = *Lk.step_ctr;
-        Lk.dM_ring[st % DM_RING] = total;
-        *Lk.step_ctr = st + 1;
+    case PH_MU:
+      for (int w = w0; w < w1; ++w) {
+        const int2 t = items[w];
+        load_lattice(L, lat, t.x, loaded);
+        if (L.eos != EOS_NONE && tile_node(L, B.tile_log2w, t.y, x, y)) phase_mu(L, x, y);
       }
+      break;
+    case PH_COLLIDE:
+      for (int w = w0; w < w1; ++w) {
+        const int2 t = items[w];
+        load_lattice(L, lat, t.x, loaded);
+        if (tile_node(L, B.tile_log2w, t.y, x, y)) phase_collide(L, cur, x, y);
+      }
+      break;
+    default:
+      // boundary links (Eqs. 16-18); each chunk's compensation sum, in a fixed order
+      for (int w = w0; w < w1; ++w) {
+        const int2 t = items[w];
+        load_lattice(L, lat, t.x, loaded);
+        const int b = t.y + threadIdx.x;
+        const double sum = b < L.n_bnodes ? phase_bc(L, cur, b) : 0.0;
+        const double bs = block_sum(sum, red);
+        if (threadIdx.x == 0) B.bc_partials[w] = bs;
+      }
+  }
+}
+
+// n_steps steps of every instance.  The launch runs in ticks separated by grid barriers; at
+// tick tau group g is at phase q = tau - SKEW g of its sequence (q / 6 = step, q % 6 = phase),
+// so with two groups their phases interleave; with one group this is the plain lockstep
+// schedule.  Each instance still runs its phases in order, so the values do not depend on the
+// schedule.
+template <typename real>
+__global__ void __launch_bounds__(BATCH_BLOCK, 6) k_batch(BatchDev B, int n_steps, int cur0) {
+  __shared__ __align__(16) Lattice<real> Ls[2];
+  __shared__ double red[32];
+  __shared__ int loaded[2];     // instance whose descriptor Ls[g] holds (block-uniform)
+  const Lattice<real>* lat = static_cast<const Lattice<real>*>(B.lat);
+  const int G = B.groups;
+  const int last_q = N_PHASES * n_steps;               // q of the final compensation sums
+  const int ticks = last_q + SKEW * (G - 1) + 1;
+  unsigned int target = 0;
+  if (threadIdx.x < 2) loaded[threadIdx.x] = -1;
+  __syncthreads();
+  for (int tau = 0; tau < ticks; ++tau) {
+    if (tau > 0 && !grid_sync(B, ++target)) return;
+    // per-instance domain sum of the compensation of the step whose boundary phase ended at
+    // the barrier just passed, chunks in order
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        if (g >= G) continue;
+        const int q = tau - SKEW * g;
+        if (q < N_PHASES || q > last_q || q % N_PHASES != 0) continue;
+        for (int k = blockIdx.x; k < B.n_inst; k += gridDim.x) {
+          if (B.inst_group[k] != g) continue;
+          double total = 0.0;
+          for (int w = B.inst_bc[k].x; w < B.inst_bc[k].y; ++w) total += B.bc_partials[w];
+          const Lattice<real>& Lk = lat[k];
+          const unsigned long long st = *Lk.step_ctr;
+          Lk.dM_ring[st % DM_RING] = total;
+          *Lk.step_ctr = st + 1;
+        }
+      }
+    }
+    // this tick's phase of each group; even blocks take group 0's share first, odd blocks
+    // group 1's, so that every SM works on both phases at once
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      const int g = h ^ (int)(blockIdx.x & 1);
+      const int q = tau - SKEW * g;
+      if (g >= G || q < 0 || q >= last_q) continue;
+      const int p = q % N_PHASES;
+      const int cur = cur0 ^ ((q / N_PHASES) & 1);
+      const int2* items;
+      int first, last, w0, w1;
+      phase_list(B, p, g, items, first, last);
+      block_range(last - first, w0, w1);
+      run_phase(B, lat, Ls[g], loaded[g], p, cur, items, first + w0, first + w1, red);
     }
   }
 }

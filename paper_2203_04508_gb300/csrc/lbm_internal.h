@@ -67,14 +67,16 @@ cudaError_t geom_fill(const GeomParams& g, const GeomScratch& s, const GeomOut& 
 struct BatchDev {
   int n_inst;
   const void* lat;              // device array of n_inst Lattice<real> descriptors
-  int n_node_tiles;             // (instance, tile) of 256 nodes, row-major over the tiles
-  int tile_log2w;               // tile width 2^tile_log2w, height 256 / 2^tile_log2w
-  const int2* node_tiles;
-  int n_s1_items, n_s2_items, n_bc_items;   // (instance, first entry) of 256 list entries
-  const int2* s1_items;
+  int groups;                   // 1: all instances in lockstep; 2: group 1 runs SKEW phases behind
+  const uint8_t* inst_group;    // group of each instance
+  // work lists, group 0's items first: group g's are [x_start[g], x_start[g+1])
+  int tile_log2w;               // node tiles: width 2^tile_log2w, height 256 / 2^tile_log2w
+  int tile_start[3], s1_start[3], s2_start[3], bc_start[3];
+  const int2* node_tiles;       // (instance, tile), row-major over each instance's tiles
+  const int2* s1_items;         // (instance, first entry) of 256 list entries
   const int2* s2_items;
   const int2* bc_items;
-  const int* inst_bc_first;     // bc items of instance k: [first[k], first[k+1])
+  const int2* inst_bc;          // bc items of instance k: [inst_bc[k].x, inst_bc[k].y)
   double* bc_partials;          // one compensation sum per bc item
   unsigned int* bar;            // grid barrier: arrivals, completed barriers
   int* err;                     // set when a barrier wait gave up

@@ -325,15 +325,23 @@ class Batch:
         """Node-tile shape of the persistent kernel: 2^log2w x 256/2^log2w (log2w in 4..8)."""
         self._check(self.lib.lbm_batch_set_tile(self.b, int(log2w)))
 
+    def set_schedule(self, groups: int):
+        """1: all instances in lockstep; 2: two node-balanced groups, the second three phases
+        behind (same results, different overlap of the phases)."""
+        self._check(self.lib.lbm_batch_set_schedule(self.b, int(groups)))
+
     def autotune(self, steps: int = 20):
-        """Times every tile shape over `steps` steps (the instances advance 10 * steps steps)
-        and keeps the fastest; returns {"log2w": chosen, "ms": {shape: ms}}."""
-        chosen = C.c_int32()
-        ms = np.zeros(5)
-        self._check(self.lib.lbm_batch_autotune(self.b, int(steps), C.byref(chosen), ms.ctypes.data))
+        """Times every tile shape, then both schedules with the fastest shape, over `steps`
+        steps each (the instances advance 14 * steps steps) and keeps the fastest; returns
+        {"log2w", "tile", "groups", "ms": {tile or schedule: ms}}."""
+        chosen, groups = C.c_int32(), C.c_int32()
+        ms = np.zeros(7)
+        self._check(self.lib.lbm_batch_autotune(self.b, int(steps), C.byref(chosen), C.byref(groups),
+                                                ms.ctypes.data))
         shapes = [f"{1 << w}x{256 >> w}" for w in range(4, 9)]
-        return {"log2w": chosen.value, "tile": shapes[chosen.value - 4],
-                "ms": {sh: round(float(t), 3) for sh, t in zip(shapes, ms)}}
+        keys = shapes + ["lockstep", "two groups"]
+        return {"log2w": chosen.value, "tile": shapes[chosen.value - 4], "groups": groups.value,
+                "ms": {k: round(float(t), 3) for k, t in zip(keys, ms)}}
 
     def info(self):
         o = np.zeros(4, np.int64)

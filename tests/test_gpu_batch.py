@@ -122,14 +122,47 @@ def test_every_tile_shape_gives_identical_results():
                 assert np.array_equal(pops[k], ref[k]), (log2w, k)
 
 
+def test_both_schedules_give_identical_results():
+    """Lockstep and the two-group skewed schedule run each instance's phases in the same
+    order: FP64 populations and compensation histories after 31 steps are the same bits, and
+    so are the oracle's."""
+    scs = _mixed(True)
+    b = _batch(scs, True)
+    ref = None
+    for groups in (1, 2, 1):
+        b.set_schedule(groups)
+        b.init([sc.droplets() for sc in scs])
+        b.step(31)
+        b.check()
+        got = [(inst.populations(), inst.dM_history(31)) for inst in b.instances]
+        if ref is None:
+            ref = got
+        else:
+            for k in range(len(scs)):
+                assert np.array_equal(got[k][0], ref[k][0]), (groups, k)
+                assert np.array_equal(got[k][1], ref[k][1]), (groups, k)
+    b.set_schedule(2)
+    b.init([sc.droplets() for sc in scs])
+    b.step(40)
+    b.check()
+    for k, sc in enumerate(scs):
+        orc = make_oracle(sc)
+        orc.step(40)
+        er, ev, ef = compare(b.instances[k], orc)
+        assert ef < 1e-11 and er < 1e-11, (sc.name, er, ev, ef)
+
+
 def test_autotune_picks_a_shape_and_the_batch_stays_correct():
     from paper_2203_04508_gb300 import LbmError
     scs = _mixed(False)
     b = _batch(scs, False)
     r = b.autotune(3)
-    assert 4 <= r["log2w"] <= 8
+    assert 4 <= r["log2w"] <= 8 and r["groups"] in (1, 2)
     assert all(v > 0 for v in r["ms"].values())
-    assert r["ms"][r["tile"]] == min(r["ms"].values())
+    tiles = {k: v for k, v in r["ms"].items() if "x" in k}
+    assert r["ms"][r["tile"]] == min(tiles.values())
+    sched = r["ms"]["lockstep"], r["ms"]["two groups"]
+    assert sched[r["groups"] - 1] == min(sched)
     b.init([sc.droplets() for sc in scs])
     b.step(17)
     b.check()
@@ -140,3 +173,5 @@ def test_autotune_picks_a_shape_and_the_batch_stays_correct():
         assert np.abs(fb.astype(np.float64) - fs).max() <= 1e-6 * np.abs(fs).max(), sc.name
     with pytest.raises(LbmError):
         b.set_tile(3)
+    with pytest.raises(LbmError):
+        b.set_schedule(3)
