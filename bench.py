@@ -20,7 +20,8 @@ reference oracle on the host cores instead (rank 0 only).
 Besides the contract keys the line carries: `roofline` (the collide kernel's algorithmic bytes
 over its CUDA-event time, against the measured HBM copy bandwidth, with the per-phase times),
 `cpu_baseline` (the oracle on the host cores), `e2e` (through the C-ABI with host buffers),
-`clocks`, `batched` (256 instances of 128^2..768^2 in one persistent launch against the same
+`clocks`, `fp64` (the same workload with FP64 populations: MLUPS and the FP32/FP64 speed
+ratio), `batched` (256 instances of 128^2..768^2 in one persistent launch against the same
 instances stepped one by one; the autotuned tile shape; the same comparison on 1024 instances
 of 64^2..128^2), and `adjoint` (512 x 512, 4000 steps, checkpoint every 200: forward,
 checkpointed forward and reverse-sweep times, one reverse step against one forward step, and
@@ -295,6 +296,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=200,
                     help="steps of the batched-instances comparison (0: skip it)")
+    ap.add_argument("--fp64-steps", type=int, default=200,
+                    help="steps of the same workload in FP64 (0: skip it)")
     ap.add_argument("--adjoint-steps", type=int, default=4000,
                     help="steps of the gradient workload (0: skip it)")
     ap.add_argument("--adjoint-every", type=int, default=200)
@@ -414,6 +417,25 @@ def main():
                "d2h_bytes_per_step": round(16 + d2h_fields / n_e2e, 2), "steps": n_e2e}
         del lat2
 
+    # the same workload with FP64 populations and arithmetic (the oracle's precision), for the
+    # FP32-versus-FP64 throughput; GB300's FP64 rate is a small fraction of its FP32 rate
+    fp64 = None
+    if args.fp64_steps > 0:
+        lat64 = G.Lattice(sc.physics(), precision=G.LBM_FP64)
+        lat64.init_droplets(sc.droplets())
+        lat64.step(10)
+        s64 = lat64.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s64)
+        lat64.step(args.fp64_steps)
+        e1.record(s64)
+        e1.synchronize()
+        ms64 = e0.elapsed_time(e1) / args.fp64_steps
+        fp64 = {"steps": args.fp64_steps, "ms_per_step": round(ms64, 4),
+                "MLUPS": round(sc.nodes / ms64 / 1e3, 1), "fp32_over_fp64": round(ms64 / ms_step, 2)}
+        del lat64
+        torch.cuda.empty_cache()
+
     batched = None
     if args.batch_steps > 0:
         batched = run_batched(G, torch, rank, world, args.batch_steps)
@@ -463,6 +485,7 @@ def main():
                          "phase_ms": {k: round(float(v), 5) for k, v in
                                       zip(("rho", "solid", "mu", "collide", "bc"), phase_ms)}},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": lps * args.steps,
+            "fp64": fp64,
             "batched": batched,
             "adjoint": adjoint,
             "mass_drift": M / M0 - 1,
