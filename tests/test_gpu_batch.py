@@ -175,3 +175,27 @@ def test_autotune_picks_a_shape_and_the_batch_stays_correct():
         b.set_tile(3)
     with pytest.raises(LbmError):
         b.set_schedule(3)
+
+
+def test_full_size_c4_batch_matches_single_instances():
+    """The benchmark's batch -- 256 instances of 128^2..768^2, FP32, default tile and schedule --
+    after 10 steps: the smallest, median and largest instance against the same lattice stepped
+    on its own (the per-node arithmetic is shared, so only the compiled kernels' FP32 rounding
+    may differ), and every instance's mass."""
+    import torch
+    scs = S.c4_batch()
+    b = _batch(scs, False)
+    b.step(10)
+    b.check()
+    order = sorted(range(len(scs)), key=lambda k: scs[k].nodes)
+    for k in (order[0], order[len(order) // 2], order[-1]):
+        single = make_lattice(scs[k], fp64=False)
+        single.step(10)
+        fb, fs = b.instances[k].populations(), single.populations()
+        assert np.abs(fb.astype(np.float64) - fs).max() <= 1e-6 * np.abs(fs).max(), scs[k].name
+        del single
+    for k in range(len(scs)):
+        M, M0, _ = b.instances[k].mass()
+        assert abs(M / M0 - 1) < 1e-6, scs[k].name
+    del b
+    torch.cuda.empty_cache()
