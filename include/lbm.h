@@ -157,7 +157,9 @@ lbm_status lbm_init(lbm_ctx* ctx, const lbm_init_spec* init);
  * chemical potential (Eq. 12); nonideal force (Eq. 9) with exact-difference forcing
  * (Eqs. 13-14), collision (Eq. 4) and streaming (Eq. 5) fused in one kernel; then every cut
  * link by Eq. 16 (q < 1/2) or Eq. 17 (q >= 1/2) with the per-node compensation of Eq. 18
- * accumulated in FP64. */
+ * accumulated in FP64.  The density pass of the next state overlaps the links on a second
+ * stream the context creates on first use (ordered with the context's stream by events; no
+ * device memory is allocated); to the caller the work is on the context's stream. */
 lbm_status lbm_step(lbm_ctx* ctx, int64_t n);
 
 /* Density and velocity v = u + F/(2 rho) of the current state (the macroscopic velocity

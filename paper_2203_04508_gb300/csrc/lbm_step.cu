@@ -1,6 +1,6 @@
 // Kernels of one time step and of the state set-up / read-out (sm_103a).
 //
-// One step is five launches on one stream:
+// The phases of one step, in the order of their dependencies:
 //   k_rho_vec       density of every fluid node from the 9 offset populations   (Sec. 2.1)
 //   k_solid (x2)    densities of the first, then second solid layer             (Eq. 15)
 //   k_mu            chemical potential at fluid nodes                            (Eq. 12)
@@ -8,6 +8,10 @@
 //                   + push streaming (Eq. 5) into the other lattice
 //   k_bc            every cut link by Eq. 16 / Eq. 17, the per-node compensation of Eq. 18
 //                   accumulated in FP64, and the deterministic domain sum of that step
+// launch_step issues them one after another on one stream (used by the reverse sweep's
+// recomputation and by the per-phase timing).  lbm_step uses launch_step_overlap instead: the
+// step starts at k_mu, and after k_collide the next state's density pass runs on a second
+// stream while k_bc and the next state's solid layers run on the first (same values).
 // The per-node bodies of the phases live in lbm_phases.cuh.
 #include <cstdio>
 
