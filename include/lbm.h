@@ -246,7 +246,9 @@ lbm_status lbm_objective(lbm_ctx* ctx, int32_t body, double* J, void* dJ_drho, i
  * doubles, layout above; FP64 accumulation) if grad is not NULL, and dJ/df of the first state
  * (same layout as dJ_df) if dJ_df0 is not NULL.  on_device applies to the three arrays.  The
  * lattice state, step counter, compensation history and carries are those after the forward
- * pass again when it returns; the call may be repeated.  Synchronises the stream. */
+ * pass again when it returns; the call may be repeated.  The recomputation of each segment
+ * overlaps the reverse steps of the previous one on a second stream the context creates on
+ * first use (the workspace holds two segment buffer sets for that).  Synchronises the stream. */
 lbm_status lbm_adjoint(lbm_ctx* ctx, const void* dJ_drho, const void* dJ_df, int32_t on_device, double* grad,
                        void* dJ_df0);
 
