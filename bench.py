@@ -25,7 +25,8 @@ ratio), `batched` (256 instances of 128^2..768^2 in one persistent launch agains
 instances stepped one by one; the autotuned tile shape; the same comparison on 1024 instances
 of 64^2..128^2), and `adjoint` (512 x 512, 4000 steps, checkpoint every 200: forward,
 checkpointed forward and reverse-sweep times, one reverse step against one forward step, and
-the gradient).  `--mode kernels` / `--mode adjoint` run only the timed step loop / only the
+the gradient), and `bc_comparison` (the boundary schemes of the paper's Sec. 4.3-4.4 on
+reduced-size drops: late per-step compensation and spurious currents).  `--mode kernels` / `--mode adjoint` run only the timed step loop / only the
 gradient workload (for profiler captures).
 """
 from __future__ import annotations
@@ -170,6 +171,48 @@ def run_adjoint(G, torch, steps, every):
             "J": J, "dJ_ddmu_w": float(grad[0]), "dJ_dcx": float(grad[2]), "dJ_dcy": float(grad[3])}
 
 
+def run_bc_comparison(G, steps):
+    """The paper's comparison of boundary schemes (Sec. 4.3-4.4) on reduced-size sessile drops
+    (FP32): per-step compensating mass of Eq. 18 late in the run and the largest speed (the
+    spurious currents), present scheme against MIBC and halfway bounce-back on a flat wall at
+    q = 0.2, and the present scheme's mass and compensation on a curved substrate."""
+    import numpy as np
+    import scenarios as S
+
+    def run(sc):
+        lat = G.Lattice(sc.physics(), precision=G.LBM_FP32)
+        lat.init_droplets(sc.droplets())
+        hist = []
+        for _ in range(steps // 1000):
+            lat.step(1000)
+            hist.append(lat.dM_history(1000))
+        M, M0, _ = lat.mass()
+        r, vx, vy = lat.fields()
+        fl = lat.kind() == 0
+        h = np.concatenate(hist)
+        return {"dM_late_mean_abs": float(np.abs(h[-1000:]).mean()), "dM_max_abs": float(np.abs(h).max()),
+                "mass_drift": M / M0 - 1, "max_speed": float(np.hypot(vx, vy)[fl].max())}
+
+    out = {"steps": steps}
+    names = {S.BC_PRESENT: "present", S.BC_MIBC: "mibc", S.BC_HBB: "hbb"}
+    for theta in (60.0, 120.0):
+        case = {}
+        for bc in (S.BC_PRESENT, S.BC_MIBC, S.BC_HBB):
+            sc = S.Scenario(name="flat_drop", nx=160, ny=100, walls=1, y_bottom=1.2, T_over_Tc=0.6,
+                            coll=S.COLL_MRT, tau=0.8, bc=bc, dmu_w_walls=S.theta_to_dmu(theta),
+                            x0=[80.0], y0=[13.2], r0=[25.0])
+            case[names[bc]] = run(sc)
+        out[f"flat_q0.2_theta{int(theta)}"] = case
+    R, r0 = 40.0, 28.0
+    cx, cy = 100.37, 2.0 + R + 0.61
+    for theta in (60.0, 120.0):
+        sc = S.Scenario(name="curved_drop", nx=200, ny=240, walls=1, T_over_Tc=0.6, coll=S.COLL_MRT, tau=0.8,
+                        cx=[cx], cy=[cy], r=[R], dmu_w=[S.theta_to_dmu(theta)],
+                        x0=[cx], y0=[cy + R + 0.5 * r0], r0=[r0])
+        out[f"curved_theta{int(theta)}_present"] = run(sc)
+    return out
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -296,6 +339,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=200,
                     help="steps of the batched-instances comparison (0: skip it)")
+    ap.add_argument("--bc-steps", type=int, default=10000,
+                    help="steps of the boundary-scheme comparison (0: skip it)")
     ap.add_argument("--fp64-steps", type=int, default=200,
                     help="steps of the same workload in FP64 (0: skip it)")
     ap.add_argument("--adjoint-steps", type=int, default=4000,
@@ -457,6 +502,10 @@ def main():
                                                                  "schedule")}
             batched["small_instances"]["sizes"] = "64^2..128^2"
 
+    bc_comparison = None
+    if args.bc_steps > 0 and rank == 0:
+        bc_comparison = run_bc_comparison(G, max(1000, args.bc_steps // 1000 * 1000))
+
     adjoint = None
     if args.adjoint_steps > 0:
         adjoint = run_adjoint(G, torch, args.adjoint_steps, args.adjoint_every)
@@ -488,6 +537,7 @@ def main():
             "fp64": fp64,
             "batched": batched,
             "adjoint": adjoint,
+            "bc_comparison": bc_comparison,
             "mass_drift": M / M0 - 1,
         }
         print(json.dumps(line), flush=True)
