@@ -43,6 +43,12 @@ WIDTH = 5.0
 # clamped to the table's ends.
 DMU_TABLE = (-0.09, -0.06, -0.045, -0.03, -0.015, 0.0, 0.015, 0.03, 0.06, 0.09, 0.12)
 THETA_TABLE = (18.836, 38.122, 54.453, 68.068, 79.213, 88.991, 97.843, 105.979, 120.462, 133.284, 146.438)
+# The same for Peng-Robinson with the paper's constants (Eqs. 10-11) at T = 0.7 Tc,
+# kappa^ = 0.01: tests/golden/contact_angle_table_pr.json, monotone over 11.4..139.8 deg.
+DMU_TABLE_PR = (-0.1, -0.08, -0.06, -0.05, -0.04, -0.03, -0.02, -0.01, 0.0, 0.01, 0.02, 0.03, 0.04, 0.05,
+                0.06, 0.08, 0.1)
+THETA_TABLE_PR = (11.351, 21.262, 40.91, 51.789, 61.062, 69.114, 76.463, 83.316, 89.75, 95.833, 101.635,
+                  107.195, 112.535, 117.659, 122.548, 131.517, 139.753)
 
 
 @dataclass
@@ -117,8 +123,11 @@ class Scenario:
         return self.nx * self.ny
 
 
-def theta_to_dmu(theta_deg: float) -> float:
-    """Wall chemical-potential offset giving (about) the contact angle theta_deg."""
+def theta_to_dmu(theta_deg: float, eos: int = EOS_CS) -> float:
+    """Wall chemical-potential offset giving (about) the contact angle theta_deg: CS at
+    0.6 Tc, or PR at 0.7 Tc with kappa^ = 0.01."""
+    if eos == EOS_PR:
+        return float(np.interp(theta_deg, THETA_TABLE_PR, DMU_TABLE_PR))
     return float(np.interp(theta_deg, THETA_TABLE, DMU_TABLE))
 
 
@@ -218,6 +227,36 @@ def small_parity(seed: int = 7, nx: int = 131, ny: int = 97, fp64: bool = False,
                     dmu_w=[theta_to_dmu(60.0), theta_to_dmu(120.0)],
                     x0=[c[0] for c in cyl], y0=[c[1] + c[2] for c in cyl], r0=[c[3] for c in cyl],
                     fp64=fp64, steps=1000)
+
+
+# ---- the paper's own drops (Sec. 4.1-4.2), Peng-Robinson with the constants of Eqs. 10-11 --
+PR_PHYSICS = dict(eos=EOS_PR, a=2 / 49, b=2 / 21, R=1.0, omega=0.344, T_over_Tc=0.7, kappa=0.01)
+
+
+def e1_flat_drop(q: float, theta: float, bc: int = BC_PRESENT, nx: int = 500, ny: int = 300,
+                 r0: float = 50.0) -> Scenario:
+    """A drop of radius r0 on a flat substrate whose wall cuts the first fluid row's links at
+    q (0 < q <= 1): the wall line is y_b = 2 - q, halfway bounce-back at the top, periodic in
+    x; its centre is half a radius above the wall (Sec. 4.1: 500 x 300, r0 = 50)."""
+    if not 0.0 < q <= 1.0:
+        raise ValueError("q must lie in (0, 1]")
+    yb = 2.0 - q
+    return Scenario(name=f"e1_flat_q{q:.1f}_th{theta:.0f}", nx=nx, ny=ny, walls=1, y_bottom=yb,
+                    coll=COLL_MRT, tau=0.8, bc=bc, dmu_w_walls=theta_to_dmu(theta, EOS_PR),
+                    x0=[nx / 2], y0=[yb + 0.5 * r0], r0=[r0], steps=20000, **PR_PHYSICS)
+
+
+def e2_curved_drop(theta: float, bc: int = BC_PRESENT, nx: int = 500, ny: int = 600,
+                   R: float = 100.0, r0: float = 70.0) -> Scenario:
+    """A drop of radius r0 resting on a cylinder of radius R at a non-lattice-aligned centre
+    (Sec. 4.2: 500 x 600, R = 100, r0 = 70; 20000 steps at 60 deg, 25000 at 120 deg); flat
+    neutral walls at the bottom and top."""
+    s = nx / 500.0
+    cx, cy = nx / 2 + 0.37, 180.0 * s + 0.61
+    return Scenario(name=f"e2_curved_th{theta:.0f}", nx=nx, ny=ny, walls=1, coll=COLL_MRT, tau=0.8,
+                    bc=bc, cx=[cx], cy=[cy], r=[R], dmu_w=[theta_to_dmu(theta, EOS_PR)],
+                    x0=[cx], y0=[cy + R + 0.5 * r0], r0=[r0],
+                    steps=20000 if theta < 90.0 else 25000, **PR_PHYSICS)
 
 
 ALL = {"c1": c1_plain_fp64, "c2": c2_fp32_single, "c3": c3_impact, "c5": c5_adjoint}

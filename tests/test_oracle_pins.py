@@ -458,3 +458,7 @@ def test_contact_angle_table_is_the_oracles_and_monotone():
         assert pairs[d] == t
     assert np.all(np.diff(S.THETA_TABLE) > 0)
     assert S.theta_to_dmu(90.0) == pytest.approx(0.0, abs=0.002)
+    tab = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "contact_angle_table_pr.json")))
+    assert list(S.DMU_TABLE_PR) == tab["dmu"] and list(S.THETA_TABLE_PR) == tab["theta_deg"]
+    assert np.all(np.diff(S.THETA_TABLE_PR) > 0)
+    assert S.theta_to_dmu(90.0, S.EOS_PR) == pytest.approx(0.0, abs=0.002)
