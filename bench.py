@@ -26,7 +26,9 @@ instances stepped one by one; the autotuned tile shape; the same comparison on 1
 of 64^2..128^2), and `adjoint` (512 x 512, 4000 steps, checkpoint every 200: forward,
 checkpointed forward and reverse-sweep times, one reverse step against one forward step, and
 the gradient), and `bc_comparison` (the boundary schemes of the paper's Sec. 4.3-4.4 on
-reduced-size drops: late per-step compensation and spurious currents).  `--mode kernels` / `--mode adjoint` run only the timed step loop / only the
+reduced-size drops: late per-step compensation and spurious currents), and `paper_runs` (the
+paper's Sec. 4.1-4.2 drops at full size with Peng-Robinson: mass change of the present scheme
+and IBC at every q, 40 flat-wall lattices in one batch, and the curved substrate).  `--mode kernels` / `--mode adjoint` run only the timed step loop / only the
 gradient workload (for profiler captures).
 """
 from __future__ import annotations
@@ -213,6 +215,56 @@ def run_bc_comparison(G, steps):
     return out
 
 
+def run_paper_runs(G, torch):
+    """The paper's own drops at full size with Peng-Robinson (Eqs. 10-11, T = 0.7 Tc), FP32:
+    Sec. 4.1 -- 500 x 300, r0 = 50, q = 0.1 ... 1.0, 60 and 120 deg, present scheme and IBC,
+    20000 steps, all 40 lattices in one batch (one persistent launch); Sec. 4.2 -- 500 x 600,
+    R = 100, r0 = 70, 60 deg (20000 steps) and 120 deg (25000 steps), each lattice on its own.
+    Reports M / M0 - 1 at the end of each run and the throughput of the runs."""
+    import scenarios as S
+    qs = [round(0.1 * k, 1) for k in range(1, 11)]
+    names = {S.BC_PRESENT: "present", S.BC_IBC: "ibc"}
+    keys = [(th, q, bc) for th in (60.0, 120.0) for q in qs for bc in names]
+    scs = [S.e1_flat_drop(q, th, bc) for th, q, bc in keys]
+    steps = scs[0].steps
+    b = G.Batch([sc.physics() for sc in scs], precision=G.LBM_FP32)
+    b.init([sc.droplets() for sc in scs])
+    nodes = sum(sc.nodes for sc in scs)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    b.step(steps)
+    e1.record(b.stream)
+    e1.synchronize()
+    b.check()
+    ms = e0.elapsed_time(e1)
+    flat = {"lattice": "500x300", "instances": len(scs), "steps": steps, "ms": round(ms, 1),
+            "mlups_batched": round(nodes * steps / ms / 1e3, 1)}
+    for k, (th, q, bc) in enumerate(keys):
+        M, M0, _ = b.instances[k].mass()
+        flat.setdefault(f"theta{int(th)}", {}).setdefault(names[bc], {})[f"q{q}"] = float(M / M0 - 1)
+    del b
+    torch.cuda.empty_cache()
+    curved = {"lattice": "500x600"}
+    for th in (60.0, 120.0):
+        case = {}
+        for bc in names:
+            sc = S.e2_curved_drop(th, bc)
+            lat = G.Lattice(sc.physics(), precision=G.LBM_FP32)
+            lat.init_droplets(sc.droplets())
+            e0.record(lat.stream)
+            lat.step(sc.steps)
+            e1.record(lat.stream)
+            e1.synchronize()
+            M, M0, _ = lat.mass()
+            ms = e0.elapsed_time(e1)
+            case[names[bc]] = {"mass_change": float(M / M0 - 1), "steps": sc.steps,
+                               "mlups": round(sc.nodes * sc.steps / ms / 1e3, 1)}
+            del lat
+        curved[f"theta{int(th)}"] = case
+    return {"eos": "PR a=2/49 b=2/21 omega=0.344, T=0.7Tc, kappa=0.01", "flat": flat, "curved": curved,
+            "mass_change": "M/M0 - 1 at the end of the run (FP64 audit over fluid nodes)"}
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -341,6 +393,8 @@ def main():
                     help="steps of the batched-instances comparison (0: skip it)")
     ap.add_argument("--bc-steps", type=int, default=10000,
                     help="steps of the boundary-scheme comparison (0: skip it)")
+    ap.add_argument("--paper-runs", type=int, default=1,
+                    help="1: run the paper's full-size PR drops (Sec. 4.1-4.2); 0: skip")
     ap.add_argument("--fp64-steps", type=int, default=200,
                     help="steps of the same workload in FP64 (0: skip it)")
     ap.add_argument("--adjoint-steps", type=int, default=4000,
@@ -506,6 +560,10 @@ def main():
     if args.bc_steps > 0 and rank == 0:
         bc_comparison = run_bc_comparison(G, max(1000, args.bc_steps // 1000 * 1000))
 
+    paper_runs = None
+    if args.paper_runs and rank == 0:
+        paper_runs = run_paper_runs(G, torch)
+
     adjoint = None
     if args.adjoint_steps > 0:
         adjoint = run_adjoint(G, torch, args.adjoint_steps, args.adjoint_every)
@@ -538,6 +596,7 @@ def main():
             "batched": batched,
             "adjoint": adjoint,
             "bc_comparison": bc_comparison,
+            "paper_runs": paper_runs,
             "mass_drift": M / M0 - 1,
         }
         print(json.dumps(line), flush=True)
