@@ -10,6 +10,7 @@ Functions whose parity with the paper is not pinned by an independent check are 
 """
 from .oracle import (Oracle, OracleConfig, build, eos_eval, lattice, mrt_matrices, feq, meq,
                      collide, link_value, q_cylinder, BC_PRESENT, BC_IBC, BC_MIBC, BC_HBB,
-                     EOS_NONE, EOS_CS, EOS_PR, COLL_BGK, COLL_MRT, set_threads, get_threads)
+                     EOS_NONE, EOS_CS, EOS_PR, COLL_BGK, COLL_MRT, FORCE_CHEMPOT, FORCE_PSEUDO,
+                     set_threads, get_threads)
 
 PARITY_UNPINNED = ()

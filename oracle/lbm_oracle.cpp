@@ -29,6 +29,7 @@ typedef struct {
   const double* r;
   const double* dmu_w;      // wall chemical potential minus the saturation value (mesh units)
   double dmu_w_walls;
+  int32_t force_model;      // 0 chemical potential (Eqs. 9, 12), 1 pseudopotential
 } orc_config;
 
 typedef struct {
@@ -83,6 +84,8 @@ void configure(orc::Sim<T>& s, const orc_config* cfg, int cs_param, int cs_body,
   s.gx = cfg->gx;
   s.gy = cfg->gy;
   s.bc = cfg->bc;
+  if (cfg->force_model != 0 && cfg->force_model != 1) throw std::runtime_error("force_model must be 0 or 1");
+  s.force_model = cfg->force_model;
   s.cx.clear(); s.cy.clear(); s.rad.clear(); s.dmu.clear();
   for (int k = 0; k < cfg->n_cyl; ++k) {
     T cx = cfg->cx[k], cy = cfg->cy[k], dm = cfg->dmu_w[k];

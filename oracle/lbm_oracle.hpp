@@ -17,6 +17,18 @@
 //   Sec. 3.2 (Eq. 18)     mass compensation of the interpolation error
 //   Sec. 4   (Eq. 19)     tanh initial density profile
 //
+// A second force model replaces Eqs. 9 and 12 by the pseudopotential interaction force that
+// the paper cites as the other nonideal-force family (Sec. 1): the Shan-Chen force with the
+// pseudopotential built from the EOS (Yuan and Schaefer),
+//   F(x) = -G psi(x) sum_i w_i psi(x + e_i) e_i,  G = -1,  w = 1/3 (|e| = 1), 1/12 (|e| = 2^1/2),
+//   psi(rho) = sqrt(2 (rho c_s^2 - k^2 p0(rho)) / (-G)),
+// so that rho c_s^2 + (G/2) psi^2 is the EOS pressure k^2 p0 in mesh units (the pressure the
+// chemical-potential force of Eq. 9 also reproduces).  The exact-difference forcing, the
+// collision, the curved boundary (Eqs. 16-18) and Eq. 15 are unchanged; the solid layers carry
+// psi(rho_s) (1 + c_w) of their Eq. 15 density rho_s, with the body's wettability parameter c_w
+// in place of the wall chemical-potential offset (c_w > -1; positive values make the wall
+// hydrophilic, zero is close to neutral).
+//
 // The scalar type T is double, or std::complex<double> for complex-step derivatives with
 // respect to the wall chemical potential and the cylinder centres.  Decisions that are
 // discrete (solid or fluid, which branch of Eqs. 16/17) are taken on real parts.
@@ -153,6 +165,16 @@ struct Eos {
              a * alph * rho * rho / (1.0 + 2.0 * b * rho - b * b * rho * rho);
     }
     return rho * R * Tabs;
+  }
+  // Pseudopotential of the pseudopotential force model: (G/2) psi^2 with G = -1 is the
+  // nonideal part k^2 p0 - rho c_s^2 of the mesh pressure.  Where k^2 p0 would exceed
+  // rho c_s^2 the radicand is clamped to zero.
+  template <class T2>
+  T2 pseudopotential(const T2& rho) const {
+    T2 arg = 2.0 * (rho / 3.0 - k * k * pressure_at(rho, T, alpha));
+    if (re(arg) < 0.0) arg = 0.0;
+    using std::sqrt;
+    return sqrt(arg);
   }
   // Bulk chemical potential psi'(rho) (the constant of integration is irrelevant: only its
   // gradient enters Eq. 9).
@@ -298,6 +320,7 @@ struct Sim {
   double tau = 1;
   double gx = 0, gy = 0;
   int bc = BC_PRESENT;
+  int force_model = 0;  // 0: chemical potential (Eqs. 9, 12); 1: pseudopotential (see the top)
   std::vector<T> cx, cy;
   std::vector<double> rad;
   std::vector<T> dmu;   // wall chemical potential offsets per cylinder (mesh units)
@@ -577,10 +600,25 @@ struct Sim {
     return eos.k * eos.k * eos.mu_sat + off;
   }
 
-  // Eq. 12 at fluid nodes; the chemical-potential wetting condition at solid nodes.
+  // Eq. 12 at fluid nodes; the chemical-potential wetting condition at solid nodes.  With
+  // the pseudopotential force model this plane holds psi instead: psi(rho) at fluid nodes,
+  // psi(rho_s) (1 + c_w) at the solid layers (rho_s from Eq. 15, c_w the body's parameter).
   void chemical_potential() {
     const int n_all = N();
     const double k2 = eos.k * eos.k;
+    if (force_model == 1) {
+#pragma omp parallel for schedule(static)
+      for (int n = 0; n < n_all; ++n) {
+        if (kind[n] == KIND_FLUID) {
+          mu[n] = eos.pseudopotential(rho[n]);
+        } else if (kind[n] == KIND_SOLID1 || kind[n] == KIND_SOLID2) {
+          int b = body[n];
+          T off = b < (int)rad.size() ? dmu[b] : dmu_walls;
+          mu[n] = eos.pseudopotential(rho[n]) * (1.0 + off);
+        }
+      }
+      return;
+    }
 #pragma omp parallel for schedule(static)
     for (int n = 0; n < n_all; ++n) {
       if (kind[n] == KIND_FLUID)
@@ -598,7 +636,18 @@ struct Sim {
     for (int n = 0; n < n_all; ++n) {
       if (kind[n] != KIND_FLUID) continue;
       T fx = rho[n] * gx, fy = rho[n] * gy;
-      if (nonideal) {
+      if (nonideal && force_model == 1) {
+        // -G psi(x) sum_i w_i psi(x + e_i) e_i with G = -1; the interaction weights are 3 w_i
+        // of the D2Q9 equilibrium (1/3 on the axes, 1/12 on the diagonals)
+        T sx = 0.0, sy = 0.0;
+        for (int i = 1; i < 9; ++i) {
+          T p = at(mu, n, EX[i], EY[i]);
+          sx += 3.0 * WT[i] * p * double(EX[i]);
+          sy += 3.0 * WT[i] * p * double(EY[i]);
+        }
+        fx += mu[n] * sx;
+        fy += mu[n] * sy;
+      } else if (nonideal) {
         fx += -rho[n] * ddx(mu, n) + CS2 * ddx(rho, n);
         fy += -rho[n] * ddy(mu, n) + CS2 * ddy(rho, n);
       }

@@ -20,6 +20,7 @@ SOURCES = [os.path.join(HERE, "lbm_oracle.cpp"), os.path.join(HERE, "lbm_oracle.
 
 BC_PRESENT, BC_IBC, BC_MIBC, BC_HBB = 0, 1, 2, 3
 EOS_NONE, EOS_CS, EOS_PR = 0, 1, 2
+FORCE_CHEMPOT, FORCE_PSEUDO = 0, 1
 COLL_BGK, COLL_MRT = 0, 1
 
 
@@ -100,7 +101,7 @@ class _CConfig(C.Structure):
         ("bc", C.c_int32), ("n_cyl", C.c_int32),
         ("cx", C.POINTER(C.c_double)), ("cy", C.POINTER(C.c_double)),
         ("r", C.POINTER(C.c_double)), ("dmu_w", C.POINTER(C.c_double)),
-        ("dmu_w_walls", C.c_double),
+        ("dmu_w_walls", C.c_double), ("force_model", C.c_int32),
     ]
 
 
@@ -144,6 +145,7 @@ class OracleConfig:
     r: Sequence[float] = field(default_factory=list)
     dmu_w: Sequence[float] = field(default_factory=list)
     dmu_w_walls: float = 0.0
+    force_model: int = 0         # 0 chemical potential (Eqs. 9, 12), 1 pseudopotential
 
     def to_c(self):
         keep = {k: np.ascontiguousarray(np.asarray(getattr(self, k), dtype=np.float64).reshape(-1))

@@ -30,6 +30,7 @@ from typing import List
 import numpy as np
 
 EOS_NONE, EOS_CS, EOS_PR = 0, 1, 2
+FORCE_CHEMPOT, FORCE_PSEUDO = 0, 1
 COLL_BGK, COLL_MRT = 0, 1
 BC_PRESENT, BC_IBC, BC_MIBC, BC_HBB = 0, 1, 2, 3
 
@@ -81,6 +82,7 @@ class Scenario:
     r: List[float] = field(default_factory=list)
     dmu_w: List[float] = field(default_factory=list)
     dmu_w_walls: float = 0.0
+    force_model: int = FORCE_CHEMPOT
     # droplets (Eq. 19)
     x0: List[float] = field(default_factory=list)
     y0: List[float] = field(default_factory=list)
@@ -103,7 +105,7 @@ class Scenario:
         """Fields shared by the oracle configuration and the library configuration."""
         keys = ("nx", "ny", "walls", "y_bottom", "eos", "a", "b", "R", "T_over_Tc", "omega",
                 "k", "kappa", "coll", "tau", "s_e", "s_eps", "s_q", "gx", "gy", "bc", "cx",
-                "cy", "r", "dmu_w", "dmu_w_walls")
+                "cy", "r", "dmu_w", "dmu_w_walls", "force_model")
         d = {k: getattr(self, k) for k in keys}
         d["y_top"] = self.y_top_value
         d["s_nu"] = self.s_nu_value
