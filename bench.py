@@ -28,7 +28,9 @@ checkpointed forward and reverse-sweep times, one reverse step against one forwa
 the gradient), and `bc_comparison` (the boundary schemes of the paper's Sec. 4.3-4.4 on
 reduced-size drops: late per-step compensation and spurious currents), and `paper_runs` (the
 paper's Sec. 4.1-4.2 drops at full size with Peng-Robinson: mass change of the present scheme
-and IBC at every q, 40 flat-wall lattices in one batch, and the curved substrate).  `--mode kernels` / `--mode adjoint` run only the timed step loop / only the
+and IBC at every q, 40 flat-wall lattices in one batch, and the curved substrate), and
+`pseudopotential` (the impact lattice with the pseudopotential force in place of the
+chemical-potential one: step time, per-phase times, against the headline step).  `--mode kernels` / `--mode adjoint` run only the timed step loop / only the
 gradient workload (for profiler captures).
 """
 from __future__ import annotations
@@ -51,14 +53,25 @@ UNIT = "MLUPS"
 # byte (1 B)
 COLLIDE_BYTES_PER_FLUID_NODE = 80
 COLLIDE_BYTES_PER_NODE = 1
+# the pseudopotential variant reads psi only (4 B) besides the populations
+PSEUDO_COLLIDE_BYTES_PER_FLUID_NODE = 76
 STEP_BYTES_PER_NODE = 72
 FALLBACK_HBM_GBS = 6800.0
+
+
+def pseudo_impact():
+    """The impact lattice with the pseudopotential force: CS at 0.7 Tc (this force model does not
+    hold the Maxwell densities of 0.6 Tc), k = 1, wall factor 0.15."""
+    import scenarios as S
+    return S.c3_impact().with_(dmu_w=[0.15], force_model=S.FORCE_PSEUDO, k=1.0, kappa=0.0, T_over_Tc=0.7)
 
 
 def workload(name):
     import scenarios as S
     if name == "c2":
         return S.c2_fp32_single(), "c2 16 droplets on cylinders 1024x1024 D2Q9 MRT CS T=0.6Tc FP32"
+    if name == "c3pp":
+        return pseudo_impact(), "c3 geometry 2048x4096 D2Q9 MRT, pseudopotential force, CS T=0.7Tc k=1, FP32"
     return S.c3_impact(), "c3 drop impact on a cylinder 2048x4096 D2Q9 MRT CS T=0.6Tc gravity FP32"
 
 
@@ -265,6 +278,43 @@ def run_paper_runs(G, torch):
             "mass_change": "M/M0 - 1 at the end of the run (FP64 audit over fluid nodes)"}
 
 
+def run_pseudopotential(G, torch, steps, ms_chempot):
+    """The impact lattice (2048 x 4096, cylinder r = 300, drop r = 100 falling at 0.05 under
+    gravity) with the pseudopotential force instead of the chemical-potential one: CS at
+    0.7 Tc, k = 1, wall factor 0.15 (the pseudopotential model does not hold the Maxwell
+    densities of the 0.6 Tc workload).  Step time from CUDA events over graph launches, the
+    per-phase times, and the step time against the chemical-potential step of the headline."""
+    sc = pseudo_impact()
+    lat = G.Lattice(sc.physics(), precision=G.LBM_FP32)
+    lat.init_droplets(sc.droplets())
+    fluid = lat.counts()["fluid"]
+    lat.step(20)
+    lat.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(lat.stream)
+    lat.step(steps)
+    e1.record(lat.stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    n_prof = max(10, min(100, steps // 5))
+    phase_ms = lat.profile_steps(n_prof) / n_prof
+    M, M0, _ = lat.mass()
+    del lat
+    torch.cuda.empty_cache()
+    peak, peak_src = measured_peak()
+    coll_bytes = PSEUDO_COLLIDE_BYTES_PER_FLUID_NODE * fluid + COLLIDE_BYTES_PER_NODE * sc.nodes
+    collide_ms = float(phase_ms[3])
+    achieved = coll_bytes / (collide_ms / 1e3) / 1e9
+    return {"workload": "c3 geometry 2048x4096, pseudopotential force, CS T=0.7Tc, k=1, FP32",
+            "roofline": {"bound": "hbm", "kernel": "k_collide<PSEUDO> (force+collide+stream)",
+                         "achieved": round(achieved, 1), "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": recorded_traffic("c3pp"),
+                         "algorithmic_bytes_per_launch": coll_bytes, "launch_ms": round(collide_ms, 5)},
+            "steps": steps, "ms_per_step": round(ms, 5), "mlups": round(sc.nodes / ms / 1e3, 1),
+            "phase_ms": {k: round(float(v), 5) for k, v in zip(("rho", "solid", "psi", "collide", "bc"), phase_ms)},
+            "step_time_vs_chemical_potential": round(ms / ms_chempot, 3), "mass_drift": M / M0 - 1}
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -386,13 +436,15 @@ def main():
     ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c3pp"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=200,
                     help="steps of the batched-instances comparison (0: skip it)")
     ap.add_argument("--bc-steps", type=int, default=10000,
                     help="steps of the boundary-scheme comparison (0: skip it)")
+    ap.add_argument("--pseudo-steps", type=int, default=1000,
+                    help="steps of the pseudopotential-force variant of the impact lattice (0: skip)")
     ap.add_argument("--paper-runs", type=int, default=1,
                     help="1: run the paper's full-size PR drops (Sec. 4.1-4.2); 0: skip")
     ap.add_argument("--fp64-steps", type=int, default=200,
@@ -560,6 +612,10 @@ def main():
     if args.bc_steps > 0 and rank == 0:
         bc_comparison = run_bc_comparison(G, max(1000, args.bc_steps // 1000 * 1000))
 
+    pseudo = None
+    if args.pseudo_steps > 0 and rank == 0:
+        pseudo = run_pseudopotential(G, torch, args.pseudo_steps, ms_step)
+
     paper_runs = None
     if args.paper_runs and rank == 0:
         paper_runs = run_paper_runs(G, torch)
@@ -597,6 +653,7 @@ def main():
             "adjoint": adjoint,
             "bc_comparison": bc_comparison,
             "paper_runs": paper_runs,
+            "pseudopotential": pseudo,
             "mass_drift": M / M0 - 1,
         }
         print(json.dumps(line), flush=True)

@@ -65,6 +65,18 @@ typedef enum {
 
 typedef enum { LBM_FP32 = 0, LBM_FP64 = 1 } lbm_prec;
 
+/* Nonideal force. */
+typedef enum {
+  LBM_FORCE_CHEMPOT = 0, /* the paper's chemical-potential force, Eqs. 9 and 12 */
+  LBM_FORCE_PSEUDO = 1   /* the pseudopotential (Shan-Chen) force with a pseudopotential built
+                            from the EOS: F = -G psi(x) sum_i w_i psi(x + e_i) e_i, G = -1,
+                            w = 1/3 on the axes, 1/12 on the diagonals,
+                            psi = [2 (rho c_s^2 - k^2 p0(rho))]^(1/2) (clamped at zero), so that
+                            rho c_s^2 + (G/2) psi^2 = k^2 p0; kappa is not used.  Exact-difference
+                            forcing, Eq. 15 and Eqs. 16-18 are unchanged.  Single lattices only:
+                            the batch and reverse-mode calls return LBM_EINVAL for it. */
+} lbm_force_model;
+
 /*
  * Configuration of one lattice.  Geometry: nodes sit at integer (x, y), 0 <= x < nx,
  * 0 <= y < ny.  A node is solid when it lies inside a cylinder, (x-cx)^2 + (y-cy)^2 <= r^2,
@@ -76,7 +88,9 @@ typedef enum { LBM_FP32 = 0, LBM_FP64 = 1 } lbm_prec;
  * Wettability (Sec. 2.3): solid nodes carry the chemical potential
  *     mu^_w = k^2 mu_sat + dmu_w,
  * where mu_sat is the bulk chemical potential at coexistence; dmu_w = 0 is a neutral wall
- * (90 degrees), dmu_w < 0 hydrophilic, dmu_w > 0 hydrophobic.
+ * (90 degrees), dmu_w < 0 hydrophilic, dmu_w > 0 hydrophobic.  With LBM_FORCE_PSEUDO the same
+ * fields hold a wall factor c_w > -1 instead: the solid layers carry psi(rho_s) (1 + c_w), rho_s
+ * their Eq. 15 density; c_w > 0 hydrophilic, c_w < 0 hydrophobic, c_w = 0 close to neutral.
  */
 typedef struct {
   int32_t nx, ny;
@@ -100,6 +114,7 @@ typedef struct {
   const double* r;
   const double* dmu_w;
   double dmu_w_walls;          /* dmu_w of the two flat walls */
+  int32_t force_model;         /* lbm_force_model */
 } lbm_config;
 
 /* Initial state, Eq. 19: around each droplet a tanh profile of width `width` between the

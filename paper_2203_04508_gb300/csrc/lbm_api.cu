@@ -232,6 +232,9 @@ void fill_lattice(lbm_ctx* c, Lattice<real>& L) {
   L.gx = (real)g.gx;
   L.gy = (real)g.gy;
   L.bc = g.bc;
+  L.pseudo = g.force_model == LBM_FORCE_PSEUDO ? 1 : 0;
+  L.n_cyl = g.n_cyl;
+  L.cw_walls = g.dmu_w_walls;
   L.n_bnodes = (int)c->n_bnodes;
   L.bnode = (const int*)(w + y.bnode);
   L.bstart = (const int*)(w + y.bstart);
@@ -289,6 +292,13 @@ lbm_status validate(const lbm_config* g, char* msg) {
     if (!g->walls && (g->cy[j] - r < 2.0 || g->cy[j] + r > g->ny - 3.0))
       return bad("cylinder must keep two nodes from the periodic y edges");
     if (!std::isfinite(g->dmu_w[j])) return bad("wall chemical potential must be finite");
+  }
+  if (g->force_model != LBM_FORCE_CHEMPOT && g->force_model != LBM_FORCE_PSEUDO) return bad("unknown force_model");
+  if (g->force_model == LBM_FORCE_PSEUDO) {
+    // the wall factor c_w multiplies psi by 1 + c_w, which must stay positive
+    for (int j = 0; j < g->n_cyl; ++j)
+      if (!(g->dmu_w[j] > -1.0)) return bad("pseudopotential wall factor must exceed -1");
+    if (!(g->dmu_w_walls > -1.0)) return bad("pseudopotential wall factor must exceed -1");
   }
   return LBM_OK;
 }
@@ -796,6 +806,7 @@ lbm_status plan_batch(int n, const lbm_config* cfgs, BatchPlan* P, char* msg) {
     lbm_status s = validate(&cfgs[k], msg);
     if (s != LBM_OK) return s;
     if (cfgs[k].precision != cfgs[0].precision) { std::snprintf(msg, 256, "all instances of a batch share one precision"); return LBM_EINVAL; }
+    if (cfgs[k].force_model != LBM_FORCE_CHEMPOT) { std::snprintf(msg, 256, "the batched kernel runs the chemical-potential force only"); return LBM_EINVAL; }
     Layout L = make_layout(&cfgs[k]);
     P->off[k] = o;
     P->bytes[k] = L.total;
@@ -1426,6 +1437,7 @@ extern "C" {
 
 lbm_status lbm_adjoint_workspace_size(lbm_ctx* c, int64_t n_steps, int64_t every, size_t* bytes) {
   if (!c || !c->built || !bytes) return LBM_ESTATE;
+  if (c->cfg.force_model != LBM_FORCE_CHEMPOT) return fail(c, LBM_EINVAL, "the reverse mode covers the chemical-potential force only");
   if (n_steps < 1 || every < 0) return fail(c, LBM_EINVAL, "n_steps must be positive and every non-negative");
   *bytes = make_adj_layout(c, n_steps, every).total;
   return LBM_OK;
@@ -1435,6 +1447,7 @@ lbm_status lbm_forward_checkpointed(lbm_ctx* c, int64_t n_steps, int64_t every, 
   if (!c || !c->inited) return LBM_ESTATE;
   if (c->sticky != LBM_OK) return c->sticky;
   if (n_steps < 1 || every < 0) return fail(c, LBM_EINVAL, "n_steps must be positive and every non-negative");
+  if (c->cfg.force_model != LBM_FORCE_CHEMPOT) return fail(c, LBM_EINVAL, "the reverse mode covers the chemical-potential force only");
   const AdjLayout A = make_adj_layout(c, n_steps, every);
   if (!workspace || ((uintptr_t)workspace) % ALIGN) return fail(c, LBM_EINVAL, "adjoint workspace must be 256-byte aligned");
   if (bytes < A.total) return fail(c, LBM_ENOMEM, "adjoint workspace of %zu bytes, %zu needed", bytes, A.total);

@@ -51,6 +51,11 @@ struct Lattice {
   real s_e, s_eps, s_q, s_nu;
   real gx, gy;
   int bc;
+  // pseudopotential force model (instead of Eqs. 9 and 12): mu holds psi, the solid layers
+  // psi(rho_s) (1 + c_w) with c_w = cyl[4 b + 3] of cylinder b, cw_walls of the flat walls
+  int pseudo;
+  int n_cyl;
+  double cw_walls;
   // cut links, CSR over boundary-fluid nodes sorted by node
   int n_bnodes;
   const int* bnode;
@@ -188,11 +193,48 @@ __device__ __forceinline__ real lap4(const real* __restrict__ p, int n, const St
   return (lx + ly) * real(1.0 / 12.0);
 }
 
-// Nonideal force of Eq. 9 in mesh units, F = -rho grad(mu^) + c_s^2 grad(rho), plus rho g.
+// Pseudopotential of the pseudopotential force model, psi = [2 (rho c_s^2 - k^2 p0(rho))]^(1/2)
+// clamped at zero (rho c_s^2 + (G/2) psi^2 = k^2 p0 with G = -1), p0 the CS or PR pressure.
 template <typename real>
+__device__ __forceinline__ real psi_of(const Lattice<real>& L, real r) {
+  real p0;
+  if (L.eos == EOS_CS) {
+    const real eta = L.b * r * real(0.25);
+    const real om = real(1) - eta;
+    p0 = r * L.RT * (real(1) + eta * (real(1) + eta * (real(1) - eta))) / (om * om * om) - L.a * r * r;
+  } else {
+    const real br = L.b * r;
+    p0 = r * L.RT / (real(1) - br) - L.aalpha * r * r / (real(1) + br * (real(2) - br));
+  }
+  const real arg = real(2) * (r * real(1.0 / 3.0) - L.k2 * p0);
+  return arg > real(0) ? sqrt(arg) : real(0);
+}
+
+// Adds the pseudopotential force -G psi(x) sum_i w_i psi(x + e_i) e_i (G = -1, w = 1/3 on the
+// axes, 1/12 on the diagonals) from the centre value c and the eight neighbours, as
+// differences of opposite neighbours (exact inside a bulk phase).
+template <typename real>
+__device__ __forceinline__ void pp_force(real c, real e, real n, real w, real s, real ne, real nw, real sw, real se,
+                                         real& Fx, real& Fy) {
+  const real d1 = ne - sw, d2 = se - nw;
+  const real third = real(1.0 / 3.0), twelfth = real(1.0 / 12.0);
+  Fx += c * ((e - w) * third + (d1 + d2) * twelfth);
+  Fy += c * ((n - s) * third + (d1 - d2) * twelfth);
+}
+
+// Nonideal force of Eq. 9 in mesh units, F = -rho grad(mu^) + c_s^2 grad(rho), plus rho g;
+// with PSEUDO the pseudopotential force from the psi plane instead.
+template <typename real, bool PSEUDO = false>
 __device__ __forceinline__ void force_at(const Lattice<real>& L, int x, int y, real r, real& Fx, real& Fy) {
   Fx = r * L.gx;
   Fy = r * L.gy;
+  if (PSEUDO) {
+    if (L.eos == EOS_NONE) return;
+    const real* __restrict__ p = L.mu;
+    auto at = [&](int dx, int dy) { return __ldg(p + node_at(L, x + dx, y + dy)); };
+    pp_force(at(0, 0), at(1, 0), at(0, 1), at(-1, 0), at(0, -1), at(1, 1), at(-1, 1), at(-1, -1), at(1, -1), Fx, Fy);
+    return;
+  }
   if (L.eos != EOS_NONE) {
     Stencil s = stencil_at(L, x, y);
     real gmx, gmy, grx, gry;

@@ -103,7 +103,8 @@ __device__ __forceinline__ void phase_collide(const Lattice<real>& L, int cur, i
 }
 
 // Boundary node b (one per thread): rebuild (rho, u, F) of step t at x1 from the
-// pre-collision lattice and the rho / mu planes (the arithmetic of the collide phase), apply
+// pre-collision lattice and the rho / mu planes (the arithmetic of the collide phase; PSEUDO:
+// the pseudopotential force from the psi plane), apply
 // Eq. 16 or 17 on each of its links, and add the FP64 sum of Eq. 18 to f_0.  Returns that sum
 // (0 for the schemes without compensation).
 //
@@ -127,7 +128,7 @@ __device__ __forceinline__ real edm_dir(int i, real r, real ux, real uy, real du
   }
 }
 
-template <typename real, int PREFETCH = 0>
+template <typename real, int PREFETCH = 0, bool PSEUDO = false>
 __device__ __forceinline__ double phase_bc(const Lattice<real>& L, int cur, int b) {
   const int n = L.bnode[b];
   const int x = n % L.pitch, y = n / L.pitch;
@@ -165,7 +166,7 @@ __device__ __forceinline__ double phase_bc(const Lattice<real>& L, int cur, int 
   moments(fl, drho, jx, jy);
   const real r = L.rho_ref + drho;
   real Fx, Fy;
-  force_at(L, x, y, r, Fx, Fy);
+  force_at<real, PSEUDO>(L, x, y, r, Fx, Fy);
   const real inv_r = real(1) / r;
   const real ux = jx * inv_r, uy = jy * inv_r, dux = Fx * inv_r, duy = Fy * inv_r;
   double sum = 0.0;

@@ -4,6 +4,7 @@
 //   k_rho_vec       density of every fluid node from the 9 offset populations   (Sec. 2.1)
 //   k_solid (x2)    densities of the first, then second solid layer             (Eq. 15)
 //   k_mu            chemical potential at fluid nodes                            (Eq. 12)
+//                   (pseudopotential force model: k_psi, psi at fluid and solid-layer nodes)
 //   k_collide       force (Eq. 9) + collision (Eq. 4) + exact-difference forcing (Eq. 13)
 //                   + push streaming (Eq. 5) into the other lattice
 //   k_bc            every cut link by Eq. 16 / Eq. 17, the per-node compensation of Eq. 18
@@ -85,15 +86,43 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_mu(Lattice<real> L) {
   phase_mu(L, x, y);
 }
 
+// Pseudopotential force model: psi(rho) at fluid nodes, psi(rho_s) (1 + c_w) at the two solid
+// layers (rho_s from Eq. 15, c_w the wall factor of the node's body).  Pointwise, so it takes
+// V consecutive nodes of a row per thread with one 16-byte density load, like k_rho_vec.
+template <typename real>
+__global__ void __launch_bounds__(NODE_BLOCK) k_psi(Lattice<real> L) {
+  using VT = typename Vec16<real>::type;
+  constexpr int V = Vec16<real>::V;
+  const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * V, y = blockIdx.y;
+  if (x0 >= L.nx) return;
+  const int n0 = y * L.pitch + x0;
+  const VT rv = __ldg(reinterpret_cast<const VT*>(L.rho + n0));
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    if (x0 + k >= L.nx) break;
+    const uint8_t kd = L.kind[n0 + k];
+    if (kd == KIND_FLUID || kd == KIND_SOLID1 || kd == KIND_SOLID2) {
+      real v = psi_of(L, lane_of<real>(rv, k));
+      if (kd != KIND_FLUID) {
+        const int b = L.body[n0 + k];
+        const double cw = b < L.n_cyl ? L.cyl[4 * b + 3] : L.cw_walls;
+        v *= real(1) + (real)cw;
+      }
+      L.mu[n0 + k] = v;
+    }
+  }
+}
+
 // Force + collision + streaming.  A block of 32 x 8 nodes (one warp per 128-byte row) first
 // stages the density and chemical potential of its tile and of a two-node halo in shared
 // memory, so that the fourth-order gradients of Eq. 9 read 16 neighbours there instead of
-// through the L1/L2 path; the arithmetic is force_at's, operation for operation.
+// through the L1/L2 path; the arithmetic is force_at's, operation for operation.  PSEUDO: the
+// pseudopotential force from the staged psi tile (its one-node halo); no density staging.
 constexpr int CT_X = 32, CT_Y = NODE_BLOCK / CT_X, CT_H = 2;
 constexpr int CT_SX = CT_X + 2 * CT_H, CT_SY = CT_Y + 2 * CT_H;
 static_assert(CT_X == 32 && CT_SX - 32 <= 32, "one warp stages a row of the tile and its halo");
 
-template <typename real>
+template <typename real, bool PSEUDO>
 __global__ void __launch_bounds__(NODE_BLOCK) k_collide(Lattice<real> L, int cur) {
   __shared__ real s_rho[CT_SY][CT_SX];
   __shared__ real s_mu[CT_SY][CT_SX];
@@ -117,10 +146,10 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide(Lattice<real> L, int cur
       const int base = (y0 - CT_H) * L.pitch + (x0 - CT_H);
       for (int r = wr; r < CT_SY; r += NODE_BLOCK / 32) {
         const int row = base + r * L.pitch;
-        s_rho[r][lane] = L.rho[row + lane];
+        if (!PSEUDO) s_rho[r][lane] = L.rho[row + lane];
         s_mu[r][lane] = L.mu[row + lane];
         if (lane < CT_SX - 32) {
-          s_rho[r][32 + lane] = L.rho[row + 32 + lane];
+          if (!PSEUDO) s_rho[r][32 + lane] = L.rho[row + 32 + lane];
           s_mu[r][32 + lane] = L.mu[row + 32 + lane];
         }
       }
@@ -133,10 +162,10 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide(Lattice<real> L, int cur
         // inside the rows; other slots are never read
         if (x <= L.nx + 1 && (L.walls ? (y >= 0 && y < L.ny) : (y <= L.ny + 1))) {
           const int n = node_at(L, x, y);
-          r = L.rho[n];
+          if (!PSEUDO) r = L.rho[n];
           m = L.mu[n];
         }
-        s_rho[ly][lx] = r;
+        if (!PSEUDO) s_rho[ly][lx] = r;
         s_mu[ly][lx] = m;
       }
     }
@@ -146,7 +175,11 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide(Lattice<real> L, int cur
   collide_loaded(L, cur, x, y, fl, [&](real r, real& Fx, real& Fy) {
     Fx = r * L.gx;
     Fy = r * L.gy;
-    if (stencils) {
+    if (stencils && PSEUDO) {
+      const int cx = lx + CT_H, cy = ly + CT_H;
+      pp_force(s_mu[cy][cx], s_mu[cy][cx + 1], s_mu[cy + 1][cx], s_mu[cy][cx - 1], s_mu[cy - 1][cx],
+               s_mu[cy + 1][cx + 1], s_mu[cy + 1][cx - 1], s_mu[cy - 1][cx - 1], s_mu[cy - 1][cx + 1], Fx, Fy);
+    } else if (stencils) {
       const int cx = lx + CT_H, cy = ly + CT_H;
       const real c = real(1.0 / 12.0), cs2 = real(1.0 / 3.0);
       const real gmx = (real(8) * (s_mu[cy][cx + 1] - s_mu[cy][cx - 1]) - (s_mu[cy][cx + 2] - s_mu[cy][cx - 2])) * c;
@@ -161,11 +194,11 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide(Lattice<real> L, int cur
 
 // Boundary links, then the deterministic domain sum of this step's Eq. 18 compensation into
 // the per-step ring (two-level reduction, the last block to finish sums the partials).
-template <typename real>
+template <typename real, bool PSEUDO>
 __global__ void __launch_bounds__(NODE_BLOCK) k_bc(Lattice<real> L, int cur) {
   __shared__ double red[32];
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  const double sum = b < L.n_bnodes ? phase_bc<real, 4>(L, cur, b) : 0.0;
+  const double sum = b < L.n_bnodes ? phase_bc<real, 4, PSEUDO>(L, cur, b) : 0.0;
   double bt = block_sum(sum, red);
   double total;
   if (finish_reduction(bt, L.partials, L.counter, &total, red)) {
@@ -268,7 +301,8 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_fields(Lattice<real> L, int cur,
   moments(fl, drho, jx, jy);
   const real r = L.rho_ref + drho;
   real Fx, Fy;
-  force_at(L, x, y, r, Fx, Fy);
+  if (L.pseudo) force_at<real, true>(L, x, y, r, Fx, Fy);
+  else force_at<real, false>(L, x, y, r, Fx, Fy);
   rho_out[d] = r;
   vx_out[d] = (jx + real(0.5) * Fx) / r;
   vy_out[d] = (jy + real(0.5) * Fy) / r;
@@ -358,16 +392,35 @@ static inline dim3 rho_grid(const Lattice<real>& L) {
   return dim3((unsigned)((nv + NODE_BLOCK - 1) / NODE_BLOCK), (unsigned)L.ny);
 }
 
+// the chemical-potential (or psi) pass, the collide and the boundary kernel of the lattice's
+// force model
+template <typename real>
+static inline void launch_mu(const Lattice<real>& L, cudaStream_t s) {
+  if (L.eos == EOS_NONE) return;
+  if (L.pseudo) k_psi<real><<<rho_grid(L), NODE_BLOCK, 0, s>>>(L);
+  else k_mu<real><<<node_grid(L), node_block(), 0, s>>>(L);
+}
+template <typename real>
+static inline void launch_collide(const Lattice<real>& L, int cur, cudaStream_t s) {
+  if (L.pseudo) k_collide<real, true><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
+  else k_collide<real, false><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
+}
+template <typename real>
+static inline void launch_bc(const Lattice<real>& L, int cur, cudaStream_t s) {
+  const unsigned gb = grid_for(L.n_bnodes, NODE_BLOCK);
+  if (L.pseudo) k_bc<real, true><<<gb > 0 ? gb : 1, NODE_BLOCK, 0, s>>>(L, cur);
+  else k_bc<real, false><<<gb > 0 ? gb : 1, NODE_BLOCK, 0, s>>>(L, cur);
+}
+
 template <typename real>
 cudaError_t launch_step(const Lattice<real>& L, int cur, cudaStream_t s) {
   const unsigned gn = grid_for(L.plane, NODE_BLOCK);
   k_rho_vec<real><<<rho_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
   if (L.n_s1 > 0) k_solid<real><<<grid_for(L.n_s1, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 1);
   if (L.n_s2 > 0) k_solid<real><<<grid_for(L.n_s2, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 2);
-  if (L.eos != EOS_NONE) k_mu<real><<<node_grid(L), node_block(), 0, s>>>(L);
-  k_collide<real><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
-  unsigned gb = grid_for(L.n_bnodes, NODE_BLOCK);
-  k_bc<real><<<gb > 0 ? gb : 1, NODE_BLOCK, 0, s>>>(L, cur);
+  launch_mu(L, s);
+  launch_collide(L, cur, s);
+  launch_bc(L, cur, s);
   return cudaGetLastError();
 }
 
@@ -383,13 +436,13 @@ template <typename real>
 cudaError_t launch_step_overlap(const Lattice<real>& Lt, const Lattice<real>& Ln, int cur, cudaStream_t s,
                                 cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join) {
   const Lattice<real>& L = Lt;
-  if (L.eos != EOS_NONE) k_mu<real><<<node_grid(L), node_block(), 0, s>>>(L);
-  k_collide<real><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
+  launch_mu(L, s);
+  launch_collide(L, cur, s);
   cudaError_t e = cudaEventRecord(fork, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, fork, 0);
   if (e != cudaSuccess) return e;
   const unsigned gb = grid_for(L.n_bnodes, NODE_BLOCK);
-  k_bc<real><<<gb > 0 ? gb : 1, NODE_BLOCK, 0, s>>>(L, cur);
+  launch_bc(L, cur, s);
   if (Ln.n_s1 > 0) k_solid1_b<real><<<grid_for(Ln.n_s1, NODE_BLOCK), NODE_BLOCK, 0, s>>>(Ln);
   if (Ln.n_s2 > 0) k_solid<real><<<grid_for(Ln.n_s2, NODE_BLOCK), NODE_BLOCK, 0, s>>>(Ln, 2);
   k_rho_vec<real><<<rho_grid(Ln), NODE_BLOCK, 0, s2>>>(Ln, cur ^ 1);
@@ -416,12 +469,9 @@ cudaError_t launch_phase(const Lattice<real>& L, int cur, int phase, cudaStream_
       if (L.n_s1 > 0) k_solid<real><<<grid_for(L.n_s1, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 1);
       if (L.n_s2 > 0) k_solid<real><<<grid_for(L.n_s2, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 2);
       break;
-    case 2: if (L.eos != EOS_NONE) k_mu<real><<<node_grid(L), node_block(), 0, s>>>(L); break;
-    case 3: k_collide<real><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur); break;
-    default: {
-      unsigned gb = grid_for(L.n_bnodes, NODE_BLOCK);
-      k_bc<real><<<gb > 0 ? gb : 1, NODE_BLOCK, 0, s>>>(L, cur);
-    }
+    case 2: launch_mu(L, s); break;
+    case 3: launch_collide(L, cur, s); break;
+    default: launch_bc(L, cur, s);
   }
   return cudaGetLastError();
 }
@@ -438,7 +488,7 @@ cudaError_t launch_macro(const Lattice<real>& L, int cur, cudaStream_t s) {
   k_rho_vec<real><<<rho_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
   if (L.n_s1 > 0) k_solid<real><<<grid_for(L.n_s1, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 1);
   if (L.n_s2 > 0) k_solid<real><<<grid_for(L.n_s2, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 2);
-  if (L.eos != EOS_NONE) k_mu<real><<<node_grid(L), node_block(), 0, s>>>(L);
+  launch_mu(L, s);
   return cudaGetLastError();
 }
 

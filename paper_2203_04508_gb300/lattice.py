@@ -21,6 +21,7 @@ def make_config(phys: dict, precision: int, rho_ref: float = -1.0):
     c = lbm_config()
     for k in _PHYS_KEYS:
         setattr(c, k, phys[k])
+    c.force_model = int(phys.get("force_model", 0))
     c.precision = precision
     c.rho_ref = rho_ref
     c.n_cyl = len(keep["r"])

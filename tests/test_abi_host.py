@@ -72,7 +72,8 @@ def test_peng_robinson_set_up_matches_the_oracle(abi):
 
 @pytest.mark.parametrize("patch", [
     dict(y_bottom=2.5), dict(y_top=10.0), dict(nx=4), dict(coll=0, tau=0.5), dict(s_nu=2.5),
-    dict(cx=[1.0]), dict(eos=7), dict(bc=9), dict(k=0.0),
+    dict(cx=[1.0]), dict(eos=7), dict(bc=9), dict(k=0.0), dict(force_model=2),
+    dict(force_model=1, dmu_w_walls=-1.0), dict(force_model=1, dmu_w=[-1.5, 0.1]),
 ])
 def test_invalid_configurations_are_rejected(abi, patch):
     phys = S.small_parity().physics()
@@ -103,3 +104,20 @@ def test_small_workspace_and_call_order(abi):
     m = C.c_double()
     assert lib.lbm_mass(ctx, C.byref(m), None, None) == abi.LBM_ESTATE
     lib.lbm_destroy(ctx)
+
+
+def test_pseudopotential_batches_are_rejected(abi):
+    """The batched kernel runs the chemical-potential force only: a batch with a
+    pseudopotential instance is refused before any device work."""
+    from paper_2203_04508_gb300.lattice import make_config
+    lib = abi.load()
+    phys = S.small_parity(T_over_Tc=0.7).physics()
+    good, k1 = make_config(phys, 0)
+    phys.update(force_model=1, k=1.0, kappa=0.0, dmu_w=[0.15, -0.15])
+    pp, k2 = make_config(phys, 0)
+    n = C.c_size_t()
+    assert lib.lbm_workspace_size(C.byref(pp), C.byref(n)) == 0
+    arr = (abi.lbm_config * 2)(good, pp)
+    assert lib.lbm_batch_workspace_size(2, arr, C.byref(n)) == abi.LBM_EINVAL
+    arr = (abi.lbm_config * 2)(good, good)
+    assert lib.lbm_batch_workspace_size(2, arr, C.byref(n)) == 0
