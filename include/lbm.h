@@ -211,6 +211,21 @@ lbm_status lbm_eos_info(lbm_ctx* ctx, double* out8);
 /* Number of kernel launches one lbm_step(ctx, 1) issues. */
 lbm_status lbm_launches_per_step(lbm_ctx* ctx, int64_t* n);
 
+/* Force + collision + streaming kernel of an FP32 lattice (Eqs. 4, 5, 9 or the pseudopotential
+ * force, 13): kind 0 the plain kernel (one 32 x 8 tile per block, populations loaded by each
+ * thread), kind 1 the TMA-pipelined one (a persistent grid; each block's next tiles -- the nine
+ * population planes, the density and chemical-potential halo -- stream into shared memory by
+ * cp.async.bulk.tensor while it computes the current one).  Both give the same values, bit for
+ * bit.  lbm_build_links picks kind 1 where it could encode the tensor maps (FP32 with a driver
+ * that has the encoder) and the lattice gives each persistent block at least 16 tiles, kind 0
+ * otherwise; setting kind 1 where the maps are missing returns LBM_EINVAL.  Call after
+ * lbm_build_links; the
+ * step graphs are captured again.  A bounded wait of kind 1 that gives up is reported as
+ * LBM_ETIMEOUT by the next lbm_mass. */
+lbm_status lbm_set_collide_kernel(lbm_ctx* ctx, int32_t kind);
+/* The collide kernel lbm_step runs now (0 plain, 1 TMA-pipelined). */
+lbm_status lbm_get_collide_kernel(lbm_ctx* ctx, int32_t* kind);
+
 /* Sets the state (a new initial state, in place of lbm_init) from 9 arrays of ny x nx
  * absolute populations in the context's precision, population i at offset i*nx*ny (the layout
  * lbm_populations writes); values at non-fluid nodes are ignored.  Clears the step counter,

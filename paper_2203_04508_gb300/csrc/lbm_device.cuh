@@ -80,6 +80,9 @@ struct Lattice {
   double* dM_ring;              // per-step domain sum of the Eq. 18 compensation
   unsigned long long* step_ctr; // steps taken (device side)
   double* scalars;              // [0] mass, [1] non-finite count
+  unsigned int* kerr;           // set by a kernel whose bounded wait gave up (0 otherwise)
+  const void* tma;              // host side: TMA descriptors of the pipelined collide kernel
+                                // (FP32), null for the plain kernel
 };
 
 template <typename real>
@@ -214,12 +217,20 @@ __device__ __forceinline__ real psi_of(const Lattice<real>& L, real r) {
 // axes, 1/12 on the diagonals) from the centre value c and the eight neighbours, as
 // differences of opposite neighbours (exact inside a bulk phase).
 template <typename real>
-__device__ __forceinline__ void pp_force(real c, real e, real n, real w, real s, real ne, real nw, real sw, real se,
-                                         real& Fx, real& Fy) {
+__device__ __forceinline__ void pp_sums(real e, real n, real w, real s, real ne, real nw, real sw, real se, real& ax,
+                                        real& ay) {
   const real d1 = ne - sw, d2 = se - nw;
   const real third = real(1.0 / 3.0), twelfth = real(1.0 / 12.0);
-  Fx += c * ((e - w) * third + (d1 + d2) * twelfth);
-  Fy += c * ((n - s) * third + (d1 - d2) * twelfth);
+  ax = (e - w) * third + (d1 + d2) * twelfth;
+  ay = (n - s) * third + (d1 - d2) * twelfth;
+}
+template <typename real>
+__device__ __forceinline__ void pp_force(real c, real e, real n, real w, real s, real ne, real nw, real sw, real se,
+                                         real& Fx, real& Fy) {
+  real ax, ay;
+  pp_sums(e, n, w, s, ne, nw, sw, se, ax, ay);
+  Fx += c * ax;
+  Fy += c * ay;
 }
 
 // Nonideal force of Eq. 9 in mesh units, F = -rho grad(mu^) + c_s^2 grad(rho), plus rho g;

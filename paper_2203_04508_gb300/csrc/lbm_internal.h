@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units (not part of the ABI).
 #pragma once
 #include <cstdint>
+#include <cuda.h>            // CUtensorMap (the type; the encoder is taken from the driver at run time)
 #include <cuda_runtime.h>
 
 #include "lbm_device.cuh"
@@ -27,6 +28,21 @@ template <typename real> cudaError_t launch_set_populations(const Lattice<real>&
 template <typename real> cudaError_t launch_mass(const Lattice<real>& L, int cur, cudaStream_t s);
 template <typename real> cudaError_t launch_init(const Lattice<real>& L, const double* drops, int n_drop, double W,
                                                  double rho_g, double rho_l, cudaStream_t s);
+
+// TMA descriptors of one FP32 lattice for the pipelined collide kernel (host side; a launch
+// copies the ones it needs into the kernel's parameters).
+struct CollideTma {
+  CUtensorMap f[2];             // the two population lattices as (x, y, plane), box 32 x 8 x 9
+  CUtensorMap rho[2];           // the two density planes, box 40 x 12 (tile plus halo)
+  CUtensorMap mu;               // the chemical-potential (psi) plane, box 40 x 12
+  const void* f_ptr[2];         // the planes the descriptors were made for: a lattice
+  const void* rho_ptr[2];       // descriptor pointing elsewhere runs the plain kernel
+  const void* mu_ptr;
+  int blocks[2];                // persistent grid of the chemical-potential / psi variant
+};
+// Encodes the descriptors for L (whose planes must not move afterwards) and sizes the grids;
+// false, with a message, when the driver cannot.
+bool collide_tma_setup(CollideTma* T, const Lattice<float>& L, const void* rho0, const void* rho1, char* err);
 
 // ---- geometry (lbm_geometry.cu, compiled without FMA contraction)
 struct GeomParams {

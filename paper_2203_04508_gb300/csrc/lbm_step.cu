@@ -113,6 +113,42 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_psi(Lattice<real> L) {
   }
 }
 
+// Terms of the force at a node from a staged tile (row stride W, the node at index c): the
+// fourth-order gradients of mu and rho of Eq. 9, or the two sums and the centre value of the
+// pseudopotential force.  Both collide kernels take them before the collision and finish the
+// force with tile_force, so that they evaluate it with the same operations.
+template <typename real, bool PSEUDO>
+__device__ __forceinline__ void tile_force_terms(const real* sm, const real* sr, int W, int c, real (&g)[4]) {
+  if (PSEUDO) {
+    pp_sums(sm[c + 1], sm[c + W], sm[c - 1], sm[c - W], sm[c + W + 1], sm[c + W - 1], sm[c - W - 1], sm[c - W + 1],
+            g[0], g[1]);
+    g[2] = sm[c];
+    g[3] = real(0);
+  } else {
+    const real k = real(1.0 / 12.0);
+    g[0] = (real(8) * (sm[c + 1] - sm[c - 1]) - (sm[c + 2] - sm[c - 2])) * k;
+    g[1] = (real(8) * (sm[c + W] - sm[c - W]) - (sm[c + 2 * W] - sm[c - 2 * W])) * k;
+    g[2] = (real(8) * (sr[c + 1] - sr[c - 1]) - (sr[c + 2] - sr[c - 2])) * k;
+    g[3] = (real(8) * (sr[c + W] - sr[c - W]) - (sr[c + 2 * W] - sr[c - 2 * W])) * k;
+  }
+}
+// F = rho g plus the nonideal force from those terms (force_at's operations)
+template <typename real, bool PSEUDO>
+__device__ __forceinline__ void tile_force(const Lattice<real>& L, bool stencils, const real (&g)[4], real r, real& Fx,
+                                           real& Fy) {
+  Fx = r * L.gx;
+  Fy = r * L.gy;
+  if (!stencils) return;
+  if (PSEUDO) {
+    Fx += g[2] * g[0];
+    Fy += g[2] * g[1];
+  } else {
+    const real cs2 = real(1.0 / 3.0);
+    Fx += -r * g[0] + cs2 * g[2];
+    Fy += -r * g[1] + cs2 * g[3];
+  }
+}
+
 // Force + collision + streaming.  A block of 32 x 8 nodes (one warp per 128-byte row) first
 // stages the density and chemical potential of its tile and of a two-node halo in shared
 // memory, so that the fourth-order gradients of Eq. 9 read 16 neighbours there instead of
@@ -172,24 +208,175 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide(Lattice<real> L, int cur
     __syncthreads();
   }
   if (!fluid) return;
-  collide_loaded(L, cur, x, y, fl, [&](real r, real& Fx, real& Fy) {
-    Fx = r * L.gx;
-    Fy = r * L.gy;
-    if (stencils && PSEUDO) {
-      const int cx = lx + CT_H, cy = ly + CT_H;
-      pp_force(s_mu[cy][cx], s_mu[cy][cx + 1], s_mu[cy + 1][cx], s_mu[cy][cx - 1], s_mu[cy - 1][cx],
-               s_mu[cy + 1][cx + 1], s_mu[cy + 1][cx - 1], s_mu[cy - 1][cx - 1], s_mu[cy - 1][cx + 1], Fx, Fy);
-    } else if (stencils) {
-      const int cx = lx + CT_H, cy = ly + CT_H;
-      const real c = real(1.0 / 12.0), cs2 = real(1.0 / 3.0);
-      const real gmx = (real(8) * (s_mu[cy][cx + 1] - s_mu[cy][cx - 1]) - (s_mu[cy][cx + 2] - s_mu[cy][cx - 2])) * c;
-      const real gmy = (real(8) * (s_mu[cy + 1][cx] - s_mu[cy - 1][cx]) - (s_mu[cy + 2][cx] - s_mu[cy - 2][cx])) * c;
-      const real grx = (real(8) * (s_rho[cy][cx + 1] - s_rho[cy][cx - 1]) - (s_rho[cy][cx + 2] - s_rho[cy][cx - 2])) * c;
-      const real gry = (real(8) * (s_rho[cy + 1][cx] - s_rho[cy - 1][cx]) - (s_rho[cy + 2][cx] - s_rho[cy - 2][cx])) * c;
-      Fx += -r * gmx + cs2 * grx;
-      Fy += -r * gmy + cs2 * gry;
+  real g[4] = {real(0), real(0), real(0), real(0)};
+  if (stencils) tile_force_terms<real, PSEUDO>(&s_mu[0][0], &s_rho[0][0], CT_SX, (ly + CT_H) * CT_SX + lx + CT_H, g);
+  collide_loaded(L, cur, x, y, fl,
+                 [&](real r, real& Fx, real& Fy) { tile_force<real, PSEUDO>(L, stencils, g, r, Fx, Fy); });
+}
+
+// ---------------------------------------------------------------------------------------
+// Force + collision + streaming, TMA-pipelined (FP32).  A persistent grid; each block walks the
+// 32 x 8 tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...  One cp.async.bulk.tensor brings a
+// tile's nine population planes (9 KB) into shared memory, two more the density and
+// chemical-potential (psi) tile with its halo (40 x 12 from x0 - 4, so that the first
+// coordinate stays on a 16-byte boundary), completing on the stage's mbarrier.  TMA_STAGES
+// stages: while the block computes tile k, the loads of the next tiles are in flight.  Tiles
+// whose halo wraps around a periodic edge stage the halo with plain loads instead (the TMA
+// fill value is zero, not the wrapped node).  Per node the arithmetic is k_collide's: the
+// same values, read from shared memory.  Every mbarrier wait is bounded: a block that gives
+// up sets L.kerr, waits (bounded) for its own copies and returns.
+// ---------------------------------------------------------------------------------------
+constexpr int TMA_STAGES = 2;
+constexpr int TMA_HX = 40, TMA_HY = CT_Y + 2 * CT_H, TMA_HOX = 4;   // halo box and x offset
+constexpr int TMA_F_BYTES = 9 * CT_Y * CT_X * 4;
+constexpr int TMA_H_BYTES = TMA_HX * TMA_HY * 4;
+constexpr int TMA_STAGE_BYTES = TMA_F_BYTES + 2 * TMA_H_BYTES;
+constexpr long long TMA_SPIN_LIMIT = 1 << 22;
+static_assert(TMA_STAGE_BYTES % 128 == 0 && TMA_F_BYTES % 128 == 0 && TMA_H_BYTES % 128 == 0,
+              "stage buffers stay 128-byte aligned");
+static_assert((TMA_HOX * 4) % 16 == 0 && (CT_X * 4) % 16 == 0 && (TMA_HX * 4) % 16 == 0,
+              "TMA boxes start and extend on 16-byte boundaries");
+
+struct CollideMaps {
+  CUtensorMap f, rho, mu;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for the phase of the given parity to complete
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (long long it = 0; it < TMA_SPIN_LIMIT; ++it) {
+    if (mbar_test(bar, parity)) return true;
+    if (it > 8) __nanosleep(32);
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// does the tile's halo stay inside the lattice (no periodic wrap), so that TMA can fetch it?
+__device__ __forceinline__ bool tma_halo(const Lattice<float>& L, int x0, int y0) {
+  return x0 - CT_H >= 0 && x0 + CT_X + CT_H <= L.nx && (L.walls || (y0 - CT_H >= 0 && y0 + CT_Y + CT_H <= L.ny));
+}
+
+template <bool PSEUDO>
+__global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, int cur, const __grid_constant__ CollideMaps M,
+                                                            int tiles_x, int n_tiles) {
+  extern __shared__ __align__(128) unsigned char tma_smem[];
+  __shared__ __align__(8) uint64_t bar[TMA_STAGES];
+  const bool stencils = L.eos != EOS_NONE;
+  const int lx = threadIdx.x % CT_X, ly = threadIdx.x / CT_X;
+  auto f_of = [&](int s) { return reinterpret_cast<float*>(tma_smem + s * TMA_STAGE_BYTES); };
+  auto rho_of = [&](int s) { return reinterpret_cast<float*>(tma_smem + s * TMA_STAGE_BYTES + TMA_F_BYTES); };
+  auto mu_of = [&](int s) {
+    return reinterpret_cast<float*>(tma_smem + s * TMA_STAGE_BYTES + TMA_F_BYTES + TMA_H_BYTES);
+  };
+  // thread 0: request tile t into stage s
+  auto issue = [&](int t, int s) {
+    const int x0 = (t % tiles_x) * CT_X, y0 = (t / tiles_x) * CT_Y;
+    const bool h = stencils && tma_halo(L, x0, y0);
+    mbar_expect_tx(&bar[s], TMA_F_BYTES + (h ? (PSEUDO ? 1 : 2) * TMA_H_BYTES : 0));
+    tma_load_3d(f_of(s), &M.f, x0, y0, 0, &bar[s]);
+    if (h) {
+      if (!PSEUDO) tma_load_2d(rho_of(s), &M.rho, x0 - TMA_HOX, y0 - CT_H, &bar[s]);
+      tma_load_2d(mu_of(s), &M.mu, x0 - TMA_HOX, y0 - CT_H, &bar[s]);
     }
-  });
+  };
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TMA_STAGES; ++s) mbar_init(&bar[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TMA_STAGES; ++s) {
+      const int t = blockIdx.x + s * gridDim.x;
+      if (t < n_tiles) issue(t, s);
+    }
+  }
+  int k = 0;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++k) {
+    const int s = k % TMA_STAGES;
+    const int x0 = (t % tiles_x) * CT_X, y0 = (t / tiles_x) * CT_Y;
+    const int x = x0 + lx, y = y0 + ly;
+    const bool fluid = x < L.nx && y < L.ny && L.kind[y * L.pitch + x] == KIND_FLUID;
+    const bool ok = mbar_wait(&bar[s], (uint32_t)((k / TMA_STAGES) & 1));
+    if (__syncthreads_or(!ok)) {
+      // give up: flag it, let this block's copies still in flight land, and leave
+      if (threadIdx.x == 0) {
+        atomicOr(L.kerr, 1u);
+        for (int j = 0; j < TMA_STAGES; ++j) {
+          const int tj = t + j * gridDim.x;
+          if (tj < n_tiles) mbar_wait(&bar[(k + j) % TMA_STAGES], (uint32_t)(((k + j) / TMA_STAGES) & 1));
+        }
+      }
+      __syncthreads();
+      return;
+    }
+    float* sr = rho_of(s);
+    float* sm = mu_of(s);
+    if (stencils && !tma_halo(L, x0, y0)) {
+      // the halo wraps around a periodic edge: plain wrap-aware loads, as k_collide stages it
+      for (int e = threadIdx.x; e < TMA_HX * TMA_HY; e += NODE_BLOCK) {
+        const int ey = e / TMA_HX, ex = e - ey * TMA_HX;
+        const int xx = x0 + ex - TMA_HOX, yy = y0 + ey - CT_H;
+        float r = 0.0f, m = 0.0f;
+        if (xx >= -CT_H && xx <= L.nx + 1 && (L.walls ? (yy >= 0 && yy < L.ny) : (yy <= L.ny + 1))) {
+          const int n = node_at(L, xx, yy);
+          if (!PSEUDO) r = L.rho[n];
+          m = L.mu[n];
+        }
+        if (!PSEUDO) sr[e] = r;
+        sm[e] = m;
+      }
+      __syncthreads();
+    }
+    float fl[9];
+    float g[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (fluid) {
+      const float* sf = f_of(s);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) fl[i] = sf[(i * CT_Y + ly) * CT_X + lx];
+      if (stencils) tile_force_terms<float, PSEUDO>(sm, sr, TMA_HX, (ly + CT_H) * TMA_HX + lx + TMA_HOX, g);
+    }
+    // every thread has read stage s: refill it with the tile TMA_STAGES ahead
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int tn = t + TMA_STAGES * gridDim.x;
+      if (tn < n_tiles) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(tn, s);
+      }
+    }
+    if (!fluid) continue;
+    collide_loaded(L, cur, x, y, fl,
+                   [&](float r, float& Fx, float& Fy) { tile_force<float, PSEUDO>(L, stencils, g, r, Fx, Fy); });
+  }
 }
 
 // Boundary links, then the deterministic domain sum of this step's Eq. 18 compensation into
@@ -402,8 +589,97 @@ static inline void launch_mu(const Lattice<real>& L, cudaStream_t s) {
 }
 template <typename real>
 static inline void launch_collide(const Lattice<real>& L, int cur, cudaStream_t s) {
+  if constexpr (sizeof(real) == 4) {
+    const CollideTma* T = static_cast<const CollideTma*>(L.tma);
+    if (T && L.f[cur] == T->f_ptr[cur] && L.mu == T->mu_ptr && (L.rho == T->rho_ptr[0] || L.rho == T->rho_ptr[1])) {
+      CollideMaps M;
+      M.f = T->f[cur];
+      M.rho = T->rho[L.rho == T->rho_ptr[1] ? 1 : 0];
+      M.mu = T->mu;
+      const int tiles_x = (L.nx + CT_X - 1) / CT_X;
+      const int tiles = tiles_x * ((L.ny + CT_Y - 1) / CT_Y);
+      const int grid = tiles < T->blocks[L.pseudo ? 1 : 0] ? tiles : T->blocks[L.pseudo ? 1 : 0];
+      const size_t smem = (size_t)TMA_STAGES * TMA_STAGE_BYTES;
+      if (L.pseudo) k_collide_tma<true><<<grid, NODE_BLOCK, smem, s>>>(L, cur, M, tiles_x, tiles);
+      else k_collide_tma<false><<<grid, NODE_BLOCK, smem, s>>>(L, cur, M, tiles_x, tiles);
+      return;
+    }
+  }
   if (L.pseudo) k_collide<real, true><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
   else k_collide<real, false><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
+}
+
+// ---- descriptors of the TMA-pipelined collide kernel
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      (void)cudaGetLastError();
+  }
+  return fn;
+}
+
+bool collide_tma_setup(CollideTma* T, const Lattice<float>& L, const void* rho0, const void* rho1, char* err) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) {
+    std::snprintf(err, 256, "the driver's tensor-map encoder is not available");
+    return false;
+  }
+  const cuuint32_t unit[3] = {1, 1, 1};
+  auto fail_enc = [&](const char* what, CUresult r) {
+    std::snprintf(err, 256, "tensor map of %s: error %d", what, (int)r);
+    return false;
+  };
+  for (int c = 0; c < 2; ++c) {
+    // populations: x (contiguous, the padded row), y (rows), plane (the nine directions)
+    const cuuint64_t dim[3] = {(cuuint64_t)L.pitch, (cuuint64_t)L.ny, 9};
+    const cuuint64_t stride[2] = {(cuuint64_t)L.pitch * 4, (cuuint64_t)L.plane * 4};
+    const cuuint32_t box[3] = {CT_X, CT_Y, 9};
+    CUresult r = enc(&T->f[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)L.f[c], dim, stride, box, unit,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail_enc("the populations", r);
+    T->f_ptr[c] = L.f[c];
+  }
+  auto plane = [&](CUtensorMap* m, const void* base) {
+    const cuuint64_t dim[2] = {(cuuint64_t)L.pitch, (cuuint64_t)L.ny};
+    const cuuint64_t stride[1] = {(cuuint64_t)L.pitch * 4};
+    const cuuint32_t box[2] = {TMA_HX, TMA_HY};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dim, stride, box, unit,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  };
+  CUresult r;
+  if ((r = plane(&T->rho[0], rho0)) != CUDA_SUCCESS) return fail_enc("density plane 0", r);
+  if ((r = plane(&T->rho[1], rho1)) != CUDA_SUCCESS) return fail_enc("density plane 1", r);
+  if ((r = plane(&T->mu, L.mu)) != CUDA_SUCCESS) return fail_enc("the chemical-potential plane", r);
+  T->rho_ptr[0] = rho0;
+  T->rho_ptr[1] = rho1;
+  T->mu_ptr = L.mu;
+  // persistent grids: every block that fits on the device at once
+  int dev = 0, sms = 0, b0 = 0, b1 = 0;
+  const size_t smem = (size_t)TMA_STAGES * TMA_STAGE_BYTES;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_collide_tma<false>, NODE_BLOCK, smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_collide_tma<true>, NODE_BLOCK, smem) != cudaSuccess) {
+    (void)cudaGetLastError();
+    std::snprintf(err, 256, "occupancy query failed");
+    return false;
+  }
+  T->blocks[0] = (b0 > 0 ? b0 : 1) * sms;
+  T->blocks[1] = (b1 > 0 ? b1 : 1) * sms;
+  return true;
 }
 template <typename real>
 static inline void launch_bc(const Lattice<real>& L, int cur, cudaStream_t s) {

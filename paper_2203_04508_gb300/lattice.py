@@ -175,6 +175,15 @@ class Lattice:
         self._c(self.lib.lbm_eos_info(self.ctx, o.ctypes.data))
         return dict(zip(("Tc", "rho_c", "T", "alpha", "rho_g", "rho_l", "mu_sat", "p_sat"), o.tolist()))
 
+    def set_collide_kernel(self, kind: int):
+        """0: the plain collide kernel; 1: the TMA-pipelined one (FP32; the default where available)."""
+        self._c(self.lib.lbm_set_collide_kernel(self.ctx, int(kind)))
+
+    def collide_kernel(self) -> int:
+        k = C.c_int32()
+        self._c(self.lib.lbm_get_collide_kernel(self.ctx, C.byref(k)))
+        return k.value
+
     def launches_per_step(self) -> int:
         n = C.c_int64()
         self._c(self.lib.lbm_launches_per_step(self.ctx, C.byref(n)))
