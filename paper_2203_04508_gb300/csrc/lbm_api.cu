@@ -54,7 +54,7 @@ struct Layout {
   long long plane;
   size_t sz;
   Caps cap;
-  size_t fA, fB, rho, rho2, mu, kind, body;
+  size_t fA, fB, rho, rho2, mu, psip, kind, body;
   size_t lq64, lq, ldir, lx2f, bnode, bstart, carry, rhob;
   size_t s1node, s1mask, s1winv, s1nb, s2node, s2mask, s2winv;
   size_t cyl, drops, partials, counter, step_ctr, scalars, kerr, dm_ring, block_sums, totals;
@@ -75,6 +75,7 @@ Layout make_layout(const lbm_config* c) {
   L.rho = take(L.plane * L.sz);
   L.rho2 = take(L.plane * L.sz);
   L.mu = take(L.plane * L.sz);
+  L.psip = take(L.plane * L.sz);
   L.kind = take(L.plane);
   L.body = take(L.plane * 4);
   L.lq64 = take(L.cap.links * 8);
@@ -200,6 +201,8 @@ void fill_lattice(lbm_ctx* c, Lattice<real>& L) {
   L.rho = (real*)(w + y.rho);
   L.rho_b = nullptr;
   L.mu = (real*)(w + y.mu);
+  // the density pass leaves psi'(rho) for the chemical-potential pass (chemical-potential force)
+  L.psip = (c->cfg.eos != LBM_EOS_NONE && c->cfg.force_model == LBM_FORCE_CHEMPOT) ? (real*)(w + y.psip) : nullptr;
   L.kind = (const uint8_t*)(w + y.kind);
   L.body = (const int*)(w + y.body);
   L.cyl = (const double*)(w + y.cyl);
@@ -1394,6 +1397,7 @@ lbm_status adjoint(lbm_ctx* c, const Lattice<real>& L, const void* drho, const v
       Lc.f[1] = (real*)seg_at(buf, i + 1);
       Lc.rho = (real*)rho_at(buf, i);
       Lc.mu = (real*)mu_at(buf, i);
+      Lc.psip = nullptr;   // the recomputation evaluates psi' in its own chemical-potential pass
     };
     if (kind == 0) {
       // the segment's states (and each step's rho, mu) from slot 0

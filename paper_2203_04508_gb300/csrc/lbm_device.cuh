@@ -34,6 +34,8 @@ struct Lattice {
   real* rho_b;                  // if set: the boundary phase leaves the density of each
                                 // boundary node's final populations here (one per node)
   real* mu;                     // chemical potential minus k^2 mu_sat (constant at solids)
+  real* psip;                   // if set: psi'(rho) - mu_sat of every fluid node, left by the
+                                // density pass for the chemical-potential pass (single lattices)
   const uint8_t* kind;
   const int* body;              // body of each solid node (cylinders 0.., then bottom, top wall)
   const double* cyl;            // per cylinder: cx, cy, r, wall chemical-potential offset

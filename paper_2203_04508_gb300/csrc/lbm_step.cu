@@ -66,7 +66,11 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_rho_vec(Lattice<real> L, int cur
       real fl[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) fl[i] = lane_of<real>(fv[i], k);
-      L.rho[n0 + k] = density_of(L, fl);
+      const real r = density_of(L, fl);
+      L.rho[n0 + k] = r;
+      // the pointwise part of Eq. 12 while the node's density is at hand (this pass is bound
+      // by its bytes, the chemical-potential pass by its instructions)
+      if (L.psip) L.psip[n0 + k] = psi_prime_shifted(L, r);
     }
   }
 }
@@ -83,6 +87,13 @@ template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_mu(Lattice<real> L) {
   int x, y, n;
   if (!node_of_thread(L, x, y, n)) return;
+  if (L.psip) {
+    // phase_mu with psi'(rho) - mu_sat from the density pass: the same value, the same sum
+    if (L.kind[n] != KIND_FLUID) return;
+    Stencil st = stencil_at(L, x, y);
+    L.mu[n] = L.k2 * L.psip[n] - L.kappa * lap4(L.rho, n, st);
+    return;
+  }
   phase_mu(L, x, y);
 }
 
@@ -415,7 +426,11 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_solid1_b(Lattice<real> L) {
 template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_rho_scatter(Lattice<real> L) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < L.n_bnodes) L.rho[L.bnode[b]] = L.rho_b[b];
+  if (b < L.n_bnodes) {
+    const real r = L.rho_b[b];
+    L.rho[L.bnode[b]] = r;
+    if (L.psip) L.psip[L.bnode[b]] = psi_prime_shifted(L, r);
+  }
 }
 
 // FP64 mass audit: sum over fluid nodes of sum_i (f_i - w_i rho_ref), plus a count of
