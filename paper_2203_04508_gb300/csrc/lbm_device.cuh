@@ -191,11 +191,41 @@ __device__ __forceinline__ void grad4(const real* __restrict__ p, const Stencil&
 // differences are exact (Sterbenz), so FP32 keeps the Laplacian's relative accuracy there
 // instead of losing it to cancellation between terms of size 30 rho.
 template <typename real>
-__device__ __forceinline__ real lap4(const real* __restrict__ p, int n, const Stencil& s) {
-  const real c = p[n];
-  real lx = real(16) * ((p[s.xp1] - c) + (p[s.xm1] - c)) - ((p[s.xp2] - c) + (p[s.xm2] - c));
-  real ly = real(16) * ((p[s.yp1] - c) + (p[s.ym1] - c)) - ((p[s.yp2] - c) + (p[s.ym2] - c));
+__device__ __forceinline__ real lap4_of(real c, real xp1, real xm1, real xp2, real xm2, real yp1, real ym1, real yp2,
+                                        real ym2) {
+  real lx = real(16) * ((xp1 - c) + (xm1 - c)) - ((xp2 - c) + (xm2 - c));
+  real ly = real(16) * ((yp1 - c) + (ym1 - c)) - ((yp2 - c) + (ym2 - c));
   return (lx + ly) * real(1.0 / 12.0);
+}
+template <typename real>
+__device__ __forceinline__ real lap4(const real* __restrict__ p, int n, const Stencil& s) {
+  return lap4_of(p[n], p[s.xp1], p[s.xm1], p[s.xp2], p[s.xm2], p[s.yp1], p[s.ym1], p[s.yp2], p[s.ym2]);
+}
+
+// Sums of products with a fixed rounding order.  Where an expression adds two products
+// the compiler may fuse either into an FMA, and may choose differently in different kernels;
+// the step's kernels assemble the force and mu through these, so that every kernel that
+// evaluates them (collide, boundary, read-out, batched) gets the same bits.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Eq. 12 in mesh units, shifted: mu~ = k^2 (psi'(rho) - mu_sat) - kappa^ lap(rho)
+template <typename real>
+__device__ __forceinline__ real mu_of(const Lattice<real>& L, real psip, real lap) {
+  return fma_rn(L.k2, psip, -mul_rn(L.kappa, lap));
+}
+// F = rho g - rho grad(mu) + c_s^2 grad(rho) (Eq. 9), one component: the two gradient terms,
+// which nearly cancel inside a bulk phase, enter by fused multiply-adds (each product exact)
+template <typename real>
+__device__ __forceinline__ real force_cp(real r, real g, real gmu, real grho) {
+  return fma_rn(-r, gmu, fma_rn(real(1.0 / 3.0), grho, mul_rn(r, g)));
+}
+// F = rho g + c a, the pseudopotential force of centre value c and sum a, one component
+template <typename real>
+__device__ __forceinline__ real force_pp(real r, real g, real c, real a) {
+  return fma_rn(c, a, mul_rn(r, g));
 }
 
 // Pseudopotential of the pseudopotential force model, psi = [2 (rho c_s^2 - k^2 p0(rho))]^(1/2)
@@ -226,14 +256,7 @@ __device__ __forceinline__ void pp_sums(real e, real n, real w, real s, real ne,
   ax = (e - w) * third + (d1 + d2) * twelfth;
   ay = (n - s) * third + (d1 - d2) * twelfth;
 }
-template <typename real>
-__device__ __forceinline__ void pp_force(real c, real e, real n, real w, real s, real ne, real nw, real sw, real se,
-                                         real& Fx, real& Fy) {
-  real ax, ay;
-  pp_sums(e, n, w, s, ne, nw, sw, se, ax, ay);
-  Fx += c * ax;
-  Fy += c * ay;
-}
+
 
 // Nonideal force of Eq. 9 in mesh units, F = -rho grad(mu^) + c_s^2 grad(rho), plus rho g;
 // with PSEUDO the pseudopotential force from the psi plane instead.
@@ -241,21 +264,24 @@ template <typename real, bool PSEUDO = false>
 __device__ __forceinline__ void force_at(const Lattice<real>& L, int x, int y, real r, real& Fx, real& Fy) {
   Fx = r * L.gx;
   Fy = r * L.gy;
+  if (L.eos == EOS_NONE) return;
   if (PSEUDO) {
-    if (L.eos == EOS_NONE) return;
     const real* __restrict__ p = L.mu;
     auto at = [&](int dx, int dy) { return __ldg(p + node_at(L, x + dx, y + dy)); };
-    pp_force(at(0, 0), at(1, 0), at(0, 1), at(-1, 0), at(0, -1), at(1, 1), at(-1, 1), at(-1, -1), at(1, -1), Fx, Fy);
+    real ax, ay;
+    pp_sums(at(1, 0), at(0, 1), at(-1, 0), at(0, -1), at(1, 1), at(-1, 1), at(-1, -1), at(1, -1), ax, ay);
+    const real c = at(0, 0);
+    Fx = force_pp(r, L.gx, c, ax);
+    Fy = force_pp(r, L.gy, c, ay);
     return;
   }
-  if (L.eos != EOS_NONE) {
+  {
     Stencil s = stencil_at(L, x, y);
     real gmx, gmy, grx, gry;
     grad4(L.mu, s, gmx, gmy);
     grad4(L.rho, s, grx, gry);
-    const real cs2 = real(1.0 / 3.0);
-    Fx += -r * gmx + cs2 * grx;
-    Fy += -r * gmy + cs2 * gry;
+    Fx = force_cp(r, L.gx, gmx, grx);
+    Fy = force_cp(r, L.gy, gmy, gry);
   }
 }
 

@@ -49,7 +49,7 @@ __device__ __forceinline__ void phase_mu(const Lattice<real>& L, int x, int y) {
   if (L.kind[n] != KIND_FLUID) return;
   Stencil s = stencil_at(L, x, y);
   const real r = L.rho[n];
-  L.mu[n] = L.k2 * psi_prime_shifted(L, r) - L.kappa * lap4(L.rho, n, s);
+  L.mu[n] = mu_of(L, psi_prime_shifted(L, r), lap4(L.rho, n, s));
 }
 
 // force (Eq. 9) + collision (Eq. 4) with exact-difference forcing (Eq. 13) + push streaming

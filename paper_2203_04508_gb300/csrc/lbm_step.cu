@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_mu(Lattice<real> L) {
     // phase_mu with psi'(rho) - mu_sat from the density pass: the same value, the same sum
     if (L.kind[n] != KIND_FLUID) return;
     Stencil st = stencil_at(L, x, y);
-    L.mu[n] = L.k2 * L.psip[n] - L.kappa * lap4(L.rho, n, st);
+    L.mu[n] = mu_of(L, L.psip[n], lap4(L.rho, n, st));
     return;
   }
   phase_mu(L, x, y);
@@ -151,12 +151,11 @@ __device__ __forceinline__ void tile_force(const Lattice<real>& L, bool stencils
   Fy = r * L.gy;
   if (!stencils) return;
   if (PSEUDO) {
-    Fx += g[2] * g[0];
-    Fy += g[2] * g[1];
+    Fx = force_pp(r, L.gx, g[2], g[0]);
+    Fy = force_pp(r, L.gy, g[2], g[1]);
   } else {
-    const real cs2 = real(1.0 / 3.0);
-    Fx += -r * g[0] + cs2 * g[2];
-    Fy += -r * g[1] + cs2 * g[3];
+    Fx = force_cp(r, L.gx, g[0], g[2]);
+    Fy = force_cp(r, L.gy, g[1], g[3]);
   }
 }
 
@@ -227,29 +226,38 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide(Lattice<real> L, int cur
 
 // ---------------------------------------------------------------------------------------
 // Force + collision + streaming, TMA-pipelined (FP32).  A persistent grid; each block walks the
-// 32 x 8 tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...  One cp.async.bulk.tensor brings a
-// tile's nine population planes (9 KB) into shared memory, two more the density and
-// chemical-potential (psi) tile with its halo (40 x 12 from x0 - 4, so that the first
-// coordinate stays on a 16-byte boundary), completing on the stage's mbarrier.  TMA_STAGES
+// 32 x 8 tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...  Per tile, cp.async.bulk.tensor loads
+// complete on the stage's mbarrier: one 3D load brings the nine population planes (9 KB), 2D
+// loads the density and chemical-potential tile with its two-node halo (chemical-potential
+// force), or the psi tile (pseudopotential force, whose stencil reaches one node), as 40 x 12
+// boxes from x0 - 4 so that the first coordinate stays on a 16-byte boundary.  TMA_STAGES
 // stages: while the block computes tile k, the loads of the next tiles are in flight.  Tiles
-// whose halo wraps around a periodic edge stage the halo with plain loads instead (the TMA
-// fill value is zero, not the wrapped node).  Per node the arithmetic is k_collide's: the
-// same values, read from shared memory.  Every mbarrier wait is bounded: a block that gives
-// up sets L.kerr, waits (bounded) for its own copies and returns.
+// whose halo wraps around a periodic edge stage it with plain loads instead (the TMA fill
+// value is zero, not the wrapped node).  Per node the arithmetic is k_collide's (the same
+// force terms, assembled in the same rounding order), so both kernels give the same bits.
+// Every mbarrier wait is bounded: a block that gives up sets L.kerr, waits (bounded) for its
+// own copies and returns.
 // ---------------------------------------------------------------------------------------
 constexpr int TMA_STAGES = 2;
-constexpr int TMA_HX = 40, TMA_HY = CT_Y + 2 * CT_H, TMA_HOX = 4;   // halo box and x offset
+constexpr int TMA_HX = 40, TMA_HOX = 4;            // width and x offset of the halo boxes
+constexpr int TMA_MY = CT_Y + 2 * CT_H;            // their rows (a two-node halo)
 constexpr int TMA_F_BYTES = 9 * CT_Y * CT_X * 4;
-constexpr int TMA_H_BYTES = TMA_HX * TMA_HY * 4;
-constexpr int TMA_STAGE_BYTES = TMA_F_BYTES + 2 * TMA_H_BYTES;
+constexpr int TMA_M_BYTES = TMA_HX * TMA_MY * 4;
+// stage: populations, then density and mu (chemical potential) or psi (pseudopotential)
+constexpr int TMA_STAGE_CP = TMA_F_BYTES + 2 * TMA_M_BYTES;
+constexpr int TMA_STAGE_PP = TMA_F_BYTES + TMA_M_BYTES;
 constexpr long long TMA_SPIN_LIMIT = 1 << 22;
-static_assert(TMA_STAGE_BYTES % 128 == 0 && TMA_F_BYTES % 128 == 0 && TMA_H_BYTES % 128 == 0,
-              "stage buffers stay 128-byte aligned");
+static_assert(TMA_F_BYTES % 128 == 0 && TMA_M_BYTES % 128 == 0, "stage buffers stay 128-byte aligned");
 static_assert((TMA_HOX * 4) % 16 == 0 && (CT_X * 4) % 16 == 0 && (TMA_HX * 4) % 16 == 0,
               "TMA boxes start and extend on 16-byte boundaries");
+static_assert(TMA_HOX >= CT_H && TMA_HX - TMA_HOX >= CT_X + CT_H, "the boxes cover the halo the stencils read");
+
+__host__ __device__ constexpr int tma_stage_bytes(bool pseudo) { return pseudo ? TMA_STAGE_PP : TMA_STAGE_CP; }
 
 struct CollideMaps {
-  CUtensorMap f, rho, mu;
+  CUtensorMap f;      // populations of the input lattice, box 32 x 8 x 9
+  CUtensorMap rho;    // density plane, box 40 x 12
+  CUtensorMap mu;     // chemical-potential (psi) plane, box 40 x 12
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -291,9 +299,12 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-// does the tile's halo stay inside the lattice (no periodic wrap), so that TMA can fetch it?
+// does every halo node the tile's stencils read lie inside the lattice (no periodic wrap), so
+// that TMA can fetch it?  Two nodes out for Eq. 9, one for the pseudopotential force.
+template <bool PSEUDO>
 __device__ __forceinline__ bool tma_halo(const Lattice<float>& L, int x0, int y0) {
-  return x0 - CT_H >= 0 && x0 + CT_X + CT_H <= L.nx && (L.walls || (y0 - CT_H >= 0 && y0 + CT_Y + CT_H <= L.ny));
+  const int h = PSEUDO ? 1 : CT_H;
+  return x0 - h >= 0 && x0 + CT_X + h <= L.nx && (L.walls || (y0 - h >= 0 && y0 + CT_Y + h <= L.ny));
 }
 
 template <bool PSEUDO>
@@ -301,22 +312,22 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, in
                                                             int tiles_x, int n_tiles) {
   extern __shared__ __align__(128) unsigned char tma_smem[];
   __shared__ __align__(8) uint64_t bar[TMA_STAGES];
+  constexpr int SB = tma_stage_bytes(PSEUDO);
   const bool stencils = L.eos != EOS_NONE;
   const int lx = threadIdx.x % CT_X, ly = threadIdx.x / CT_X;
-  auto f_of = [&](int s) { return reinterpret_cast<float*>(tma_smem + s * TMA_STAGE_BYTES); };
-  auto rho_of = [&](int s) { return reinterpret_cast<float*>(tma_smem + s * TMA_STAGE_BYTES + TMA_F_BYTES); };
-  auto mu_of = [&](int s) {
-    return reinterpret_cast<float*>(tma_smem + s * TMA_STAGE_BYTES + TMA_F_BYTES + TMA_H_BYTES);
-  };
+  auto f_of = [&](int s) { return reinterpret_cast<float*>(tma_smem + s * SB); };
+  // mu (or psi) right after the populations, the density (chemical potential) after it
+  auto mu_of = [&](int s) { return reinterpret_cast<float*>(tma_smem + s * SB + TMA_F_BYTES); };
+  auto rho_of = [&](int s) { return reinterpret_cast<float*>(tma_smem + s * SB + TMA_F_BYTES + TMA_M_BYTES); };
   // thread 0: request tile t into stage s
   auto issue = [&](int t, int s) {
     const int x0 = (t % tiles_x) * CT_X, y0 = (t / tiles_x) * CT_Y;
-    const bool h = stencils && tma_halo(L, x0, y0);
-    mbar_expect_tx(&bar[s], TMA_F_BYTES + (h ? (PSEUDO ? 1 : 2) * TMA_H_BYTES : 0));
+    const bool h = stencils && tma_halo<PSEUDO>(L, x0, y0);
+    mbar_expect_tx(&bar[s], TMA_F_BYTES + (h ? (PSEUDO ? 1 : 2) * TMA_M_BYTES : 0));
     tma_load_3d(f_of(s), &M.f, x0, y0, 0, &bar[s]);
     if (h) {
-      if (!PSEUDO) tma_load_2d(rho_of(s), &M.rho, x0 - TMA_HOX, y0 - CT_H, &bar[s]);
       tma_load_2d(mu_of(s), &M.mu, x0 - TMA_HOX, y0 - CT_H, &bar[s]);
+      if (!PSEUDO) tma_load_2d(rho_of(s), &M.rho, x0 - TMA_HOX, y0 - CT_H, &bar[s]);
     }
   };
   if (threadIdx.x == 0) {
@@ -349,15 +360,16 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, in
       __syncthreads();
       return;
     }
-    float* sr = rho_of(s);
     float* sm = mu_of(s);
-    if (stencils && !tma_halo(L, x0, y0)) {
+    float* sr = rho_of(s);
+    if (stencils && !tma_halo<PSEUDO>(L, x0, y0)) {
       // the halo wraps around a periodic edge: plain wrap-aware loads, as k_collide stages it
-      for (int e = threadIdx.x; e < TMA_HX * TMA_HY; e += NODE_BLOCK) {
+      const int h = PSEUDO ? 1 : CT_H;
+      for (int e = threadIdx.x; e < TMA_HX * TMA_MY; e += NODE_BLOCK) {
         const int ey = e / TMA_HX, ex = e - ey * TMA_HX;
         const int xx = x0 + ex - TMA_HOX, yy = y0 + ey - CT_H;
         float r = 0.0f, m = 0.0f;
-        if (xx >= -CT_H && xx <= L.nx + 1 && (L.walls ? (yy >= 0 && yy < L.ny) : (yy <= L.ny + 1))) {
+        if (xx >= -h && xx <= L.nx + h - 1 && (L.walls ? (yy >= 0 && yy < L.ny) : (yy >= -h && yy <= L.ny + h - 1))) {
           const int n = node_at(L, xx, yy);
           if (!PSEUDO) r = L.rho[n];
           m = L.mu[n];
@@ -596,6 +608,19 @@ static inline dim3 rho_grid(const Lattice<real>& L) {
 
 // the chemical-potential (or psi) pass, the collide and the boundary kernel of the lattice's
 // force model
+// the collide kernel of the lattice: the TMA-pipelined one where its descriptors match the
+// planes of this step (the reverse sweep's recomputation points elsewhere), else the plain one
+template <typename real>
+static inline const CollideTma* tma_for(const Lattice<real>& L, int cur) {
+  if constexpr (sizeof(real) == 4) {
+    const CollideTma* T = static_cast<const CollideTma*>(L.tma);
+    if (T && L.f[cur] == T->f_ptr[cur] && L.mu == T->mu_ptr && (L.rho == T->rho_ptr[0] || L.rho == T->rho_ptr[1]))
+      return T;
+  }
+  return nullptr;
+}
+
+// the chemical-potential (or psi) pass
 template <typename real>
 static inline void launch_mu(const Lattice<real>& L, cudaStream_t s) {
   if (L.eos == EOS_NONE) return;
@@ -605,16 +630,16 @@ static inline void launch_mu(const Lattice<real>& L, cudaStream_t s) {
 template <typename real>
 static inline void launch_collide(const Lattice<real>& L, int cur, cudaStream_t s) {
   if constexpr (sizeof(real) == 4) {
-    const CollideTma* T = static_cast<const CollideTma*>(L.tma);
-    if (T && L.f[cur] == T->f_ptr[cur] && L.mu == T->mu_ptr && (L.rho == T->rho_ptr[0] || L.rho == T->rho_ptr[1])) {
+    if (const CollideTma* T = tma_for(L, cur)) {
       CollideMaps M;
       M.f = T->f[cur];
       M.rho = T->rho[L.rho == T->rho_ptr[1] ? 1 : 0];
       M.mu = T->mu;
       const int tiles_x = (L.nx + CT_X - 1) / CT_X;
       const int tiles = tiles_x * ((L.ny + CT_Y - 1) / CT_Y);
-      const int grid = tiles < T->blocks[L.pseudo ? 1 : 0] ? tiles : T->blocks[L.pseudo ? 1 : 0];
-      const size_t smem = (size_t)TMA_STAGES * TMA_STAGE_BYTES;
+      const int P = L.pseudo ? 1 : 0;
+      const int grid = tiles < T->blocks[P] ? tiles : T->blocks[P];
+      const size_t smem = (size_t)TMA_STAGES * tma_stage_bytes(L.pseudo);
       if (L.pseudo) k_collide_tma<true><<<grid, NODE_BLOCK, smem, s>>>(L, cur, M, tiles_x, tiles);
       else k_collide_tma<false><<<grid, NODE_BLOCK, smem, s>>>(L, cur, M, tiles_x, tiles);
       return;
@@ -622,6 +647,12 @@ static inline void launch_collide(const Lattice<real>& L, int cur, cudaStream_t 
   }
   if (L.pseudo) k_collide<real, true><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
   else k_collide<real, false><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
+}
+template <typename real>
+static inline void launch_bc(const Lattice<real>& L, int cur, cudaStream_t s) {
+  const unsigned gb = grid_for(L.n_bnodes, NODE_BLOCK);
+  if (L.pseudo) k_bc<real, true><<<gb > 0 ? gb : 1, NODE_BLOCK, 0, s>>>(L, cur);
+  else k_bc<real, false><<<gb > 0 ? gb : 1, NODE_BLOCK, 0, s>>>(L, cur);
 }
 
 // ---- descriptors of the TMA-pipelined collide kernel
@@ -667,27 +698,28 @@ bool collide_tma_setup(CollideTma* T, const Lattice<float>& L, const void* rho0,
     if (r != CUDA_SUCCESS) return fail_enc("the populations", r);
     T->f_ptr[c] = L.f[c];
   }
-  auto plane = [&](CUtensorMap* m, const void* base) {
+  auto plane = [&](CUtensorMap* m, const void* base, CUtensorMapDataType type, int esize, cuuint32_t bx, cuuint32_t by) {
     const cuuint64_t dim[2] = {(cuuint64_t)L.pitch, (cuuint64_t)L.ny};
-    const cuuint64_t stride[1] = {(cuuint64_t)L.pitch * 4};
-    const cuuint32_t box[2] = {TMA_HX, TMA_HY};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dim, stride, box, unit,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const cuuint64_t stride[1] = {(cuuint64_t)L.pitch * esize};
+    const cuuint32_t box[2] = {bx, by};
+    return enc(m, type, 2, const_cast<void*>(base), dim, stride, box, unit, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   };
+  const CUtensorMapDataType F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   CUresult r;
-  if ((r = plane(&T->rho[0], rho0)) != CUDA_SUCCESS) return fail_enc("density plane 0", r);
-  if ((r = plane(&T->rho[1], rho1)) != CUDA_SUCCESS) return fail_enc("density plane 1", r);
-  if ((r = plane(&T->mu, L.mu)) != CUDA_SUCCESS) return fail_enc("the chemical-potential plane", r);
+  if ((r = plane(&T->rho[0], rho0, F32, 4, TMA_HX, TMA_MY)) != CUDA_SUCCESS) return fail_enc("density plane 0", r);
+  if ((r = plane(&T->rho[1], rho1, F32, 4, TMA_HX, TMA_MY)) != CUDA_SUCCESS) return fail_enc("density plane 1", r);
+  if ((r = plane(&T->mu, L.mu, F32, 4, TMA_HX, TMA_MY)) != CUDA_SUCCESS) return fail_enc("the mu plane", r);
   T->rho_ptr[0] = rho0;
   T->rho_ptr[1] = rho1;
   T->mu_ptr = L.mu;
   // persistent grids: every block that fits on the device at once
   int dev = 0, sms = 0, b0 = 0, b1 = 0;
-  const size_t smem = (size_t)TMA_STAGES * TMA_STAGE_BYTES;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_collide_tma<false>, NODE_BLOCK, smem) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_collide_tma<true>, NODE_BLOCK, smem) != cudaSuccess) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_collide_tma<false>, NODE_BLOCK,
+                                                    (size_t)TMA_STAGES * tma_stage_bytes(false)) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_collide_tma<true>, NODE_BLOCK,
+                                                    (size_t)TMA_STAGES * tma_stage_bytes(true)) != cudaSuccess) {
     (void)cudaGetLastError();
     std::snprintf(err, 256, "occupancy query failed");
     return false;
@@ -695,12 +727,6 @@ bool collide_tma_setup(CollideTma* T, const Lattice<float>& L, const void* rho0,
   T->blocks[0] = (b0 > 0 ? b0 : 1) * sms;
   T->blocks[1] = (b1 > 0 ? b1 : 1) * sms;
   return true;
-}
-template <typename real>
-static inline void launch_bc(const Lattice<real>& L, int cur, cudaStream_t s) {
-  const unsigned gb = grid_for(L.n_bnodes, NODE_BLOCK);
-  if (L.pseudo) k_bc<real, true><<<gb > 0 ? gb : 1, NODE_BLOCK, 0, s>>>(L, cur);
-  else k_bc<real, false><<<gb > 0 ? gb : 1, NODE_BLOCK, 0, s>>>(L, cur);
 }
 
 template <typename real>
