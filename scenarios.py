@@ -231,6 +231,11 @@ def small_parity(seed: int = 7, nx: int = 131, ny: int = 97, fp64: bool = False,
                     fp64=fp64, steps=1000)
 
 
+# Surface tension of the CS model at 0.6 Tc (k = 0.25, kappa^ = 0.05), measured with the
+# reference oracle by the Laplace law (tests/golden/surface_tension.json, written by
+# tests/golden/make_surface_tension.py); it sets the Bond number of the drop-impact runs.
+SIGMA_CS06 = 0.004918094961305327
+
 # ---- the paper's own drops (Sec. 4.1-4.2), Peng-Robinson with the constants of Eqs. 10-11 --
 PR_PHYSICS = dict(eos=EOS_PR, a=2 / 49, b=2 / 21, R=1.0, omega=0.344, T_over_Tc=0.7, kappa=0.01)
 

@@ -462,3 +462,39 @@ def test_contact_angle_table_is_the_oracles_and_monotone():
     assert list(S.DMU_TABLE_PR) == tab["dmu"] and list(S.THETA_TABLE_PR) == tab["theta_deg"]
     assert np.all(np.diff(S.THETA_TABLE_PR) > 0)
     assert S.theta_to_dmu(90.0, S.EOS_PR) == pytest.approx(0.0, abs=0.002)
+
+
+def test_surface_tension_obeys_laplace_and_the_flat_interface_balance():
+    """The stored surface tension (tests/golden/surface_tension.json, written by the oracle-only
+    script beside it) against two things the mathematics fixes: the Laplace law, dp R the same
+    for both drop radii; and the mechanical surface tension of a flat interface, the integral of
+    P_N - P_T across it.  With the exact-difference forcing the normal pressure carries
+    F^2 / (4 rho) besides the Korteweg term (the equilibrium of f~ holds rho u u with
+    u = -F / (2 rho)), so that integral is kappa^ int rho'^2 + int F^2 / (4 rho); it must match
+    the Laplace value to the discretisation error (measured 1.1 %)."""
+    import json
+    import os
+    tab = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "surface_tension.json")))
+    s = [d["dp"] * d["r_equimolar"] for d in tab["drops"]]
+    assert abs(s[0] / s[1] - 1) < 5e-3
+    assert tab["sigma"] == pytest.approx(np.mean(s), rel=1e-12)
+    import scenarios as S
+    assert S.SIGMA_CS06 == tab["sigma"]
+    ny = 96
+    cfg = O.OracleConfig(nx=5, ny=ny, walls=0, eos=O.EOS_CS, T_over_Tc=tab["T_over_Tc"], k=tab["k"],
+                         kappa=tab["kappa"], coll=O.COLL_BGK, tau=1.0)
+    o = O.Oracle(cfg)
+    info = o.eos_info()
+    y = np.arange(ny)
+    phi = 0.5 * (np.tanh((y - ny / 4) / 2.5) - np.tanh((y - 3 * ny / 4) / 2.5))
+    rho = info["rho_g"] + (info["rho_l"] - info["rho_g"]) * phi
+    o.set_state(np.repeat(rho, 5), np.zeros(5 * ny), np.zeros(5 * ny))
+    o.step(40000)
+    r = o.fields()[0][:, 0]
+    F = o.mu_force()[2][:, 0]
+    d = (np.roll(r, -1) - np.roll(r, 1)) / 2
+    half = slice(0, ny // 2)
+    korteweg = tab["kappa"] * np.sum(d[half] ** 2)
+    edm = np.sum((F ** 2 / (4 * r))[half])
+    assert edm > 2 * korteweg                       # the forcing's share dominates here
+    assert korteweg + edm == pytest.approx(tab["sigma"], rel=0.02)
