@@ -28,7 +28,8 @@ checkpointed forward and reverse-sweep times, one reverse step against one forwa
 the gradient), and `bc_comparison` (the boundary schemes of the paper's Sec. 4.3-4.4 on
 reduced-size drops: late per-step compensation and spurious currents), and `paper_runs` (the
 paper's Sec. 4.1-4.2 drops at full size with Peng-Robinson: mass change of the present scheme
-and IBC at every q, 40 flat-wall lattices in one batch, and the curved substrate), and
+and IBC at every q, 40 flat-wall lattices in one batch, and the curved substrate; and Sec. 4.5's
+drop impact at its three Bond numbers: the film on the cylinder's top against the h*(t*) laws), and
 `pseudopotential` (the impact lattice with the pseudopotential force in place of the
 chemical-potential one: step time, per-phase times, against the headline step).  `--mode kernels` / `--mode adjoint` run only the timed step loop / only the
 gradient workload (for profiler captures).
@@ -321,6 +322,51 @@ def run_pseudopotential(G, torch, steps, ms_chempot):
             "steps": steps, "ms_per_step": round(ms, 5), "mlups": round(sc.nodes / ms / 1e3, 1),
             "phase_ms": {k: round(float(v), 5) for k, v in zip(("rho", "solid", "psi", "collide", "bc"), phase_ms)},
             "step_time_vs_chemical_potential": round(ms / ms_chempot, 3), "mass_drift": M / M0 - 1}
+
+
+def run_film(G, torch):
+    """The paper's drop impact on a cylinder (Sec. 4.5) at full size, 600 x 1200, cylinder R = 100,
+    drop D = 200, for its three Bond numbers and contact angles (2.2 / 60 deg, 4.0 / 150 deg,
+    14.5 / 150 deg), CS 0.6 Tc, FP32, 30000 steps each, the film on the cylinder's top sampled every
+    100 steps through lbm_column_density: the impact (t_i, U_i, h_i), Re and We, h* at a few t*
+    against the laws h* = 1 - t* and 0.15 t*^-2, and the throughput of the runs."""
+    import numpy as np
+    import scenarios as S
+    from paper_2203_04508_gb300.film import FilmProbe
+    out = {}
+    for bo, theta in ((2.2, 60.0), (4.0, 150.0), (14.5, 150.0)):
+        sc = S.e5_impact(bo, theta)
+        lat = G.Lattice(sc.physics(), precision=G.LBM_FP32)
+        lat.init_droplets(sc.droplets())
+        info = lat.eos_info()
+        probe = FilmProbe(lat, sc.cx[0], sc.cy[0] + sc.r[0], info["rho_g"], info["rho_l"], 2 * sc.r0[0])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(0, sc.steps, 100):
+            probe.sample(k)
+            lat.step(100)
+        lat.synchronize()
+        dt = time.perf_counter() - t0
+        res = probe.result()
+        M, M0, _ = lat.mass()
+        case = {"steps": sc.steps, "mass_change": M / M0 - 1,
+                "mlups_with_sampling": round(sc.nodes * sc.steps / dt / 1e6, 1)}
+        if res["impact"]:
+            nu = (sc.tau - 0.5) / 3.0
+            D = 2 * sc.r0[0]
+            ts, hs = res["tstar"], res["hstar"]
+            pts = {}
+            for a in (0.25, 0.5, 1.0, 1.5, 2.0, 2.5):
+                j = int(np.argmin(np.abs(ts - a)))
+                pts[f"t*={a:g}"] = {"h*": round(float(hs[j]), 4), "1-t*": round(1 - float(ts[j]), 4),
+                                    "0.15t*^-2": round(0.15 / float(ts[j]) ** 2, 4)}
+            case.update(t_i=round(res["t_i"], 1), U_i=round(res["U_i"], 5), h_i=round(res["h_i"], 2),
+                        Re=round(res["U_i"] * D / nu, 1),
+                        We=round(S.RHO_L_CS06 * res["U_i"] ** 2 * D / S.SIGMA_CS06, 2), h_star=pts)
+        out[f"Bo{bo:g}_theta{int(theta)}"] = case
+        del lat
+        torch.cuda.empty_cache()
+    return out
 
 
 def measured_peak():
@@ -628,6 +674,7 @@ def main():
     paper_runs = None
     if args.paper_runs and rank == 0:
         paper_runs = run_paper_runs(G, torch)
+        paper_runs["impact_film"] = run_film(G, torch)
 
     adjoint = None
     if args.adjoint_steps > 0:

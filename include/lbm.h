@@ -183,6 +183,14 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n);
  * asynchronously; 0: host pointers, the call synchronises. */
 lbm_status lbm_fields(lbm_ctx* ctx, void* rho, void* vx, void* vy, int32_t on_device);
 
+/* Density of the current state along one column: rho = sum_i f_i (Sec. 2.1) of the nodes
+ * (x, y0 + j), j = 0 .. n-1, NaN at solid nodes, as n FP64 values into `out` (host memory, or
+ * device memory if on_device).  Requires 0 <= x < nx, y0 >= 0, n >= 1, y0 + n <= ny, else
+ * LBM_EINVAL.  For diagnostics that follow an interface along a line, such as the film on top
+ * of a cylinder (Sec. 4.5), without copying the whole field.  Synchronises when copying to the
+ * host. */
+lbm_status lbm_column_density(lbm_ctx* ctx, int32_t x, int32_t y0, int32_t n, double* out, int32_t on_device);
+
 /* Populations f_i (not offset) of the current state, 9 planes of nx*ny values of the
  * context's precision; zero at solid nodes.  on_device as for lbm_fields. */
 lbm_status lbm_populations(lbm_ctx* ctx, void* f, int32_t on_device);

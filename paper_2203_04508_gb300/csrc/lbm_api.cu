@@ -682,6 +682,23 @@ lbm_status lbm_fields(lbm_ctx* c, void* rho, void* vx, void* vy, int32_t on_devi
   return LBM_OK;
 }
 
+lbm_status lbm_column_density(lbm_ctx* c, int32_t x, int32_t y0, int32_t n, double* out, int32_t on_device) {
+  if (!c || !c->inited) return LBM_ESTATE;
+  if (c->sticky != LBM_OK) return c->sticky;
+  if (!out) return fail(c, LBM_EINVAL, "null output");
+  if (x < 0 || x >= c->cfg.nx || y0 < 0 || n < 1 || (long long)y0 + n > c->cfg.ny)
+    return fail(c, LBM_EINVAL, "column outside the lattice");
+  // the lattice that the next step overwrites completely serves as staging memory
+  double* d = on_device ? out : (double*)(c->ws + (c->cur ? c->lay.fA : c->lay.fB));
+  if (c->fp64) CUDA_OK(c, launch_column(c->Ld, c->cur, x, y0, n, d, c->stream));
+  else CUDA_OK(c, launch_column(c->Lf, c->cur, x, y0, n, d, c->stream));
+  if (!on_device) {
+    CUDA_OK(c, cudaMemcpyAsync(out, d, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  }
+  return LBM_OK;
+}
+
 lbm_status lbm_populations(lbm_ctx* c, void* f, int32_t on_device) {
   if (!c || !c->inited) return LBM_ESTATE;
   if (c->sticky != LBM_OK) return c->sticky;

@@ -24,6 +24,8 @@ cudaError_t launch_step_overlap(const Lattice<real>& Lt, const Lattice<real>& Ln
 template <typename real> int launches_per_step_overlap(const Lattice<real>& L);
 template <typename real> cudaError_t launch_fields(const Lattice<real>& L, int cur, real* r, real* vx, real* vy, cudaStream_t s);
 template <typename real> cudaError_t launch_populations(const Lattice<real>& L, int cur, real* out, cudaStream_t s);
+template <typename real>
+cudaError_t launch_column(const Lattice<real>& L, int cur, int x, int y0, int n, double* out, cudaStream_t s);
 template <typename real> cudaError_t launch_set_populations(const Lattice<real>& L, int cur, const real* in, cudaStream_t s);
 template <typename real> cudaError_t launch_mass(const Lattice<real>& L, int cur, cudaStream_t s);
 template <typename real> cudaError_t launch_init(const Lattice<real>& L, const double* drops, int n_drop, double W,

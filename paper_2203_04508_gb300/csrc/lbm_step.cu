@@ -522,6 +522,23 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_fields(Lattice<real> L, int cur,
   vy_out[d] = (jy + real(0.5) * Fy) / r;
 }
 
+// Density of the nodes (x, y0 + j), j < n, of the current state (NaN at solid nodes), in FP64.
+template <typename real>
+__global__ void __launch_bounds__(NODE_BLOCK) k_column(Lattice<real> L, int cur, int x, int y0, int n, double* out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int node = (y0 + j) * L.pitch + x;
+  if (L.kind[node] != KIND_FLUID) {
+    out[j] = __longlong_as_double(0x7ff8000000000000LL);
+    return;
+  }
+  const real* __restrict__ f = L.f[cur];
+  real fl[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) fl[i] = f[i * L.plane + node];
+  out[j] = (double)density_of(L, fl);
+}
+
 template <typename real>
 __global__ void k_populations(Lattice<real> L, int cur, real* out) {
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -818,6 +835,12 @@ cudaError_t launch_fields(const Lattice<real>& L, int cur, real* r, real* vx, re
 }
 
 template <typename real>
+cudaError_t launch_column(const Lattice<real>& L, int cur, int x, int y0, int n, double* out, cudaStream_t s) {
+  k_column<real><<<grid_for(n, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, cur, x, y0, n, out);
+  return cudaGetLastError();
+}
+
+template <typename real>
 cudaError_t launch_populations(const Lattice<real>& L, int cur, real* out, cudaStream_t s) {
   k_populations<real><<<grid_for(L.plane, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, cur, out);
   return cudaGetLastError();
@@ -852,6 +875,7 @@ cudaError_t launch_init(const Lattice<real>& L, const double* drops, int n_drop,
   template int launches_per_step_overlap<real>(const Lattice<real>&);                                   \
   template cudaError_t launch_fields<real>(const Lattice<real>&, int, real*, real*, real*, cudaStream_t); \
   template cudaError_t launch_populations<real>(const Lattice<real>&, int, real*, cudaStream_t);        \
+  template cudaError_t launch_column<real>(const Lattice<real>&, int, int, int, int, double*, cudaStream_t); \
   template cudaError_t launch_set_populations<real>(const Lattice<real>&, int, const real*, cudaStream_t); \
   template cudaError_t launch_mass<real>(const Lattice<real>&, int, cudaStream_t);                      \
   template cudaError_t launch_init<real>(const Lattice<real>&, const double*, int, double, double,      \

@@ -175,6 +175,13 @@ class Lattice:
         self._c(self.lib.lbm_eos_info(self.ctx, o.ctypes.data))
         return dict(zip(("Tc", "rho_c", "T", "alpha", "rho_g", "rho_l", "mu_sat", "p_sat"), o.tolist()))
 
+    def column_density(self, x: int, y0: int = 0, n: Optional[int] = None) -> np.ndarray:
+        """Density of the nodes (x, y0 .. y0+n-1) of the current state (NaN at solid nodes)."""
+        n = self.ny - y0 if n is None else n
+        out = np.empty(n, np.float64)
+        self._c(self.lib.lbm_column_density(self.ctx, int(x), int(y0), int(n), C.c_void_p(out.ctypes.data), 0))
+        return out
+
     def set_collide_kernel(self, kind: int):
         """0: the plain collide kernel; 1: the TMA-pipelined one (FP32; the default where available)."""
         self._c(self.lib.lbm_set_collide_kernel(self.ctx, int(kind)))

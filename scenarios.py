@@ -235,6 +235,7 @@ def small_parity(seed: int = 7, nx: int = 131, ny: int = 97, fp64: bool = False,
 # reference oracle by the Laplace law (tests/golden/surface_tension.json, written by
 # tests/golden/make_surface_tension.py); it sets the Bond number of the drop-impact runs.
 SIGMA_CS06 = 0.004918094961305327
+RHO_G_CS06, RHO_L_CS06 = 0.0030814585387010035, 0.4062041397690057   # Maxwell densities, same file
 
 # ---- the paper's own drops (Sec. 4.1-4.2), Peng-Robinson with the constants of Eqs. 10-11 --
 PR_PHYSICS = dict(eos=EOS_PR, a=2 / 49, b=2 / 21, R=1.0, omega=0.344, T_over_Tc=0.7, kappa=0.01)
@@ -264,6 +265,20 @@ def e2_curved_drop(theta: float, bc: int = BC_PRESENT, nx: int = 500, ny: int = 
                     bc=bc, cx=[cx], cy=[cy], r=[R], dmu_w=[theta_to_dmu(theta, EOS_PR)],
                     x0=[cx], y0=[cy + R + 0.5 * r0], r0=[r0],
                     steps=20000 if theta < 90.0 else 25000, **PR_PHYSICS)
+
+
+def e5_impact(bo: float = 4.0, theta: float = 150.0, nx: int = 600, ny: int = 1200, R: float = 100.0,
+              r0: float = 100.0, U0: float = 0.02, gap: float = 20.0, tau: float = 0.8) -> Scenario:
+    """A drop falling onto a cylinder (Sec. 4.5: 600 x 1200, cylinder R = 100, drop D = 200, Bond
+    numbers 2.2 / 4.0 / 14.5, contact angles 60 and 150 deg): CS at 0.6 Tc, gravity from
+    Bo = g (rho_l - rho_g) D^2 / sigma with the oracle-measured sigma, the drop starting `gap`
+    above the cylinder and moving down at U0, neutral flat walls at the bottom and top."""
+    D = 2.0 * r0
+    g = bo * SIGMA_CS06 / ((RHO_L_CS06 - RHO_G_CS06) * D * D)
+    cx, cy = nx / 2 + 0.37, R + 60.61
+    return Scenario(name=f"e5_impact_bo{bo:g}_th{theta:.0f}", nx=nx, ny=ny, walls=1, T_over_Tc=0.6, coll=COLL_MRT,
+                    tau=tau, gy=-g, cx=[cx], cy=[cy], r=[R], dmu_w=[theta_to_dmu(theta)],
+                    x0=[cx], y0=[cy + R + gap + r0], r0=[r0], ux0=[0.0], uy0=[-U0], steps=30000)
 
 
 ALL = {"c1": c1_plain_fp64, "c2": c2_fp32_single, "c3": c3_impact, "c5": c5_adjoint}

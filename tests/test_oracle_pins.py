@@ -480,6 +480,7 @@ def test_surface_tension_obeys_laplace_and_the_flat_interface_balance():
     assert tab["sigma"] == pytest.approx(np.mean(s), rel=1e-12)
     import scenarios as S
     assert S.SIGMA_CS06 == tab["sigma"]
+    assert (S.RHO_G_CS06, S.RHO_L_CS06) == (tab["rho_g"], tab["rho_l"])
     ny = 96
     cfg = O.OracleConfig(nx=5, ny=ny, walls=0, eos=O.EOS_CS, T_over_Tc=tab["T_over_Tc"], k=tab["k"],
                          kappa=tab["kappa"], coll=O.COLL_BGK, tau=1.0)
