@@ -378,10 +378,18 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+COLLIDE_REGION = (b"// Terms of the force at a node from a staged tile", b"// Boundary links, then the deterministic")
+
+
 def collide_source_hash():
-    h = hashlib.sha256()
-    for f in ("lbm_step.cu", "lbm_device.cuh", "lbm_phases.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2203_04508_gb300", "csrc", f), "rb").read())
+    """Hash of the source the collide kernels are built from: their region of lbm_step.cu (the
+    force terms, the plain and the TMA-pipelined kernel) and the device headers they include."""
+    csrc = os.path.join(ROOT, "paper_2203_04508_gb300", "csrc")
+    step = open(os.path.join(csrc, "lbm_step.cu"), "rb").read()
+    a, b = step.index(COLLIDE_REGION[0]), step.index(COLLIDE_REGION[1])
+    h = hashlib.sha256(step[a:b])
+    for f in ("lbm_device.cuh", "lbm_phases.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
