@@ -102,7 +102,7 @@ Layout make_layout(const lbm_config* c) {
   L.step_ctr = take(16);
   L.scalars = take(4 * 8);
   L.kerr = take(16);
-  L.dm_ring = take((size_t)DM_RING * 8);
+  L.dm_ring = take((size_t)(DM_RING + 1) * 8);   // the ring, then the last step's value
   L.block_sums = take(((size_t)(L.plane + 1023) / 1024 + 1) * 4);
   L.totals = take(16 * 4);
   L.total = o;
@@ -134,7 +134,7 @@ struct lbm_ctx {
   Lattice<float> Lf{};
   Lattice<double> Ld{};
   double mass0 = 0;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};   // step graphs: 2 steps, 1 step (x parity)
   // FP32: TMA descriptors of the pipelined collide kernel (set up by lbm_build_links) and the
   // collide kernel in use (0 plain, 1 TMA-pipelined)
   CollideTma tma{};
@@ -345,24 +345,41 @@ lbm_status do_step(lbm_ctx* c, const Lattice<real>& L, long long n) {
     CUDA_OK(c, launch_phase(Lt, c->cur, 1, c->stream));
     c->rho_ok = true;
   }
-  if (n >= 2 && c->stream != nullptr) {
-    int p = c->cur;
-    if (!c->graph[p]) {
+  // graphs of two steps (slot p) and of one step (slot 2 + p) from lattice parity p
+  auto graph_of = [&](int p, int steps, cudaGraphExec_t* out) -> lbm_status {
+    cudaGraphExec_t& slot = c->graph[(steps == 2 ? 0 : 2) + p];
+    if (!slot) {
       cudaGraph_t g;
       CUDA_OK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-      step_lattices(c, L, p, Lt, Ln);
-      cudaError_t e1 = launch_step_overlap(Lt, Ln, p, c->stream, c->side, c->ev_fork, c->ev_join);
-      step_lattices(c, L, p ^ 1, Lt, Ln);
-      cudaError_t e2 = e1 == cudaSuccess ? launch_step_overlap(Lt, Ln, p ^ 1, c->stream, c->side, c->ev_fork, c->ev_join) : e1;
+      cudaError_t e1 = cudaSuccess;
+      for (int k = 0; k < steps && e1 == cudaSuccess; ++k) {
+        step_lattices(c, L, p ^ (k & 1), Lt, Ln);
+        e1 = launch_step_overlap(Lt, Ln, p ^ (k & 1), c->stream, c->side, c->ev_fork, c->ev_join);
+      }
       cudaError_t e3 = cudaStreamEndCapture(c->stream, &g);
-      if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
-        return fail(c, LBM_ECUDA, "graph capture failed: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3)));
-      cudaError_t e4 = cudaGraphInstantiate(&c->graph[p], g, 0);
+      if (e1 != cudaSuccess || e3 != cudaSuccess)
+        return fail(c, LBM_ECUDA, "graph capture failed: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e3));
+      cudaError_t e4 = cudaGraphInstantiate(&slot, g, 0);
       cudaGraphDestroy(g);
       if (e4 != cudaSuccess) return fail(c, LBM_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e4));
     }
-    for (long long k = 0; k < n / 2; ++k) CUDA_OK(c, cudaGraphLaunch(c->graph[p], c->stream));
+    *out = slot;
+    return LBM_OK;
+  };
+  if (n >= 2 && c->stream != nullptr) {
+    cudaGraphExec_t g2;
+    lbm_status st = graph_of(c->cur, 2, &g2);
+    if (st != LBM_OK) return st;
+    for (long long k = 0; k < n / 2; ++k) CUDA_OK(c, cudaGraphLaunch(g2, c->stream));
     n -= 2 * (n / 2);
+  }
+  if (n == 1 && c->stream != nullptr) {
+    cudaGraphExec_t g1;
+    lbm_status st = graph_of(c->cur, 1, &g1);
+    if (st != LBM_OK) return st;
+    CUDA_OK(c, cudaGraphLaunch(g1, c->stream));
+    c->cur ^= 1;
+    n = 0;
   }
   for (long long k = 0; k < n; ++k) {
     step_lattices(c, L, c->cur, Lt, Ln);
@@ -516,7 +533,7 @@ lbm_status lbm_build_links(lbm_ctx* c) {
   CUDA_OK(c, cudaMemsetAsync(w + y.counter, 0, 16, c->stream));
   CUDA_OK(c, cudaMemsetAsync(w + y.step_ctr, 0, 16, c->stream));
   CUDA_OK(c, cudaMemsetAsync(w + y.kerr, 0, 16, c->stream));
-  CUDA_OK(c, cudaMemsetAsync(w + y.dm_ring, 0, (size_t)DM_RING * 8, c->stream));
+  CUDA_OK(c, cudaMemsetAsync(w + y.dm_ring, 0, (size_t)(DM_RING + 1) * 8, c->stream));
   CUDA_OK(c, cudaMemsetAsync(w + y.rho, 0, y.plane * y.sz, c->stream));
   CUDA_OK(c, cudaStreamSynchronize(c->stream));
   c->built = true;
@@ -607,7 +624,7 @@ lbm_status lbm_init(lbm_ctx* c, const lbm_init_spec* s) {
   if (c->fp64) CUDA_OK(c, launch_init(c->Ld, dd, s->n_drop, s->width, c->eos.rho_g, c->eos.rho_l, c->stream));
   else CUDA_OK(c, launch_init(c->Lf, dd, s->n_drop, s->width, c->eos.rho_g, c->eos.rho_l, c->stream));
   CUDA_OK(c, cudaMemsetAsync(c->ws + y.step_ctr, 0, 16, c->stream));
-  CUDA_OK(c, cudaMemsetAsync(c->ws + y.dm_ring, 0, (size_t)DM_RING * 8, c->stream));
+  CUDA_OK(c, cudaMemsetAsync(c->ws + y.dm_ring, 0, (size_t)(DM_RING + 1) * 8, c->stream));
   CUDA_OK(c, cudaMemsetAsync(c->ws + y.carry, 0, (size_t)y.cap.bnodes * 8, c->stream));
   c->cur = 0;
   c->steps = 0;
@@ -731,7 +748,7 @@ lbm_status lbm_set_populations(lbm_ctx* c, const void* f, int32_t on_device) {
   if (c->fp64) CUDA_OK(c, launch_set_populations(c->Ld, 0, (const double*)src, c->stream));
   else CUDA_OK(c, launch_set_populations(c->Lf, 0, (const float*)src, c->stream));
   CUDA_OK(c, cudaMemsetAsync(c->ws + y.step_ctr, 0, 16, c->stream));
-  CUDA_OK(c, cudaMemsetAsync(c->ws + y.dm_ring, 0, (size_t)DM_RING * 8, c->stream));
+  CUDA_OK(c, cudaMemsetAsync(c->ws + y.dm_ring, 0, (size_t)(DM_RING + 1) * 8, c->stream));
   CUDA_OK(c, cudaMemsetAsync(c->ws + y.carry, 0, (size_t)y.cap.bnodes * 8, c->stream));
   c->steps = 0;
   if (c->fp64) CUDA_OK(c, launch_mass(c->Ld, 0, c->stream)); else CUDA_OK(c, launch_mass(c->Lf, 0, c->stream));
@@ -790,15 +807,15 @@ lbm_status lbm_dM_history(lbm_ctx* c, double* out, int64_t n, int64_t* n_out) {
 lbm_status lbm_last_dM(lbm_ctx* c, double* dM) {
   if (!c || !c->inited || !dM) return LBM_ESTATE;
   if (c->sticky != LBM_OK) return c->sticky;
-  const Layout& y = c->lay;
-  unsigned long long ctr = 0;
-  CUDA_OK(c, cudaMemcpyAsync(&ctr, c->ws + y.step_ctr, 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaMemcpyAsync(dM, c->ws + c->lay.dm_ring + (size_t)DM_RING * 8, 8, cudaMemcpyDeviceToHost, c->stream));
   CUDA_OK(c, cudaStreamSynchronize(c->stream));
-  *dM = 0.0;
-  if (ctr > 0) {
-    CUDA_OK(c, cudaMemcpyAsync(dM, c->ws + y.dm_ring + ((ctr - 1) % DM_RING) * 8, 8, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_OK(c, cudaStreamSynchronize(c->stream));
-  }
+  return LBM_OK;
+}
+
+lbm_status lbm_last_dM_async(lbm_ctx* c, double* dM) {
+  if (!c || !c->inited || !dM) return LBM_ESTATE;
+  if (c->sticky != LBM_OK) return c->sticky;
+  CUDA_OK(c, cudaMemcpyAsync(dM, c->ws + c->lay.dm_ring + (size_t)DM_RING * 8, 8, cudaMemcpyDeviceToHost, c->stream));
   return LBM_OK;
 }
 
@@ -1272,7 +1289,7 @@ AdjLayout make_adj_layout(const lbm_ctx* c, long long n, long long every) {
   A.Lmu = take(pl);
   A.Lrho = take(pl);
   A.bct = take((size_t)y.plane);
-  A.ring = take((size_t)DM_RING * 8);
+  A.ring = take((size_t)(DM_RING + 1) * 8);
   A.ctr = take(16);
   A.carry = take((size_t)y.cap.bnodes * 8);
   A.grad = take((size_t)(3 * c->cfg.n_cyl + 1) * 8);
@@ -1342,7 +1359,7 @@ lbm_status adjoint(lbm_ctx* c, const Lattice<real>& L, const void* drho, const v
   const long long dn = (long long)c->cfg.nx * c->cfg.ny;
   const size_t pl = (size_t)y.plane * y.sz;
   // snapshots of the forward state that the recomputation overwrites
-  CUDA_OK(c, cudaMemcpyAsync(w + A.ring, L.dM_ring, (size_t)DM_RING * 8, cudaMemcpyDeviceToDevice, st));
+  CUDA_OK(c, cudaMemcpyAsync(w + A.ring, L.dM_ring, (size_t)(DM_RING + 1) * 8, cudaMemcpyDeviceToDevice, st));
   CUDA_OK(c, cudaMemcpyAsync(w + A.ctr, L.step_ctr, 8, cudaMemcpyDeviceToDevice, st));
   if (c->n_bnodes > 0)
     CUDA_OK(c, cudaMemcpyAsync(w + A.carry, L.carry, (size_t)c->n_bnodes * 8, cudaMemcpyDeviceToDevice, st));
@@ -1494,7 +1511,7 @@ lbm_status adjoint(lbm_ctx* c, const Lattice<real>& L, const void* drho, const v
   std::vector<double> g(3 * c->cfg.n_cyl + 1);
   CUDA_OK(c, cudaMemcpyAsync(g.data(), w + A.grad, g.size() * 8, cudaMemcpyDeviceToHost, st));
   // the forward state as it was after lbm_forward_checkpointed
-  CUDA_OK(c, cudaMemcpyAsync(L.dM_ring, w + A.ring, (size_t)DM_RING * 8, cudaMemcpyDeviceToDevice, st));
+  CUDA_OK(c, cudaMemcpyAsync(L.dM_ring, w + A.ring, (size_t)(DM_RING + 1) * 8, cudaMemcpyDeviceToDevice, st));
   CUDA_OK(c, cudaMemcpyAsync(L.step_ctr, w + A.ctr, 8, cudaMemcpyDeviceToDevice, st));
   if (c->n_bnodes > 0)
     CUDA_OK(c, cudaMemcpyAsync(L.carry, w + A.carry, (size_t)c->n_bnodes * 8, cudaMemcpyDeviceToDevice, st));

@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(BATCH_BLOCK, 6) k_batch(BatchDev B, int n_step
           const Lattice<real>& Lk = lat[k];
           const unsigned long long st = *Lk.step_ctr;
           Lk.dM_ring[st % DM_RING] = total;
+          Lk.dM_ring[DM_RING] = total;
           *Lk.step_ctr = st + 1;
         }
       }

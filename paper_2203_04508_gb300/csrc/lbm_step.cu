@@ -414,6 +414,7 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_bc(Lattice<real> L, int cur) {
   if (finish_reduction(bt, L.partials, L.counter, &total, red)) {
     unsigned long long st = *L.step_ctr;
     L.dM_ring[st % DM_RING] = total;
+    L.dM_ring[DM_RING] = total;   // the last step's value, for a read-back without the counter
     *L.step_ctr = st + 1;
   }
 }

@@ -164,6 +164,11 @@ class Lattice:
         self._c(self.lib.lbm_last_dM(self.ctx, C.byref(d)))
         return d.value
 
+    def last_dM_async(self, out, index: int = 0):
+        """Queues the last step's compensation sum into element `index` of the FP64 host tensor
+        `out` (page-locked for the copy to overlap the next steps); valid after synchronize()."""
+        self._c(self.lib.lbm_last_dM_async(self.ctx, C.c_void_p(out.data_ptr() + 8 * int(index))))
+
     def profile_steps(self, n: int):
         """Per-phase device time (ms) summed over n steps: rho, solid, mu, collide, bc."""
         ms = np.zeros(5)

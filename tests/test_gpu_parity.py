@@ -208,3 +208,23 @@ def test_instability_is_reported():
             lat.step(50)
             lat.mass()
     assert e.value.status == 5
+
+
+def test_single_steps_and_the_asynchronous_read_back():
+    """Steps taken one at a time (the one-step graphs) give the bits of steps taken together
+    (the two-step graphs), and the compensation sums read back asynchronously, one per step, are
+    the per-step history."""
+    import torch
+    sc = S.small_parity()
+    a, b = make_lattice(sc, fp64=False), make_lattice(sc, fp64=False)
+    n = 9
+    buf = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    for k in range(n):
+        a.step(1)
+        a.last_dM_async(buf, k)
+    b.step(n)
+    a.synchronize()
+    assert np.array_equal(a.populations(), b.populations())
+    hist = b.dM_history(n)
+    assert np.array_equal(buf.numpy(), hist)
+    assert a.last_dM() == hist[-1]
