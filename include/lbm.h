@@ -42,7 +42,8 @@ typedef enum {
   LBM_ESTATE = 4,     /* call out of order */
   LBM_EUNSTABLE = 5,  /* a NaN or Inf appeared in the mass audit */
   LBM_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
-  LBM_EINTERNAL = 7
+  LBM_EINTERNAL = 7,
+  LBM_ECORRUPT = 8    /* a checkpoint file is truncated, altered or not a checkpoint */
 } lbm_status;
 
 /* Equation of state of the nonideal fluid (Sec. 2.2). */
@@ -182,6 +183,20 @@ lbm_status lbm_step(lbm_ctx* ctx, int64_t n);
  * (float or double); zero at solid nodes.  on_device != 0: device pointers, written
  * asynchronously; 0: host pointers, the call synchronises. */
 lbm_status lbm_fields(lbm_ctx* ctx, void* rho, void* vx, void* vy, int32_t on_device);
+
+/* Checkpoint / resume.  lbm_save writes the state of an initialised context to `path`: a
+ * header (magic "LBMGBCK1", format version, a hash of the configuration, lattice size,
+ * precision, step count, lattice parity, M0), then the current lattice's populations as stored
+ * (offset form, padded rows), the per-boundary-node FP64 carry of Eq. 18, the per-step
+ * compensation ring with its counter, and a CRC-32 of everything before it.  lbm_load restores
+ * such a state into a context created with the same configuration and past lbm_build_links (in
+ * place of lbm_init): stepping on from it gives the bits of the run that was saved.  A file
+ * that is truncated, altered or not a checkpoint returns LBM_ECORRUPT; a checkpoint of another
+ * configuration LBM_EINVAL; I/O failures LBM_EINVAL with the message in lbm_last_error.  Both
+ * synchronise the context's stream.  Files carry host byte order (little-endian on the x86 and
+ * Arm hosts this targets). */
+lbm_status lbm_save(lbm_ctx* ctx, const char* path);
+lbm_status lbm_load(lbm_ctx* ctx, const char* path);
 
 /* Density of the current state along one column: rho = sum_i f_i (Sec. 2.1) of the nodes
  * (x, y0 + j), j = 0 .. n-1, NaN at solid nodes, as n FP64 values into `out` (host memory, or

@@ -8,7 +8,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblbm_gb300.so")
 
-LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ESTATE, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_EINTERNAL = range(8)
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ESTATE, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_EINTERNAL, LBM_ECORRUPT = range(9)
 LBM_FP32, LBM_FP64 = 0, 1
 LBM_FORCE_CHEMPOT, LBM_FORCE_PSEUDO = 0, 1
 
@@ -63,6 +63,8 @@ _SIGS = {
     "lbm_set_collide_kernel": (I32, [P, I32]),
     "lbm_column_density": (I32, [P, I32, I32, I32, P, I32]),
     "lbm_last_dM_async": (I32, [P, P]),
+    "lbm_save": (I32, [P, C.c_char_p]),
+    "lbm_load": (I32, [P, C.c_char_p]),
     "lbm_get_collide_kernel": (I32, [P, C.POINTER(I32)]),
     "lbm_batch_workspace_size": (I32, [I32, P, C.POINTER(SZ)]),
     "lbm_batch_create": (I32, [I32, P, P, P, SZ, C.POINTER(P)]),

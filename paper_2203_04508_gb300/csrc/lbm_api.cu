@@ -430,6 +430,7 @@ const char* lbm_status_str(lbm_status s) {
     case LBM_ESTATE: return "call out of order";
     case LBM_EUNSTABLE: return "non-finite populations";
     case LBM_ETIMEOUT: return "device wait timed out";
+    case LBM_ECORRUPT: return "corrupt checkpoint";
     default: return "internal error";
   }
 }
@@ -696,6 +697,145 @@ lbm_status lbm_fields(lbm_ctx* c, void* rho, void* vx, void* vy, int32_t on_devi
     CUDA_OK(c, cudaMemcpyAsync(vy, v, dn * sz, cudaMemcpyDeviceToHost, c->stream));
     CUDA_OK(c, cudaStreamSynchronize(c->stream));
   }
+  return LBM_OK;
+}
+
+// ---- checkpoint / resume ------------------------------------------------------------------
+namespace {
+
+// CRC-32 (IEEE 802.3, reflected polynomial 0xEDB88320), table-driven
+uint32_t crc32_update(uint32_t crc, const unsigned char* p, size_t n) {
+  static uint32_t table[256];
+  static bool ready = false;
+  if (!ready) {
+    for (uint32_t i = 0; i < 256; ++i) {
+      uint32_t v = i;
+      for (int k = 0; k < 8; ++k) v = (v & 1u) ? (v >> 1) ^ 0xEDB88320u : v >> 1;
+      table[i] = v;
+    }
+    ready = true;
+  }
+  crc = ~crc;
+  for (size_t i = 0; i < n; ++i) crc = table[(crc ^ p[i]) & 0xffu] ^ (crc >> 8);
+  return ~crc;
+}
+
+// FNV-1a over the configuration's values (not its pointers), so a checkpoint is only loaded
+// into a context that steps the same problem
+uint64_t config_hash(const lbm_ctx* c) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) { h ^= b[i]; h *= 1099511628211ull; }
+  };
+  const lbm_config& g = c->cfg;
+  const int32_t ints[] = {g.nx, g.ny, g.walls, g.eos, g.coll, g.bc, g.precision, g.n_cyl, g.force_model};
+  const double reals[] = {g.y_bottom, g.y_top, g.a, g.b, g.R, g.T_over_Tc, g.omega, g.k, g.kappa, g.tau,
+                          g.s_e, g.s_eps, g.s_q, g.s_nu, g.gx, g.gy, c->rho_ref, g.dmu_w_walls};
+  mix(ints, sizeof(ints));
+  mix(reals, sizeof(reals));
+  for (const std::vector<double>* v : {&c->cx, &c->cy, &c->r, &c->dmu}) mix(v->data(), v->size() * sizeof(double));
+  return h;
+}
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version, precision;
+  int32_t nx, ny, pitch, cur;
+  uint64_t config_hash;
+  int64_t steps;
+  uint64_t n_bnodes;
+  double mass0;
+  uint64_t pop_bytes;
+};
+constexpr char CKPT_MAGIC[8] = {'L', 'B', 'M', 'G', 'B', 'C', 'K', '1'};
+constexpr uint32_t CKPT_VERSION = 1;
+
+}  // namespace
+
+lbm_status lbm_save(lbm_ctx* c, const char* path) {
+  if (!c || !c->inited) return LBM_ESTATE;
+  if (c->sticky != LBM_OK) return c->sticky;
+  if (!path) return fail(c, LBM_EINVAL, "null path");
+  const Layout& y = c->lay;
+  CkptHeader h{};
+  std::memcpy(h.magic, CKPT_MAGIC, 8);
+  h.version = CKPT_VERSION;
+  h.precision = c->fp64 ? 1u : 0u;
+  h.nx = c->cfg.nx; h.ny = c->cfg.ny; h.pitch = (int32_t)y.pitch; h.cur = c->cur;
+  h.config_hash = config_hash(c);
+  h.steps = c->steps;
+  h.n_bnodes = (uint64_t)c->n_bnodes;
+  h.mass0 = c->mass0;
+  h.pop_bytes = 9ull * (uint64_t)y.plane * y.sz;
+  const size_t ring_bytes = (size_t)(DM_RING + 1) * 8;
+  std::vector<unsigned char> buf(sizeof(h) + h.pop_bytes + h.n_bnodes * 8 + ring_bytes + 8);
+  unsigned char* p = buf.data();
+  std::memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  CUDA_OK(c, cudaMemcpy(p, c->ws + (c->cur ? y.fB : y.fA), h.pop_bytes, cudaMemcpyDeviceToHost));
+  p += h.pop_bytes;
+  if (h.n_bnodes) CUDA_OK(c, cudaMemcpy(p, c->ws + y.carry, h.n_bnodes * 8, cudaMemcpyDeviceToHost));
+  p += h.n_bnodes * 8;
+  CUDA_OK(c, cudaMemcpy(p, c->ws + y.dm_ring, ring_bytes, cudaMemcpyDeviceToHost));
+  p += ring_bytes;
+  CUDA_OK(c, cudaMemcpy(p, c->ws + y.step_ctr, 8, cudaMemcpyDeviceToHost));
+  const uint32_t crc = crc32_update(0u, buf.data(), buf.size());
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(c, LBM_EINVAL, "cannot open %s for writing", path);
+  const bool ok = std::fwrite(buf.data(), 1, buf.size(), f) == buf.size() && std::fwrite(&crc, 4, 1, f) == 1;
+  const bool closed = std::fclose(f) == 0;
+  if (!ok || !closed) return fail(c, LBM_EINVAL, "writing %s failed", path);
+  return LBM_OK;
+}
+
+lbm_status lbm_load(lbm_ctx* c, const char* path) {
+  if (!c || !c->built) return LBM_ESTATE;
+  if (c->sticky != LBM_OK) return c->sticky;
+  if (!path) return fail(c, LBM_EINVAL, "null path");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(c, LBM_EINVAL, "cannot open %s", path);
+  std::vector<unsigned char> buf;
+  unsigned char chunk[1 << 16];
+  size_t got;
+  while ((got = std::fread(chunk, 1, sizeof(chunk), f)) > 0) buf.insert(buf.end(), chunk, chunk + got);
+  const bool read_error = std::ferror(f) != 0;
+  std::fclose(f);
+  if (read_error) return fail(c, LBM_EINVAL, "reading %s failed", path);
+  CkptHeader h{};
+  if (buf.size() < sizeof(h) + 4) return fail(c, LBM_ECORRUPT, "%s is too short for a checkpoint", path);
+  std::memcpy(&h, buf.data(), sizeof(h));
+  if (std::memcmp(h.magic, CKPT_MAGIC, 8) != 0) return fail(c, LBM_ECORRUPT, "%s is not a checkpoint", path);
+  if (h.version != CKPT_VERSION) return fail(c, LBM_ECORRUPT, "checkpoint format version %u", h.version);
+  const size_t ring_bytes = (size_t)(DM_RING + 1) * 8;
+  const uint64_t body = (uint64_t)sizeof(h) + h.pop_bytes + h.n_bnodes * 8 + ring_bytes + 8;
+  if (h.pop_bytes > buf.size() || h.n_bnodes > buf.size() || buf.size() != body + 4)
+    return fail(c, LBM_ECORRUPT, "%s is truncated or has trailing data", path);
+  uint32_t crc;
+  std::memcpy(&crc, buf.data() + body, 4);
+  if (crc32_update(0u, buf.data(), (size_t)body) != crc) return fail(c, LBM_ECORRUPT, "%s fails its CRC-32", path);
+  const Layout& y = c->lay;
+  if (h.config_hash != config_hash(c) || h.nx != c->cfg.nx || h.ny != c->cfg.ny || h.pitch != (int32_t)y.pitch ||
+      h.precision != (c->fp64 ? 1u : 0u) || h.n_bnodes != (uint64_t)c->n_bnodes ||
+      h.pop_bytes != 9ull * (uint64_t)y.plane * y.sz || (h.cur != 0 && h.cur != 1))
+    return fail(c, LBM_EINVAL, "%s is a checkpoint of another configuration", path);
+  const unsigned char* p = buf.data() + sizeof(h);
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  CUDA_OK(c, cudaMemcpy(c->ws + (h.cur ? y.fB : y.fA), p, h.pop_bytes, cudaMemcpyHostToDevice));
+  p += h.pop_bytes;
+  if (h.n_bnodes) CUDA_OK(c, cudaMemcpy(c->ws + y.carry, p, h.n_bnodes * 8, cudaMemcpyHostToDevice));
+  p += h.n_bnodes * 8;
+  CUDA_OK(c, cudaMemcpy(c->ws + y.dm_ring, p, ring_bytes, cudaMemcpyHostToDevice));
+  p += ring_bytes;
+  CUDA_OK(c, cudaMemcpy(c->ws + y.step_ctr, p, 8, cudaMemcpyHostToDevice));
+  CUDA_OK(c, cudaMemset(c->ws + y.kerr, 0, 16));
+  c->cur = h.cur;
+  c->steps = h.steps;
+  c->mass0 = h.mass0;
+  c->inited = true;
+  c->rho_ok = false;     // the next step forms the density and solid layers from the populations
+  c->tape.valid = false;
   return LBM_OK;
 }
 

@@ -164,6 +164,14 @@ class Lattice:
         self._c(self.lib.lbm_last_dM(self.ctx, C.byref(d)))
         return d.value
 
+    def save(self, path: str):
+        """Checkpoint of the current state (see lbm_save)."""
+        self._c(self.lib.lbm_save(self.ctx, str(path).encode()))
+
+    def load(self, path: str):
+        """Restores a checkpoint written by save() for the same configuration (in place of init)."""
+        self._c(self.lib.lbm_load(self.ctx, str(path).encode()))
+
     def last_dM_async(self, out, index: int = 0):
         """Queues the last step's compensation sum into element `index` of the FP64 host tensor
         `out` (page-locked for the copy to overlap the next steps); valid after synchronize()."""
