@@ -21,7 +21,8 @@ Besides the contract keys the line carries: `roofline` (the collide kernel's alg
 over its CUDA-event time, against the measured HBM copy bandwidth, with the per-phase times),
 `cpu_baseline` (the oracle on the host cores), `e2e` (through the C-ABI with host buffers),
 `clocks`, `fp64` (the same workload with FP64 populations: MLUPS and the FP32/FP64 speed
-ratio), `batched` (256 instances of 128^2..768^2 in one persistent launch against the same
+ratio; the drop's interface on the centre line in FP32 and FP64 over 10000 steps; the 128 x 128
+FP64 case's mass change with the present scheme and IBC), `batched` (256 instances of 128^2..768^2 in one persistent launch against the same
 instances stepped one by one; the autotuned tile shape; the same comparison on 1024 instances
 of 64^2..128^2), and `adjoint` (512 x 512, 4000 steps, checkpoint every 200: forward,
 checkpointed forward and reverse-sweep times, one reverse step against one forward step, and
@@ -369,6 +370,54 @@ def run_film(G, torch):
     return out
 
 
+def interface_series(G, torch, sc, precision, steps, every):
+    """The drop's lower and upper interface on the vertical line through the cylinder centre
+    (the mid-density crossings above the cylinder) every `every` steps, and the final mass
+    change, for one precision."""
+    from paper_2203_04508_gb300.film import FilmProbe
+    lat = G.Lattice(sc.physics(), precision=precision)
+    lat.init_droplets(sc.droplets())
+    info = lat.eos_info()
+    probe = FilmProbe(lat, sc.cx[0], sc.cy[0] + sc.r[0], info["rho_g"], info["rho_l"], 2 * sc.r0[0])
+    for k in range(0, steps + 1, every):
+        probe.sample(k)
+        if k < steps:
+            lat.step(every)
+    M, M0, _ = lat.mass()
+    del lat
+    torch.cuda.empty_cache()
+    return probe, M / M0 - 1
+
+
+def run_precision_comparison(G, torch, sc, steps):
+    """The impact workload in FP32 and in FP64 over `steps` steps: the drop's lower and upper
+    interface on the centre line at five instants and the mass change of each."""
+    every = steps // 4
+    p32, m32 = interface_series(G, torch, sc, G.LBM_FP32, steps, every)
+    p64, m64 = interface_series(G, torch, sc, G.LBM_FP64, steps, every)
+    rows = {}
+    for k, t in enumerate(p32.t):
+        rows[f"t={int(t)}"] = {"bottom_fp32": round(p32.bottom[k], 3), "bottom_fp64": round(p64.bottom[k], 3),
+                               "top_fp32": round(p32.top[k], 3), "top_fp64": round(p64.top[k], 3)}
+    return {"steps": steps, "line": "x = cylinder centre, mid-density crossings above the cylinder",
+            "interface": rows, "mass_change_fp32": m32, "mass_change_fp64": m64}
+
+
+def run_c1_mass(G):
+    """The 128 x 128 FP64 case (CS 0.7 Tc, BGK tau = 1, cylinder R = 20, drop r0 = 15, neutral
+    wall), 2000 steps: the mass change with the present scheme and with IBC."""
+    import scenarios as S
+    out = {}
+    for name, bc in (("present", S.BC_PRESENT), ("ibc", S.BC_IBC)):
+        sc = S.c1_plain_fp64().with_(bc=bc)
+        lat = G.Lattice(sc.physics(), precision=G.LBM_FP64)
+        lat.init_droplets(sc.droplets())
+        lat.step(sc.steps)
+        M, M0, _ = lat.mass()
+        out[name] = M / M0 - 1
+    return {"steps": 2000, "mass_change": out}
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -505,6 +554,8 @@ def main():
                     help="steps of the batched-instances comparison (0: skip it)")
     ap.add_argument("--bc-steps", type=int, default=10000,
                     help="steps of the boundary-scheme comparison (0: skip it)")
+    ap.add_argument("--precision-steps", type=int, default=10000,
+                    help="steps of the FP32-versus-FP64 interface comparison on c3 (0: skip)")
     ap.add_argument("--pseudo-steps", type=int, default=1000,
                     help="steps of the pseudopotential-force variant of the impact lattice (0: skip)")
     ap.add_argument("--paper-runs", type=int, default=1,
@@ -651,6 +702,10 @@ def main():
                 "MLUPS": round(sc.nodes / ms64 / 1e3, 1), "fp32_over_fp64": round(ms64 / ms_step, 2)}
         del lat64
         torch.cuda.empty_cache()
+        if args.precision_steps > 0 and rank == 0 and args.workload == "c3":
+            fp64["fp32_vs_fp64"] = run_precision_comparison(G, torch, sc, args.precision_steps)
+        if rank == 0:
+            fp64["c1_128x128"] = run_c1_mass(G)
 
     batched = None
     if args.batch_steps > 0:
@@ -693,12 +748,17 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, n, cores = oracle_rate(sc, max_seconds=20.0, max_steps=50)
+        rate1, n1, _ = oracle_rate(sc, max_seconds=8.0, max_steps=50, threads=1)
+        import oracle as O
+        O.set_threads(cores)
         cpu = {"value": round(rate, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{n} FP64 oracle steps of the full {sc.nx}x{sc.ny} lattice after one untimed step"}
+               "sample": f"{n} FP64 oracle steps of the full {sc.nx}x{sc.ny} lattice after one untimed step",
+               "single_thread": {"value": round(rate1, 3), "cores": 1, "sample": f"{n1} steps"}}
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT,
+            "value_fluid_nodes": round(value * counts["fluid"] / sc.nodes, 2), "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wname, "nodes": sc.nodes, "fluid_nodes": counts["fluid"],
