@@ -97,6 +97,60 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_mu(Lattice<real> L) {
   phase_mu(L, x, y);
 }
 
+// The chemical-potential pass with psi' from the density pass, V = 16/sizeof(real) consecutive
+// nodes of a row per thread: the centre row from three 16-byte loads (x0 - V .. x0 + 2V - 1), the
+// four rows above and below and psi' from one each, so the 9-point Laplacians of V nodes take 8
+// vector loads instead of 9 V scalar ones.  Threads whose stencils would wrap around a periodic
+// edge take k_mu's per-node path.  Same values and the same sums as k_mu (lap4_of, mu_of).
+template <typename real>
+__global__ void __launch_bounds__(NODE_BLOCK) k_mu_vec(Lattice<real> L) {
+  using VT = typename Vec16<real>::type;
+  constexpr int V = Vec16<real>::V;
+  const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * V, y = blockIdx.y;
+  if (x0 >= L.nx) return;
+  const int n0 = y * L.pitch + x0;
+  bool fluid[V];
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    fluid[k] = x0 + k < L.nx && L.kind[n0 + k] == KIND_FLUID;
+    any |= fluid[k];
+  }
+  if (!any) return;
+  // no wrap within two nodes (with walls a fluid row keeps two solid rows below and above it)
+  const bool inner = x0 - V >= 0 && x0 + V + 2 <= L.nx && (L.walls || (y >= 2 && y < L.ny - 2));
+  if (!inner) {
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      if (!fluid[k]) continue;
+      Stencil st = stencil_at(L, x0 + k, y);
+      L.mu[n0 + k] = mu_of(L, L.psip[n0 + k], lap4(L.rho, n0 + k, st));
+    }
+    return;
+  }
+  const real* __restrict__ r = L.rho;
+  real c[3 * V];   // the centre row, x0 - V .. x0 + 2V - 1
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const VT v = __ldg(reinterpret_cast<const VT*>(r + n0 + (j - 1) * V));
+#pragma unroll
+    for (int k = 0; k < V; ++k) c[j * V + k] = lane_of<real>(v, k);
+  }
+  const VT up1 = __ldg(reinterpret_cast<const VT*>(r + n0 + L.pitch));
+  const VT dn1 = __ldg(reinterpret_cast<const VT*>(r + n0 - L.pitch));
+  const VT up2 = __ldg(reinterpret_cast<const VT*>(r + n0 + 2 * L.pitch));
+  const VT dn2 = __ldg(reinterpret_cast<const VT*>(r + n0 - 2 * L.pitch));
+  const VT pp = __ldg(reinterpret_cast<const VT*>(L.psip + n0));
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    if (!fluid[k]) continue;
+    const int i = V + k;
+    const real lap = lap4_of(c[i], c[i + 1], c[i - 1], c[i + 2], c[i - 2], lane_of<real>(up1, k), lane_of<real>(dn1, k),
+                             lane_of<real>(up2, k), lane_of<real>(dn2, k));
+    L.mu[n0 + k] = mu_of(L, lane_of<real>(pp, k), lap);
+  }
+}
+
 // Pseudopotential force model: psi(rho) at fluid nodes, psi(rho_s) (1 + c_w) at the two solid
 // layers (rho_s from Eq. 15, c_w the wall factor of the node's body).  Pointwise, so it takes
 // V consecutive nodes of a row per thread with one 16-byte density load, like k_rho_vec.
@@ -638,11 +692,12 @@ static inline const CollideTma* tma_for(const Lattice<real>& L, int cur) {
   return nullptr;
 }
 
-// the chemical-potential (or psi) pass
+// the chemical-potential (or psi) pass; with psi' from the density pass, the vector kernel
 template <typename real>
 static inline void launch_mu(const Lattice<real>& L, cudaStream_t s) {
   if (L.eos == EOS_NONE) return;
   if (L.pseudo) k_psi<real><<<rho_grid(L), NODE_BLOCK, 0, s>>>(L);
+  else if (L.psip) k_mu_vec<real><<<rho_grid(L), NODE_BLOCK, 0, s>>>(L);
   else k_mu<real><<<node_grid(L), node_block(), 0, s>>>(L);
 }
 template <typename real>
