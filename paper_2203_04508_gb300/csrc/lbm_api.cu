@@ -54,7 +54,7 @@ struct Layout {
   long long plane;
   size_t sz;
   Caps cap;
-  size_t fA, fB, rho, rho2, mu, psip, kind, body;
+  size_t fA, fB, rho, rho2, mu, mu2, psip, kind, body;
   size_t lq64, lq, ldir, lx2f, bnode, bstart, carry, rhob;
   size_t s1node, s1mask, s1winv, s1nb, s2node, s2mask, s2winv;
   size_t cyl, drops, partials, counter, step_ctr, scalars, kerr, dm_ring, block_sums, totals;
@@ -75,6 +75,7 @@ Layout make_layout(const lbm_config* c) {
   L.rho = take(L.plane * L.sz);
   L.rho2 = take(L.plane * L.sz);
   L.mu = take(L.plane * L.sz);
+  L.mu2 = take(c->force_model == LBM_FORCE_PSEUDO ? L.plane * L.sz : 0);   // the second psi plane
   L.psip = take(L.plane * L.sz);
   L.kind = take(L.plane);
   L.body = take(L.plane * 4);
@@ -325,8 +326,15 @@ void step_lattices(const lbm_ctx* c, const Lattice<real>& L, int cur, Lattice<re
   Lt = L;
   Lt.rho = planes[cur];
   Lt.rho_b = (real*)(c->ws + c->lay.rhob);
+  if (c->cfg.force_model == LBM_FORCE_PSEUDO) {
+    // psi alternates like the density: the next state's is formed while the boundary phase
+    // still reads this one's
+    real* psi[2] = {(real*)(c->ws + c->lay.mu), (real*)(c->ws + c->lay.mu2)};
+    Lt.mu = psi[cur];
+  }
   Ln = Lt;
   Ln.rho = planes[cur ^ 1];
+  if (c->cfg.force_model == LBM_FORCE_PSEUDO) Ln.mu = (real*)(c->ws + (cur ? c->lay.mu : c->lay.mu2));
 }
 
 template <typename real>
@@ -546,7 +554,8 @@ lbm_status lbm_build_links(lbm_ctx* c) {
   if (!c->fp64) {
     // the pipelined collide kernel's descriptors; without them the plain kernel runs
     char msg[256] = {0};
-    c->tma_ok = collide_tma_setup(&c->tma, c->Lf, w + y.rho, w + y.rho2, msg);
+    c->tma_ok = collide_tma_setup(&c->tma, c->Lf, w + y.rho, w + y.rho2,
+                                  w + (g.force_model == LBM_FORCE_PSEUDO ? y.mu2 : y.mu), msg);
     // the pipeline pays off once each persistent block has enough tiles to stream (measured:
     // 43 tiles per block 10 % faster than the plain kernel, 5 tiles per block 7 % slower)
     const long long tiles = (long long)((g.nx + 31) / 32) * ((g.ny + 7) / 8);

@@ -36,15 +36,17 @@ template <typename real> cudaError_t launch_init(const Lattice<real>& L, const d
 struct CollideTma {
   CUtensorMap f[2];             // the two population lattices as (x, y, plane), box 32 x 8 x 9
   CUtensorMap rho[2];           // the two density planes, box 40 x 12 (tile plus halo)
-  CUtensorMap mu;               // the chemical-potential (psi) plane, box 40 x 12
+  CUtensorMap mu[2];            // the chemical-potential plane (and the second psi plane of the
+                                // pseudopotential force, which alternates like the density), box 40 x 12
   const void* f_ptr[2];         // the planes the descriptors were made for: a lattice
   const void* rho_ptr[2];       // descriptor pointing elsewhere runs the plain kernel
-  const void* mu_ptr;
+  const void* mu_ptr[2];
   int blocks[2];                // persistent grid of the chemical-potential / psi variant
 };
 // Encodes the descriptors for L (whose planes must not move afterwards) and sizes the grids;
 // false, with a message, when the driver cannot.
-bool collide_tma_setup(CollideTma* T, const Lattice<float>& L, const void* rho0, const void* rho1, char* err);
+bool collide_tma_setup(CollideTma* T, const Lattice<float>& L, const void* rho0, const void* rho1, const void* mu1,
+                       char* err);
 
 // ---- geometry (lbm_geometry.cu, compiled without FMA contraction)
 struct GeomParams {

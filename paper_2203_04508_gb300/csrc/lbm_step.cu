@@ -69,17 +69,33 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_rho_vec(Lattice<real> L, int cur
       const real r = density_of(L, fl);
       L.rho[n0 + k] = r;
       // the pointwise part of Eq. 12 while the node's density is at hand (this pass is bound
-      // by its bytes, the chemical-potential pass by its instructions)
+      // by its bytes, the chemical-potential pass by its instructions); with the
+      // pseudopotential force, psi itself
       if (L.psip) L.psip[n0 + k] = psi_prime_shifted(L, r);
+      else if (L.pseudo && L.eos != EOS_NONE) L.mu[n0 + k] = psi_of(L, r);
     }
   }
 }
 
+// psi(rho_s) (1 + c_w) of a solid-layer node whose density is rho_s (pseudopotential force)
+template <typename real>
+__device__ __forceinline__ real psi_wall(const Lattice<real>& L, int n, real rs) {
+  const int b = L.body[n];
+  const double cw = b < L.n_cyl ? L.cyl[4 * b + 3] : L.cw_walls;
+  return psi_of(L, rs) * (real(1) + (real)cw);
+}
+
+// Eq. 15 for one solid layer; with the pseudopotential force also the layer's psi, so that the
+// psi plane of the state is complete without a separate pass
 template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_solid(Lattice<real> L, int layer) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= (layer == 1 ? L.n_s1 : L.n_s2)) return;
   phase_solid(L, layer, j);
+  if (L.pseudo && L.eos != EOS_NONE) {
+    const int n = layer == 1 ? L.s1node[j] : L.s2node[j];
+    L.mu[n] = psi_wall(L, n, L.rho[n]);
+  }
 }
 
 
@@ -486,7 +502,9 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_solid1_b(Lattice<real> L) {
   for (int i = 1; i < 9; ++i) {
     if (m & (1u << (i - 1))) acc += real(wgt(i)) * L.rho_b[L.s1nb[8 * j + i - 1]];
   }
-  L.rho[L.s1node[j]] = acc * L.s1winv[j];
+  const real rs = acc * L.s1winv[j];
+  L.rho[L.s1node[j]] = rs;
+  if (L.pseudo && L.eos != EOS_NONE) L.mu[L.s1node[j]] = psi_wall(L, L.s1node[j], rs);
 }
 
 // Boundary nodes' densities, left by the boundary phase in rho_b, into the density plane.
@@ -497,6 +515,7 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_rho_scatter(Lattice<real> L) {
     const real r = L.rho_b[b];
     L.rho[L.bnode[b]] = r;
     if (L.psip) L.psip[L.bnode[b]] = psi_prime_shifted(L, r);
+    else if (L.pseudo && L.eos != EOS_NONE) L.mu[L.bnode[b]] = psi_of(L, r);
   }
 }
 
@@ -686,7 +705,8 @@ template <typename real>
 static inline const CollideTma* tma_for(const Lattice<real>& L, int cur) {
   if constexpr (sizeof(real) == 4) {
     const CollideTma* T = static_cast<const CollideTma*>(L.tma);
-    if (T && L.f[cur] == T->f_ptr[cur] && L.mu == T->mu_ptr && (L.rho == T->rho_ptr[0] || L.rho == T->rho_ptr[1]))
+    if (T && L.f[cur] == T->f_ptr[cur] && (L.mu == T->mu_ptr[0] || L.mu == T->mu_ptr[1]) &&
+        (L.rho == T->rho_ptr[0] || L.rho == T->rho_ptr[1]))
       return T;
   }
   return nullptr;
@@ -707,7 +727,7 @@ static inline void launch_collide(const Lattice<real>& L, int cur, cudaStream_t 
       CollideMaps M;
       M.f = T->f[cur];
       M.rho = T->rho[L.rho == T->rho_ptr[1] ? 1 : 0];
-      M.mu = T->mu;
+      M.mu = T->mu[L.mu == T->mu_ptr[1] ? 1 : 0];
       const int tiles_x = (L.nx + CT_X - 1) / CT_X;
       const int tiles = tiles_x * ((L.ny + CT_Y - 1) / CT_Y);
       const int P = L.pseudo ? 1 : 0;
@@ -749,7 +769,8 @@ static EncodeTiledFn encode_tiled() {
   return fn;
 }
 
-bool collide_tma_setup(CollideTma* T, const Lattice<float>& L, const void* rho0, const void* rho1, char* err) {
+bool collide_tma_setup(CollideTma* T, const Lattice<float>& L, const void* rho0, const void* rho1, const void* mu1,
+                       char* err) {
   EncodeTiledFn enc = encode_tiled();
   if (!enc) {
     std::snprintf(err, 256, "the driver's tensor-map encoder is not available");
@@ -782,10 +803,12 @@ bool collide_tma_setup(CollideTma* T, const Lattice<float>& L, const void* rho0,
   CUresult r;
   if ((r = plane(&T->rho[0], rho0, F32, 4, TMA_HX, TMA_MY)) != CUDA_SUCCESS) return fail_enc("density plane 0", r);
   if ((r = plane(&T->rho[1], rho1, F32, 4, TMA_HX, TMA_MY)) != CUDA_SUCCESS) return fail_enc("density plane 1", r);
-  if ((r = plane(&T->mu, L.mu, F32, 4, TMA_HX, TMA_MY)) != CUDA_SUCCESS) return fail_enc("the mu plane", r);
+  if ((r = plane(&T->mu[0], L.mu, F32, 4, TMA_HX, TMA_MY)) != CUDA_SUCCESS) return fail_enc("the mu plane", r);
+  if ((r = plane(&T->mu[1], mu1, F32, 4, TMA_HX, TMA_MY)) != CUDA_SUCCESS) return fail_enc("the second psi plane", r);
   T->rho_ptr[0] = rho0;
   T->rho_ptr[1] = rho1;
-  T->mu_ptr = L.mu;
+  T->mu_ptr[0] = L.mu;
+  T->mu_ptr[1] = mu1;
   // persistent grids: every block that fits on the device at once
   int dev = 0, sms = 0, b0 = 0, b1 = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -826,7 +849,7 @@ template <typename real>
 cudaError_t launch_step_overlap(const Lattice<real>& Lt, const Lattice<real>& Ln, int cur, cudaStream_t s,
                                 cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join) {
   const Lattice<real>& L = Lt;
-  launch_mu(L, s);
+  if (!L.pseudo) launch_mu(L, s);   // psi: left by the previous step's density pass, scatter, layers
   launch_collide(L, cur, s);
   cudaError_t e = cudaEventRecord(fork, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, fork, 0);
@@ -845,7 +868,7 @@ cudaError_t launch_step_overlap(const Lattice<real>& Lt, const Lattice<real>& Ln
 
 template <typename real>
 int launches_per_step_overlap(const Lattice<real>& L) {
-  return launches_per_step(L) + (L.n_bnodes > 0);
+  return launches_per_step(L) + (L.n_bnodes > 0) - (L.pseudo && L.eos != EOS_NONE);
 }
 
 // one phase of a step: 0 density, 1 solid layers, 2 chemical potential, 3 force+collide+stream,

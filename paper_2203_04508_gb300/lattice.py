@@ -118,9 +118,17 @@ class Lattice:
         self.stream.synchronize()
 
     # ---- read-outs
-    def fields(self, on_device: bool = False):
-        """(rho, vx, vy) of the current state, as numpy arrays (host) or torch tensors."""
+    def fields(self, on_device: bool = False, out=None):
+        """(rho, vx, vy) of the current state, as numpy arrays (host) or torch tensors.  `out`:
+        three caller-owned host tensors of shape (ny, nx) in the lattice's precision, ideally
+        page-locked, which the library fills (and which are returned)."""
         import torch
+        if out is not None:
+            for t in out:
+                if tuple(t.shape) != (self.ny, self.nx) or t.dtype != self.tdtype or t.is_cuda or not t.is_contiguous():
+                    raise ValueError("out: three contiguous host tensors of shape (ny, nx) in the lattice's precision")
+            self._c(self.lib.lbm_fields(self.ctx, *[C.c_void_p(t.data_ptr()) for t in out], 0))
+            return tuple(out)
         if on_device:
             out = [torch.empty((self.ny, self.nx), dtype=self.tdtype, device="cuda") for _ in range(3)]
             self.stream.wait_stream(torch.cuda.current_stream())

@@ -228,3 +228,19 @@ def test_single_steps_and_the_asynchronous_read_back():
     hist = b.dM_history(n)
     assert np.array_equal(buf.numpy(), hist)
     assert a.last_dM() == hist[-1]
+
+
+def test_fields_into_caller_buffers():
+    """fields(out=...) fills caller-owned page-locked host tensors with the values fields()
+    returns, and refuses buffers of the wrong shape or precision."""
+    import torch
+    sc = S.small_parity()
+    lat = make_lattice(sc, fp64=False)
+    lat.step(7)
+    ref = lat.fields()
+    out = [torch.empty((sc.ny, sc.nx), dtype=torch.float32, pin_memory=True) for _ in range(3)]
+    got = lat.fields(out=out)
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b.numpy())
+    with pytest.raises(ValueError):
+        lat.fields(out=[torch.empty((sc.ny, sc.nx), dtype=torch.float64) for _ in range(3)])
