@@ -1,17 +1,22 @@
 // Kernels of one time step and of the state set-up / read-out (sm_103a).
 //
 // The phases of one step, in the order of their dependencies:
-//   k_rho_vec       density of every fluid node from the 9 offset populations   (Sec. 2.1)
+//   k_rho_vec       density of every fluid node from the 9 offset populations   (Sec. 2.1),
+//                   and the pointwise part of Eq. 12, psi'(rho) (or psi, pseudopotential force)
 //   k_solid (x2)    densities of the first, then second solid layer             (Eq. 15)
-//   k_mu            chemical potential at fluid nodes                            (Eq. 12)
-//                   (pseudopotential force model: k_psi, psi at fluid and solid-layer nodes)
-//   k_collide       force (Eq. 9) + collision (Eq. 4) + exact-difference forcing (Eq. 13)
-//                   + push streaming (Eq. 5) into the other lattice
+//   k_mu_vec        chemical potential at fluid nodes                            (Eq. 12)
+//                   (k_mu per node where psi' is not supplied; k_psi for the pseudopotential
+//                   force outside the overlapped step)
+//   k_collide_tma / k_collide
+//                   force (Eq. 9) + collision (Eq. 4) + exact-difference forcing (Eq. 13)
+//                   + push streaming (Eq. 5) into the other lattice: TMA-pipelined persistent
+//                   kernel on large FP32 lattices, one tile per block otherwise
 //   k_bc            every cut link by Eq. 16 / Eq. 17, the per-node compensation of Eq. 18
 //                   accumulated in FP64, and the deterministic domain sum of that step
 // launch_step issues them one after another on one stream (used by the reverse sweep's
 // recomputation and by the per-phase timing).  lbm_step uses launch_step_overlap instead: the
-// step starts at k_mu, and after k_collide the next state's density pass runs on a second
+// step starts at the chemical potential (none for the pseudopotential force, whose psi the
+// previous step formed), and after the collide the next state's density pass runs on a second
 // stream while k_bc and the next state's solid layers run on the first (same values).
 // The per-node bodies of the phases live in lbm_phases.cuh.
 #include <cstdio>

@@ -72,7 +72,7 @@ def test_peng_robinson_set_up_matches_the_oracle(abi):
 
 @pytest.mark.parametrize("patch", [
     dict(y_bottom=2.5), dict(y_top=10.0), dict(nx=4), dict(coll=0, tau=0.5), dict(s_nu=2.5),
-    dict(cx=[1.0]), dict(eos=7), dict(bc=9), dict(k=0.0), dict(force_model=2),
+    dict(cx=[1.0]), dict(eos=7), dict(bc=9), dict(k=0.0), dict(force_model=2), dict(nx=20001, ny=10000),
     dict(force_model=1, dmu_w_walls=-1.0), dict(force_model=1, dmu_w=[-1.5, 0.1]),
 ])
 def test_invalid_configurations_are_rejected(abi, patch):
@@ -121,3 +121,17 @@ def test_pseudopotential_batches_are_rejected(abi):
     assert lib.lbm_batch_workspace_size(2, arr, C.byref(n)) == abi.LBM_EINVAL
     arr = (abi.lbm_config * 2)(good, good)
     assert lib.lbm_batch_workspace_size(2, arr, C.byref(n)) == 0
+
+
+def test_the_largest_lattice_is_accepted(abi):
+    """2e8 nodes (32-bit plane offsets) is the largest lattice: one node more is refused."""
+    from paper_2203_04508_gb300.lattice import make_config
+    lib = abi.load()
+    phys = S.Scenario(name="big", nx=20000, ny=10000, walls=0).physics()
+    c, keep = make_config(phys, 0)
+    n = C.c_size_t()
+    assert lib.lbm_workspace_size(C.byref(c), C.byref(n)) == 0
+    assert n.value > 2 * 9 * 4 * 20000 * 10000
+    phys.update(nx=20001)
+    c, keep = make_config(phys, 0)
+    assert lib.lbm_workspace_size(C.byref(c), C.byref(n)) == abi.LBM_EINVAL

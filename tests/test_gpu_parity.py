@@ -45,6 +45,10 @@ GEOMETRIES = {
     "flat_q07": lambda: _flat_q(0.7, 1.3),
     "periodic_cyl": lambda: S.Scenario(name="p", nx=61, ny=53, walls=0, cx=[30.41], cy=[26.77], r=[11.3],
                                         dmu_w=[0.0]),
+    # degenerate: centre on a node and an integer radius, so that nodes lie exactly on the circle
+    # (solid) and links are cut at exactly q = 1; flat walls at q = 1 (y_b = 1) and q = 1/2
+    "node_centred": lambda: S.Scenario(name="n", nx=64, ny=64, walls=1, y_bottom=1.0, cx=[32.0], cy=[32.0],
+                                       r=[10.0], dmu_w=[0.0], x0=[32.0], y0=[47.0], r0=[6.0]),
 }
 
 
@@ -244,3 +248,16 @@ def test_fields_into_caller_buffers():
         assert np.array_equal(a, b.numpy())
     with pytest.raises(ValueError):
         lat.fields(out=[torch.empty((sc.ny, sc.nx), dtype=torch.float64) for _ in range(3)])
+
+
+def test_fp64_degenerate_geometry():
+    """The node-centred cylinder of integer radius with a wall at q = 1: FP64 against the oracle
+    over 50 steps, and the links cut at exactly q = 1 are there."""
+    sc = GEOMETRIES["node_centred"]().with_(fp64=True)
+    lat, orc = make_lattice(sc), make_oracle(sc)
+    q = lat.links()["q"]
+    assert np.any(q == 1.0)
+    lat.step(50)
+    orc.step(50)
+    er, ev, ef = compare(lat, orc)
+    assert ef < 1e-10 and er < 1e-10, (er, ev, ef)
