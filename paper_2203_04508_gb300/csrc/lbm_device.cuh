@@ -101,6 +101,16 @@ __device__ __forceinline__ int node_at(const Lattice<real>& L, int x, int y) {
   return wrap_y(L, y) * L.pitch + wrap_x(L, x);
 }
 
+// Sums of products with a fixed rounding order.  Where an expression adds two products
+// the compiler may fuse either into an FMA, and may choose differently in different kernels;
+// the EOS terms, the force and mu are assembled through these, so that every kernel that
+// evaluates them (density, scatter, chemical potential, collide, boundary, read-out, batched)
+// gets the same bits.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // ---------------------------------------------------------------------------------------
 // Equation of state: bulk chemical potential psi'(rho) minus its coexistence value.
 //   CS: psi' = RT [ln rho + (8 eta - 9 eta^2 + 3 eta^3)/(1-eta)^3] - 2 a rho,  eta = b rho/4
@@ -129,22 +139,27 @@ __device__ __forceinline__ real psi_prime_shifted(const Lattice<real>& L, real r
     const int k = r > L.rho_split ? 1 : 0;
     const real dr = r - L.cs_r0[k];
     const real eta0 = L.cs_eta0[k], a = L.cs_a0[k];
-    const real eta = L.b * r * real(0.25);
-    const real h = L.b * dr * real(0.25);
+    const real eta = mul_rn(mul_rn(L.b, r), real(0.25));
+    const real h = mul_rn(mul_rn(L.b, dr), real(0.25));
     const real bb = real(1) - eta;
     const real ib = real(1) / bb;
-    const real ib3 = ib * ib * ib;
-    const real q1 = real(8) - real(9) * (eta + eta0) + real(3) * (eta * eta + eta * eta0 + eta0 * eta0);
-    const real q2 = L.cs_p0a3[k] * (a * a + a * bb + bb * bb);
-    return L.RT * dev_log1p(dr * L.cs_inv_r0[k]) + L.RT * h * ((q1 + q2) * ib3) - real(2) * L.a * dr + L.cs_c0[k];
+    const real ib3 = mul_rn(mul_rn(ib, ib), ib);
+    // 8 - 9 (eta + eta0) + 3 (eta^2 + eta eta0 + eta0^2),  P(eta0) (a^2 + a b + b^2) / (a^3 b^3)
+    const real sq = fma_rn(eta, eta, fma_rn(eta, eta0, mul_rn(eta0, eta0)));
+    const real q1 = fma_rn(real(3), sq, fma_rn(real(-9), eta + eta0, real(8)));
+    const real q2 = mul_rn(L.cs_p0a3[k], fma_rn(a, a, fma_rn(a, bb, mul_rn(bb, bb))));
+    const real t1 = mul_rn(L.RT, dev_log1p(mul_rn(dr, L.cs_inv_r0[k])));
+    const real t2 = mul_rn(mul_rn(L.RT, h), mul_rn(q1 + q2, ib3));
+    return (t1 + t2) + fma_rn(mul_rn(real(-2), L.a), dr, L.cs_c0[k]);
   }
   // Peng-Robinson, Eq. 11 without the gradient term
   const real s2 = real(1.4142135623730951);
-  real br = L.b * r;
-  real om = real(1) - br;
-  return L.RT * dev_log(r / om) -
-         L.aalpha / (real(2) * s2 * L.b) * dev_log((s2 - real(1) + br) / (s2 + real(1) - br)) +
-         L.RT / om - L.aalpha * r / (real(1) + real(2) * br - br * br) - L.mu_sat;
+  const real br = mul_rn(L.b, r);
+  const real om = real(1) - br;
+  const real t1 = mul_rn(L.RT, dev_log(r / om));
+  const real t2 = mul_rn(L.aalpha / mul_rn(real(2) * s2, L.b), dev_log((s2 - real(1) + br) / (s2 + real(1) - br)));
+  const real t4 = mul_rn(L.aalpha, r) / fma_rn(-br, br, fma_rn(real(2), br, real(1)));
+  return (((t1 - t2) + L.RT / om) - t4) - L.mu_sat;
 }
 
 // Fourth-order central first derivatives and Laplacian along the lattice axes.
@@ -202,14 +217,6 @@ __device__ __forceinline__ real lap4(const real* __restrict__ p, int n, const St
   return lap4_of(p[n], p[s.xp1], p[s.xm1], p[s.xp2], p[s.xm2], p[s.yp1], p[s.ym1], p[s.yp2], p[s.ym2]);
 }
 
-// Sums of products with a fixed rounding order.  Where an expression adds two products
-// the compiler may fuse either into an FMA, and may choose differently in different kernels;
-// the step's kernels assemble the force and mu through these, so that every kernel that
-// evaluates them (collide, boundary, read-out, batched) gets the same bits.
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // Eq. 12 in mesh units, shifted: mu~ = k^2 (psi'(rho) - mu_sat) - kappa^ lap(rho)
 template <typename real>
@@ -234,14 +241,15 @@ template <typename real>
 __device__ __forceinline__ real psi_of(const Lattice<real>& L, real r) {
   real p0;
   if (L.eos == EOS_CS) {
-    const real eta = L.b * r * real(0.25);
+    const real eta = mul_rn(mul_rn(L.b, r), real(0.25));
     const real om = real(1) - eta;
-    p0 = r * L.RT * (real(1) + eta * (real(1) + eta * (real(1) - eta))) / (om * om * om) - L.a * r * r;
+    const real poly = fma_rn(eta, fma_rn(eta, real(1) - eta, real(1)), real(1));   // 1 + eta + eta^2 - eta^3
+    p0 = mul_rn(mul_rn(r, L.RT), poly) / mul_rn(mul_rn(om, om), om) - mul_rn(mul_rn(L.a, r), r);
   } else {
-    const real br = L.b * r;
-    p0 = r * L.RT / (real(1) - br) - L.aalpha * r * r / (real(1) + br * (real(2) - br));
+    const real br = mul_rn(L.b, r);
+    p0 = mul_rn(r, L.RT) / (real(1) - br) - mul_rn(mul_rn(L.aalpha, r), r) / fma_rn(br, real(2) - br, real(1));
   }
-  const real arg = real(2) * (r * real(1.0 / 3.0) - L.k2 * p0);
+  const real arg = mul_rn(real(2), fma_rn(r, real(1.0 / 3.0), -mul_rn(L.k2, p0)));
   return arg > real(0) ? sqrt(arg) : real(0);
 }
 

@@ -53,6 +53,10 @@ template <> __device__ __forceinline__ float lane_of<float>(const float4& v, int
   return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
 }
 template <> __device__ __forceinline__ double lane_of<double>(const double2& v, int k) { return k == 0 ? v.x : v.y; }
+template <typename real>
+__device__ __forceinline__ typename Vec16<real>::type make_vec(const real (&a)[Vec16<real>::V]);
+template <> __device__ __forceinline__ float4 make_vec<float>(const float (&a)[4]) { return make_float4(a[0], a[1], a[2], a[3]); }
+template <> __device__ __forceinline__ double2 make_vec<double>(const double (&a)[2]) { return make_double2(a[0], a[1]); }
 
 template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_rho_vec(Lattice<real> L, int cur) {
@@ -65,20 +69,38 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_rho_vec(Lattice<real> L, int cur
   VT fv[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) fv[i] = __ldg(reinterpret_cast<const VT*>(f + i * L.plane + n0));
+  bool fluid[V];
+  bool all = true;
 #pragma unroll
   for (int k = 0; k < V; ++k) {
-    if (x0 + k < L.nx && L.kind[n0 + k] == KIND_FLUID) {
-      real fl[9];
+    fluid[k] = x0 + k < L.nx && L.kind[n0 + k] == KIND_FLUID;
+    all &= fluid[k];
+  }
+  // the pointwise part of Eq. 12 while the node's density is at hand (this pass is bound by its
+  // bytes, the chemical-potential pass by its instructions); with the pseudopotential force,
+  // psi itself
+  real* second = L.psip ? L.psip : ((L.pseudo && L.eos != EOS_NONE) ? L.mu : nullptr);
+  real r[V], p[V];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) fl[i] = lane_of<real>(fv[i], k);
-      const real r = density_of(L, fl);
-      L.rho[n0 + k] = r;
-      // the pointwise part of Eq. 12 while the node's density is at hand (this pass is bound
-      // by its bytes, the chemical-potential pass by its instructions); with the
-      // pseudopotential force, psi itself
-      if (L.psip) L.psip[n0 + k] = psi_prime_shifted(L, r);
-      else if (L.pseudo && L.eos != EOS_NONE) L.mu[n0 + k] = psi_of(L, r);
-    }
+  for (int k = 0; k < V; ++k) {
+    real fl[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fl[i] = lane_of<real>(fv[i], k);
+    r[k] = density_of(L, fl);
+    p[k] = (!second || !fluid[k]) ? real(0) : (L.psip ? psi_prime_shifted(L, r[k]) : psi_of(L, r[k]));
+  }
+  if (all) {
+    // every node fluid: 16-byte stores (a solid node's slot belongs to the solid-layer kernels,
+    // which may be writing it concurrently, so mixed vectors take the scalar path)
+    *reinterpret_cast<VT*>(L.rho + n0) = make_vec<real>(r);
+    if (second) *reinterpret_cast<VT*>(second + n0) = make_vec<real>(p);
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    if (!fluid[k]) continue;
+    L.rho[n0 + k] = r[k];
+    if (second) second[n0 + k] = p[k];
   }
 }
 
