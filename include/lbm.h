@@ -206,6 +206,13 @@ lbm_status lbm_load(lbm_ctx* ctx, const char* path);
  * host. */
 lbm_status lbm_column_density(lbm_ctx* ctx, int32_t x, int32_t y0, int32_t n, double* out, int32_t on_device);
 
+/* Largest speed |v| over the fluid nodes of the current state, v = u + F/(2 rho) as lbm_fields
+ * returns it (the velocity defined under Eq. 14), formed in FP64 from the lattice's precision;
+ * NaN when a fluid node's velocity is not a number.  Synchronous (one small read-back); it forms
+ * the density and chemical potential of the current state like lbm_fields and leaves the next
+ * step's result unchanged.  Status: LBM_ESTATE before lbm_init, LBM_EINVAL for a null pointer. */
+lbm_status lbm_max_speed(lbm_ctx* ctx, double* vmax);
+
 /* Populations f_i (not offset) of the current state, 9 planes of nx*ny values of the
  * context's precision; zero at solid nodes.  on_device as for lbm_fields. */
 lbm_status lbm_populations(lbm_ctx* ctx, void* f, int32_t on_device);
@@ -255,6 +262,13 @@ lbm_status lbm_launches_per_step(lbm_ctx* ctx, int64_t* n);
 lbm_status lbm_set_collide_kernel(lbm_ctx* ctx, int32_t kind);
 /* The collide kernel lbm_step runs now (0 plain, 1 TMA-pipelined). */
 lbm_status lbm_get_collide_kernel(lbm_ctx* ctx, int32_t* kind);
+
+/* Polls before the TMA-pipelined kernel's wait for a tile's loads gives up (default 2^22, a
+ * second or more); 0 makes every such wait give up at once, to test the timeout path.  A block
+ * that gives up still waits, with the default limit, for its own copies in flight, then leaves;
+ * the next lbm_mass returns LBM_ETIMEOUT and the context stays in that state (the lattice is not
+ * a valid state any more).  Call after lbm_build_links; the step graphs are captured again. */
+lbm_status lbm_set_spin_limit(lbm_ctx* ctx, int64_t polls);
 
 /* Sets the state (a new initial state, in place of lbm_init) from 9 arrays of ny x nx
  * absolute populations in the context's precision, population i at offset i*nx*ny (the layout

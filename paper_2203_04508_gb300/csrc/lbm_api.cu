@@ -141,6 +141,7 @@ struct lbm_ctx {
   CollideTma tma{};
   bool tma_ok = false;
   int collide_kind = 1;
+  long long spin_limit = 1LL << 22;   // polls before a pipelined kernel's wait gives up
   lbm_status sticky = LBM_OK;
   std::string err;
   // one segment's recomputation (kind 0) or reverse steps (kind 1), captured once per
@@ -267,6 +268,7 @@ void fill_lattice(lbm_ctx* c, Lattice<real>& L) {
   L.step_ctr = (unsigned long long*)(w + y.step_ctr);
   L.scalars = (double*)(w + y.scalars);
   L.kerr = (unsigned int*)(w + y.kerr);
+  L.spin_limit = c->spin_limit;
   L.tma = nullptr;
   if constexpr (sizeof(real) == 4) {
     if (c->tma_ok && c->collide_kind == 1) L.tma = &c->tma;
@@ -404,7 +406,9 @@ lbm_status profile_steps(lbm_ctx* c, const Lattice<real>& L, long long n, double
   for (int k = 0; k < 5; ++k) ms[k] = 0.0;
   lbm_status st = LBM_OK;
   for (long long s = 0; s < n && st == LBM_OK; ++s) {
+    static const char* const phase_name[5] = {"density", "solid layers", "chemical potential", "collide", "boundary"};
     for (int ph = 0; ph < 5; ++ph) {
+      LBM_RANGE(phase_name[ph]);
       cudaEventRecord(ev[ph], c->stream);
       cudaError_t e = launch_phase(L, c->cur, ph, c->stream);
       if (e != cudaSuccess) { st = fail(c, LBM_ECUDA, "launch failed: %s", cudaGetErrorString(e)); break; }
@@ -455,6 +459,7 @@ lbm_status lbm_workspace_size(const lbm_config* cfg, size_t* bytes) {
 }
 
 lbm_status lbm_create(const lbm_config* cfg, void* stream, void* workspace, size_t bytes, lbm_ctx** out) {
+  LBM_RANGE("lbm_create");
   if (!cfg || !out) return LBM_EINVAL;
   *out = nullptr;
   lbm_ctx* c = new lbm_ctx();
@@ -495,6 +500,7 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, void* workspace, size
 }
 
 lbm_status lbm_build_links(lbm_ctx* c) {
+  LBM_RANGE("lbm_build_links");
   if (!c || !c->ws) return LBM_ESTATE;
   if (c->sticky != LBM_OK) return c->sticky;
   for (auto& gr : c->graph)
@@ -618,6 +624,7 @@ lbm_status lbm_get_kind(lbm_ctx* c, uint8_t* kind) {
 }
 
 lbm_status lbm_init(lbm_ctx* c, const lbm_init_spec* s) {
+  LBM_RANGE("lbm_init");
   if (!c || !c->built) return LBM_ESTATE;
   if (c->sticky != LBM_OK) return c->sticky;
   if (!s || s->n_drop < 0 || s->n_drop > MAX_DROPS) return fail(c, LBM_EINVAL, "n_drop must lie in [0, %d]", MAX_DROPS);
@@ -650,6 +657,7 @@ lbm_status lbm_init(lbm_ctx* c, const lbm_init_spec* s) {
 }
 
 lbm_status lbm_step(lbm_ctx* c, int64_t n) {
+  LBM_RANGE("lbm_step");
   if (!c || !c->inited) return LBM_ESTATE;
   if (c->sticky != LBM_OK) return c->sticky;
   if (n < 0) return fail(c, LBM_EINVAL, "negative step count");
@@ -675,6 +683,18 @@ lbm_status lbm_set_collide_kernel(lbm_ctx* c, int32_t kind) {
   return LBM_OK;
 }
 
+lbm_status lbm_set_spin_limit(lbm_ctx* c, int64_t polls) {
+  if (!c || !c->built) return LBM_ESTATE;
+  if (polls < 0) return fail(c, LBM_EINVAL, "negative spin limit");
+  c->spin_limit = polls;
+  for (auto& gr : c->graph)
+    if (gr) { cudaGraphExecDestroy(gr); gr = nullptr; }
+  for (auto& a : c->adj_graphs) cudaGraphExecDestroy(a.exec);
+  c->adj_graphs.clear();
+  refresh(c);
+  return LBM_OK;
+}
+
 lbm_status lbm_get_collide_kernel(lbm_ctx* c, int32_t* kind) {
   if (!c || !c->built || !kind) return LBM_ESTATE;
   *kind = (!c->fp64 && c->tma_ok && c->collide_kind == 1) ? 1 : 0;
@@ -688,6 +708,7 @@ lbm_status lbm_launches_per_step(lbm_ctx* c, int64_t* n) {
 }
 
 lbm_status lbm_fields(lbm_ctx* c, void* rho, void* vx, void* vy, int32_t on_device) {
+  LBM_RANGE("lbm_fields");
   if (!c || !c->inited) return LBM_ESTATE;
   if (c->sticky != LBM_OK) return c->sticky;
   if (!rho || !vx || !vy) return fail(c, LBM_EINVAL, "null output");
@@ -763,6 +784,7 @@ constexpr uint32_t CKPT_VERSION = 1;
 }  // namespace
 
 lbm_status lbm_save(lbm_ctx* c, const char* path) {
+  LBM_RANGE("lbm_save");
   if (!c || !c->inited) return LBM_ESTATE;
   if (c->sticky != LBM_OK) return c->sticky;
   if (!path) return fail(c, LBM_EINVAL, "null path");
@@ -800,6 +822,7 @@ lbm_status lbm_save(lbm_ctx* c, const char* path) {
 }
 
 lbm_status lbm_load(lbm_ctx* c, const char* path) {
+  LBM_RANGE("lbm_load");
   if (!c || !c->built) return LBM_ESTATE;
   if (c->sticky != LBM_OK) return c->sticky;
   if (!path) return fail(c, LBM_EINVAL, "null path");
@@ -849,6 +872,7 @@ lbm_status lbm_load(lbm_ctx* c, const char* path) {
 }
 
 lbm_status lbm_column_density(lbm_ctx* c, int32_t x, int32_t y0, int32_t n, double* out, int32_t on_device) {
+  LBM_RANGE("lbm_column_density");
   if (!c || !c->inited) return LBM_ESTATE;
   if (c->sticky != LBM_OK) return c->sticky;
   if (!out) return fail(c, LBM_EINVAL, "null output");
@@ -865,7 +889,23 @@ lbm_status lbm_column_density(lbm_ctx* c, int32_t x, int32_t y0, int32_t n, doub
   return LBM_OK;
 }
 
+lbm_status lbm_max_speed(lbm_ctx* c, double* vmax) {
+  LBM_RANGE("lbm_max_speed");
+  if (!c || !c->inited) return LBM_ESTATE;
+  if (c->sticky != LBM_OK) return c->sticky;
+  if (!vmax) return fail(c, LBM_EINVAL, "null output");
+  // the lattice that the next step overwrites completely serves as the reduction slot
+  auto* d = (unsigned long long*)(c->ws + (c->cur ? c->lay.fA : c->lay.fB));
+  CUDA_OK(c, cudaMemsetAsync(d, 0, 8, c->stream));
+  if (c->fp64) CUDA_OK(c, launch_max_speed(c->Ld, c->cur, d, c->stream));
+  else CUDA_OK(c, launch_max_speed(c->Lf, c->cur, d, c->stream));
+  CUDA_OK(c, cudaMemcpyAsync(vmax, d, 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
 lbm_status lbm_populations(lbm_ctx* c, void* f, int32_t on_device) {
+  LBM_RANGE("lbm_populations");
   if (!c || !c->inited) return LBM_ESTATE;
   if (c->sticky != LBM_OK) return c->sticky;
   if (!f) return fail(c, LBM_EINVAL, "null output");
@@ -883,6 +923,7 @@ lbm_status lbm_populations(lbm_ctx* c, void* f, int32_t on_device) {
 }
 
 lbm_status lbm_set_populations(lbm_ctx* c, const void* f, int32_t on_device) {
+  LBM_RANGE("lbm_set_populations");
   if (!c || !c->built) return LBM_ESTATE;
   if (c->sticky != LBM_OK) return c->sticky;
   if (!f) return fail(c, LBM_EINVAL, "null input");
@@ -912,6 +953,7 @@ lbm_status lbm_set_populations(lbm_ctx* c, const void* f, int32_t on_device) {
 }
 
 lbm_status lbm_mass(lbm_ctx* c, double* M, double* M0, double* dM_last) {
+  LBM_RANGE("lbm_mass");
   if (!c || !c->inited) return LBM_ESTATE;
   if (c->sticky != LBM_OK) return c->sticky;
   const Layout& y = c->lay;
@@ -969,6 +1011,7 @@ lbm_status lbm_last_dM_async(lbm_ctx* c, double* dM) {
 }
 
 lbm_status lbm_profile_steps(lbm_ctx* c, int64_t n, double* ms5) {
+  LBM_RANGE("lbm_profile_steps");
   if (!c || !c->inited || !ms5) return LBM_ESTATE;
   if (c->sticky != LBM_OK) return c->sticky;
   return c->fp64 ? profile_steps(c, c->Ld, n, ms5) : profile_steps(c, c->Lf, n, ms5);
@@ -1185,6 +1228,7 @@ lbm_status lbm_batch_workspace_size(int32_t n, const lbm_config* cfgs, size_t* b
 
 lbm_status lbm_batch_create(int32_t n, const lbm_config* cfgs, void* stream, void* workspace, size_t bytes,
                             lbm_batch** out) {
+  LBM_RANGE("lbm_batch_create");
   if (!out) return LBM_EINVAL;
   lbm_batch* b = new lbm_batch();
   *out = b;
@@ -1213,6 +1257,7 @@ lbm_status lbm_batch_create(int32_t n, const lbm_config* cfgs, void* stream, voi
 }
 
 lbm_status lbm_batch_build_links(lbm_batch* b) {
+  LBM_RANGE("lbm_batch_build_links");
   if (!b || b->ctx.empty()) return LBM_ESTATE;
   for (int k = 0; k < b->n; ++k) {
     lbm_status st = lbm_build_links(b->ctx[k]);
@@ -1223,6 +1268,7 @@ lbm_status lbm_batch_build_links(lbm_batch* b) {
 }
 
 lbm_status lbm_batch_init(lbm_batch* b, const lbm_init_spec* specs) {
+  LBM_RANGE("lbm_batch_init");
   if (!b || !b->tables || !specs) return LBM_ESTATE;
   for (int k = 0; k < b->n; ++k) {
     lbm_status st = lbm_init(b->ctx[k], &specs[k]);
@@ -1233,6 +1279,7 @@ lbm_status lbm_batch_init(lbm_batch* b, const lbm_init_spec* specs) {
 }
 
 lbm_status lbm_batch_step(lbm_batch* b, int64_t n) {
+  LBM_RANGE("lbm_batch_step");
   if (!b || !b->tables) return LBM_ESTATE;
   for (int k = 0; k < b->n; ++k) {
     if (!b->ctx[k]->inited) return bfail(b, LBM_ESTATE, "instance %d not initialised", k);
@@ -1335,6 +1382,7 @@ lbm_status time_batch(lbm_batch* b, int64_t steps, cudaEvent_t e0, cudaEvent_t e
 
 lbm_status lbm_batch_autotune(lbm_batch* b, int64_t steps, int32_t* chosen_log2w, int32_t* chosen_groups,
                               double* ms) {
+  LBM_RANGE("lbm_batch_autotune");
   if (!b || !b->tables) return LBM_ESTATE;
   if (steps < 1 || steps > (1LL << 20)) return bfail(b, LBM_EINVAL, "trial steps must lie in [1, 2^20]");
   cudaEvent_t e0, e1;
@@ -1682,6 +1730,7 @@ lbm_status lbm_adjoint_workspace_size(lbm_ctx* c, int64_t n_steps, int64_t every
 }
 
 lbm_status lbm_forward_checkpointed(lbm_ctx* c, int64_t n_steps, int64_t every, void* workspace, size_t bytes) {
+  LBM_RANGE("lbm_forward_checkpointed");
   if (!c || !c->inited) return LBM_ESTATE;
   if (c->sticky != LBM_OK) return c->sticky;
   if (n_steps < 1 || every < 0) return fail(c, LBM_EINVAL, "n_steps must be positive and every non-negative");
@@ -1713,6 +1762,7 @@ lbm_status lbm_objective(lbm_ctx* c, int32_t body, double* J, void* dJ_drho, int
 
 lbm_status lbm_adjoint(lbm_ctx* c, const void* dJ_drho, const void* dJ_df, int32_t on_device, double* grad,
                        void* dJ_df0) {
+  LBM_RANGE("lbm_adjoint");
   if (!c || !c->inited) return LBM_ESTATE;
   if (c->sticky != LBM_OK) return c->sticky;
   if (!c->tape.valid || c->tape.steps_end != c->steps || c->tape.cur_end != c->cur)

@@ -83,6 +83,8 @@ struct Lattice {
   unsigned long long* step_ctr; // steps taken (device side)
   double* scalars;              // [0] mass, [1] non-finite count
   unsigned int* kerr;           // set by a kernel whose bounded wait gave up (0 otherwise)
+  long long spin_limit;         // polls before a pipelined kernel's wait for its loads gives up
+                                // (its wait for copies in flight before leaving keeps the full limit)
   const void* tma;              // host side: TMA descriptors of the pipelined collide kernel
                                 // (FP32), null for the plain kernel
 };

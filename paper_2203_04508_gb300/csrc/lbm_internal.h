@@ -3,10 +3,21 @@
 #include <cstdint>
 #include <cuda.h>            // CUtensorMap (the type; the encoder is taken from the driver at run time)
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>   // header-only; a no-op unless a profiler attaches
 
 #include "lbm_device.cuh"
 
 namespace lbmgb {
+
+// A named NVTX range around a host call, so that a timeline profiler shows the library's entry
+// points (set-up, stepping, read-outs, checkpoints) over the kernels they launch.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define LBM_RANGE(name) ::lbmgb::NvtxRange lbm_nvtx_range_(name)
 
 inline unsigned mass_blocks() { return 152 * 4; }
 
@@ -26,6 +37,8 @@ template <typename real> cudaError_t launch_fields(const Lattice<real>& L, int c
 template <typename real> cudaError_t launch_populations(const Lattice<real>& L, int cur, real* out, cudaStream_t s);
 template <typename real>
 cudaError_t launch_column(const Lattice<real>& L, int cur, int x, int y0, int n, double* out, cudaStream_t s);
+template <typename real>
+cudaError_t launch_max_speed(const Lattice<real>& L, int cur, unsigned long long* out, cudaStream_t s);
 template <typename real> cudaError_t launch_set_populations(const Lattice<real>& L, int cur, const real* in, cudaStream_t s);
 template <typename real> cudaError_t launch_mass(const Lattice<real>& L, int cur, cudaStream_t s);
 template <typename real> cudaError_t launch_init(const Lattice<real>& L, const double* drops, int n_drop, double W,

@@ -19,6 +19,7 @@
 // previous step formed), and after the collide the next state's density pass runs on a second
 // stream while k_bc and the next state's solid layers run on the first (same values).
 // The per-node bodies of the phases live in lbm_phases.cuh.
+#include <algorithm>
 #include <cstdio>
 
 #include "lbm_device.cuh"
@@ -375,9 +376,9 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait for the phase of the given parity to complete
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (long long it = 0; it < TMA_SPIN_LIMIT; ++it) {
+// bounded wait for the phase of the given parity to complete (at most `limit` polls)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = TMA_SPIN_LIMIT) {
+  for (long long it = 0; it < limit; ++it) {
     if (mbar_test(bar, parity)) return true;
     if (it > 8) __nanosleep(32);
   }
@@ -444,7 +445,7 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, in
     const int x0 = (t % tiles_x) * CT_X, y0 = (t / tiles_x) * CT_Y;
     const int x = x0 + lx, y = y0 + ly;
     const bool fluid = x < L.nx && y < L.ny && L.kind[y * L.pitch + x] == KIND_FLUID;
-    const bool ok = mbar_wait(&bar[s], (uint32_t)((k / TMA_STAGES) & 1));
+    const bool ok = mbar_wait(&bar[s], (uint32_t)((k / TMA_STAGES) & 1), L.spin_limit);
     if (__syncthreads_or(!ok)) {
       // give up: flag it, let this block's copies still in flight land, and leave
       if (threadIdx.x == 0) {
@@ -621,6 +622,46 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_fields(Lattice<real> L, int cur,
   rho_out[d] = r;
   vx_out[d] = (jx + real(0.5) * Fx) / r;
   vy_out[d] = (jy + real(0.5) * Fy) / r;
+}
+
+// Largest speed |v| = |u + F/(2 rho)| over the fluid nodes of the current state, combined into
+// *out as FP64 bits (the caller zeroes it): non-negative doubles order like their bit patterns,
+// and a NaN, stored as the positive quiet NaN, lies above every number.  The speed is formed in
+// FP64 from the velocity k_fields writes, squares and sum rounded in that order.
+template <typename real>
+__global__ void __launch_bounds__(NODE_BLOCK) k_max_speed(Lattice<real> L, int cur, unsigned long long* out) {
+  unsigned long long b = 0ull;
+  const real* __restrict__ f = L.f[cur];
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < L.plane;
+       n += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(n % L.pitch), y = (int)(n / L.pitch);
+    if (x >= L.nx || L.kind[n] != KIND_FLUID) continue;
+    real fl[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fl[i] = f[i * L.plane + n];
+    real drho, jx, jy;
+    moments(fl, drho, jx, jy);
+    const real r = L.rho_ref + drho;
+    real Fx, Fy;
+    if (L.pseudo) force_at<real, true>(L, x, y, r, Fx, Fy);
+    else force_at<real, false>(L, x, y, r, Fx, Fy);
+    const double vx = (double)((jx + real(0.5) * Fx) / r), vy = (double)((jy + real(0.5) * Fy) / r);
+    const double sp = sqrt(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)));
+    const unsigned long long bits = sp == sp ? (unsigned long long)__double_as_longlong(sp) : 0x7ff8000000000000ull;
+    b = bits > b ? bits : b;
+  }
+  __shared__ unsigned long long part[NODE_BLOCK / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, b, o);
+    b = v > b ? v : b;
+  }
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = b;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < NODE_BLOCK / 32; ++w) b = part[w] > b ? part[w] : b;
+    atomicMax(out, b);
+  }
 }
 
 // Density of the nodes (x, y0 + j), j < n, of the current state (NaN at solid nodes), in FP64.
@@ -941,6 +982,15 @@ cudaError_t launch_fields(const Lattice<real>& L, int cur, real* r, real* vx, re
 }
 
 template <typename real>
+cudaError_t launch_max_speed(const Lattice<real>& L, int cur, unsigned long long* out, cudaStream_t s) {
+  cudaError_t e = launch_macro(L, cur, s);
+  if (e != cudaSuccess) return e;
+  const long long blocks = std::min<long long>(grid_for(L.plane, NODE_BLOCK), 152LL * 8);
+  k_max_speed<real><<<(unsigned)blocks, NODE_BLOCK, 0, s>>>(L, cur, out);
+  return cudaGetLastError();
+}
+
+template <typename real>
 cudaError_t launch_column(const Lattice<real>& L, int cur, int x, int y0, int n, double* out, cudaStream_t s) {
   k_column<real><<<grid_for(n, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, cur, x, y0, n, out);
   return cudaGetLastError();
@@ -982,6 +1032,7 @@ cudaError_t launch_init(const Lattice<real>& L, const double* drops, int n_drop,
   template cudaError_t launch_fields<real>(const Lattice<real>&, int, real*, real*, real*, cudaStream_t); \
   template cudaError_t launch_populations<real>(const Lattice<real>&, int, real*, cudaStream_t);        \
   template cudaError_t launch_column<real>(const Lattice<real>&, int, int, int, int, double*, cudaStream_t); \
+  template cudaError_t launch_max_speed<real>(const Lattice<real>&, int, unsigned long long*, cudaStream_t); \
   template cudaError_t launch_set_populations<real>(const Lattice<real>&, int, const real*, cudaStream_t); \
   template cudaError_t launch_mass<real>(const Lattice<real>&, int, cudaStream_t);                      \
   template cudaError_t launch_init<real>(const Lattice<real>&, const double*, int, double, double,      \

@@ -203,9 +203,19 @@ class Lattice:
         self._c(self.lib.lbm_column_density(self.ctx, int(x), int(y0), int(n), C.c_void_p(out.ctypes.data), 0))
         return out
 
+    def max_speed(self) -> float:
+        """Largest |v| over the fluid nodes of the current state (NaN if one is not a number)."""
+        v = C.c_double()
+        self._c(self.lib.lbm_max_speed(self.ctx, C.byref(v)))
+        return v.value
+
     def set_collide_kernel(self, kind: int):
         """0: the plain collide kernel; 1: the TMA-pipelined one (FP32; the default where available)."""
         self._c(self.lib.lbm_set_collide_kernel(self.ctx, int(kind)))
+
+    def set_spin_limit(self, polls: int):
+        """Polls before the pipelined kernel's waits give up (0: at once, to test that path)."""
+        self._c(self.lib.lbm_set_spin_limit(self.ctx, int(polls)))
 
     def collide_kernel(self) -> int:
         k = C.c_int32()

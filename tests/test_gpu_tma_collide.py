@@ -86,3 +86,28 @@ def test_fp64_has_only_the_plain_kernel():
     assert lat.collide_kernel() == 0
     with pytest.raises(G.LbmError):
         lat.set_collide_kernel(1)
+
+
+def test_a_wait_that_gives_up_is_reported():
+    """With the pipelined kernel's wait limit at zero every block gives up at its first tile: it
+    flags the error, waits (with the full limit) for its own copies in flight and leaves; the
+    next mass audit reports LBM_ETIMEOUT, and the context keeps that status."""
+    import paper_2203_04508_gb300 as G
+    from paper_2203_04508_gb300 import _abi
+    lat = make_lattice(S.c3_impact(256, 512), fp64=False)
+    lat.set_collide_kernel(1)
+    lat.step(3)
+    lat.mass()
+    lat.set_spin_limit(0)
+    lat.step(1)
+    with pytest.raises(G.LbmError) as e:
+        lat.mass()
+    assert e.value.args[0].startswith(f"lbm status {_abi.LBM_ETIMEOUT}")
+    with pytest.raises(G.LbmError):
+        lat.step(1)
+    # a fresh context on the same device is unaffected
+    other = make_lattice(S.c3_impact(256, 512), fp64=False)
+    other.set_collide_kernel(1)
+    other.step(3)
+    M, M0, _ = other.mass()
+    assert abs(M / M0 - 1) < 1e-6
