@@ -263,6 +263,14 @@ lbm_status lbm_set_collide_kernel(lbm_ctx* ctx, int32_t kind);
 /* The collide kernel lbm_step runs now (0 plain, 1 TMA-pipelined). */
 lbm_status lbm_get_collide_kernel(lbm_ctx* ctx, int32_t* kind);
 
+/* The chemical-potential pass (Eq. 12) of the chemical-potential force model: 0 one node a
+ * thread, 1 four (FP64: two) consecutive nodes of a row a thread from 16-byte loads, 2 (FP32
+ * only, the FP32 default; FP64 defaults to 1) row sweeps, a thread walking down a column of
+ * four-node groups with the stencil's rows in registers.  All three give the same bits.  Call
+ * after lbm_build_links; the step graphs are captured again.  LBM_EINVAL for another value or
+ * for 2 on an FP64 lattice. */
+lbm_status lbm_set_mu_kernel(lbm_ctx* ctx, int32_t kind);
+
 /* Polls before the TMA-pipelined kernel's wait for a tile's loads gives up (default 2^22, a
  * second or more); 0 makes every such wait give up at once, to test the timeout path.  A block
  * that gives up still waits, with the default limit, for its own copies in flight, then leaves;

@@ -62,6 +62,7 @@ _SIGS = {
     "lbm_launches_per_step": (I32, [P, C.POINTER(I64)]),
     "lbm_set_collide_kernel": (I32, [P, I32]),
     "lbm_set_spin_limit": (I32, [P, I64]),
+    "lbm_set_mu_kernel": (I32, [P, I32]),
     "lbm_max_speed": (I32, [P, P]),
     "lbm_column_density": (I32, [P, I32, I32, I32, P, I32]),
     "lbm_last_dM_async": (I32, [P, P]),

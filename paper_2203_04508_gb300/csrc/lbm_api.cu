@@ -142,6 +142,7 @@ struct lbm_ctx {
   bool tma_ok = false;
   int collide_kind = 1;
   long long spin_limit = 1LL << 22;   // polls before a pipelined kernel's wait gives up
+  int mu_kind = -1;                   // chemical-potential pass (-1: the precision's default)
   lbm_status sticky = LBM_OK;
   std::string err;
   // one segment's recomputation (kind 0) or reverse steps (kind 1), captured once per
@@ -269,6 +270,7 @@ void fill_lattice(lbm_ctx* c, Lattice<real>& L) {
   L.scalars = (double*)(w + y.scalars);
   L.kerr = (unsigned int*)(w + y.kerr);
   L.spin_limit = c->spin_limit;
+  L.mu_kernel = c->mu_kind >= 0 ? c->mu_kind : (c->fp64 ? 1 : 2);
   L.tma = nullptr;
   if constexpr (sizeof(real) == 4) {
     if (c->tma_ok && c->collide_kind == 1) L.tma = &c->tma;
@@ -687,6 +689,19 @@ lbm_status lbm_set_spin_limit(lbm_ctx* c, int64_t polls) {
   if (!c || !c->built) return LBM_ESTATE;
   if (polls < 0) return fail(c, LBM_EINVAL, "negative spin limit");
   c->spin_limit = polls;
+  for (auto& gr : c->graph)
+    if (gr) { cudaGraphExecDestroy(gr); gr = nullptr; }
+  for (auto& a : c->adj_graphs) cudaGraphExecDestroy(a.exec);
+  c->adj_graphs.clear();
+  refresh(c);
+  return LBM_OK;
+}
+
+lbm_status lbm_set_mu_kernel(lbm_ctx* c, int32_t kind) {
+  if (!c || !c->built) return LBM_ESTATE;
+  if (kind < 0 || kind > 2) return fail(c, LBM_EINVAL, "chemical-potential kernel must be 0, 1 or 2");
+  if (kind == 2 && c->fp64) return fail(c, LBM_EINVAL, "the row-sweep chemical-potential kernel is FP32 only");
+  c->mu_kind = kind;
   for (auto& gr : c->graph)
     if (gr) { cudaGraphExecDestroy(gr); gr = nullptr; }
   for (auto& a : c->adj_graphs) cudaGraphExecDestroy(a.exec);

@@ -85,6 +85,8 @@ struct Lattice {
   unsigned int* kerr;           // set by a kernel whose bounded wait gave up (0 otherwise)
   long long spin_limit;         // polls before a pipelined kernel's wait for its loads gives up
                                 // (its wait for copies in flight before leaving keeps the full limit)
+  int mu_kernel;                // host side: the chemical-potential pass (0 per node, 1 row
+                                // vectors, 2 row sweeps, FP32 only)
   const void* tma;              // host side: TMA descriptors of the pipelined collide kernel
                                 // (FP32), null for the plain kernel
 };

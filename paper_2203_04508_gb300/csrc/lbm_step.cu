@@ -195,6 +195,76 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_mu_vec(Lattice<real> L) {
   }
 }
 
+// Chemical potential (FP32) by row sweeps: a thread holds four consecutive nodes of a row and
+// walks MU_ROWS rows down its column, keeping the five rows of the 9-point stencil in registers
+// and loading the row two ahead while it computes the current one, so that a row costs it one
+// density vector, one psi' vector and the node classes.  The centre row's two further nodes on
+// each side come from the neighbouring lanes; lanes at a warp's edge, at the lattice's x edges
+// or at a ragged end load them one by one with the periodic wrap.  Same values and the same
+// sums as k_mu (lap4_of, mu_of).
+// Rows a thread walks and threads a block (a 512-node strip): 16 x 128 was the fastest of 4-32
+// rows and 64-256 threads on the 2048 x 4096 impact lattice (0.030 ms; 0.033 for k_mu_vec).
+constexpr int MU_ROWS = 16, MU_BLOCK = 128;
+__global__ void __launch_bounds__(MU_BLOCK) k_mu_sweep(Lattice<float> L) {
+  const int lane = threadIdx.x & 31;
+  const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  const int ya = blockIdx.y * MU_ROWS, yb = min(ya + MU_ROWS, L.ny);
+  const bool live = x0 < L.nx, full = x0 + 4 <= L.nx;
+  const float* __restrict__ r = L.rho;
+  // this thread's vector of row y (zeros beyond a wall, wrapped on a periodic lattice)
+  auto row = [&](int y) -> float4 {
+    if (!live) return make_float4(0.f, 0.f, 0.f, 0.f);
+    if (y < 0 || y >= L.ny) {
+      if (L.walls) return make_float4(0.f, 0.f, 0.f, 0.f);
+      y = y < 0 ? y + L.ny : y - L.ny;
+    }
+    return __ldg(reinterpret_cast<const float4*>(r + y * L.pitch + x0));
+  };
+  float4 w0 = row(ya - 2), w1 = row(ya - 1), w2 = row(ya), w3 = row(ya + 1), w4 = row(ya + 2);
+  // lanes whose centre-row neighbours the next lanes hold
+  const bool left_ok = lane > 0 && full;
+  const bool right_ok = lane < 31 && x0 + 6 <= L.nx;
+  for (int y = ya; y < yb; ++y) {
+    const float4 ahead = y + 1 < yb ? row(y + 3) : w4;
+    const int n0 = y * L.pitch + x0;
+    uchar4 kind = make_uchar4(KIND_PAD, KIND_PAD, KIND_PAD, KIND_PAD);
+    float4 pp = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (live) {
+      kind = __ldg(reinterpret_cast<const uchar4*>(L.kind + n0));
+      pp = __ldg(reinterpret_cast<const float4*>(L.psip + n0));
+    }
+    const float lz = __shfl_up_sync(0xffffffffu, w2.z, 1), lw = __shfl_up_sync(0xffffffffu, w2.w, 1);
+    const float rx = __shfl_down_sync(0xffffffffu, w2.x, 1), ry = __shfl_down_sync(0xffffffffu, w2.y, 1);
+    const bool fl[4] = {kind.x == KIND_FLUID && x0 < L.nx, kind.y == KIND_FLUID && x0 + 1 < L.nx,
+                        kind.z == KIND_FLUID && x0 + 2 < L.nx, kind.w == KIND_FLUID && x0 + 3 < L.nx};
+    if (fl[0] || fl[1] || fl[2] || fl[3]) {
+      float c[8];   // the centre row, x0 - 2 .. x0 + 5
+      const int rb = y * L.pitch;
+      if (full) {
+        c[2] = w2.x; c[3] = w2.y; c[4] = w2.z; c[5] = w2.w;
+      } else {
+#pragma unroll
+        for (int j = 2; j < 6; ++j) c[j] = r[rb + wrap_x(L, x0 - 2 + j)];
+      }
+      if (left_ok) { c[0] = lz; c[1] = lw; }
+      else { c[0] = r[rb + wrap_x(L, x0 - 2)]; c[1] = r[rb + wrap_x(L, x0 - 1)]; }
+      if (right_ok && full) { c[6] = rx; c[7] = ry; }
+      else { c[6] = r[rb + wrap_x(L, x0 + 4)]; c[7] = r[rb + wrap_x(L, x0 + 5)]; }
+      const float up1[4] = {w3.x, w3.y, w3.z, w3.w}, dn1[4] = {w1.x, w1.y, w1.z, w1.w};
+      const float up2[4] = {w4.x, w4.y, w4.z, w4.w}, dn2[4] = {w0.x, w0.y, w0.z, w0.w};
+      const float ps[4] = {pp.x, pp.y, pp.z, pp.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (!fl[k]) continue;
+        const int i = k + 2;
+        const float lap = lap4_of(c[i], c[i + 1], c[i - 1], c[i + 2], c[i - 2], up1[k], dn1[k], up2[k], dn2[k]);
+        L.mu[n0 + k] = mu_of(L, ps[k], lap);
+      }
+    }
+    w0 = w1; w1 = w2; w2 = w3; w3 = w4; w4 = ahead;
+  }
+}
+
 // Pseudopotential force model: psi(rho) at fluid nodes, psi(rho_s) (1 + c_w) at the two solid
 // layers (rho_s from Eq. 15, c_w the wall factor of the node's body).  Pointwise, so it takes
 // V consecutive nodes of a row per thread with one 16-byte density load, like k_rho_vec.
@@ -785,7 +855,12 @@ template <typename real>
 static inline void launch_mu(const Lattice<real>& L, cudaStream_t s) {
   if (L.eos == EOS_NONE) return;
   if (L.pseudo) k_psi<real><<<rho_grid(L), NODE_BLOCK, 0, s>>>(L);
-  else if (L.psip) k_mu_vec<real><<<rho_grid(L), NODE_BLOCK, 0, s>>>(L);
+  else if (L.psip && L.mu_kernel == 2 && sizeof(real) == 4) {
+    if constexpr (sizeof(real) == 4) {
+      const unsigned gx = (unsigned)((L.nx + 4 * MU_BLOCK - 1) / (4 * MU_BLOCK));
+      k_mu_sweep<<<dim3(gx, (unsigned)((L.ny + MU_ROWS - 1) / MU_ROWS)), MU_BLOCK, 0, s>>>(L);
+    }
+  } else if (L.psip && L.mu_kernel != 0) k_mu_vec<real><<<rho_grid(L), NODE_BLOCK, 0, s>>>(L);
   else k_mu<real><<<node_grid(L), node_block(), 0, s>>>(L);
 }
 template <typename real>

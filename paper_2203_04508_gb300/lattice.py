@@ -213,6 +213,10 @@ class Lattice:
         """0: the plain collide kernel; 1: the TMA-pipelined one (FP32; the default where available)."""
         self._c(self.lib.lbm_set_collide_kernel(self.ctx, int(kind)))
 
+    def set_mu_kernel(self, kind: int):
+        """Chemical-potential pass: 0 per node, 1 row vectors, 2 row sweeps (FP32); same bits."""
+        self._c(self.lib.lbm_set_mu_kernel(self.ctx, int(kind)))
+
     def set_spin_limit(self, polls: int):
         """Polls before the pipelined kernel's waits give up (0: at once, to test that path)."""
         self._c(self.lib.lbm_set_spin_limit(self.ctx, int(polls)))
