@@ -190,6 +190,20 @@ lbm_status fail(lbm_ctx* c, lbm_status s, const char* fmt, ...) {
       return fail(ctx, LBM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));           \
   } while (0)
 
+// The chemical-potential pass by default: row sweeps (FP32) where their grid of 512-node strips
+// x 16-row sweeps fills the GPU four times over, else row vectors (a 512 x 512 lattice gives
+// the sweeps only 32 blocks).
+int default_mu_kernel(const lbm_ctx* c) {
+  if (c->fp64) return 1;
+  const long long blocks = (long long)((c->cfg.nx + 511) / 512) * ((c->cfg.ny + 15) / 16);
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    sms = 152;
+  }
+  return blocks >= 4LL * sms ? 2 : 1;
+}
+
 template <typename real>
 void fill_lattice(lbm_ctx* c, Lattice<real>& L) {
   const Layout& y = c->lay;
@@ -270,7 +284,7 @@ void fill_lattice(lbm_ctx* c, Lattice<real>& L) {
   L.scalars = (double*)(w + y.scalars);
   L.kerr = (unsigned int*)(w + y.kerr);
   L.spin_limit = c->spin_limit;
-  L.mu_kernel = c->mu_kind >= 0 ? c->mu_kind : (c->fp64 ? 1 : 2);
+  L.mu_kernel = c->mu_kind >= 0 ? c->mu_kind : default_mu_kernel(c);
   L.tma = nullptr;
   if constexpr (sizeof(real) == 4) {
     if (c->tma_ok && c->collide_kind == 1) L.tma = &c->tma;
