@@ -4,9 +4,10 @@
 //   k_rho_vec       density of every fluid node from the 9 offset populations   (Sec. 2.1),
 //                   and the pointwise part of Eq. 12, psi'(rho) (or psi, pseudopotential force)
 //   k_solid (x2)    densities of the first, then second solid layer             (Eq. 15)
-//   k_mu_vec        chemical potential at fluid nodes                            (Eq. 12)
-//                   (k_mu per node where psi' is not supplied; k_psi for the pseudopotential
-//                   force outside the overlapped step)
+//   k_mu_sweep      chemical potential at fluid nodes by row sweeps (large FP32  (Eq. 12)
+//                   lattices; k_mu_vec by row vectors otherwise, k_mu per node where psi' is
+//                   not supplied; k_psi for the pseudopotential force outside the overlapped
+//                   step)
 //   k_collide_tma / k_collide
 //                   force (Eq. 9) + collision (Eq. 4) + exact-difference forcing (Eq. 13)
 //                   + push streaming (Eq. 5) into the other lattice: TMA-pipelined persistent
