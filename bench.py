@@ -666,7 +666,7 @@ def main():
     # (queued, not waited for), fields back to the host at the end
     e2e = None
     if not args.no_e2e:
-        n_e2e = min(args.steps, 400)
+        n_e2e = args.steps                # the workload the device-timed value measures
         # the caller's page-locked host buffers, made before the clock starts
         dm = torch.empty(n_e2e, dtype=torch.float64, pin_memory=True)
         host = [torch.empty((sc.ny, sc.nx), dtype=torch.float32, pin_memory=True) for _ in range(3)]
