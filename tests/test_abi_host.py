@@ -105,6 +105,7 @@ def test_small_workspace_and_call_order(abi):
     assert lib.lbm_mass(ctx, C.byref(m), None, None) == abi.LBM_ESTATE
     assert lib.lbm_max_speed(ctx, C.byref(m)) == abi.LBM_ESTATE   # before lbm_init
     assert lib.lbm_set_spin_limit(ctx, 0) == abi.LBM_ESTATE       # before lbm_build_links
+    assert lib.lbm_set_mu_kernel(ctx, 1) == abi.LBM_ESTATE
     assert lib.lbm_max_speed(None, C.byref(m)) == abi.LBM_ESTATE
     lib.lbm_destroy(ctx)
 
