@@ -40,6 +40,23 @@ def test_library_exports_every_declared_symbol(abi):
         assert hasattr(lib, name), name
 
 
+def test_header_is_plain_c(abi):
+    """include/lbm.h is a C header (no C++ types or torch types): it compiles as C99 and as
+    C++, and every call it declares is bound with the same name in the Python binding."""
+    import shutil
+    import subprocess
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lbm.h")
+    for cc, lang, std in (("gcc", "c", "-std=c99"), ("g++", "c++", "-std=c++17")):
+        if shutil.which(cc) is None:
+            pytest.skip(f"{cc} not found")
+        r = subprocess.run([cc, "-fsyntax-only", "-x", lang, std, "-Wall", "-Wextra", "-Werror", hdr],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+    bound = set(abi._SIGS)
+    missing = [n for n in abi.declared_symbols() if n not in bound]
+    assert not missing, missing
+
+
 def test_workspace_and_eos_match_the_oracle(abi):
     import oracle as O
     for sc in (S.c1_plain_fp64(), S.small_parity(), S.c3_impact(256, 512)):
