@@ -1,7 +1,8 @@
 """The three chemical-potential passes (Eq. 12; lbm_set_mu_kernel) -- one node a thread, row
 vectors, row sweeps -- give the same bits: populations after a run on walled and periodic
-lattices, ragged sizes (partial vectors, partial sweeps, lanes at warp and lattice edges) and the
-large impact lattice with the TMA-pipelined collide."""
+lattices, ragged sizes (partial vectors, partial sweeps, lanes at warp and lattice edges),
+lattices narrower than two vectors, and the large impact lattice with the TMA-pipelined
+collide."""
 from __future__ import annotations
 
 import numpy as np
@@ -29,6 +30,11 @@ CASES = {
     "periodic_multiple_of_4": lambda: S.Scenario(name="p4", nx=64, ny=40, walls=0, T_over_Tc=0.7,
                                                  x0=[31.0], y0=[20.5], r0=[9.0]),
     "impact": lambda: S.c3_impact(1024, 2048),
+    # narrower than two vectors: every lane's outer neighbours wrap around the lattice
+    "tiny_periodic": lambda: S.Scenario(name="t", nx=6, ny=9, walls=0, T_over_Tc=0.9, x0=[2.7], y0=[4.4],
+                                        r0=[2.0]),
+    "smallest_walled": lambda: S.Scenario(name="w", nx=5, ny=21, walls=1, T_over_Tc=0.9, x0=[2.5], y0=[10.3],
+                                          r0=[2.0]),
 }
 
 
