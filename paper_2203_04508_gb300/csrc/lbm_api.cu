@@ -135,7 +135,8 @@ struct lbm_ctx {
   Lattice<float> Lf{};
   Lattice<double> Ld{};
   double mass0 = 0;
-  cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};   // step graphs: 2 steps, 1 step (x parity)
+  // step graphs (x lattice parity): 2 steps, 1 step, STEPS_LONG steps
+  cudaGraphExec_t graph[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   // FP32: TMA descriptors of the pipelined collide kernel (set up by lbm_build_links) and the
   // collide kernel in use (0 plain, 1 TMA-pipelined)
   CollideTma tma{};
@@ -355,6 +356,10 @@ void step_lattices(const lbm_ctx* c, const Lattice<real>& L, int cur, Lattice<re
   if (c->cfg.force_model == LBM_FORCE_PSEUDO) Ln.mu = (real*)(c->ws + (cur ? c->lay.mu : c->lay.mu2));
 }
 
+// Steps in the longest step graph (even, so that a launch keeps the lattice parity): fewer
+// graph launches, and so fewer gaps between them, for long runs.
+constexpr int STEPS_LONG = 8;
+
 template <typename real>
 lbm_status do_step(lbm_ctx* c, const Lattice<real>& L, long long n) {
   if (n <= 0) return LBM_OK;
@@ -371,9 +376,10 @@ lbm_status do_step(lbm_ctx* c, const Lattice<real>& L, long long n) {
     CUDA_OK(c, launch_phase(Lt, c->cur, 1, c->stream));
     c->rho_ok = true;
   }
-  // graphs of two steps (slot p) and of one step (slot 2 + p) from lattice parity p
+  // graphs of two steps (slot p), one step (slot 2 + p) and STEPS_LONG steps (slot 4 + p) from
+  // lattice parity p
   auto graph_of = [&](int p, int steps, cudaGraphExec_t* out) -> lbm_status {
-    cudaGraphExec_t& slot = c->graph[(steps == 2 ? 0 : 2) + p];
+    cudaGraphExec_t& slot = c->graph[(steps == 2 ? 0 : steps == 1 ? 2 : 4) + p];
     if (!slot) {
       cudaGraph_t g;
       CUDA_OK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
@@ -392,6 +398,13 @@ lbm_status do_step(lbm_ctx* c, const Lattice<real>& L, long long n) {
     *out = slot;
     return LBM_OK;
   };
+  if (n >= STEPS_LONG && c->stream != nullptr) {
+    cudaGraphExec_t gl;
+    lbm_status st = graph_of(c->cur, STEPS_LONG, &gl);
+    if (st != LBM_OK) return st;
+    for (long long k = 0; k < n / STEPS_LONG; ++k) CUDA_OK(c, cudaGraphLaunch(gl, c->stream));
+    n -= STEPS_LONG * (n / STEPS_LONG);
+  }
   if (n >= 2 && c->stream != nullptr) {
     cudaGraphExec_t g2;
     lbm_status st = graph_of(c->cur, 2, &g2);
