@@ -129,7 +129,7 @@ def run_batched(G, torch, rank, world, steps, small=False):
     for sc in scs:
         lat = G.Lattice(sc.physics(), precision=G.LBM_FP32)
         lat.init_droplets(sc.droplets())
-        lat.step(2)
+        lat.step(10)                     # warm-up: captures the eight- and two-step graphs
         lats.append(lat)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
