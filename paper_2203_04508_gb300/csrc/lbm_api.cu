@@ -700,7 +700,7 @@ lbm_status lbm_set_collide_kernel(lbm_ctx* c, int32_t kind) {
   if (!c || !c->built) return LBM_ESTATE;
   if (kind != 0 && kind != 1) return fail(c, LBM_EINVAL, "collide kernel must be 0 (plain) or 1 (TMA-pipelined)");
   if (kind == 1 && (c->fp64 || !c->tma_ok))
-    return fail(c, LBM_EINVAL, "the TMA-pipelined collide kernel needs FP32 and the driver's tensor-map encoder");
+    return fail(c, LBM_EINVAL, "the TMA-pipelined collide kernel needs FP32 and the CUDA driver's tensor-map encoder");
   if (kind == c->collide_kind) return LBM_OK;
   c->collide_kind = kind;
   // captured launches carry the old kernel: capture again

@@ -1,7 +1,7 @@
 // Internal declarations shared by the library's translation units (not part of the ABI).
 #pragma once
 #include <cstdint>
-#include <cuda.h>            // CUtensorMap (the type; the encoder is taken from the driver at run time)
+#include <cuda.h>            // CUtensorMap (the type; the encoder is taken from the CUDA driver at run time)
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>   // header-only; a no-op unless a profiler attaches
 
@@ -57,7 +57,7 @@ struct CollideTma {
   int blocks[2];                // persistent grid of the chemical-potential / psi variant
 };
 // Encodes the descriptors for L (whose planes must not move afterwards) and sizes the grids;
-// false, with a message, when the driver cannot.
+// false, with a message, when the CUDA driver cannot.
 bool collide_tma_setup(CollideTma* T, const Lattice<float>& L, const void* rho0, const void* rho1, const void* mu1,
                        char* err);
 

@@ -917,7 +917,7 @@ bool collide_tma_setup(CollideTma* T, const Lattice<float>& L, const void* rho0,
                        char* err) {
   EncodeTiledFn enc = encode_tiled();
   if (!enc) {
-    std::snprintf(err, 256, "the driver's tensor-map encoder is not available");
+    std::snprintf(err, 256, "the CUDA driver's tensor-map encoder is not available");
     return false;
   }
   const cuuint32_t unit[3] = {1, 1, 1};
