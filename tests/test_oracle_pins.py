@@ -499,3 +499,35 @@ def test_surface_tension_obeys_laplace_and_the_flat_interface_balance():
     edm = np.sum((F ** 2 / (4 * r))[half])
     assert edm > 2 * korteweg                       # the forcing's share dominates here
     assert korteweg + edm == pytest.approx(tab["sigma"], rel=0.02)
+
+
+@pytest.mark.parametrize("k", [0.0, 0.25])
+def test_chemical_potential_and_force_of_a_cosine_density(k):
+    """Eq. 12 and Eq. 9 on a periodic cosine density rho = rho0 + A cos(theta), where the
+    fourth-order stencils have exact Fourier symbols: the Laplacian multiplies cos(theta) by
+    L = sum over the axes of (32 cos k - 2 cos 2k - 30) / 12, and the first derivative turns it
+    into -sin(theta) G with G = (8 sin k - sin 2k) / 6.  So mu = k^2 psi'(rho) - kappa A L
+    cos(theta) (psi' from the EOS), and with k = 0, where mu is itself a cosine, the force is
+    F = -rho kappa A L G sin(theta) - c_s^2 A G sin(theta) per axis.  A wrong sign, weight or
+    reach in either stencil, or the kappa term entering with the wrong sign, fails."""
+    kappa = 0.05
+    cfg = OracleConfig(nx=24, ny=20, walls=0, eos=O.EOS_CS, T_over_Tc=0.7, k=k, kappa=kappa, coll=O.COLL_BGK,
+                       tau=1.0)
+    kx, ky = 2 * np.pi * 2 / cfg.nx, 2 * np.pi * 3 / cfg.ny
+    X, Y = np.meshgrid(np.arange(cfg.nx), np.arange(cfg.ny))
+    theta = kx * X + ky * Y
+    rho0, A = 0.2, 0.01
+    rho = rho0 + A * np.cos(theta)
+    o = Oracle(cfg)
+    o.set_state(rho.ravel(), np.zeros(rho.size), np.zeros(rho.size))
+    o.fields()
+    mu, fx, fy = o.mu_force()
+    L = sum(32 * np.cos(q) - 2 * np.cos(2 * q) - 30 for q in (kx, ky)) / 12
+    _, psip, _ = O.eos_eval(cfg, rho.ravel())
+    mu_ex = k * k * psip.reshape(rho.shape) - kappa * A * L * np.cos(theta)
+    assert np.abs(mu - mu_ex).max() <= 1e-12 * max(1.0, np.abs(mu_ex).max())
+    if k == 0.0:
+        for f, q in ((fx, kx), (fy, ky)):
+            G = (8 * np.sin(q) - np.sin(2 * q)) / 6
+            f_ex = -rho * kappa * A * L * G * np.sin(theta) - A * G * np.sin(theta) / 3.0
+            assert np.abs(f - f_ex).max() < 1e-15, np.abs(f - f_ex).max()
