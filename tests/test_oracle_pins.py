@@ -531,3 +531,36 @@ def test_chemical_potential_and_force_of_a_cosine_density(k):
             G = (8 * np.sin(q) - np.sin(2 * q)) / 6
             f_ex = -rho * kappa * A * L * G * np.sin(theta) - A * G * np.sin(theta) / 3.0
             assert np.abs(f - f_ex).max() < 1e-15, np.abs(f - f_ex).max()
+
+
+def test_solid_layer_densities_of_a_cosine_row_profile():
+    """Eq. 15 between flat walls (rows 0, 1 and ny-2, ny-1 solid), seen through Eq. 12 at the
+    first fluid rows, whose fourth-order Laplacian reaches two rows into the wall.  For
+    rho = a + c cos(k x) on every fluid row, the first layer averages the three fluid nodes above
+    it with weights 1/36, 1/9, 1/36, so it holds a + c phi cos(k x), phi = (2 + cos k) / 3, and the
+    second layer averages the first the same way: a + c phi^2 cos(k x).  With k = 0 in Eq. 12
+    (mu = -kappa lap rho), mu / (-kappa c cos(k x)) is S_x = (32 cos k - 2 cos 2k - 30) / 12
+    in the bulk, S_x + (1 - phi) / 12 one row further from the wall than the first fluid row,
+    and S_x + (16 phi - phi^2 - 15) / 12 on it.  Other weights, or a second layer averaging the
+    fluid, give another phi."""
+    kappa, nx, ny = 0.05, 24, 20
+    cfg = OracleConfig(nx=nx, ny=ny, walls=1, eos=O.EOS_CS, T_over_Tc=0.7, k=0.0, kappa=kappa, coll=O.COLL_BGK,
+                       tau=1.0)
+    kx = 2 * np.pi * 3 / nx
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    a, c = 0.2, 0.01
+    rho = a + c * np.cos(kx * X)
+    o = Oracle(cfg)
+    kind, _ = o.kind()
+    assert np.all(kind[[0, 1, ny - 2, ny - 1], :] != 0) and np.all(kind[2:ny - 2, :] == 0)
+    o.set_state(rho.ravel(), np.zeros(rho.size), np.zeros(rho.size))
+    o.fields()
+    mu = o.mu_force()[0]
+    phi = (2 + np.cos(kx)) / 3
+    Sx = (32 * np.cos(kx) - 2 * np.cos(2 * kx) - 30) / 12
+    shape = np.full(ny, Sx)
+    shape[[2, ny - 3]] = Sx + (16 * phi - phi ** 2 - 15) / 12
+    shape[[3, ny - 4]] = Sx + (1 - phi) / 12
+    ex = -kappa * c * np.cos(kx * X) * shape[:, None]
+    fluid = kind == 0
+    assert np.abs(mu[fluid] - ex[fluid]).max() < 1e-15, np.abs(mu[fluid] - ex[fluid]).max()
