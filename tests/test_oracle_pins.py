@@ -289,6 +289,112 @@ def test_boundary_rule_is_continuous_at_half_and_bounce_back_there():
     assert O.link_value(O.BC_PRESENT, 0.2, a, b2, 0, c, F) == a
 
 
+# Distinct a = f~_i(x1), b2 = f~_i(x2), c = f~_ibar(x1), F = F_i(x1), and the link values
+# worked out by hand.  Eq. 17 (q >= 1/2): a/(2q) + (2q-1)/(2q) c + (2q-1)/(2q) F, i.e. the
+# weights (1/(2q), (2q-1)/(2q)) are (5/6, 1/6) at q = 0.6, (2/3, 1/3) at 0.75, (1/2, 1/2) at 1.
+# Eq. 16 (q < 1/2): 2q a + (1-2q) b2 + (1-2q) F.  MIBC and IBC drop the F term (Sec. 3.2).
+_A, _B2, _C, _F = 0.12, 0.05, 0.03, 0.006
+_EQ16_17_BY_HAND = [
+    # q,    present,                         MIBC / IBC
+    (0.6,  0.1 + 0.005 + 0.001,              0.1 + 0.005),
+    (0.75, 0.08 + 0.01 + 0.002,              0.08 + 0.01),
+    (1.0,  0.06 + 0.015 + 0.003,             0.06 + 0.015),
+    (0.25, 0.06 + 0.025 + 0.003,             0.06 + 0.025),
+    (0.1,  0.024 + 0.04 + 0.0048,            0.024 + 0.04),
+]
+
+
+@pytest.mark.parametrize("q,present,mibc", _EQ16_17_BY_HAND)
+def test_link_rule_values_by_hand(q, present, mibc):
+    """Eqs. 16 and 17 on one link with distinct inputs: the F_i term enters with weight
+    (1-2q) below one half and (2q-1)/(2q) above it, and only in the present scheme."""
+    assert O.link_value(O.BC_PRESENT, q, _A, _B2, 1, _C, _F) == pytest.approx(present, abs=1e-15)
+    for bc in (O.BC_MIBC, O.BC_IBC):
+        assert O.link_value(bc, q, _A, _B2, 1, _C, _F) == pytest.approx(mibc, abs=1e-15)
+    assert O.link_value(O.BC_HBB, q, _A, _B2, 1, _C, _F) == _A
+
+
+# Whole-step toy for the wiring of Eqs. 16-18 inside a step.  Ideal gas (no nonideal force),
+# uniform rho = 1, u = 0, gravity g = (0, -0.01): the force is F = rho g = (0, -0.01) at every
+# fluid node and the initial populations are f_eq(1, 0) = w_i, so any collision leaves
+# f~_i = w_i + F_i with the exact-difference term of Eq. 13
+#     F_i = f_eq(1, g) - f_eq(1, 0) = w_i [3 e_iy g_y + 4.5 (e_iy g_y)^2 - 1.5 g_y^2],
+# i.e. f~_i = w_i * 1.0303 for e_iy = -1, w_i * 0.9703 for e_iy = +1, w_i * 0.99985 for e_iy = 0,
+# and F_i = w_i * 0.0303, w_i * -0.0297, w_i * -0.00015.  The wall links of the bottom row
+# (directions with e_iy = -1, w_i = 1/9, 1/36, 1/36) and of the top row (e_iy = +1) are then
+# known in closed form.
+_TOY_F = {-1: 0.0303, 1: -0.0297, 0: -0.00015}          # F_i / w_i by e_iy
+_TOY_FT = {k: 1.0 + v for k, v in _TOY_F.items()}      # f~_i / w_i by e_iy
+
+
+def _toy_after_one_step(yb, yt, bc, coll, ny=10, nx=5):
+    o = Oracle(OracleConfig(nx=nx, ny=ny, walls=1, y_bottom=yb, y_top=yt, eos=O.EOS_NONE,
+                            coll=coll, tau=0.7, gx=0.0, gy=-0.01, bc=bc))
+    o.set_state(np.ones(nx * ny), np.zeros(nx * ny), np.zeros(nx * ny))
+    o.step(1)
+    return o.populations(), o.dM_history()
+
+
+# (y_b, y_t, q of the bottom row, q of the top row, f_ibar(x1, t+1) / w_ibar by hand at the
+#  bottom (e_iy = -1 links) and at the top (e_iy = +1 links), present scheme)
+#  bottom q = 0.75: (2/3)(1.0303) + (1/3)(0.9703) + (1/3)(0.0303)   = 1.0204
+#  top    q = 0.6:  (5/6)(0.9703)  + (1/6)(1.0303) + (1/6)(-0.0297)  = 0.97535
+#  bottom q = 1.0:  (1/2)(1.0303)  + (1/2)(0.9703) + (1/2)(0.0303)   = 1.01545
+#  top    q = 1.0:  (1/2)(0.9703)  + (1/2)(1.0303) + (1/2)(-0.0297)  = 0.98545
+#  bottom q = 0.25 (Eq. 16, x2 fluid and equal to x1): 1.0303 + (1/2)(0.0303) = 1.04545
+#  top    q = 0.3  (Eq. 16): 0.9703 + (0.4)(-0.0297) = 0.95842
+_TOY_CASES = [
+    (1.25, 10 - 2.4, 1.0204, 0.97535),
+    (1.0, 10 - 2.0, 1.01545, 0.98545),
+    (1.75, 10 - 2.7, 1.04545, 0.95842),
+]
+
+
+@pytest.mark.parametrize("coll", [O.COLL_BGK, O.COLL_MRT])
+@pytest.mark.parametrize("yb,yt,bottom,top", _TOY_CASES)
+def test_boundary_step_of_a_uniform_gravity_toy_by_hand(yb, yt, bottom, top, coll):
+    """One whole step of the toy: every wall-row population that the boundary rule writes,
+    and the rest population that Eq. 18 corrects, equal the closed-form values above."""
+    ny, nx = 10, 5
+    ex, ey, w, opp = O.lattice()
+    f, dM = _toy_after_one_step(yb, yt, O.BC_PRESENT, coll)
+    yb_row = 2
+    yt_row = ny - 3   # every case puts the top wall between rows 7 and 8
+    for i in range(9):
+        # populations coming back from the bottom wall point up, from the top wall down
+        if ey[i] == 1:
+            assert np.allclose(f[i, yb_row, :], w[i] * bottom, rtol=0, atol=1e-15)
+        if ey[i] == -1:
+            assert np.allclose(f[i, yt_row, :], w[i] * top, rtol=0, atol=1e-15)
+    # Eq. 18 at a wall node: f0 = f~_0 + sum over its three links of (f~_i - f_ibar(t+1)); the
+    # three links carry w = 1/9 + 1/36 + 1/36 = 1/6 of the per-unit differences
+    f0_bottom = (4 / 9) * _TOY_FT[0] + (1 / 6) * (_TOY_FT[-1] - bottom)
+    f0_top = (4 / 9) * _TOY_FT[0] + (1 / 6) * (_TOY_FT[1] - top)
+    assert np.allclose(f[0, yb_row, :], f0_bottom, rtol=0, atol=1e-15)
+    assert np.allclose(f[0, yt_row, :], f0_top, rtol=0, atol=1e-15)
+    assert dM[0] == pytest.approx(nx * ((1 / 6) * (_TOY_FT[-1] - bottom) + (1 / 6) * (_TOY_FT[1] - top)),
+                                  abs=1e-14)
+    # nodes away from the walls only stream: they keep f~ = w_i (1 + F_i / w_i)
+    for i in range(9):
+        assert np.allclose(f[i, 3:yt_row, :], w[i] * _TOY_FT[int(ey[i])], rtol=0, atol=1e-15)
+
+
+def test_boundary_step_toy_without_the_nonideal_term():
+    """The same toy under MIBC and IBC: Eq. 17 without F_i at q = 0.75 gives
+    (2/3)(1.0303) + (1/3)(0.9703) = 1.0103 at the bottom; MIBC compensates by Eq. 18, IBC not."""
+    _, ey, w, _ = O.lattice()
+    f_m, dM_m = _toy_after_one_step(1.25, 10 - 2.4, O.BC_MIBC, O.COLL_BGK)
+    f_i, dM_i = _toy_after_one_step(1.25, 10 - 2.4, O.BC_IBC, O.COLL_BGK)
+    for i in range(9):
+        if ey[i] == 1:
+            assert np.allclose(f_m[i, 2, :], w[i] * 1.0103, rtol=0, atol=1e-15)
+            assert np.allclose(f_i[i, 2, :], w[i] * 1.0103, rtol=0, atol=1e-15)
+    assert np.allclose(f_m[0, 2, :], (4 / 9) * _TOY_FT[0] + (1 / 6) * (_TOY_FT[-1] - 1.0103),
+                       rtol=0, atol=1e-15)
+    assert np.allclose(f_i[0, 2, :], (4 / 9) * _TOY_FT[0], rtol=0, atol=1e-15)
+    assert np.all(dM_i == 0)
+
+
 # ----------------------------------------------------------------------------- whole steps
 def _drop_on_flat(bc, yb, dmu, nx=96, ny=48, r0=18.0):
     o = Oracle(_flat(nx=nx, ny=ny, yb=yb, yt=ny - 2.5, bc=bc, T_over_Tc=0.7, coll=O.COLL_MRT,
