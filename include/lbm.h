@@ -419,10 +419,11 @@ void lbm_batch_destroy(lbm_batch* b);
  *          order), and the number of non-finite values.  The call synchronises the stream.
  *
  * Scratch: a fixed 16.6 kB array in the library's own device memory (a static __device__
- * variable, present on every GPU the library is loaded on until the process exits), looked up
- * with cudaGetSymbolAddress by the first call on each device -- make that first call before
- * any stream capture.  Every call reuses the array; calls whose kernels overlap on the GPU
- * race on it and must be serialised by the caller. */
+ * variable, present on every GPU the library is loaded on until the process exits), whose
+ * device address every call looks up with cudaGetSymbolAddress on the current device, so the
+ * call stays valid after the device's context has been reset and created again.  Every call
+ * reuses the array; calls whose kernels overlap on the GPU race on it and must be serialised
+ * by the caller. */
 #define LBM_NOALLOC_MAX_NODES (1LL << 30)
 lbm_status lbm_mass_noalloc(const void* f, const uint8_t* kind, int64_t n_nodes, int32_t precision,
                             void* stream, double* out2);

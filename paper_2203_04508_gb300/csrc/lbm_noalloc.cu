@@ -13,7 +13,6 @@
 // the GPU (different streams, or different host threads) race on it and must be serialised
 // by the caller.
 #include <cstdio>
-#include <mutex>
 
 #include "../../include/lbm.h"
 #include "lbm_device.cuh"
@@ -31,10 +30,6 @@ constexpr int NA_PARTIALS = 32;
 constexpr int NA_DOUBLES = NA_PARTIALS + 2 * NA_MAX_BLOCKS;   // 16,640 bytes
 
 static __device__ __align__(256) double g_noalloc_scratch[NA_DOUBLES];
-
-constexpr int NA_MAX_DEVICES = 64;
-std::mutex g_setup_mutex;
-double* g_scratch_ptr[NA_MAX_DEVICES] = {nullptr};
 
 __device__ __forceinline__ double na_block_sum(double v, double* smem) {
 #pragma unroll
@@ -100,20 +95,14 @@ __global__ void __launch_bounds__(NA_BLOCK) k_mass_noalloc(const real* __restric
   }
 }
 
-// Device address of the scratch array on the current device, looked up once per device.
+// Device address of the scratch array in the current device's context.  It is looked up on
+// every call rather than cached: a context that was torn down (cudaDeviceReset) and created
+// again reloads the module, and an address kept from the old context would no longer be valid.
 cudaError_t scratch_on_current_device(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 

@@ -27,14 +27,23 @@ def _built():
     build.build()
 
 
+def _case(name):
+    if name == "small":
+        return S.small_parity()
+    # 1024 x 512 = 524,288 nodes: twice the nodes the audit's capped grid of 1024 blocks of 256
+    # threads covers in one pass, so every thread sums two strided chunks
+    return S.c2_fp32_single(nx=1024, ny=512, n_cyl=4)
+
+
+@pytest.mark.parametrize("case", ["small", "1024x512"])
 @pytest.mark.parametrize("fp64", [False, True])
-def test_noalloc_mass_matches_lbm_mass_twice(fp64):
+def test_noalloc_mass_matches_lbm_mass_twice(case, fp64):
     import torch
     from paper_2203_04508_gb300 import _abi
     lib = _abi.load()
-    sc = S.small_parity(fp64=fp64)
+    sc = _case(case)
     lat = make_lattice(sc, fp64=fp64)
-    lat.step(50)
+    lat.step(50 if case == "small" else 20)
     M_ref, _, _ = lat.mass()
     n = sc.nx * sc.ny
     dtype = torch.float64 if fp64 else torch.float32
