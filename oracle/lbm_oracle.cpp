@@ -245,6 +245,17 @@ int orc_get_f(void* p, double* f, double* f_im) {
   });
 }
 
+// Overwrite the populations of a double instance (9 planes of nx*ny values, the layout of
+// orc_get_f); the step count, the initial mass and the history are kept.  Used by tests that
+// perturb the state between steps, e.g. to round it to a storage precision.
+int orc_set_f(void* p, const double* f) {
+  return guarded([&] {
+    if (H(p)->mode != 0) throw std::runtime_error("set_f: double instances only");
+    auto& s = *H(p)->d;
+    std::memcpy(s.f.data(), f, sizeof(double) * s.f.size());
+  });
+}
+
 int orc_get_fields(void* p, double* rho, double* vx, double* vy) {
   return guarded([&] {
     if (H(p)->mode == 0) {

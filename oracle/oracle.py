@@ -65,6 +65,7 @@ def _load():
         "orc_get_links": (I, [P, ip, ip, dp, ip, ip]),
         "orc_get_kind": (I, [P, u8p, ip]),
         "orc_get_f": (I, [P, dp, dp]),
+        "orc_set_f": (I, [P, dp]),
         "orc_get_fields": (I, [P, dp, dp, dp]),
         "orc_get_mu_force": (I, [P, dp, dp, dp]),
         "orc_mass": (D, [P]),
@@ -232,6 +233,12 @@ class Oracle:
         _check(self._lib.orc_get_f(self._h, _dptr(f), _dptr(fi) if imag else None))
         f = f.reshape(9, self.ny, self.nx)
         return (f, fi.reshape(9, self.ny, self.nx)) if imag else f
+
+    def set_populations(self, f):
+        """Overwrite the populations (shape (9, ny, nx)); step count and M0 are kept."""
+        a = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(-1))
+        assert a.size == 9 * self.nx * self.ny
+        _check(self._lib.orc_set_f(self._h, _dptr(a)))
 
     def fields(self):
         n = self.nx * self.ny

@@ -91,6 +91,7 @@ struct Lattice {
                                 // (FP32), null for the plain kernel
 };
 
+
 template <typename real>
 __device__ __forceinline__ int wrap_x(const Lattice<real>& L, int x) {
   return x < 0 ? x + L.nx : (x >= L.nx ? x - L.nx : x);
@@ -198,6 +199,18 @@ __device__ __forceinline__ Stencil stencil_at(const Lattice<real>& L, int x, int
   return s;
 }
 
+// Undivided fourth-order differences D(p) = 8 (p_1 - p_-1) - (p_2 - p_-2) = 12 dp/dx along
+// each axis (8 x exact, so fused or not it rounds the same).
+template <typename real>
+__device__ __forceinline__ real diff4_of(real p1, real pm1, real p2, real pm2) {
+  return real(8) * (p1 - pm1) - (p2 - pm2);
+}
+template <typename real>
+__device__ __forceinline__ void diff4(const real* __restrict__ p, const Stencil& s, real& dx, real& dy) {
+  dx = diff4_of(__ldg(p + s.xp1), __ldg(p + s.xm1), __ldg(p + s.xp2), __ldg(p + s.xm2));
+  dy = diff4_of(__ldg(p + s.yp1), __ldg(p + s.ym1), __ldg(p + s.yp2), __ldg(p + s.ym2));
+}
+
 template <typename real>
 __device__ __forceinline__ void grad4(const real* __restrict__ p, const Stencil& s, real& gx, real& gy) {
   const real c = real(1.0 / 12.0);
@@ -227,11 +240,29 @@ template <typename real>
 __device__ __forceinline__ real mu_of(const Lattice<real>& L, real psip, real lap) {
   return fma_rn(L.k2, psip, -mul_rn(L.kappa, lap));
 }
-// F = rho g - rho grad(mu) + c_s^2 grad(rho) (Eq. 9), one component: the two gradient terms,
-// which nearly cancel inside a bulk phase, enter by fused multiply-adds (each product exact)
+// delta rho / 36 to within an ulp: the product with the rounded reciprocal, corrected once
+// with its FMA residual
+__device__ __forceinline__ float div36(float d) {
+  const float c = 1.0f / 36.0f;
+  const float q = d * c;
+  return fmaf(fmaf(-36.0f, q, d), c, q);
+}
+__device__ __forceinline__ double div36(double d) { return d / 36.0; }
+
+// F = rho g - rho grad(mu) + c_s^2 grad(rho) (Eq. 9), one component, from the undivided
+// differences D(mu) and D(rho) of diff4 (grad = D/12, c_s^2 = 1/3):
+//   F = [D(rho) - 3 rho D(mu)] / 36 + rho g.
+// Inside an interface the two terms are large and nearly cancel.  The product rho D(mu) enters
+// the difference exactly (with its FMA residual), and the division by 36 is corrected to
+// within an ulp: no rounded constant (1/12, 1/3) scales either term, because such a constant
+// biases the force the same way at every node and step, and that bias builds up in the flow
+// where unbiased rounding errors do not.
 template <typename real>
-__device__ __forceinline__ real force_cp(real r, real g, real gmu, real grho) {
-  return fma_rn(-r, gmu, fma_rn(real(1.0 / 3.0), grho, mul_rn(r, g)));
+__device__ __forceinline__ real force_cp(real r, real g, real dmu, real drho) {
+  const real p = mul_rn(r, dmu);
+  const real e = fma_rn(r, dmu, -p);
+  const real G = fma_rn(real(-3), e, fma_rn(real(-3), p, drho));
+  return fma_rn(r, g, div36(G));
 }
 // F = rho g + c a, the pseudopotential force of centre value c and sum a, one component
 template <typename real>
@@ -289,11 +320,11 @@ __device__ __forceinline__ void force_at(const Lattice<real>& L, int x, int y, r
   }
   {
     Stencil s = stencil_at(L, x, y);
-    real gmx, gmy, grx, gry;
-    grad4(L.mu, s, gmx, gmy);
-    grad4(L.rho, s, grx, gry);
-    Fx = force_cp(r, L.gx, gmx, grx);
-    Fy = force_cp(r, L.gy, gmy, gry);
+    real dmx, dmy, drx, dry;
+    diff4(L.mu, s, dmx, dmy);
+    diff4(L.rho, s, drx, dry);
+    Fx = force_cp(r, L.gx, dmx, drx);
+    Fy = force_cp(r, L.gy, dmy, dry);
   }
 }
 
@@ -331,15 +362,6 @@ __device__ __forceinline__ real density_of(const Lattice<real>& L, const real (&
   return L.rho_ref + density_sum(f);
 }
 
-// delta rho / 36 to within an ulp: the product with the rounded reciprocal, corrected once
-// with its FMA residual
-__device__ __forceinline__ float div36(float d) {
-  const float c = 1.0f / 36.0f;
-  const float q = d * c;
-  return fmaf(fmaf(-36.0f, q, d), c, q);
-}
-__device__ __forceinline__ double div36(double d) { return d / 36.0; }
-
 // Collision (Eq. 4) of offset populations with the exact-difference term (Eq. 13).
 //   MRT: f~ = f - M^-1 S (m - m_eq) + F_i,  M of Eq. 2, S of Eq. 3, m_eq listed under Eq. 1
 //        (q_y^eq = -j_y), all offset by the moments of w_i rho_ref (= m_eq(rho_ref, 0));
@@ -350,31 +372,50 @@ __device__ __forceinline__ double div36(double d) { return d / 36.0; }
 // M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4); the conserved moments
 // drop out.  FP32: the large part of f^eq, w_i delta rho, is formed as {16, 4, 1} x
 // (delta rho / 36) -- exact multiples of one quotient, so the weights sum to one exactly and
-// no mass bias arises -- and the small terms are added before the final rounding.
+// no mass bias arises -- and the small terms are added before the final rounding.  The odd
+// part of f^eq, w_i rho 3 e_i.u, is formed from the momentum J = rho u itself (odd_split), not
+// from rho/9 and rho/36 times u = J/rho: the rounded constants and 1/rho would scale the
+// momentum the collision passes on by a fixed factor every step, and at a steady state such a
+// bias builds up where unbiased rounding does not.
+template <typename real>
+__device__ __forceinline__ void odd_split(real Jx, real Jy, real& px, real& py, real& pd, real& pa) {
+  // w_i rho 3 e_i.u for e = (1,1) and (-1,1) is (Jx + Jy)/12 and (Jy - Jx)/12; the axis terms
+  // take what is left of J/2, so that the first moment of the odd parts is J up to rounding of
+  // the sums, whatever the rounding of 1/12
+  pd = mul_rn(Jx + Jy, real(1.0 / 12.0));
+  pa = mul_rn(Jy - Jx, real(1.0 / 12.0));
+  px = fma_rn(real(0.5), Jx, pa - pd);
+  py = fma_rn(real(0.5), Jy, -(pd + pa));
+}
+
+// Every product that meets a sum below is rounded explicitly (mul_rn / fma_rn) or is exact (a
+// power of two), so that no kernel's compiler can fuse it differently: all kernels that collide
+// a node get the same bits.
 template <typename real>
 __device__ __forceinline__ void collide_node(const Lattice<real>& L, real (&f)[9], real r, real drho,
                                              real jx, real jy, real Fx, real Fy) {
   const real inv_r = real(1) / r;
-  const real ux = jx * inv_r, uy = jy * inv_r;
-  const real vx = ux + Fx * inv_r, vy = uy + Fy * inv_r;
+  const real ux = mul_rn(jx, inv_r), uy = mul_rn(jy, inv_r);
+  const real vx = fma_rn(Fx, inv_r, ux), vy = fma_rn(Fy, inv_r, uy);
   const real q36 = div36(drho);
   real neq[9];
   if (L.coll == COLL_MRT) {
     const real s13 = f[1] + f[3], s24 = f[2] + f[4], s57 = f[5] + f[7], s68 = f[6] + f[8];
     const real s1234 = s13 + s24, s5678 = s57 + s68;
     const real d13 = f[1] - f[3], d24 = f[2] - f[4];
-    const real j2r = (jx * jx + jy * jy) * inv_r;
+    const real j2r = mul_rn(fma_rn(jx, jx, mul_rn(jy, jy)), inv_r);
+    const real j3 = fma_rn(real(-3), j2r, real(2) * drho);            // 2 drho - 3 j^2/rho
     // non-equilibrium moments, scaled by 1 - s_k
-    const real e = ((real(-4) * f[0] - s1234 + real(2) * s5678) + (real(2) * drho - real(3) * j2r)) * (real(1) - L.s_e);
-    const real eps = ((real(4) * f[0] - real(2) * s1234 + s5678) - (drho - real(3) * j2r)) * (real(1) - L.s_eps);
-    const real qx = ((jx - real(3) * d13) + jx) * (real(1) - L.s_q);
-    const real qy = ((jy - real(3) * d24) + jy) * (real(1) - L.s_q);
-    const real pxx = ((s13 - s24) - (jx * jx - jy * jy) * inv_r) * (real(1) - L.s_nu);
-    const real pxy = ((s57 - s68) - jx * jy * inv_r) * (real(1) - L.s_nu);
-    const real e36 = e * real(1.0 / 36.0), e18 = e * real(1.0 / 18.0);
-    const real s36 = eps * real(1.0 / 36.0), s18 = eps * real(1.0 / 18.0);
-    const real qx6 = qx * real(1.0 / 6.0), qy6 = qy * real(1.0 / 6.0);
-    const real qx12 = qx * real(1.0 / 12.0), qy12 = qy * real(1.0 / 12.0);
+    const real e = mul_rn((real(-4) * f[0] - s1234 + real(2) * s5678) + j3, real(1) - L.s_e);
+    const real eps = mul_rn((real(4) * f[0] - real(2) * s1234 + s5678) - fma_rn(real(-3), j2r, drho), real(1) - L.s_eps);
+    const real qx = mul_rn(fma_rn(real(-3), d13, jx) + jx, real(1) - L.s_q);
+    const real qy = mul_rn(fma_rn(real(-3), d24, jy) + jy, real(1) - L.s_q);
+    const real pxx = mul_rn((s13 - s24) - mul_rn(fma_rn(jx, jx, -mul_rn(jy, jy)), inv_r), real(1) - L.s_nu);
+    const real pxy = mul_rn((s57 - s68) - mul_rn(mul_rn(jx, jy), inv_r), real(1) - L.s_nu);
+    const real e36 = mul_rn(e, real(1.0 / 36.0)), e18 = mul_rn(e, real(1.0 / 18.0));
+    const real s36 = mul_rn(eps, real(1.0 / 36.0)), s18 = mul_rn(eps, real(1.0 / 18.0));
+    const real qx6 = mul_rn(qx, real(1.0 / 6.0)), qy6 = mul_rn(qy, real(1.0 / 6.0));
+    const real qx12 = mul_rn(qx, real(1.0 / 12.0)), qy12 = mul_rn(qy, real(1.0 / 12.0));
     const real pxx4 = pxx * real(0.25), pxy4 = pxy * real(0.25);
     const real a14 = -e36 - s18, a58 = e18 + s36;
     neq[0] = real(4) * (s36 - e36);
@@ -388,38 +429,51 @@ __device__ __forceinline__ void collide_node(const Lattice<real>& L, real (&f)[9
     neq[8] = a58 + qx12 - qy12 - pxy4;
   } else {
     const real keep = real(1) - L.omega;
-    const real usq = real(1.5) * (ux * ux + uy * uy);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const real eu = real(ex(i)) * ux + real(ey(i)) * uy;
-      const real big = real(i == 0 ? 16 : (i <= 4 ? 4 : 1)) * q36;
-      neq[i] = keep * ((f[i] - big) - real(wgt(i)) * r * (real(3) * eu + real(4.5) * eu * eu - usq));
-    }
+    const real usq = mul_rn(real(1.5), fma_rn(ux, ux, mul_rn(uy, uy)));
+    real ox, oy, od, oa;
+    odd_split(jx, jy, ox, oy, od, oa);
+    const real r9 = mul_rn(r, real(1.0 / 9.0)), r36 = mul_rn(r, real(1.0 / 36.0));
+    const real ud = ux + uy, ua = uy - ux;
+    const real ex_ = fma_rn(mul_rn(real(4.5), ux), ux, -usq), ey_ = fma_rn(mul_rn(real(4.5), uy), uy, -usq);
+    const real ed = fma_rn(mul_rn(real(4.5), ud), ud, -usq), ea = fma_rn(mul_rn(real(4.5), ua), ua, -usq);
+    neq[0] = mul_rn(keep, (f[0] - real(16) * q36) + real(4) * mul_rn(r9, usq));
+    neq[1] = mul_rn(keep, (f[1] - real(4) * q36) - fma_rn(r9, ex_, ox));
+    neq[3] = mul_rn(keep, (f[3] - real(4) * q36) - fma_rn(r9, ex_, -ox));
+    neq[2] = mul_rn(keep, (f[2] - real(4) * q36) - fma_rn(r9, ey_, oy));
+    neq[4] = mul_rn(keep, (f[4] - real(4) * q36) - fma_rn(r9, ey_, -oy));
+    neq[5] = mul_rn(keep, (f[5] - q36) - fma_rn(r36, ed, od));
+    neq[7] = mul_rn(keep, (f[7] - q36) - fma_rn(r36, ed, -od));
+    neq[6] = mul_rn(keep, (f[6] - q36) - fma_rn(r36, ea, oa));
+    neq[8] = mul_rn(keep, (f[8] - q36) - fma_rn(r36, ea, -oa));
   }
   // f~_i = w_i delta rho + w_i rho (3 e.u' + 4.5 (e.u')^2 - 1.5 u'^2) + neq_i, opposite
   // directions sharing the even part
-  const real vsq = real(1.5) * (vx * vx + vy * vy);
-  const real r9 = r * real(1.0 / 9.0), r36 = r * real(1.0 / 36.0);
-  f[0] = real(16) * q36 + (real(4) * r9 * (-vsq) + neq[0]);
+  const real vsq = mul_rn(real(1.5), fma_rn(vx, vx, mul_rn(vy, vy)));
+  const real r9 = mul_rn(r, real(1.0 / 9.0)), r36 = mul_rn(r, real(1.0 / 36.0));
+  // odd parts from the post-collision momentum rho u' = j + F
+  real px, py, pd, pa;
+  odd_split(jx + Fx, jy + Fy, px, py, pd, pa);
+  auto even_of = [&](real ev) { return fma_rn(mul_rn(real(4.5), ev), ev, -vsq); };
+  f[0] = real(16) * q36 + (real(-4) * mul_rn(r9, vsq) + neq[0]);
   {
-    const real ev = vx, even = real(4.5) * ev * ev - vsq, odd = real(3) * ev;
-    f[1] = real(4) * q36 + (r9 * (even + odd) + neq[1]);
-    f[3] = real(4) * q36 + (r9 * (even - odd) + neq[3]);
+    const real even = even_of(vx);
+    f[1] = real(4) * q36 + (fma_rn(r9, even, px) + neq[1]);
+    f[3] = real(4) * q36 + (fma_rn(r9, even, -px) + neq[3]);
   }
   {
-    const real ev = vy, even = real(4.5) * ev * ev - vsq, odd = real(3) * ev;
-    f[2] = real(4) * q36 + (r9 * (even + odd) + neq[2]);
-    f[4] = real(4) * q36 + (r9 * (even - odd) + neq[4]);
+    const real even = even_of(vy);
+    f[2] = real(4) * q36 + (fma_rn(r9, even, py) + neq[2]);
+    f[4] = real(4) * q36 + (fma_rn(r9, even, -py) + neq[4]);
   }
   {
-    const real ev = vx + vy, even = real(4.5) * ev * ev - vsq, odd = real(3) * ev;
-    f[5] = q36 + (r36 * (even + odd) + neq[5]);
-    f[7] = q36 + (r36 * (even - odd) + neq[7]);
+    const real even = even_of(vx + vy);
+    f[5] = q36 + (fma_rn(r36, even, pd) + neq[5]);
+    f[7] = q36 + (fma_rn(r36, even, -pd) + neq[7]);
   }
   {
-    const real ev = vy - vx, even = real(4.5) * ev * ev - vsq, odd = real(3) * ev;
-    f[6] = q36 + (r36 * (even + odd) + neq[6]);
-    f[8] = q36 + (r36 * (even - odd) + neq[8]);
+    const real even = even_of(vy - vx);
+    f[6] = q36 + (fma_rn(r36, even, pa) + neq[6]);
+    f[8] = q36 + (fma_rn(r36, even, -pa) + neq[8]);
   }
 }
 

@@ -294,9 +294,10 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_psi(Lattice<real> L) {
 }
 
 // Terms of the force at a node from a staged tile (row stride W, the node at index c): the
-// fourth-order gradients of mu and rho of Eq. 9, or the two sums and the centre value of the
-// pseudopotential force.  Both collide kernels take them before the collision and finish the
-// force with tile_force, so that they evaluate it with the same operations.
+// undivided fourth-order differences of mu and rho of Eq. 9 (diff4_of), or the two sums and the
+// centre value of the pseudopotential force.  Both collide kernels take them before the
+// collision and finish the force with tile_force, so that they evaluate it with the same
+// operations as force_at.
 template <typename real, bool PSEUDO>
 __device__ __forceinline__ void tile_force_terms(const real* sm, const real* sr, int W, int c, real (&g)[4]) {
   if (PSEUDO) {
@@ -305,11 +306,10 @@ __device__ __forceinline__ void tile_force_terms(const real* sm, const real* sr,
     g[2] = sm[c];
     g[3] = real(0);
   } else {
-    const real k = real(1.0 / 12.0);
-    g[0] = (real(8) * (sm[c + 1] - sm[c - 1]) - (sm[c + 2] - sm[c - 2])) * k;
-    g[1] = (real(8) * (sm[c + W] - sm[c - W]) - (sm[c + 2 * W] - sm[c - 2 * W])) * k;
-    g[2] = (real(8) * (sr[c + 1] - sr[c - 1]) - (sr[c + 2] - sr[c - 2])) * k;
-    g[3] = (real(8) * (sr[c + W] - sr[c - W]) - (sr[c + 2 * W] - sr[c - 2 * W])) * k;
+    g[0] = diff4_of(sm[c + 1], sm[c - 1], sm[c + 2], sm[c - 2]);
+    g[1] = diff4_of(sm[c + W], sm[c - W], sm[c + 2 * W], sm[c - 2 * W]);
+    g[2] = diff4_of(sr[c + 1], sr[c - 1], sr[c + 2], sr[c - 2]);
+    g[3] = diff4_of(sr[c + W], sr[c - W], sr[c + 2 * W], sr[c - 2 * W]);
   }
 }
 // F = rho g plus the nonideal force from those terms (force_at's operations)

@@ -6,10 +6,11 @@ Bars:
     fields within 1e-9 after 1000 steps (only the order of rounding differs; transcendental
     functions differ by an ulp);
   - FP32 GPU vs oracle: within 1e-5 (rho pointwise relative, v normwise relative) over the
-    first 20 steps at full size; after 1000 steps within 5e-5 (rho) and 1.5e-4 (v).  The
-    1000-step target of 1e-5 is not met: the droplet transients amplify rounding about
-    300-fold over 1000 steps (measured with the FP64 path: 1e-16 per step grows to 3e-14), so
-    FP32 rounding (6e-8) ends at 1-3e-5 in rho, largest in the dilute gas next to interfaces;
+    first 20 steps at full size, and after 1000 steps.  One case, the 128 x 128 drop on a
+    neutral cylinder run in FP32 (BGK tau = 1, 0.7 Tc), reaches 1.2e-5 in v: its transient gas
+    flow amplifies rounding the most.  Rounding every stored FP32 quantity (populations,
+    density, chemical potential, force, velocity) of the FP64 oracle once per step gives it
+    8.3e-6 already, so its bar is 1.5e-5;
   - mass: FP64 drift <= 1e-12, FP32 drift (FP64 audit) <= 1e-6 over 2000 steps.
 """
 import numpy as np
@@ -108,23 +109,25 @@ def test_fp64_long_run_mass_and_compensation():
     assert np.allclose(hist_g, hist_o, rtol=1e-7, atol=1e-12 * M0)
 
 
+# (scenario, bar on v); rho within 1e-5 everywhere
 FP32_CASES = {
-    "c1_neutral_bgk_0.7": lambda: S.c1_plain_fp64().with_(fp64=False),
-    "c1_hydrophilic_bgk_0.7": lambda: S.c1_plain_fp64().with_(fp64=False, dmu_w=[-0.03]),
-    "small_60_120_mrt_0.6": lambda: S.small_parity(fp64=False),
-    "c2_256_four_cylinders": lambda: S.c2_fp32_single(nx=256, ny=256, n_cyl=4),
+    "c1_neutral_bgk_0.7": (lambda: S.c1_plain_fp64().with_(fp64=False), 1.5e-5),
+    "c1_hydrophilic_bgk_0.7": (lambda: S.c1_plain_fp64().with_(fp64=False, dmu_w=[-0.03]), 1e-5),
+    "small_60_120_mrt_0.6": (lambda: S.small_parity(fp64=False), 1e-5),
+    "c2_256_four_cylinders": (lambda: S.c2_fp32_single(nx=256, ny=256, n_cyl=4), 1e-5),
 }
 
 
 @pytest.mark.parametrize("which", list(FP32_CASES))
 def test_fp32_matches_oracle_after_1000_steps(which):
-    sc = FP32_CASES[which]()
+    mk, v_bar = FP32_CASES[which]
+    sc = mk()
     lat, orc = make_lattice(sc, fp64=False), make_oracle(sc)
     lat.step(1000)
     orc.step(1000)
     er, ev, ef = compare(lat, orc)
     print(f"{which}: rho {er:.2e} v {ev:.2e} f {ef:.2e}")
-    assert er <= 5e-5 and ev <= 1.5e-4, (er, ev, ef)
+    assert er <= 1e-5 and ev <= v_bar, (er, ev, ef)
 
 
 def test_fp32_mass_audit():
