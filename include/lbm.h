@@ -406,6 +406,46 @@ lbm_status lbm_batch_info(lbm_batch* b, int64_t* out4);
 const char* lbm_batch_last_error(const lbm_batch* b);
 void lbm_batch_destroy(lbm_batch* b);
 
+/* ---- y-slab decomposition of one lattice over several GPUs (one context per slab) ----------
+ * The method is a local stencil: a node's next state depends only on nodes within a few rows
+ * (the streaming of Eq. 5, the fourth-order stencils of Eqs. 9 and 12, the two solid layers of
+ * Eq. 15, the second fluid node x2 of Eq. 16), at most 7 rows in y.  A lattice split into
+ * slabs of whole rows therefore advances exactly as the undivided one if, after every step,
+ * each slab's halo of H >= 7 rows on either side is overwritten with its neighbour's own rows.
+ *
+ * lbm_slab_workspace_size / lbm_create_slab take the GLOBAL configuration (cylinders in global
+ * coordinates) and the global rows [y0, y1) the slab owns; the context then holds those rows,
+ * an H-row halo on each side that has a neighbour (none where a walled lattice ends: the
+ * bottom slab owns global rows 0, 1, the top slab rows ny-2, ny-1), and two solid rows beyond
+ * each halo that terminate the local lattice (their values never reach the own rows).  With
+ * walls = 0 the slabs wrap around in y.  Then lbm_build_links, lbm_init with the global drop
+ * positions, and per step: lbm_step(ctx, 1); for each edge with a neighbour, lbm_slab_pack into
+ * a device buffer of lbm_slab_message_bytes bytes; the caller moves the message to the
+ * neighbour (NCCL send/recv, a peer copy, or host copies) and the neighbour calls
+ * lbm_slab_unpack on its facing edge (the bottom slab's top edge faces the next slab's bottom
+ * edge).  All four calls are asynchronous on the context's stream.  The message holds the H
+ * own rows next to that edge: nine population planes, the density plane, the per-node EOS plane
+ * the next step starts from, and the Eq. 18 FP64 carries of the boundary nodes in those rows.
+ * Own rows are then bit-identical to the undivided lattice's.
+ *
+ * lbm_mass and lbm_dM_history of a slab count its own rows and own boundary nodes only: the
+ * global M and Delta M are the sums over slabs (an FP64 all-reduce).  lbm_fields and
+ * lbm_populations return the whole local lattice (ny = the local rows).
+ *
+ * lbm_slab_info fills 10 ints: global row of local row 0 (before the periodic wrap), local ny,
+ * first and one-past-last own local row, H, bottom edge has a neighbour, top edge has one, first
+ * local row of the bottom halo, first local row of the top halo, global lattice periodic in y.
+ * Errors: LBM_EINVAL for H < 7, rows outside [0, ny), a slab with a neighbour owning fewer than
+ * H rows, wall rows split from their slab, an edge without a neighbour or a short buffer;
+ * LBM_ESTATE for a whole-lattice context or a pack/unpack before the first step. */
+lbm_status lbm_slab_workspace_size(const lbm_config* cfg, int32_t y0, int32_t y1, int32_t halo, size_t* bytes);
+lbm_status lbm_create_slab(const lbm_config* cfg, int32_t y0, int32_t y1, int32_t halo, void* stream,
+                           void* workspace, size_t bytes, lbm_ctx** out);
+lbm_status lbm_slab_info(lbm_ctx* ctx, int32_t* info10);
+lbm_status lbm_slab_message_bytes(lbm_ctx* ctx, size_t* bytes);
+lbm_status lbm_slab_pack(lbm_ctx* ctx, int32_t edge, void* device_buffer, size_t bytes);
+lbm_status lbm_slab_unpack(lbm_ctx* ctx, int32_t edge, const void* device_buffer, size_t bytes);
+
 /* Mass audit that allocates no device memory (the paper has no counterpart: this serves
  * callers that may not call cudaMalloc -- a host callback, a monitor, or a process whose device
  * memory budget belongs to another allocator -- but already hold populations on the device).

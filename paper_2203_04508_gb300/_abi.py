@@ -46,6 +46,12 @@ _SIGS = {
     "lbm_workspace_size": (I32, [C.POINTER(lbm_config), C.POINTER(SZ)]),
     "lbm_create": (I32, [C.POINTER(lbm_config), P, P, SZ, C.POINTER(P)]),
     "lbm_build_links": (I32, [P]),
+    "lbm_slab_workspace_size": (I32, [C.POINTER(lbm_config), I32, I32, I32, C.POINTER(SZ)]),
+    "lbm_create_slab": (I32, [C.POINTER(lbm_config), I32, I32, I32, P, P, SZ, C.POINTER(P)]),
+    "lbm_slab_info": (I32, [P, P]),
+    "lbm_slab_message_bytes": (I32, [P, C.POINTER(SZ)]),
+    "lbm_slab_pack": (I32, [P, I32, P, SZ]),
+    "lbm_slab_unpack": (I32, [P, I32, P, SZ]),
     "lbm_counts": (I32, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)]),
     "lbm_get_links": (I32, [P, I64, P, P, P, P, P]),
     "lbm_get_kind": (I32, [P, P]),

@@ -25,6 +25,7 @@ UNITS = [
     ("lbm_geometry.cu", ["-fmad=false"]),
     ("lbm_eos.cpp", ["-x", "cu"]),
     ("lbm_noalloc.cu", []),
+    ("lbm_slab.cu", []),
     ("lbm_batch.cu", []),
     ("lbm_adjoint.cu", []),
 ]

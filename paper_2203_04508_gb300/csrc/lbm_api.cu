@@ -16,6 +16,7 @@ using namespace lbmgb;
 namespace {
 
 constexpr int MAX_DROPS = 4096;
+constexpr int SLAB_MIN_HALO = 7;
 constexpr size_t ALIGN = 256;
 
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
@@ -158,6 +159,20 @@ struct lbm_ctx {
   // second stream and events of the reverse sweep (created on its first use)
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_start = nullptr, ev_rec[2] = {nullptr, nullptr}, ev_rev[2] = {nullptr, nullptr};
+  // y-slab of a larger lattice (lbm_create_slab).  Local row y is global row y + y_off (mod
+  // the global ny when the global lattice is periodic in y); rows [own_lo, own_hi) are this
+  // slab's own; on edge e (0 bottom, 1 top) with a neighbour, rows [recv_lo[e], recv_lo[e] + H)
+  // are the halo it receives and [send_lo[e], send_lo[e] + H) the own rows it sends.
+  struct Slab {
+    bool on = false;
+    int y_off = 0, ny_glob = 0, periodic = 0, halo = 0;
+    int own_lo = 0, own_hi = 0;
+    bool edge[2] = {false, false};
+    int recv_lo[2] = {0, 0}, send_lo[2] = {0, 0};
+    // boundary-node index ranges of the own rows and of each edge's received and sent rows
+    int b_own[2] = {0, 0}, b_recv[2][2] = {{0, 0}, {0, 0}}, b_send[2][2] = {{0, 0}, {0, 0}};
+    long long n_fluid_own = 0;
+  } slab;
   // the last checkpointed forward pass (lbm_forward_checkpointed), for lbm_adjoint
   struct Tape {
     bool valid = false;
@@ -289,6 +304,21 @@ void fill_lattice(lbm_ctx* c, Lattice<real>& L) {
   L.tma = nullptr;
   if constexpr (sizeof(real) == 4) {
     if (c->tma_ok && c->collide_kind == 1) L.tma = &c->tma;
+  }
+  if (c->slab.on) {
+    L.y_off = c->slab.y_off;
+    L.ny_glob = c->slab.periodic ? c->slab.ny_glob : 0;
+    L.own_lo = c->slab.own_lo;
+    L.own_hi = c->slab.own_hi;
+    L.b_lo = c->slab.b_own[0];
+    L.b_hi = c->slab.b_own[1];
+  } else {
+    L.y_off = 0;
+    L.ny_glob = 0;
+    L.own_lo = 0;
+    L.own_hi = c->cfg.ny;
+    L.b_lo = 0;
+    L.b_hi = (int)c->n_bnodes;
   }
 }
 
@@ -458,6 +488,111 @@ lbm_status profile_steps(lbm_ctx* c, const Lattice<real>& L, long long n, double
   return st;
 }
 
+// Fluid nodes the mass audit counts: a slab's own rows only.
+long long fluid_count(const lbm_ctx* c) { return c->slab.on ? c->slab.n_fluid_own : c->n_fluid; }
+
+// A slab's local configuration: the global one with ny = the rows it holds and flat walls at
+// both ends of them -- the global walls where the slab reaches a global wall row, else two
+// solid rows beyond the halo at the halfway line (local y 1.5 and ny - 2.5).  Cylinders keep
+// their global coordinates; the geometry tests them at global rows.
+lbm_status slab_local_config(const lbm_config* g, int y0, int y1, int H, lbm_config* loc, lbm_ctx::Slab* sl,
+                             char* msg) {
+  auto bad = [&](const char* m) { std::snprintf(msg, 256, "%s", m); return LBM_EINVAL; };
+  if (H < SLAB_MIN_HALO) return bad("slab halo must be at least 7 rows (the reach of one step)");
+  if (!(0 <= y0 && y0 < y1 && y1 <= g->ny)) return bad("slab rows must satisfy 0 <= y0 < y1 <= ny");
+  const int own = y1 - y0;
+  const bool bottom = !(g->walls && y0 == 0), top = !(g->walls && y1 == g->ny);
+  if ((bottom || top) && own < H) return bad("a slab with a neighbour must own at least halo rows");
+  if (g->walls && bottom && y0 < 2) return bad("a walled lattice's wall rows belong to the bottom slab");
+  if (g->walls && top && y1 > g->ny - 2) return bad("a walled lattice's wall rows belong to the top slab");
+  const int below = bottom ? 2 + H : 0, above = top ? H + 2 : 0;
+  *loc = *g;
+  loc->ny = own + below + above;
+  loc->walls = 1;
+  sl->on = true;
+  sl->y_off = y0 - below;
+  sl->ny_glob = g->ny;
+  sl->periodic = g->walls ? 0 : 1;
+  sl->halo = H;
+  sl->own_lo = below;
+  sl->own_hi = below + own;
+  sl->edge[0] = bottom;
+  sl->edge[1] = top;
+  sl->recv_lo[0] = 2;
+  sl->send_lo[0] = below;
+  sl->recv_lo[1] = below + own;
+  sl->send_lo[1] = below + own - H;
+  // the global wall lines in local rows (exact: integer shifts of numbers below 2^31)
+  loc->y_bottom = bottom ? 1.5 : g->y_bottom - (double)sl->y_off;
+  loc->y_top = top ? loc->ny - 2.5 : g->y_top - (double)sl->y_off;
+  return LBM_OK;
+}
+
+// After the geometry: the boundary-node index ranges of the own rows and of the rows each edge
+// sends and receives (the list is sorted by node, so rows are contiguous ranges of it), and the
+// fluid nodes of the own rows.
+lbm_status slab_ranges(lbm_ctx* c) {
+  const Layout& y = c->lay;
+  std::vector<int> bnode(c->n_bnodes > 0 ? c->n_bnodes : 1);
+  std::vector<uint8_t> kind(y.plane);
+  if (c->n_bnodes > 0)
+    CUDA_OK(c, cudaMemcpy(bnode.data(), c->ws + y.bnode, c->n_bnodes * 4, cudaMemcpyDeviceToHost));
+  CUDA_OK(c, cudaMemcpy(kind.data(), c->ws + y.kind, y.plane, cudaMemcpyDeviceToHost));
+  auto first_at_row = [&](int row) {
+    const int key = row * y.pitch;
+    return (int)(std::lower_bound(bnode.begin(), bnode.begin() + c->n_bnodes, key) - bnode.begin());
+  };
+  lbm_ctx::Slab& sl = c->slab;
+  sl.b_own[0] = first_at_row(sl.own_lo);
+  sl.b_own[1] = first_at_row(sl.own_hi);
+  for (int e = 0; e < 2; ++e) {
+    sl.b_recv[e][0] = first_at_row(sl.recv_lo[e]);
+    sl.b_recv[e][1] = first_at_row(sl.recv_lo[e] + sl.halo);
+    sl.b_send[e][0] = first_at_row(sl.send_lo[e]);
+    sl.b_send[e][1] = first_at_row(sl.send_lo[e] + sl.halo);
+  }
+  long long nf = 0;
+  for (long long n = (long long)sl.own_lo * y.pitch; n < (long long)sl.own_hi * y.pitch; ++n)
+    nf += kind[n] == KIND_FLUID;
+  sl.n_fluid_own = nf;
+  return LBM_OK;
+}
+
+// the current density plane and EOS plane (psi'(rho) - mu_sat, or psi) a step starts from
+template <typename real>
+void slab_planes(const lbm_ctx* c, real** rho, real** aux) {
+  *rho = (real*)(c->ws + (c->cur ? c->lay.rho2 : c->lay.rho));
+  if (c->cfg.force_model == LBM_FORCE_PSEUDO) *aux = (real*)(c->ws + (c->cur ? c->lay.mu2 : c->lay.mu));
+  else *aux = (real*)(c->ws + c->lay.psip);
+}
+
+lbm_status slab_move(lbm_ctx* c, int32_t edge, void* buf, size_t bytes, bool pack) {
+  if (!c || !c->inited) return LBM_ESTATE;
+  if (c->sticky != LBM_OK) return c->sticky;
+  if (!c->slab.on) return fail(c, LBM_ESTATE, "not a slab context");
+  if (edge != 0 && edge != 1) return fail(c, LBM_EINVAL, "edge must be 0 (bottom) or 1 (top)");
+  if (!c->slab.edge[edge]) return fail(c, LBM_EINVAL, "edge %d ends in a wall of the global lattice", edge);
+  if (!c->rho_ok) return fail(c, LBM_ESTATE, "exchange halos after a step (the density planes are not current)");
+  if (!buf) return fail(c, LBM_EINVAL, "message buffer is NULL");
+  const lbm_ctx::Slab& sl = c->slab;
+  const size_t need = slab_msg_layout(sl.halo, c->lay.pitch, c->cfg.nx, (int)c->lay.sz).total;
+  if (bytes < need) return fail(c, LBM_EINVAL, "message buffer of %zu bytes, %zu needed", bytes, need);
+  const int row0 = pack ? sl.send_lo[edge] : sl.recv_lo[edge];
+  const int* br = pack ? sl.b_send[edge] : sl.b_recv[edge];
+  if (c->fp64) {
+    double *rho, *aux;
+    slab_planes(c, &rho, &aux);
+    CUDA_OK(c, pack ? launch_slab_pack(c->Ld, c->cur, rho, aux, row0, sl.halo, br[0], br[1], buf, c->stream)
+                    : launch_slab_unpack(c->Ld, c->cur, rho, aux, row0, sl.halo, br[0], br[1], buf, c->stream));
+  } else {
+    float *rho, *aux;
+    slab_planes(c, &rho, &aux);
+    CUDA_OK(c, pack ? launch_slab_pack(c->Lf, c->cur, rho, aux, row0, sl.halo, br[0], br[1], buf, c->stream)
+                    : launch_slab_unpack(c->Lf, c->cur, rho, aux, row0, sl.halo, br[0], br[1], buf, c->stream));
+  }
+  return LBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -528,6 +663,71 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, void* workspace, size
   return LBM_OK;
 }
 
+lbm_status lbm_slab_workspace_size(const lbm_config* cfg, int32_t y0, int32_t y1, int32_t halo, size_t* bytes) {
+  if (!cfg || !bytes) return LBM_EINVAL;
+  char msg[256];
+  lbm_status s = validate(cfg, msg);
+  if (s != LBM_OK) return s;
+  lbm_config loc;
+  lbm_ctx::Slab sl;
+  s = slab_local_config(cfg, y0, y1, halo, &loc, &sl, msg);
+  if (s != LBM_OK) return s;
+  *bytes = make_layout(&loc).total;
+  return LBM_OK;
+}
+
+lbm_status lbm_create_slab(const lbm_config* cfg, int32_t y0, int32_t y1, int32_t halo, void* stream, void* workspace,
+                           size_t bytes, lbm_ctx** out) {
+  LBM_RANGE("lbm_create_slab");
+  if (!cfg || !out) return LBM_EINVAL;
+  *out = nullptr;
+  char msg[256] = {0};
+  lbm_status s = validate(cfg, msg);
+  lbm_config loc{};
+  lbm_ctx::Slab sl;
+  if (s == LBM_OK) s = slab_local_config(cfg, y0, y1, halo, &loc, &sl, msg);
+  if (s != LBM_OK) {
+    lbm_ctx* c = new lbm_ctx();
+    c->err = msg;
+    *out = c;
+    return s;
+  }
+  s = lbm_create(&loc, stream, workspace, bytes, out);
+  if (*out) {
+    (*out)->slab = sl;
+    refresh(*out);
+  }
+  return s;
+}
+
+lbm_status lbm_slab_info(lbm_ctx* c, int32_t* info) {
+  if (!c || !info) return LBM_EINVAL;
+  if (!c->slab.on) return fail(c, LBM_ESTATE, "not a slab context");
+  const lbm_ctx::Slab& sl = c->slab;
+  const int32_t v[10] = {sl.y_off, c->cfg.ny, sl.own_lo, sl.own_hi, sl.halo, sl.edge[0], sl.edge[1],
+                         sl.recv_lo[0], sl.recv_lo[1], sl.periodic};
+  std::memcpy(info, v, sizeof(v));
+  return LBM_OK;
+}
+
+lbm_status lbm_slab_message_bytes(lbm_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return LBM_EINVAL;
+  if (!c->slab.on) return fail(c, LBM_ESTATE, "not a slab context");
+  *bytes = slab_msg_layout(c->slab.halo, c->lay.pitch, c->cfg.nx, (int)c->lay.sz).total;
+  return LBM_OK;
+}
+
+
+lbm_status lbm_slab_pack(lbm_ctx* c, int32_t edge, void* buf, size_t bytes) {
+  LBM_RANGE("lbm_slab_pack");
+  return slab_move(c, edge, buf, bytes, true);
+}
+
+lbm_status lbm_slab_unpack(lbm_ctx* c, int32_t edge, const void* buf, size_t bytes) {
+  LBM_RANGE("lbm_slab_unpack");
+  return slab_move(c, edge, const_cast<void*>(buf), bytes, false);
+}
+
 lbm_status lbm_build_links(lbm_ctx* c) {
   LBM_RANGE("lbm_build_links");
   if (!c || !c->ws) return LBM_ESTATE;
@@ -548,6 +748,8 @@ lbm_status lbm_build_links(lbm_ctx* c) {
   gp.nx = g.nx; gp.ny = g.ny; gp.pitch = y.pitch; gp.walls = g.walls; gp.plane = y.plane;
   gp.y_bottom = g.y_bottom; gp.y_top = g.y_top; gp.n_cyl = g.n_cyl; gp.cyl = (const double*)(w + y.cyl);
   gp.dmu_walls = g.dmu_w_walls;
+  gp.y_off = c->slab.on ? c->slab.y_off : 0;
+  gp.ny_glob = c->slab.on && c->slab.periodic ? c->slab.ny_glob : 0;
   // the second lattice is free until lbm_init: it holds the per-node scratch of the set-up
   GeomScratch sc{};
   sc.body = (int*)(w + y.body);
@@ -580,6 +782,10 @@ lbm_status lbm_build_links(lbm_ctx* c) {
   CUDA_OK(c, cudaMemsetAsync(w + y.dm_ring, 0, (size_t)(DM_RING + 1) * 8, c->stream));
   CUDA_OK(c, cudaMemsetAsync(w + y.rho, 0, y.plane * y.sz, c->stream));
   CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  if (c->slab.on) {
+    lbm_status st = slab_ranges(c);
+    if (st != LBM_OK) return st;
+  }
   c->built = true;
   c->inited = false;
   c->rho_ok = false;
@@ -678,7 +884,7 @@ lbm_status lbm_init(lbm_ctx* c, const lbm_init_spec* s) {
   double sc[2];
   CUDA_OK(c, cudaMemcpyAsync(sc, c->ws + y.scalars, 16, cudaMemcpyDeviceToHost, c->stream));
   CUDA_OK(c, cudaStreamSynchronize(c->stream));
-  c->mass0 = sc[0] + (double)c->n_fluid * c->rho_ref;
+  c->mass0 = sc[0] + (double)fluid_count(c) * c->rho_ref;
   c->inited = true;
   c->rho_ok = false;
   c->tape.valid = false;
@@ -987,7 +1193,7 @@ lbm_status lbm_set_populations(lbm_ctx* c, const void* f, int32_t on_device) {
   double sc[2];
   CUDA_OK(c, cudaMemcpyAsync(sc, c->ws + y.scalars, 16, cudaMemcpyDeviceToHost, c->stream));
   CUDA_OK(c, cudaStreamSynchronize(c->stream));
-  c->mass0 = sc[0] + (double)c->n_fluid * c->rho_ref;
+  c->mass0 = sc[0] + (double)fluid_count(c) * c->rho_ref;
   c->inited = true;
   c->rho_ok = false;
   c->tape.valid = false;
@@ -1014,7 +1220,7 @@ lbm_status lbm_mass(lbm_ctx* c, double* M, double* M0, double* dM_last) {
   double last = 0.0;
   if (ctr > 0)
     CUDA_OK(c, cudaMemcpy(&last, c->ws + y.dm_ring + ((ctr - 1) % DM_RING) * 8, 8, cudaMemcpyDeviceToHost));
-  if (M) *M = sc[0] + (double)c->n_fluid * c->rho_ref;
+  if (M) *M = sc[0] + (double)fluid_count(c) * c->rho_ref;
   if (M0) *M0 = c->mass0;
   if (dM_last) *dM_last = last;
   if (sc[1] != 0.0) return fail(c, LBM_EUNSTABLE, "%.0f non-finite populations", sc[1]);

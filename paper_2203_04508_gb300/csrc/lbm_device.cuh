@@ -89,8 +89,21 @@ struct Lattice {
                                 // vectors, 2 row sweeps, FP32 only)
   const void* tma;              // host side: TMA descriptors of the pipelined collide kernel
                                 // (FP32), null for the plain kernel
+  // y-slab of a larger lattice: local row y is global row y + y_off (mod ny_glob when ny_glob >
+  // 0); the audits sum rows [own_lo, own_hi) and the Eq. 18 sum boundary nodes [b_lo, b_hi)
+  // only.  A whole lattice has y_off = ny_glob = 0, own = [0, ny), b = [0, n_bnodes).
+  int y_off, ny_glob;
+  int own_lo, own_hi;
+  int b_lo, b_hi;
 };
 
+// global row of local row y (slabs; the identity for a whole lattice)
+template <typename real>
+__device__ __forceinline__ int global_row(const Lattice<real>& L, int y) {
+  int g = y + L.y_off;
+  if (L.ny_glob > 0) g = g < 0 ? g + L.ny_glob : (g >= L.ny_glob ? g - L.ny_glob : g);
+  return g;
+}
 
 template <typename real>
 __device__ __forceinline__ int wrap_x(const Lattice<real>& L, int x) {

@@ -29,11 +29,18 @@ __device__ __forceinline__ bool gnb(const GeomParams& g, int x, int y, int i, in
   return true;
 }
 
+// global row of local row y (a slab's rows are a window of a larger lattice)
+__device__ __forceinline__ int grow(const GeomParams& g, int y) {
+  int r = y + g.y_off;
+  if (g.ny_glob > 0) r = r < 0 ? r + g.ny_glob : (r >= g.ny_glob ? r - g.ny_glob : r);
+  return r;
+}
+
 __device__ __forceinline__ bool inside_body(const GeomParams& g, int b, int x, int y) {
   if (b < g.n_cyl) {
     const double* c = g.cyl + 4 * b;
     double dx = (double)x - c[0];
-    double dy = (double)y - c[1];
+    double dy = (double)grow(g, y) - c[1];
     double d2 = dx * dx + dy * dy;
     return d2 <= c[2] * c[2];
   }
@@ -45,7 +52,7 @@ __device__ __forceinline__ double q_body(const GeomParams& g, int b, int x, int 
   if (b < g.n_cyl) {
     const double* c = g.cyl + 4 * b;
     double dx = (double)x - c[0];
-    double dy = (double)y - c[1];
+    double dy = (double)grow(g, y) - c[1];
     double A = (double)(ex(i) * ex(i) + ey(i) * ey(i));
     double B = 2.0 * (dx * (double)ex(i) + dy * (double)ey(i));
     double C = (dx * dx + dy * dy) - c[2] * c[2];

@@ -61,6 +61,22 @@ struct CollideTma {
 bool collide_tma_setup(CollideTma* T, const Lattice<float>& L, const void* rho0, const void* rho1, const void* mu1,
                        char* err);
 
+// ---- halo messages of a y-slab (lbm_slab.cu)
+constexpr int SLAB_PLANES = 11;   // nine populations, density, psi'(rho) - mu_sat or psi
+struct SlabMsgLayout {
+  long long cap;                  // carries a message can hold (H * nx)
+  size_t carry, key, planes;      // byte offsets
+  long long plane_elems;          // H * pitch
+  size_t total;
+};
+SlabMsgLayout slab_msg_layout(int nrows, int pitch, int nx, int sz);
+template <typename real>
+cudaError_t launch_slab_pack(const Lattice<real>& L, int cur, real* rho, real* aux, int row0, int nrows, int b0,
+                             int b1, void* msg, cudaStream_t s);
+template <typename real>
+cudaError_t launch_slab_unpack(const Lattice<real>& L, int cur, real* rho, real* aux, int row0, int nrows, int b0,
+                               int b1, const void* msg, cudaStream_t s);
+
 // ---- geometry (lbm_geometry.cu, compiled without FMA contraction)
 struct GeomParams {
   int nx, ny, pitch, walls;
@@ -69,6 +85,9 @@ struct GeomParams {
   int n_cyl;
   const double* cyl;          // device: n_cyl x {cx, cy, r, dmu}
   double dmu_walls;
+  // y-slab: cylinders are tested at global row y + y_off (mod ny_glob when ny_glob > 0); the
+  // flat walls stay in local rows.  A whole lattice has 0, 0.
+  int y_off, ny_glob;
 };
 
 struct GeomScratch {

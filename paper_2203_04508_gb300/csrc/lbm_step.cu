@@ -577,7 +577,8 @@ template <typename real, bool PSEUDO>
 __global__ void __launch_bounds__(NODE_BLOCK) k_bc(Lattice<real> L, int cur) {
   __shared__ double red[32];
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  const double sum = b < L.n_bnodes ? phase_bc<real, 4, PSEUDO>(L, cur, b) : 0.0;
+  double sum = b < L.n_bnodes ? phase_bc<real, 4, PSEUDO>(L, cur, b) : 0.0;
+  if (b < L.b_lo || b >= L.b_hi) sum = 0.0;   // a slab's halo nodes belong to its neighbour's sum
   double bt = block_sum(sum, red);
   double total;
   if (finish_reduction(bt, L.partials, L.counter, &total, red)) {
@@ -626,7 +627,8 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_mass(Lattice<real> L, int cur) {
   __shared__ double red2[32];
   double s = 0.0, bad = 0.0;
   const real* __restrict__ f = L.f[cur];
-  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < L.plane;
+  const long long n_lo = (long long)L.own_lo * L.pitch, n_hi = (long long)L.own_hi * L.pitch;
+  for (long long n = n_lo + (long long)blockIdx.x * blockDim.x + threadIdx.x; n < n_hi;
        n += (long long)gridDim.x * blockDim.x) {
     if (L.kind[n] != KIND_FLUID) continue;
     double t = 0.0;
@@ -703,7 +705,8 @@ template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_max_speed(Lattice<real> L, int cur, unsigned long long* out) {
   unsigned long long b = 0ull;
   const real* __restrict__ f = L.f[cur];
-  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < L.plane;
+  const long long n_lo = (long long)L.own_lo * L.pitch, n_hi = (long long)L.own_hi * L.pitch;
+  for (long long n = n_lo + (long long)blockIdx.x * blockDim.x + threadIdx.x; n < n_hi;
        n += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(n % L.pitch), y = (int)(n / L.pitch);
     if (x >= L.nx || L.kind[n] != KIND_FLUID) continue;
@@ -798,7 +801,7 @@ __global__ void k_init(Lattice<real> L, const double* __restrict__ drops, int n_
   double phi = 0.0, u0 = 0.0, v0 = 0.0;
   for (int d = 0; d < n_drop; ++d) {
     const double* p = drops + 5 * d;
-    double dx = x - p[0], dy = y - p[1];
+    double dx = x - p[0], dy = global_row(L, y) - p[1];
     double rr = sqrt(dx * dx + dy * dy);
     double ph = 0.5 - 0.5 * tanh(2.0 * (rr - p[2]) / W);
     if (ph > phi) { phi = ph; u0 = p[3]; v0 = p[4]; }

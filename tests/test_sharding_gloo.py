@@ -22,10 +22,10 @@ def _free_port():
 def _worker(rank, world, port, q):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    import bench
     import scenarios as S
+    from paper_2203_04508_gb300.slab import shard_instances
     sizes = [sc.nodes for sc in S.c4_batch()]
-    mine = bench.shard_instances(sizes, world)[rank]
+    mine = shard_instances(sizes, world)[rank]
     load = torch.tensor([float(sum(sizes[k] for k in mine))])
     loads = [torch.zeros(1) for _ in range(world)]
     dist.all_gather(loads, load)
