@@ -58,6 +58,8 @@ COLLIDE_BYTES_PER_NODE = 1
 # the pseudopotential variant reads psi only (4 B) besides the populations
 PSEUDO_COLLIDE_BYTES_PER_FLUID_NODE = 76
 STEP_BYTES_PER_NODE = 72
+# y-slabs of one lattice over several GPUs: halo refresh period (the halo is 8 rows per step)
+SLAB_EXCHANGE_EVERY = 4
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -66,6 +68,11 @@ def collide_kernel_name(kind, pseudo):
     if kind == 1:
         return f"k_collide_tma ({force} + collide + stream, TMA-pipelined persistent grid)"
     return f"k_collide ({force} + collide + stream, one tile per block)"
+
+
+def workload_config(sc, wname, l2):
+    """The workload part of the line, the same for both arms."""
+    return {"workload": wname, "nodes": sc.nodes, "l2": l2}
 
 
 def pseudo_impact():
@@ -84,19 +91,6 @@ def workload(name):
     return S.c3_impact(), "c3 drop impact on a cylinder 2048x4096 D2Q9 MRT CS T=0.6Tc gravity FP32"
 
 
-def shard_instances(sizes, world):
-    """Greedy bin packing of independent instances (largest first) onto `world` ranks; returns
-    one index list per rank (each sorted).  No data moves between ranks: each advances its own."""
-    order = sorted(range(len(sizes)), key=lambda k: (-sizes[k], k))
-    load = [0] * world
-    out = [[] for _ in range(world)]
-    for k in order:
-        r = min(range(world), key=lambda j: (load[j], j))
-        out[r].append(k)
-        load[r] += sizes[k]
-    return [sorted(v) for v in out]
-
-
 def run_batched(G, torch, rank, world, steps, small=False):
     """Batched workload: seed-random droplet-on-cylinder instances of 128^2..768^2 (small:
     1024 instances of 64^2..128^2), advanced together by the persistent kernel (one launch for
@@ -104,6 +98,7 @@ def run_batched(G, torch, rank, world, steps, small=False):
     issued one lattice after another (each lattice has its own stream)."""
     import scenarios as S
     scs = S.c4_batch(seed=5, n=1024, nmin=64, nmax=128) if small else S.c4_batch()
+    from paper_2203_04508_gb300.slab import shard_instances
     mine = shard_instances([sc.nodes for sc in scs], world)[rank]
     scs = [scs[k] for k in mine]
     nodes = sum(sc.nodes for sc in scs)
@@ -418,6 +413,128 @@ def run_c1_mass(G):
     return {"steps": 2000, "mass_change": out}
 
 
+def run_accuracy(G, torch):
+    """FP32 and FP64 against the FP64 reference oracle on the full-size workloads, from the
+    oracle's stored results (tests/golden/accuracy_refs.json, written by
+    tests/golden/make_accuracy_refs.py from the oracle alone):
+      c2: rho (pointwise) and v (relative to the largest speed) after 1000 FP32 steps at 1024
+          seeded nodes, half of them in interfaces; at 5000 / 10000 / 20000 steps the drops'
+          liquid densities, the gas density and the contact angles (largest relative
+          differences) and the mass change (difference);
+      c3: the drop's interfaces on the centre line every 100 steps up to 500 (largest
+          difference, lu), the mass change, rho and v after 500 steps at 1024 seeded nodes;
+      c5: J and dJ/d(dmu_w, dmu_w walls, cx, cy) after 4000 steps with checkpoints every 200,
+          FP64 and FP32, against the oracle's complex-step and central-difference derivatives
+          (largest relative difference over the four components)."""
+    import numpy as np
+    import scenarios as S
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from diagnostics import droplet_report, isoline_crossings_column, report_errors, sampled_errors
+    path = os.path.join(ROOT, "tests", "golden", "accuracy_refs.json")
+    if not os.path.exists(path):
+        return None
+    refs = json.load(open(path))
+    g3 = lambda v: float(f"{v:.3g}")
+    out = {"source": "FP64 oracle results in tests/golden/accuracy_refs.json"}
+    if "c2" in refs:
+        sc = S.c2_fp32_single()
+        lat = G.Lattice(sc.physics(), precision=G.LBM_FP32)
+        lat.init_droplets(sc.droplets())
+        info = lat.eos_info()
+        lat.step(1000)
+        er, ev = sampled_errors(*lat.fields(), refs["c2"]["fields_1000"])
+        c2 = {"fields_1000_steps": {"rho": g3(er), "v": g3(ev)}}
+        done = 0 + 1000
+        d = sc.droplets()
+        for t in ("5000", "10000", "20000"):
+            lat.step(int(t) - done)
+            done = int(t)
+            r, _, _ = lat.fields()
+            rep = droplet_report(r.astype(np.float64), lat.kind() == 0, info["rho_g"], info["rho_l"],
+                                 sc.cx, sc.cy, sc.r, d["x0"], d["y0"], d["r0"])
+            M, M0, _ = lat.mass()
+            rep["mass_change"] = M / M0 - 1
+            e = report_errors(rep, refs["c2"]["reports"][t])
+            c2[f"steady_{t}"] = {k: (g3(v) if isinstance(v, float) else v) for k, v in e.items()}
+        out["c2_fp32"] = c2
+        del lat
+    if "c3" in refs:
+        ref = refs["c3"]
+        sc = S.c3_impact()
+        lat = G.Lattice(sc.physics(), precision=G.LBM_FP32)
+        lat.init_droplets(sc.droplets())
+        info = lat.eos_info()
+        mid = 0.5 * (info["rho_g"] + info["rho_l"])
+        xc = ref["x_line"]
+        dpos, dmass = 0.0, 0.0
+        for k, st in enumerate(ref["steps"]):
+            if k:
+                lat.step(st - ref["steps"][k - 1])
+            r, _, _ = lat.fields()
+            ys = isoline_crossings_column(r[:, xc].astype(np.float64), lat.kind()[:, xc] == 0, mid,
+                                          y_min=sc.cy[0] + sc.r[0] + 5.0)
+            M, M0, _ = lat.mass()
+            dpos = max(dpos, abs(ys[0] - ref["lower"][k]), abs(ys[-1] - ref["upper"][k]))
+            dmass = max(dmass, abs((M / M0 - 1) - ref["mass_change"][k]))
+        er, ev = sampled_errors(*lat.fields(), ref["fields_500"])
+        out["c3_fp32_500_steps"] = {"interface_lu": g3(dpos), "mass_change": g3(dmass), "rho": g3(er), "v": g3(ev)}
+        del lat
+    if "c5" in refs:
+        ref = refs["c5"]
+        sc = S.c5_adjoint()
+        cs = np.array([ref["complex_step"][k] for k in ref["order"]])
+        cd = np.array([ref["central_differences"][k] for k in ref["order"]])
+        c5 = {"steps": ref["steps"], "checkpoint_every": 200, "oracle_complex_vs_central": g3(np.max(np.abs(cd - cs) / np.abs(cs)))}
+        for name, prec in (("fp64", G.LBM_FP64), ("fp32", G.LBM_FP32)):
+            lat = G.Lattice(sc.physics(), precision=prec)
+            lat.init_droplets(sc.droplets())
+            lat.forward_checkpointed(ref["steps"], 200)
+            J, seed = lat.objective(0, seed=True)
+            g = np.asarray(lat.adjoint(drho=seed), dtype=np.float64)
+            c5[name] = {"J": g3(abs(J - ref["J"]) / abs(ref["J"])),
+                        "vs_complex_step": g3(np.max(np.abs(g - cs) / np.abs(cs))),
+                        "vs_central_differences": g3(np.max(np.abs(g - cd) / np.abs(cd)))}
+            del lat
+        out["c5_gradients"] = c5
+    torch.cuda.empty_cache()
+    return out
+
+
+def compact_paper_runs(pr):
+    """The paper runs' mass changes reduced to their range per scheme and angle."""
+    if pr is None:
+        return None
+    out = {"eos": pr["eos"], "flat_500x300": {"instances": pr["flat"]["instances"], "steps": pr["flat"]["steps"],
+                                              "mlups_batched": pr["flat"]["mlups_batched"]}}
+    for th in ("theta60", "theta120"):
+        for sch in ("present", "ibc"):
+            v = list(pr["flat"][th][sch].values())
+            out["flat_500x300"][f"{th}_{sch}_mass_change"] = [float(f"{min(v):.3g}"), float(f"{max(v):.3g}")]
+    out["curved_500x600"] = {f"{th}_{sch}_mass_change": float(f"{pr['curved'][th][sch]['mass_change']:.3g}")
+                             for th in ("theta60", "theta120") for sch in ("present", "ibc")}
+    film = pr.get("impact_film")
+    if film:
+        out["impact_film"] = {k: {kk: (v[kk] if kk != "h_star" else {t: h["h*"] for t, h in v[kk].items()})
+                                  for kk in ("U_i", "Re", "We", "mass_change", "h_star") if kk in v}
+                              for k, v in film.items()}
+    return out
+
+
+def compact_bc(bc):
+    if bc is None:
+        return None
+    out = {"steps": bc["steps"]}
+    for k, v in bc.items():
+        if k == "steps":
+            continue
+        if "present" in v:
+            out[k] = {sch: {"dM_late": float(f"{r['dM_late_mean_abs']:.3g}"), "max_speed": float(f"{r['max_speed']:.3g}")}
+                      for sch, r in v.items()}
+        else:
+            out[k] = {"dM_late": float(f"{v['dM_late_mean_abs']:.3g}"), "max_speed": float(f"{v['max_speed']:.3g}")}
+    return out
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -524,18 +641,41 @@ def oracle_rate(sc, max_seconds, max_steps, threads=None):
     return sc.nodes * n / dt / 1e6, n, O.get_threads()
 
 
+def l2_note(workload_name):
+    return ("flushed before every timed step" if workload_name == "c2"
+            else "working set (0.68 GB) larger than L2, no flush")
+
+
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands on the host cores, on the same workload:
+    `--warmup` untimed steps, then `--steps` timed ones (fewer if they would take more than 90 s;
+    the line says how many ran).  Rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    import oracle as O
     sc, wname = workload(args.workload)
-    rate, n, cores = oracle_rate(sc, max_seconds=90.0, max_steps=max(1, args.steps))
-    ms = sc.nodes / rate / 1e3
-    sample = f"{n} of the {args.steps} requested steps of the full {sc.nx}x{sc.ny} lattice, FP64, {cores} threads"
+    O.build()
+    o = O.Oracle(O.OracleConfig(**sc.physics()))
+    d = sc.droplets()
+    o.init_droplets(d["x0"], d["y0"], d["r0"], d["width"], d["ux0"], d["uy0"])
+    t0 = time.perf_counter()
+    o.step(1)
+    per = time.perf_counter() - t0
+    warm = max(0, min(args.warmup - 1, int(30.0 / max(per, 1e-6))))
+    o.step(warm)
+    n = max(1, min(args.steps, int(90.0 / max(per, 1e-6))))
+    t0 = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t0
+    rate = sc.nodes * n / dt / 1e6
+    cores = O.get_threads()
+    sample = (f"{n} of the {args.steps} requested steps of the full {sc.nx}x{sc.ny} lattice after {warm + 1} "
+              f"untimed ones, FP64, {cores} threads")
     line = {"metric": METRIC, "value": round(rate, 3), "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
-            "steps": n, "warmup": 1, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wname, "nodes": sc.nodes},
+            "steps": n, "warmup": warm + 1, "ms_per_step": round(dt / n * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(sc, wname, l2_note(args.workload)),
             "cpu_baseline": {"value": round(rate, 3), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": round(rate, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -565,6 +705,8 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=4000,
                     help="steps of the gradient workload (0: skip it)")
     ap.add_argument("--adjoint-every", type=int, default=200)
+    ap.add_argument("--accuracy", type=int, default=1,
+                    help="1: FP32/FP64 against the oracle's stored full-size results (c2, c3, c5); 0: skip")
     ap.add_argument("--mode", default="full", choices=["full", "kernels", "adjoint"],
                     help="kernels: only warm-up and timed steps; adjoint: only the gradient "
                          "workload (both for profiler captures)")
@@ -594,9 +736,24 @@ def main():
         return
 
     sc, wname = workload(args.workload)
-    lat = G.Lattice(sc.physics(), precision=G.LBM_FP32)
-    lat.init_droplets(sc.droplets())
-    counts = lat.counts()
+    # one lattice on one GPU, or its y-slabs on several (each rank its own rows plus halos
+    # refreshed every SLAB_EXCHANGE_EVERY steps over NCCL)
+    dslab = None
+    if world > 1:
+        from paper_2203_04508_gb300.slab import DistSlab
+        dslab = DistSlab(sc.physics(), rank, world, halo=8 * SLAB_EXCHANGE_EVERY, precision=G.LBM_FP32,
+                         steps_per_exchange=SLAB_EXCHANGE_EVERY)
+        dslab.init_droplets(sc.droplets())
+        lat = dslab.slab
+        counts = {"fluid": None, "links": None}
+        args.steps = max(SLAB_EXCHANGE_EVERY, args.steps // SLAB_EXCHANGE_EVERY * SLAB_EXCHANGE_EVERY)
+        args.warmup = max(SLAB_EXCHANGE_EVERY, -(-args.warmup // SLAB_EXCHANGE_EVERY) * SLAB_EXCHANGE_EVERY)
+        advance = dslab.step
+    else:
+        lat = G.Lattice(sc.physics(), precision=G.LBM_FP32)
+        lat.init_droplets(sc.droplets())
+        counts = lat.counts()
+        advance = lat.step
     if args.mode == "kernels":
         for _ in range(args.warmup + args.steps):
             lat.step(1)
@@ -611,7 +768,7 @@ def main():
     if args.workload == "c2":
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    lat.step(args.warmup)
+    advance(args.warmup)
     lat.synchronize()
     if world > 1:
         dist.barrier()
@@ -623,7 +780,7 @@ def main():
     if flush is None:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s)
-        lat.step(args.steps)
+        advance(args.steps)
         e1.record(s)
         e1.synchronize()
         ms_total = e0.elapsed_time(e1)
@@ -646,26 +803,30 @@ def main():
         ms_total = float(t.item())
         dist.barrier()
     ms_step = ms_total / args.steps
-    value = world * sc.nodes * args.steps / (ms_total / 1e3) / 1e6
+    # the whole lattice's nodes: one lattice on one GPU, or shared out as slabs
+    value = sc.nodes * args.steps / (ms_total / 1e3) / 1e6
 
-    # dominant kernel: per-phase CUDA-event times on the library's stream
-    n_prof = max(10, min(200, args.steps // 10))
-    phase_ms = lat.profile_steps(n_prof) / n_prof
-    collide_ms = float(phase_ms[3])
+    # dominant kernel: per-phase CUDA-event times on the library's stream (rank 0's lattice or slab)
     peak, peak_src = measured_peak()
-    coll_bytes = COLLIDE_BYTES_PER_FLUID_NODE * counts["fluid"] + COLLIDE_BYTES_PER_NODE * sc.nodes
-    achieved = coll_bytes / (collide_ms / 1e3) / 1e9
-    traffic = recorded_traffic(args.workload)
+    n_prof = max(10, min(200, args.steps // 10))
+    if world == 1:
+        phase_ms = lat.profile_steps(n_prof) / n_prof
+        collide_ms = float(phase_ms[3])
+        coll_bytes = COLLIDE_BYTES_PER_FLUID_NODE * counts["fluid"] + COLLIDE_BYTES_PER_NODE * sc.nodes
+        achieved = coll_bytes / (collide_ms / 1e3) / 1e9
+        traffic = recorded_traffic(args.workload)
+        M, M0, _ = lat.mass()
+    else:
+        M, M0, _ = dslab.mass()
     step_eff = STEP_BYTES_PER_NODE * sc.nodes / (ms_step / 1e3) / 1e9
-    M, M0, _ = lat.mass()
-    del lat
+    del lat, dslab
     torch.cuda.empty_cache()
 
     # end to end through the public API with host buffers: set-up from host inputs, every step
     # one C-ABI call plus an 8-byte copy of its compensation sum into page-locked host memory
     # (queued, not waited for), fields back to the host at the end
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and world == 1:
         n_e2e = args.steps                # the workload the device-timed value measures
         # the caller's page-locked host buffers, made before the clock starts
         dm = torch.empty(n_e2e, dtype=torch.float64, pin_memory=True)
@@ -681,15 +842,18 @@ def main():
         dt = time.perf_counter() - t0
         h2d = 8 * (4 * len(sc.r) + 5 * len(sc.r0)) + 4
         d2h_fields = 3 * sc.nodes * 4
-        e2e = {"value": round(world * sc.nodes * n_e2e / dt / 1e6, 2), "unit": UNIT,
+        e2e = {"value": round(sc.nodes * n_e2e / dt / 1e6, 2), "unit": UNIT,
                "h2d_bytes_per_step": round(h2d / n_e2e, 2),
                "d2h_bytes_per_step": round(8 + d2h_fields / n_e2e, 2), "steps": n_e2e}
         del lat2
 
+    single = world == 1 and rank == 0
+    accuracy = run_accuracy(G, torch) if (single and args.accuracy) else None
+
     # the same workload with FP64 populations and arithmetic (the oracle's precision), for the
     # FP32-versus-FP64 throughput; GB300's FP64 rate is a small fraction of its FP32 rate
     fp64 = None
-    if args.fp64_steps > 0:
+    if args.fp64_steps > 0 and single:
         lat64 = G.Lattice(sc.physics(), precision=G.LBM_FP64)
         lat64.init_droplets(sc.droplets())
         lat64.step(10)
@@ -704,10 +868,9 @@ def main():
                 "MLUPS": round(sc.nodes / ms64 / 1e3, 1), "fp32_over_fp64": round(ms64 / ms_step, 2)}
         del lat64
         torch.cuda.empty_cache()
-        if args.precision_steps > 0 and rank == 0 and args.workload == "c3":
+        if args.precision_steps > 0 and args.workload == "c3":
             fp64["fp32_vs_fp64"] = run_precision_comparison(G, torch, sc, args.precision_steps)
-        if rank == 0:
-            fp64["c1_128x128"] = run_c1_mass(G)
+        fp64["c1_128x128"] = run_c1_mass(G)
 
     batched = None
     if args.batch_steps > 0:
@@ -730,25 +893,25 @@ def main():
                                                                  "schedule")}
             batched["small_instances"]["sizes"] = "64^2..128^2"
 
-    bc_comparison = None
-    if args.bc_steps > 0 and rank == 0:
-        bc_comparison = run_bc_comparison(G, max(1000, args.bc_steps // 1000 * 1000))
+    adjoint = None
+    if args.adjoint_steps > 0 and single:
+        adjoint = run_adjoint(G, torch, args.adjoint_steps, args.adjoint_every)
 
     pseudo = None
-    if args.pseudo_steps > 0 and rank == 0:
+    if args.pseudo_steps > 0 and single:
         pseudo = run_pseudopotential(G, torch, args.pseudo_steps, ms_step)
 
+    bc_comparison = None
+    if args.bc_steps > 0 and single:
+        bc_comparison = run_bc_comparison(G, max(1000, args.bc_steps // 1000 * 1000))
+
     paper_runs = None
-    if args.paper_runs and rank == 0:
+    if args.paper_runs and single:
         paper_runs = run_paper_runs(G, torch)
         paper_runs["impact_film"] = run_film(G, torch)
 
-    adjoint = None
-    if args.adjoint_steps > 0:
-        adjoint = run_adjoint(G, torch, args.adjoint_steps, args.adjoint_every)
-
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if single and not args.no_cpu_baseline:
         rate, n, cores = oracle_rate(sc, max_seconds=20.0, max_steps=50)
         rate1, n1, _ = oracle_rate(sc, max_seconds=8.0, max_steps=50, threads=1)
         import oracle as O
@@ -758,30 +921,40 @@ def main():
                "single_thread": {"value": round(rate1, 3), "cores": 1, "sample": f"{n1} steps"}}
 
     if rank == 0:
+        l2 = l2_note(args.workload)
+        if world == 1:
+            roof = {"bound": "hbm", "kernel": collide_name,
+                    "achieved": round(achieved, 1), "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "traffic": traffic,
+                    "algorithmic_bytes_per_launch": coll_bytes, "launch_ms": round(collide_ms, 5),
+                    "step_effective_GBs": round(step_eff, 1), "step_effective_frac": round(step_eff / peak, 4),
+                    "phase_ms": {k: round(float(v), 5) for k, v in
+                                 zip(("rho", "solid", "mu", "collide", "bc"), phase_ms)}}
+        else:
+            # several GPUs: the whole step's effective bandwidth over all of them
+            roof = {"bound": "hbm", "kernel": "whole step (y-slabs)", "achieved": round(step_eff, 1),
+                    "peak": round(peak * world, 1), "peak_source": peak_src, "unit": "GB/s",
+                    "frac": round(step_eff / (peak * world), 4), "traffic": None}
         line = {
-            "metric": METRIC, "value": round(value, 2), "unit": UNIT,
-            "value_fluid_nodes": round(value * counts["fluid"] / sc.nodes, 2), "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True,
+            "scaling": "weak" if world == 1 else "strong",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wname, "nodes": sc.nodes, "fluid_nodes": counts["fluid"],
-                       "cut_links": counts["links"], "parallelism": f"replicas x{world}",
-                       "l2": "flushed before every timed step" if flush is not None else
-                             "working set (0.68 GB) larger than L2, no flush"},
-            "roofline": {"bound": "hbm", "kernel": collide_name,
-                         "achieved": round(achieved, 1), "peak": peak, "peak_source": peak_src, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "algorithmic_bytes_per_launch": coll_bytes, "launch_ms": round(collide_ms, 5),
-                         "step_effective_GBs": round(step_eff, 1),
-                         "step_effective_frac": round(step_eff / peak, 4),
-                         "phase_ms": {k: round(float(v), 5) for k, v in
-                                      zip(("rho", "solid", "mu", "collide", "bc"), phase_ms)}},
-            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": lps * args.steps,
-            "fp64": fp64,
+            "config": workload_config(sc, wname, l2),
+            "parallelism": "one lattice on one GPU" if world == 1 else
+                           f"one lattice in {world} y-slabs (halo {8 * SLAB_EXCHANGE_EVERY} rows, exchanged every "
+                           f"{SLAB_EXCHANGE_EVERY} steps over NCCL)",
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": lps * args.steps,
+            "accuracy": accuracy,
             "batched": batched,
             "adjoint": adjoint,
-            "bc_comparison": bc_comparison,
-            "paper_runs": paper_runs,
-            "pseudopotential": pseudo,
+            "fp64": fp64,
+            "pseudopotential": None if pseudo is None else {k: pseudo[k] for k in ("ms_per_step", "mlups",
+                                                                                    "step_time_vs_chemical_potential")}
+                               | {"collide_frac": pseudo["roofline"]["frac"]},
+            "bc_comparison": compact_bc(bc_comparison),
+            "paper_runs": compact_paper_runs(paper_runs),
+            "value_fluid_nodes": None if counts["fluid"] is None else round(value * counts["fluid"] / sc.nodes, 2),
             "mass_drift": M / M0 - 1,
         }
         print(json.dumps(line), flush=True)
