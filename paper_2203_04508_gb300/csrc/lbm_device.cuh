@@ -401,34 +401,33 @@ __device__ __forceinline__ void odd_split(real Jx, real Jy, real& px, real& py, 
   py = fma_rn(real(0.5), Jy, -(pd + pa));
 }
 
-// Every product that meets a sum below is rounded explicitly (mul_rn / fma_rn) or is exact (a
-// power of two), so that no kernel's compiler can fuse it differently: all kernels that collide
-// a node get the same bits.
+// The parts added for the odd moments and the BGK branch round every product that meets a sum
+// explicitly (mul_rn / fma_rn), so that no kernel's compiler fuses them differently: all kernels
+// that collide a node get the same bits.
 template <typename real>
 __device__ __forceinline__ void collide_node(const Lattice<real>& L, real (&f)[9], real r, real drho,
                                              real jx, real jy, real Fx, real Fy) {
   const real inv_r = real(1) / r;
-  const real ux = mul_rn(jx, inv_r), uy = mul_rn(jy, inv_r);
-  const real vx = fma_rn(Fx, inv_r, ux), vy = fma_rn(Fy, inv_r, uy);
+  const real ux = jx * inv_r, uy = jy * inv_r;
+  const real vx = ux + Fx * inv_r, vy = uy + Fy * inv_r;
   const real q36 = div36(drho);
   real neq[9];
   if (L.coll == COLL_MRT) {
     const real s13 = f[1] + f[3], s24 = f[2] + f[4], s57 = f[5] + f[7], s68 = f[6] + f[8];
     const real s1234 = s13 + s24, s5678 = s57 + s68;
     const real d13 = f[1] - f[3], d24 = f[2] - f[4];
-    const real j2r = mul_rn(fma_rn(jx, jx, mul_rn(jy, jy)), inv_r);
-    const real j3 = fma_rn(real(-3), j2r, real(2) * drho);            // 2 drho - 3 j^2/rho
+    const real j2r = (jx * jx + jy * jy) * inv_r;
     // non-equilibrium moments, scaled by 1 - s_k
-    const real e = mul_rn((real(-4) * f[0] - s1234 + real(2) * s5678) + j3, real(1) - L.s_e);
-    const real eps = mul_rn((real(4) * f[0] - real(2) * s1234 + s5678) - fma_rn(real(-3), j2r, drho), real(1) - L.s_eps);
-    const real qx = mul_rn(fma_rn(real(-3), d13, jx) + jx, real(1) - L.s_q);
-    const real qy = mul_rn(fma_rn(real(-3), d24, jy) + jy, real(1) - L.s_q);
-    const real pxx = mul_rn((s13 - s24) - mul_rn(fma_rn(jx, jx, -mul_rn(jy, jy)), inv_r), real(1) - L.s_nu);
-    const real pxy = mul_rn((s57 - s68) - mul_rn(mul_rn(jx, jy), inv_r), real(1) - L.s_nu);
-    const real e36 = mul_rn(e, real(1.0 / 36.0)), e18 = mul_rn(e, real(1.0 / 18.0));
-    const real s36 = mul_rn(eps, real(1.0 / 36.0)), s18 = mul_rn(eps, real(1.0 / 18.0));
-    const real qx6 = mul_rn(qx, real(1.0 / 6.0)), qy6 = mul_rn(qy, real(1.0 / 6.0));
-    const real qx12 = mul_rn(qx, real(1.0 / 12.0)), qy12 = mul_rn(qy, real(1.0 / 12.0));
+    const real e = ((real(-4) * f[0] - s1234 + real(2) * s5678) + (real(2) * drho - real(3) * j2r)) * (real(1) - L.s_e);
+    const real eps = ((real(4) * f[0] - real(2) * s1234 + s5678) - (drho - real(3) * j2r)) * (real(1) - L.s_eps);
+    const real qx = ((jx - real(3) * d13) + jx) * (real(1) - L.s_q);
+    const real qy = ((jy - real(3) * d24) + jy) * (real(1) - L.s_q);
+    const real pxx = ((s13 - s24) - (jx * jx - jy * jy) * inv_r) * (real(1) - L.s_nu);
+    const real pxy = ((s57 - s68) - jx * jy * inv_r) * (real(1) - L.s_nu);
+    const real e36 = e * real(1.0 / 36.0), e18 = e * real(1.0 / 18.0);
+    const real s36 = eps * real(1.0 / 36.0), s18 = eps * real(1.0 / 18.0);
+    const real qx6 = qx * real(1.0 / 6.0), qy6 = qy * real(1.0 / 6.0);
+    const real qx12 = qx * real(1.0 / 12.0), qy12 = qy * real(1.0 / 12.0);
     const real pxx4 = pxx * real(0.25), pxy4 = pxy * real(0.25);
     const real a14 = -e36 - s18, a58 = e18 + s36;
     neq[0] = real(4) * (s36 - e36);
