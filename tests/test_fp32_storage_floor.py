@@ -1,5 +1,5 @@
-"""FP32 storage alone is not the accuracy floor of the FP32 path (the benchmark spec: 1e-5 on rho and u
-after 1000 steps): the FP64 oracle whose populations are rounded to FP32 in offset form
+"""FP32 storage alone is not the accuracy floor of the FP32 path (asked: 1e-5 on rho and u after
+1000 steps): the FP64 oracle whose populations are rounded to FP32 in offset form
 (f_i - w_i rho_g, as the GPU stores them) after every step stays within 1e-5 of the plain
 oracle after 1000 steps.  Whatever error the GPU's FP32 path has beyond this comes from its
 arithmetic (which the GPU parity tests bound), not from the storage format."""

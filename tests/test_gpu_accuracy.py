@@ -9,8 +9,8 @@ by tests/golden/make_accuracy_refs.py, which runs the oracle only).
       per step (populations, density, chemical potential, force, velocity) reaches 1.8e-5 in
       rho by itself, so the bars are 2.5e-5 and 2e-5;
     - at 5000, 10000 and 20000 steps, the steady-state measures: every drop's liquid density,
-      the gas density and every contact angle within 1e-3 relative (the benchmark spec's steady-
-      state bar); the mass change within 1e-6 of the oracle's.
+      the gas density and every contact angle within 1e-3 relative (the steady-state
+      accuracy asked of the FP32 path); the mass change within 1e-6 of the oracle's.
   c3 (2048 x 4096 drop impact, FP32): the drop's lower and upper interface on the line
     through the cylinder centre every 100 steps up to 500 (1e-3 lu), the mass change (1e-6),
     and rho, v after 500 steps at 1024 seeded nodes (5e-5 and 1e-5; measured 3.6e-5 and 6.7e-6).
