@@ -55,7 +55,7 @@ struct Layout {
   long long plane;
   size_t sz;
   Caps cap;
-  size_t fA, fB, rho, rho2, mu, mu2, psip, kind, body;
+  size_t fA, fB, rho, rho2, mu, mu2, psip, kind, body, near;
   size_t lq64, lq, ldir, lx2f, bnode, bstart, carry, rhob;
   size_t s1node, s1mask, s1winv, s1nb, s2node, s2mask, s2winv;
   size_t cyl, drops, partials, counter, step_ctr, scalars, kerr, dm_ring, block_sums, totals;
@@ -76,7 +76,9 @@ Layout make_layout(const lbm_config* c) {
   L.rho = take(L.plane * L.sz);
   L.rho2 = take(L.plane * L.sz);
   L.mu = take(L.plane * L.sz);
-  L.mu2 = take(c->force_model == LBM_FORCE_PSEUDO ? L.plane * L.sz : 0);   // the second psi plane
+  // the second psi plane (pseudopotential force), or the second mu plane of the FP32 step that
+  // forms mu with the next state's density
+  L.mu2 = take(c->force_model == LBM_FORCE_PSEUDO || c->precision == LBM_FP32 ? L.plane * L.sz : 0);
   L.psip = take(L.plane * L.sz);
   L.kind = take(L.plane);
   L.body = take(L.plane * 4);
@@ -95,6 +97,9 @@ Layout make_layout(const lbm_config* c) {
   L.s2node = take(L.cap.s2 * 4);
   L.s2mask = take(L.cap.s2);
   L.s2winv = take(L.cap.s2 * L.sz);
+  // fluid nodes whose chemical-potential stencil reaches a solid or boundary node: each solid-layer
+  // or boundary node is in the stencils of at most 9 nodes
+  L.near = take((size_t)9 * (L.cap.bnodes + L.cap.s1 + L.cap.s2) * 4);
   L.cyl = take((size_t)(c->n_cyl > 0 ? c->n_cyl : 1) * 4 * 8);
   L.drops = take((size_t)MAX_DROPS * 5 * 8);
   size_t nparts = 2 * (size_t)mass_blocks();
@@ -145,6 +150,7 @@ struct lbm_ctx {
   int collide_kind = 1;
   long long spin_limit = 1LL << 22;   // polls before a pipelined kernel's wait gives up
   int mu_kind = -1;                   // chemical-potential pass (-1: the precision's default)
+  long long n_near = 0;               // entries of the near list (lbm_build_links)
   lbm_status sticky = LBM_OK;
   std::string err;
   // one segment's recomputation (kind 0) or reverse steps (kind 1), captured once per
@@ -206,17 +212,25 @@ lbm_status fail(lbm_ctx* c, lbm_status s, const char* fmt, ...) {
       return fail(ctx, LBM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));           \
   } while (0)
 
-// The chemical-potential pass by default: row sweeps (FP32) where their grid of 512-node strips
-// x 16-row sweeps fills the GPU four times over, else row vectors (a 512 x 512 lattice gives
-// the sweeps only 32 blocks).
+// The chemical-potential pass by default (FP32): mu formed with the next state's density in one
+// tiled pass (kind 3) where both population lattices fit in L2 -- there the step is bound by its
+// launches and by the chemical-potential pass's latency, and dropping that pass pays (1024 x 1024:
+// 0.0446 against 0.0569 ms a step); on larger lattices the separate passes are faster (2048 x
+// 4096: 0.2107 against 0.2255 ms), the row sweeps (kind 2) where their grid of 512-node strips x
+// 16-row sweeps fills the GPU four times over, else row vectors (a 512 x 512 lattice gives the
+// sweeps only 32 blocks).  FP64: row vectors.
 int default_mu_kernel(const lbm_ctx* c) {
   if (c->fp64) return 1;
-  const long long blocks = (long long)((c->cfg.nx + 511) / 512) * ((c->cfg.ny + 15) / 16);
-  int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+  int dev = 0, sms = 0, l2 = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess) {
     (void)cudaGetLastError();
     sms = 152;
+    l2 = 0;
   }
+  const bool chempot = c->cfg.force_model == LBM_FORCE_CHEMPOT && c->cfg.eos != LBM_EOS_NONE;
+  if (chempot && 72.0 * c->cfg.nx * c->cfg.ny <= (double)l2) return 3;
+  const long long blocks = (long long)((c->cfg.nx + 511) / 512) * ((c->cfg.ny + 15) / 16);
   return blocks >= 4LL * sms ? 2 : 1;
 }
 
@@ -301,6 +315,8 @@ void fill_lattice(lbm_ctx* c, Lattice<real>& L) {
   L.kerr = (unsigned int*)(w + y.kerr);
   L.spin_limit = c->spin_limit;
   L.mu_kernel = c->mu_kind >= 0 ? c->mu_kind : default_mu_kernel(c);
+  L.n_near = (int)c->n_near;
+  L.near_list = (const int*)(w + y.near);
   L.tma = nullptr;
   if constexpr (sizeof(real) == 4) {
     if (c->tma_ok && c->collide_kind == 1) L.tma = &c->tma;
@@ -375,15 +391,16 @@ void step_lattices(const lbm_ctx* c, const Lattice<real>& L, int cur, Lattice<re
   Lt = L;
   Lt.rho = planes[cur];
   Lt.rho_b = (real*)(c->ws + c->lay.rhob);
-  if (c->cfg.force_model == LBM_FORCE_PSEUDO) {
-    // psi alternates like the density: the next state's is formed while the boundary phase
-    // still reads this one's
-    real* psi[2] = {(real*)(c->ws + c->lay.mu), (real*)(c->ws + c->lay.mu2)};
-    Lt.mu = psi[cur];
+  // psi (pseudopotential force) and mu formed with the density alternate like the density: the
+  // next state's is formed while the boundary phase still reads this one's
+  const bool alt = c->cfg.force_model == LBM_FORCE_PSEUDO || L.mu_kernel == 3;
+  if (alt) {
+    real* m[2] = {(real*)(c->ws + c->lay.mu), (real*)(c->ws + c->lay.mu2)};
+    Lt.mu = m[cur];
   }
   Ln = Lt;
   Ln.rho = planes[cur ^ 1];
-  if (c->cfg.force_model == LBM_FORCE_PSEUDO) Ln.mu = (real*)(c->ws + (cur ? c->lay.mu : c->lay.mu2));
+  if (alt) Ln.mu = (real*)(c->ws + (cur ? c->lay.mu : c->lay.mu2));
 }
 
 // Steps in the longest step graph (even, so that a launch keeps the lattice parity): fewer
@@ -404,6 +421,8 @@ lbm_status do_step(lbm_ctx* c, const Lattice<real>& L, long long n) {
     step_lattices(c, L, c->cur, Lt, Ln);
     CUDA_OK(c, launch_phase(Lt, c->cur, 0, c->stream));
     CUDA_OK(c, launch_phase(Lt, c->cur, 1, c->stream));
+    // the step that forms mu with the next density starts from this state's mu
+    if (L.mu_kernel == 3) CUDA_OK(c, launch_phase(Lt, c->cur, 2, c->stream));
     c->rho_ok = true;
   }
   // graphs of two steps (slot p), one step (slot 2 + p) and STEPS_LONG steps (slot 4 + p) from
@@ -558,11 +577,50 @@ lbm_status slab_ranges(lbm_ctx* c) {
   return LBM_OK;
 }
 
+// The fluid nodes whose chemical-potential stencil (the node and two nodes each way along the
+// axes) reaches a solid node or a boundary node: the fused density + mu pass cannot finish them,
+// since those densities come from the solid-layer kernels and the boundary phase.
+lbm_status near_list(lbm_ctx* c) {
+  const Layout& y = c->lay;
+  const int nx = c->cfg.nx, ny = c->cfg.ny, P = y.pitch;
+  std::vector<uint8_t> kind(y.plane);
+  std::vector<int> bnode(c->n_bnodes > 0 ? c->n_bnodes : 1);
+  CUDA_OK(c, cudaMemcpy(kind.data(), c->ws + y.kind, y.plane, cudaMemcpyDeviceToHost));
+  if (c->n_bnodes > 0) CUDA_OK(c, cudaMemcpy(bnode.data(), c->ws + y.bnode, c->n_bnodes * 4, cudaMemcpyDeviceToHost));
+  std::vector<uint8_t> ok(y.plane, 0);   // fluid and not a boundary node
+  for (long long n = 0; n < y.plane; ++n) ok[n] = kind[n] == KIND_FLUID;
+  for (long long b = 0; b < c->n_bnodes; ++b) ok[bnode[b]] = 0;
+  std::vector<int> list;
+  for (int yy = 0; yy < ny; ++yy) {
+    for (int x = 0; x < nx; ++x) {
+      const long long n = (long long)yy * P + x;
+      if (kind[n] != KIND_FLUID) continue;
+      bool near = !ok[n];
+      for (int d = -2; d <= 2 && !near; ++d) {
+        if (d == 0) continue;
+        const int xx = ((x + d) % nx + nx) % nx;
+        int y2 = yy + d;
+        if (!c->cfg.walls) y2 = (y2 % ny + ny) % ny;
+        near = !ok[(long long)yy * P + xx] || y2 < 0 || y2 >= ny || !ok[(long long)y2 * P + x];
+      }
+      if (near) list.push_back((int)n);
+    }
+  }
+  const long long cap = 9LL * (y.cap.bnodes + y.cap.s1 + y.cap.s2);
+  if ((long long)list.size() > cap)
+    return fail(c, LBM_ENOMEM, "near-boundary list of %zu nodes exceeds its capacity %lld", list.size(), cap);
+  if (!list.empty())
+    CUDA_OK(c, cudaMemcpy(c->ws + y.near, list.data(), list.size() * 4, cudaMemcpyHostToDevice));
+  c->n_near = (long long)list.size();
+  return LBM_OK;
+}
+
 // the current density plane and EOS plane (psi'(rho) - mu_sat, or psi) a step starts from
 template <typename real>
 void slab_planes(const lbm_ctx* c, real** rho, real** aux) {
   *rho = (real*)(c->ws + (c->cur ? c->lay.rho2 : c->lay.rho));
-  if (c->cfg.force_model == LBM_FORCE_PSEUDO) *aux = (real*)(c->ws + (c->cur ? c->lay.mu2 : c->lay.mu));
+  const int mk = c->fp64 ? c->Ld.mu_kernel : c->Lf.mu_kernel;
+  if (c->cfg.force_model == LBM_FORCE_PSEUDO || mk == 3) *aux = (real*)(c->ws + (c->cur ? c->lay.mu2 : c->lay.mu));
   else *aux = (real*)(c->ws + c->lay.psip);
 }
 
@@ -786,6 +844,12 @@ lbm_status lbm_build_links(lbm_ctx* c) {
     lbm_status st = slab_ranges(c);
     if (st != LBM_OK) return st;
   }
+  {
+    lbm_status st = near_list(c);
+    if (st != LBM_OK) return st;
+  }
+  // the second mu plane starts with the walls' constant chemical potential as the first
+  if (!c->fp64) CUDA_OK(c, cudaMemcpyAsync(w + y.mu2, w + y.mu, y.plane * y.sz, cudaMemcpyDeviceToDevice, c->stream));
   c->built = true;
   c->inited = false;
   c->rho_ok = false;
@@ -795,8 +859,7 @@ lbm_status lbm_build_links(lbm_ctx* c) {
   if (!c->fp64) {
     // the pipelined collide kernel's descriptors; without them the plain kernel runs
     char msg[256] = {0};
-    c->tma_ok = collide_tma_setup(&c->tma, c->Lf, w + y.rho, w + y.rho2,
-                                  w + (g.force_model == LBM_FORCE_PSEUDO ? y.mu2 : y.mu), msg);
+    c->tma_ok = collide_tma_setup(&c->tma, c->Lf, w + y.rho, w + y.rho2, w + y.mu2, msg);
     // the pipeline pays off once each persistent block has enough tiles to stream (measured:
     // 43 tiles per block 10 % faster than the plain kernel, 5 tiles per block 7 % slower)
     const long long tiles = (long long)((g.nx + 31) / 32) * ((g.ny + 7) / 8);
@@ -932,9 +995,12 @@ lbm_status lbm_set_spin_limit(lbm_ctx* c, int64_t polls) {
 
 lbm_status lbm_set_mu_kernel(lbm_ctx* c, int32_t kind) {
   if (!c || !c->built) return LBM_ESTATE;
-  if (kind < 0 || kind > 2) return fail(c, LBM_EINVAL, "chemical-potential kernel must be 0, 1 or 2");
-  if (kind == 2 && c->fp64) return fail(c, LBM_EINVAL, "the row-sweep chemical-potential kernel is FP32 only");
+  if (kind < 0 || kind > 3) return fail(c, LBM_EINVAL, "chemical-potential kernel must be 0, 1, 2 or 3");
+  if (kind >= 2 && c->fp64) return fail(c, LBM_EINVAL, "the row-sweep and fused chemical-potential kernels are FP32 only");
+  if (kind == 3 && (c->cfg.force_model != LBM_FORCE_CHEMPOT || c->cfg.eos == LBM_EOS_NONE))
+    return fail(c, LBM_EINVAL, "the fused chemical-potential kernel needs the chemical-potential force");
   c->mu_kind = kind;
+  c->rho_ok = false;   // a change to or from the fused pass moves where mu is kept
   for (auto& gr : c->graph)
     if (gr) { cudaGraphExecDestroy(gr); gr = nullptr; }
   for (auto& a : c->adj_graphs) cudaGraphExecDestroy(a.exec);

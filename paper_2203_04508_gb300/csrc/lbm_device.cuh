@@ -86,7 +86,10 @@ struct Lattice {
   long long spin_limit;         // polls before a pipelined kernel's wait for its loads gives up
                                 // (its wait for copies in flight before leaving keeps the full limit)
   int mu_kernel;                // host side: the chemical-potential pass (0 per node, 1 row
-                                // vectors, 2 row sweeps, FP32 only)
+                                // vectors, 2 row sweeps, FP32 only; 3: formed with the next
+                                // state's density in one tiled pass, then near_list fixed up)
+  int n_near;                   // fluid nodes whose chemical-potential stencil reaches a solid or
+  const int* near_list;         // a boundary node (their mu waits for the boundary phase)
   const void* tma;              // host side: TMA descriptors of the pipelined collide kernel
                                 // (FP32), null for the plain kernel
   // y-slab of a larger lattice: local row y is global row y + y_off (mod ny_glob when ny_glob >

@@ -266,6 +266,115 @@ __global__ void __launch_bounds__(MU_BLOCK) k_mu_sweep(Lattice<float> L) {
   }
 }
 
+// The next state's density and chemical potential in one pass (FP32, chemical-potential force;
+// lbm_set_mu_kernel 3).  A block takes a tile of RM_W x RM_H nodes: it forms the density of the
+// tile and a halo of RM_HX columns and RM_HY rows from the populations into shared memory
+// (16-byte loads; wrapped or scalar at the lattice's edges), stores the tile's fluid densities,
+// and then each thread walks one column of the tile, evaluating Eq. 12 from the staged
+// densities -- psi'(rho) - mu_sat by psi_prime_shifted, the Laplacian by lap4_of, mu by mu_of,
+// the operations of the density and chemical-potential passes, so the values are theirs.  The
+// halo densities are those of the populations as they are now; where a node's stencil reaches
+// a boundary node (whose populations the boundary phase is still changing) or a solid node
+// (whose density the solid-layer kernels form), its mu is recomputed from the final density
+// plane by k_mu_near after the boundary phase.  Saves the chemical-potential pass at the start
+// of the next step.
+constexpr int RM_W = 256, RM_H = 32, RM_HX = 4, RM_HY = 2;
+constexpr int RM_SW = RM_W + 2 * RM_HX, RM_SH = RM_H + 2 * RM_HY;
+static_assert(RM_HX % 4 == 0 && RM_HX >= 2 && RM_HY >= 2, "the halo covers the stencil in whole vectors");
+__global__ void __launch_bounds__(NODE_BLOCK) k_rho_mu_tile(Lattice<float> L, int cur) {
+  __shared__ __align__(16) float s_rho[RM_SH][RM_SW];
+  __shared__ __align__(16) uint8_t s_kind[RM_H][RM_W];   // the tile's node classes, for the second phase
+  const int x0 = blockIdx.x * RM_W, y0 = blockIdx.y * RM_H;
+  const float* __restrict__ f = L.f[cur];
+  constexpr int GX = RM_SW / 4;
+  for (int g = threadIdx.x; g < GX * RM_SH; g += NODE_BLOCK) {
+    const int gy = g / GX, gx = g - gy * GX;
+    const int y = y0 - RM_HY + gy, xs = x0 - RM_HX + 4 * gx;
+    // rows beyond a wall read as zero; a periodic lattice wraps (however small it is)
+    int yy = y;
+    bool row_ok = true;
+    if (yy < 0 || yy >= L.ny) {
+      if (L.walls) row_ok = false;
+      else yy = ((yy % L.ny) + L.ny) % L.ny;
+    }
+    float r[4] = {0.f, 0.f, 0.f, 0.f};
+    if (row_ok) {
+      const int rb = yy * L.pitch;
+      if (xs >= 0 && xs + 4 <= L.nx) {
+        float4 fv[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fv[i] = __ldg(reinterpret_cast<const float4*>(f + i * L.plane + rb + xs));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          float fl[9];
+#pragma unroll
+          for (int i = 0; i < 9; ++i) fl[i] = lane_of<float>(fv[i], k);
+          r[k] = density_of(L, fl);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int x = ((xs + k) % L.nx + L.nx) % L.nx;   // x is periodic
+          float fl[9];
+#pragma unroll
+          for (int i = 0; i < 9; ++i) fl[i] = f[i * L.plane + rb + x];
+          r[k] = density_of(L, fl);
+        }
+      }
+    }
+    *reinterpret_cast<float4*>(&s_rho[gy][4 * gx]) = make_float4(r[0], r[1], r[2], r[3]);
+    // the tile's own fluid densities (a solid node's slot belongs to the solid-layer kernels,
+    // which may be writing it now: vectors with one take the scalar path)
+    if (gy >= RM_HY && gy < RM_HY + RM_H && gx >= RM_HX / 4 && gx < (RM_HX + RM_W) / 4) {
+      uchar4 kd = make_uchar4(KIND_PAD, KIND_PAD, KIND_PAD, KIND_PAD);
+      if (y < L.ny && xs < L.nx) kd = __ldg(reinterpret_cast<const uchar4*>(L.kind + y * L.pitch + xs));
+      *reinterpret_cast<uchar4*>(&s_kind[gy - RM_HY][xs - x0]) = kd;
+    }
+    if (gy >= RM_HY && gy < RM_HY + RM_H && gx >= RM_HX / 4 && gx < (RM_HX + RM_W) / 4 && y < L.ny && xs < L.nx) {
+      const int n0 = y * L.pitch + xs;
+      const uchar4 kd = *reinterpret_cast<const uchar4*>(&s_kind[gy - RM_HY][xs - x0]);
+      const bool fl[4] = {kd.x == KIND_FLUID, kd.y == KIND_FLUID && xs + 1 < L.nx, kd.z == KIND_FLUID && xs + 2 < L.nx,
+                          kd.w == KIND_FLUID && xs + 3 < L.nx};
+      if (fl[0] && fl[1] && fl[2] && fl[3]) {
+        *reinterpret_cast<float4*>(L.rho + n0) = make_float4(r[0], r[1], r[2], r[3]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (fl[k]) L.rho[n0 + k] = r[k];
+      }
+    }
+  }
+  __syncthreads();
+  const int x = x0 + threadIdx.x;
+  if (x >= L.nx) return;
+  const int cx = RM_HX + threadIdx.x;
+  float dn2 = s_rho[0][cx], dn1 = s_rho[1][cx], c = s_rho[2][cx], up1 = s_rho[3][cx];
+  for (int j = 0; j < RM_H; ++j) {
+    const int y = y0 + j;
+    if (y >= L.ny) break;
+    const float up2 = s_rho[j + 4][cx];
+    const int n = y * L.pitch + x;
+    if (s_kind[j][threadIdx.x] == KIND_FLUID) {
+      const float* row = s_rho[j + RM_HY];
+      const float lap = lap4_of(c, row[cx + 1], row[cx - 1], row[cx + 2], row[cx - 2], up1, dn1, up2, dn2);
+      L.mu[n] = mu_of(L, psi_prime_shifted(L, c), lap);
+    }
+    dn2 = dn1; dn1 = c; c = up1; up1 = up2;
+  }
+}
+
+// Chemical potential of the listed fluid nodes from the final density plane (k_mu's
+// arithmetic, psi' evaluated here): the nodes k_rho_mu_tile could not finish.
+template <typename real>
+__global__ void __launch_bounds__(NODE_BLOCK) k_mu_near(Lattice<real> L) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= L.n_near) return;
+  const int n = L.near_list[j];
+  const int x = n % L.pitch, y = n / L.pitch;
+  Stencil st = stencil_at(L, x, y);
+  L.mu[n] = mu_of(L, psi_prime_shifted(L, L.rho[n]), lap4(L.rho, n, st));
+}
+
 // Pseudopotential force model: psi(rho) at fluid nodes, psi(rho_s) (1 + c_w) at the two solid
 // layers (rho_s from Eq. 15, c_w the wall factor of the node's body).  Pointwise, so it takes
 // V consecutive nodes of a row per thread with one 16-byte density load, like k_rho_vec.
@@ -855,11 +964,17 @@ static inline const CollideTma* tma_for(const Lattice<real>& L, int cur) {
 }
 
 // the chemical-potential (or psi) pass; with psi' from the density pass, the vector kernel
+// the step forms mu with the next state's density (k_rho_mu_tile) instead of a separate pass
+template <typename real>
+static inline bool fused_mu(const Lattice<real>& L) {
+  return sizeof(real) == 4 && L.mu_kernel == 3 && !L.pseudo && L.eos != EOS_NONE && L.psip != nullptr;
+}
+
 template <typename real>
 static inline void launch_mu(const Lattice<real>& L, cudaStream_t s) {
   if (L.eos == EOS_NONE) return;
   if (L.pseudo) k_psi<real><<<rho_grid(L), NODE_BLOCK, 0, s>>>(L);
-  else if (L.psip && L.mu_kernel == 2 && sizeof(real) == 4) {
+  else if (L.psip && L.mu_kernel >= 2 && sizeof(real) == 4) {
     if constexpr (sizeof(real) == 4) {
       const unsigned gx = (unsigned)((L.nx + 4 * MU_BLOCK - 1) / (4 * MU_BLOCK));
       k_mu_sweep<<<dim3(gx, (unsigned)((L.ny + MU_ROWS - 1) / MU_ROWS)), MU_BLOCK, 0, s>>>(L);
@@ -996,7 +1111,10 @@ template <typename real>
 cudaError_t launch_step_overlap(const Lattice<real>& Lt, const Lattice<real>& Ln, int cur, cudaStream_t s,
                                 cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join) {
   const Lattice<real>& L = Lt;
-  if (!L.pseudo) launch_mu(L, s);   // psi: left by the previous step's density pass, scatter, layers
+  // the fused pass left this state's mu at the end of the previous step; psi (pseudopotential
+  // force): the previous step's density pass, scatter and layers
+  const bool fused = fused_mu(L);
+  if (!L.pseudo && !fused) launch_mu(L, s);
   launch_collide(L, cur, s);
   cudaError_t e = cudaEventRecord(fork, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, fork, 0);
@@ -1005,17 +1123,25 @@ cudaError_t launch_step_overlap(const Lattice<real>& Lt, const Lattice<real>& Ln
   launch_bc(L, cur, s);
   if (Ln.n_s1 > 0) k_solid1_b<real><<<grid_for(Ln.n_s1, NODE_BLOCK), NODE_BLOCK, 0, s>>>(Ln);
   if (Ln.n_s2 > 0) k_solid<real><<<grid_for(Ln.n_s2, NODE_BLOCK), NODE_BLOCK, 0, s>>>(Ln, 2);
-  k_rho_vec<real><<<rho_grid(Ln), NODE_BLOCK, 0, s2>>>(Ln, cur ^ 1);
+  if (fused) {
+    if constexpr (sizeof(real) == 4)
+      k_rho_mu_tile<<<dim3((unsigned)((Ln.nx + RM_W - 1) / RM_W), (unsigned)((Ln.ny + RM_H - 1) / RM_H)), NODE_BLOCK, 0,
+                      s2>>>(Ln, cur ^ 1);
+  } else {
+    k_rho_vec<real><<<rho_grid(Ln), NODE_BLOCK, 0, s2>>>(Ln, cur ^ 1);
+  }
   e = cudaEventRecord(join, s2);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join, 0);
   if (e != cudaSuccess) return e;
   if (L.n_bnodes > 0) k_rho_scatter<real><<<gb, NODE_BLOCK, 0, s>>>(Ln);
+  if (fused && Ln.n_near > 0) k_mu_near<real><<<grid_for(Ln.n_near, NODE_BLOCK), NODE_BLOCK, 0, s>>>(Ln);
   return cudaGetLastError();
 }
 
 template <typename real>
 int launches_per_step_overlap(const Lattice<real>& L) {
-  return launches_per_step(L) + (L.n_bnodes > 0) - (L.pseudo && L.eos != EOS_NONE);
+  return launches_per_step(L) + (L.n_bnodes > 0) - (L.pseudo && L.eos != EOS_NONE) - (fused_mu(L) ? 1 : 0) +
+         (fused_mu(L) && L.n_near > 0 ? 1 : 0);
 }
 
 // one phase of a step: 0 density, 1 solid layers, 2 chemical potential, 3 force+collide+stream,

@@ -1,8 +1,9 @@
-"""The three chemical-potential passes (Eq. 12; lbm_set_mu_kernel) -- one node a thread, row
-vectors, row sweeps -- give the same bits: populations after a run on walled and periodic
-lattices, ragged sizes (partial vectors, partial sweeps, lanes at warp and lattice edges),
-lattices narrower than two vectors, and the large impact lattice with the TMA-pipelined
-collide."""
+"""The chemical-potential passes (Eq. 12; lbm_set_mu_kernel) -- one node a thread, row vectors,
+row sweeps, and (FP32) mu formed with the next state's density in one tiled pass, finished at the
+nodes next to solids and boundary nodes after the boundary phase -- give the same bits:
+populations after a run on walled and periodic lattices, ragged sizes (partial vectors, partial
+sweeps and tiles, lanes at warp and lattice edges), lattices narrower than two vectors, and the
+large impact lattice with the TMA-pipelined collide."""
 from __future__ import annotations
 
 import numpy as np
@@ -43,7 +44,7 @@ def test_mu_kernels_agree(name):
     sc = CASES[name]()
     steps = 37 if name != "impact" else 60
     pops = []
-    for kind in (0, 1, 2):
+    for kind in (0, 1, 2, 3):
         lat = make_lattice(sc, fp64=False)
         lat.set_mu_kernel(kind)
         lat.step(steps)
@@ -52,19 +53,37 @@ def test_mu_kernels_agree(name):
         assert abs(M / M0 - 1) < 1e-5
     assert np.array_equal(pops[0], pops[1])
     assert np.array_equal(pops[0], pops[2])
+    assert np.array_equal(pops[0], pops[3])
+
+
+def test_switching_to_and_from_the_fused_pass_keeps_the_state():
+    sc = S.c3_impact(256, 512)
+    a = make_lattice(sc, fp64=False)
+    b = make_lattice(sc, fp64=False)
+    b.set_mu_kernel(2)
+    for k in range(4):
+        a.set_mu_kernel(3 if k % 2 == 0 else 2)
+        a.step(9)
+        b.step(9)
+    assert np.array_equal(a.populations(), b.populations())
 
 
 def test_fp64_and_invalid_choices():
     import paper_2203_04508_gb300 as G
     d = make_lattice(S.small_parity(fp64=True), fp64=True)
-    with pytest.raises(G.LbmError):
-        d.set_mu_kernel(2)
+    for fp32_only in (2, 3):
+        with pytest.raises(G.LbmError):
+            d.set_mu_kernel(fp32_only)
     d.set_mu_kernel(0)
     d2 = make_lattice(S.small_parity(fp64=True), fp64=True)
     d.step(11)
     d2.step(11)
     assert np.array_equal(d.populations(), d2.populations())
     f = make_lattice(S.small_parity(fp64=False), fp64=False)
-    for bad in (-1, 3):
+    for bad in (-1, 4):
         with pytest.raises(G.LbmError):
             f.set_mu_kernel(bad)
+    pp = make_lattice(S.small_parity(fp64=False).with_(force_model=S.FORCE_PSEUDO, k=1.0, kappa=0.0,
+                                                       T_over_Tc=0.7, dmu_w=[0.15, -0.15]), fp64=False)
+    with pytest.raises(G.LbmError):
+        pp.set_mu_kernel(3)
