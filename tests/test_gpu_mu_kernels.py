@@ -31,6 +31,8 @@ CASES = {
     "periodic_multiple_of_4": lambda: S.Scenario(name="p4", nx=64, ny=40, walls=0, T_over_Tc=0.7,
                                                  x0=[31.0], y0=[20.5], r0=[9.0]),
     "impact": lambda: S.c3_impact(1024, 2048),
+    # large enough for the column-strip form of the fused pass (a full wave of strips x bands)
+    "impact_full": lambda: S.c3_impact(),
     # narrower than two vectors: every lane's outer neighbours wrap around the lattice
     "tiny_periodic": lambda: S.Scenario(name="t", nx=6, ny=9, walls=0, T_over_Tc=0.9, x0=[2.7], y0=[4.4],
                                         r0=[2.0]),
@@ -42,7 +44,7 @@ CASES = {
 @pytest.mark.parametrize("name", list(CASES))
 def test_mu_kernels_agree(name):
     sc = CASES[name]()
-    steps = 37 if name != "impact" else 60
+    steps = 37 if not name.startswith("impact") else 60
     pops = []
     for kind in (0, 1, 2, 3):
         lat = make_lattice(sc, fp64=False)
