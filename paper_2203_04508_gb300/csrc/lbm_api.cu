@@ -150,7 +150,8 @@ struct lbm_ctx {
   int collide_kind = 1;
   long long spin_limit = 1LL << 22;   // polls before a pipelined kernel's wait gives up
   int mu_kind = -1;                   // chemical-potential pass (-1: the precision's default)
-  long long n_near = 0;               // entries of the near list (lbm_build_links)
+  long long n_near = 0;               // entries of the near list, built where the fused density +
+  bool near_built = false;            // mu pass is selected (lbm_build_links, lbm_set_mu_kernel)
   lbm_status sticky = LBM_OK;
   std::string err;
   // one segment's recomputation (kind 0) or reverse steps (kind 1), captured once per
@@ -612,6 +613,7 @@ lbm_status near_list(lbm_ctx* c) {
   if (!list.empty())
     CUDA_OK(c, cudaMemcpy(c->ws + y.near, list.data(), list.size() * 4, cudaMemcpyHostToDevice));
   c->n_near = (long long)list.size();
+  c->near_built = true;
   return LBM_OK;
 }
 
@@ -844,10 +846,8 @@ lbm_status lbm_build_links(lbm_ctx* c) {
     lbm_status st = slab_ranges(c);
     if (st != LBM_OK) return st;
   }
-  {
-    lbm_status st = near_list(c);
-    if (st != LBM_OK) return st;
-  }
+  c->n_near = 0;
+  c->near_built = false;
   // the second mu plane starts with the walls' constant chemical potential as the first
   if (!c->fp64) CUDA_OK(c, cudaMemcpyAsync(w + y.mu2, w + y.mu, y.plane * y.sz, cudaMemcpyDeviceToDevice, c->stream));
   c->built = true;
@@ -865,6 +865,12 @@ lbm_status lbm_build_links(lbm_ctx* c) {
     const long long tiles = (long long)((g.nx + 31) / 32) * ((g.ny + 7) / 8);
     c->collide_kind = (c->tma_ok && tiles >= 16LL * c->tma.blocks[g.force_model == LBM_FORCE_PSEUDO ? 1 : 0]) ? 1 : 0;
     refresh(c);
+    // the list of nodes the fused density + mu pass leaves to k_mu_near, where that pass runs
+    if (c->Lf.mu_kernel == 3) {
+      lbm_status st = near_list(c);
+      if (st != LBM_OK) return st;
+      refresh(c);
+    }
   }
   return LBM_OK;
 }
@@ -1001,6 +1007,10 @@ lbm_status lbm_set_mu_kernel(lbm_ctx* c, int32_t kind) {
     return fail(c, LBM_EINVAL, "the fused chemical-potential kernel needs the chemical-potential force");
   c->mu_kind = kind;
   c->rho_ok = false;   // a change to or from the fused pass moves where mu is kept
+  if (kind == 3 && !c->near_built) {
+    lbm_status st = near_list(c);
+    if (st != LBM_OK) return st;
+  }
   for (auto& gr : c->graph)
     if (gr) { cudaGraphExecDestroy(gr); gr = nullptr; }
   for (auto& a : c->adj_graphs) cudaGraphExecDestroy(a.exec);
