@@ -65,6 +65,8 @@ FALLBACK_HBM_GBS = 6800.0
 
 def collide_kernel_name(kind, pseudo):
     force = "pseudopotential force" if pseudo else "Eq. 9 force"
+    if kind == 2:
+        return f"k_collide_tma ({force} + collide + stream + the next density, TMA-pipelined column sweeps)"
     if kind == 1:
         return f"k_collide_tma ({force} + collide + stream, TMA-pipelined persistent grid)"
     return f"k_collide ({force} + collide + stream, one tile per block)"
@@ -707,6 +709,9 @@ def main():
     ap.add_argument("--adjoint-every", type=int, default=200)
     ap.add_argument("--accuracy", type=int, default=1,
                     help="1: FP32/FP64 against the oracle's stored full-size results (c2, c3, c5); 0: skip")
+    ap.add_argument("--collide-kernel", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="collide kernel of the single lattice (-1: the library's choice; 2: the column "
+                         "sweeps that also form the next density, for comparison)")
     ap.add_argument("--mode", default="full", choices=["full", "kernels", "adjoint"],
                     help="kernels: only warm-up and timed steps; adjoint: only the gradient "
                          "workload (both for profiler captures)")
@@ -752,6 +757,8 @@ def main():
     else:
         lat = G.Lattice(sc.physics(), precision=G.LBM_FP32)
         lat.init_droplets(sc.droplets())
+        if args.collide_kernel >= 0:
+            lat.set_collide_kernel(args.collide_kernel)
         counts = lat.counts()
         advance = lat.step
     if args.mode == "kernels":

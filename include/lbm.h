@@ -252,15 +252,22 @@ lbm_status lbm_launches_per_step(lbm_ctx* ctx, int64_t* n);
  * force, 13): kind 0 the plain kernel (one 32 x 8 tile per block, populations loaded by each
  * thread), kind 1 the TMA-pipelined one (a persistent grid; each block's next tiles -- the nine
  * population planes, the density and chemical-potential halo -- stream into shared memory by
- * cp.async.bulk.tensor while it computes the current one).  Both give the same values, bit for
- * bit.  lbm_build_links picks kind 1 where it could encode the tensor maps (FP32 with a driver
- * that has the encoder) and the lattice gives each persistent block at least 16 tiles, kind 0
- * otherwise; setting kind 1 where the maps are missing returns LBM_EINVAL.  Call after
- * lbm_build_links; the
- * step graphs are captured again.  A bounded wait of kind 1 that gives up is reported as
- * LBM_ETIMEOUT by the next lbm_mass. */
+ * cp.async.bulk.tensor while it computes the current one), kind 2 the same pipeline walking
+ * 32-column strips upwards through bands of tile rows, which also sums the populations streaming
+ * into the rows it has finished into the next state's density (Sec. 2.1) and psi'(rho), so that
+ * the step's separate density pass shrinks to the strips' edge columns and the bands' edge rows.
+ * All give the same values, bit for bit.  Kind 2 needs the chemical-potential force with an
+ * equation of state, nx a multiple of 32 and ny of 8, and a whole lattice (not a slab); under the
+ * fused chemical-potential pass (lbm_set_mu_kernel 3) the step runs kind 1 instead, and
+ * lbm_get_collide_kernel reports the kind that runs.  lbm_build_links picks kind 1 where it could
+ * encode the tensor maps (FP32 with a driver that has the encoder) and the lattice gives each
+ * persistent block at least 16 tiles, kind 0 otherwise; kind 2 runs only when set (on GB300 its
+ * added density work slows a collide kernel that is already bound by instruction issue more
+ * than the separate density pass costs).  Setting a kind the lattice cannot run returns
+ * LBM_EINVAL.  Call after lbm_build_links; the step graphs are captured again.  A
+ * bounded wait of kind 1 or 2 that gives up is reported as LBM_ETIMEOUT by the next lbm_mass. */
 lbm_status lbm_set_collide_kernel(lbm_ctx* ctx, int32_t kind);
-/* The collide kernel lbm_step runs now (0 plain, 1 TMA-pipelined). */
+/* The collide kernel lbm_step runs now (0 plain, 1 TMA-pipelined, 2 column sweeps). */
 lbm_status lbm_get_collide_kernel(lbm_ctx* ctx, int32_t* kind);
 
 /* The chemical-potential pass (Eq. 12) of the chemical-potential force model: 0 one node a

@@ -55,12 +55,19 @@ struct Layout {
   long long plane;
   size_t sz;
   Caps cap;
-  size_t fA, fB, rho, rho2, mu, mu2, psip, kind, body, near;
+  size_t fA, fB, rho, rho2, mu, mu2, psip, kind, body, near, edge, edge_bytes;
   size_t lq64, lq, ldir, lx2f, bnode, bstart, carry, rhob;
   size_t s1node, s1mask, s1winv, s1nb, s2node, s2mask, s2winv;
   size_t cyl, drops, partials, counter, step_ctr, scalars, kerr, dm_ring, block_sums, totals;
   size_t total;
 };
+
+// can the collide kernel form the next density by column sweeps on this lattice?  FP32, the
+// chemical-potential force with an equation of state, whole 32 x 8 tiles
+bool sweep_shape(const lbm_config* c) {
+  return c->precision == LBM_FP32 && c->force_model == LBM_FORCE_CHEMPOT && c->eos != LBM_EOS_NONE && c->nx % 32 == 0 &&
+         c->ny % 8 == 0;
+}
 
 Layout make_layout(const lbm_config* c) {
   Layout L{};
@@ -100,6 +107,10 @@ Layout make_layout(const lbm_config* c) {
   // fluid nodes whose chemical-potential stencil reaches a solid or boundary node: each solid-layer
   // or boundary node is in the stencils of at most 9 nodes
   L.near = take((size_t)9 * (L.cap.bnodes + L.cap.s1 + L.cap.s2) * 4);
+  // edge buffer of the FP32 collide kernel that forms the next density by column sweeps (lattices
+  // of whole 32 x 8 tiles, chemical-potential force): nine values per strip-edge node
+  L.edge_bytes = sweep_shape(c) ? (size_t)9 * 2 * (c->nx / 32) * c->ny * 4 : 0;
+  L.edge = take(L.edge_bytes);
   L.cyl = take((size_t)(c->n_cyl > 0 ? c->n_cyl : 1) * 4 * 8);
   L.drops = take((size_t)MAX_DROPS * 5 * 8);
   size_t nparts = 2 * (size_t)mass_blocks();
@@ -144,7 +155,8 @@ struct lbm_ctx {
   // step graphs (x lattice parity): 2 steps, 1 step, STEPS_LONG steps
   cudaGraphExec_t graph[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   // FP32: TMA descriptors of the pipelined collide kernel (set up by lbm_build_links) and the
-  // collide kernel in use (0 plain, 1 TMA-pipelined)
+  // collide kernel in use (0 plain, 1 TMA-pipelined, 2 TMA-pipelined column sweeps that form the
+  // next density)
   CollideTma tma{};
   bool tma_ok = false;
   int collide_kind = 1;
@@ -320,8 +332,9 @@ void fill_lattice(lbm_ctx* c, Lattice<real>& L) {
   L.near_list = (const int*)(w + y.near);
   L.tma = nullptr;
   if constexpr (sizeof(real) == 4) {
-    if (c->tma_ok && c->collide_kind == 1) L.tma = &c->tma;
+    if (c->tma_ok && c->collide_kind >= 1) L.tma = &c->tma;
   }
+  L.sweep = (sizeof(real) == 4 && c->tma_ok && c->collide_kind == 2 && !c->slab.on && sweep_shape(&c->cfg)) ? 1 : 0;
   if (c->slab.on) {
     L.y_off = c->slab.y_off;
     L.ny_glob = c->slab.periodic ? c->slab.ny_glob : 0;
@@ -484,6 +497,42 @@ lbm_status profile_steps(lbm_ctx* c, const Lattice<real>& L, long long n, double
   for (auto& e : ev) CUDA_OK(c, cudaEventCreate(&e));
   for (int k = 0; k < 5; ++k) ms[k] = 0.0;
   lbm_status st = LBM_OK;
+  if (step_sweeps(L, c->cur)) {
+    // the collide kernel forms most of the next density: the phases in the order they depend on
+    // one another (chemical potential, collide, boundary links, the next state's solid layers,
+    // the densities the collide left), the density planes alternating as lbm_step keeps them
+    Lattice<real> Lt, Ln;
+    if (!c->rho_ok) {
+      step_lattices(c, L, c->cur, Lt, Ln);
+      CUDA_OK(c, launch_phase(Lt, c->cur, 0, c->stream));
+      CUDA_OK(c, launch_phase(Lt, c->cur, 1, c->stream));
+      c->rho_ok = true;
+    }
+    static const int order[5] = {2, 3, 4, 1, 0};
+    for (long long s = 0; s < n && st == LBM_OK; ++s) {
+      static const char* const phase_name[5] = {"density", "solid layers", "chemical potential", "collide", "boundary"};
+      step_lattices(c, L, c->cur, Lt, Ln);
+      for (int k = 0; k < 5; ++k) {
+        LBM_RANGE(phase_name[order[k]]);
+        cudaEventRecord(ev[k], c->stream);
+        cudaError_t e = launch_phase_sweep(Lt, Ln, c->cur, order[k], c->stream);
+        if (e != cudaSuccess) { st = fail(c, LBM_ECUDA, "launch failed: %s", cudaGetErrorString(e)); break; }
+      }
+      if (st != LBM_OK) break;
+      cudaEventRecord(ev[5], c->stream);
+      cudaError_t e = cudaEventSynchronize(ev[5]);
+      if (e != cudaSuccess) { st = fail(c, LBM_ECUDA, "step failed: %s", cudaGetErrorString(e)); break; }
+      for (int k = 0; k < 5; ++k) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+        ms[order[k]] += t;
+      }
+      c->cur ^= 1;
+      c->steps += 1;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    return st;
+  }
   for (long long s = 0; s < n && st == LBM_OK; ++s) {
     static const char* const phase_name[5] = {"density", "solid layers", "chemical potential", "collide", "boundary"};
     for (int ph = 0; ph < 5; ++ph) {
@@ -859,9 +908,13 @@ lbm_status lbm_build_links(lbm_ctx* c) {
   if (!c->fp64) {
     // the pipelined collide kernel's descriptors; without them the plain kernel runs
     char msg[256] = {0};
-    c->tma_ok = collide_tma_setup(&c->tma, c->Lf, w + y.rho, w + y.rho2, w + y.mu2, msg);
+    c->tma_ok = collide_tma_setup(&c->tma, c->Lf, w + y.rho, w + y.rho2, w + y.mu2, y.edge_bytes ? w + y.edge : nullptr,
+                                  msg);
     // the pipeline pays off once each persistent block has enough tiles to stream (measured:
-    // 43 tiles per block 10 % faster than the plain kernel, 5 tiles per block 7 % slower)
+    // 43 tiles per block 10 % faster than the plain kernel, 5 tiles per block 7 % slower).  The
+    // column sweeps (kind 2) are not the default: on the 2048 x 4096 impact lattice the sweep
+    // kernel took 0.24 ms against 0.125 ms (its added density work lands on a kernel already
+    // bound by instruction issue) and the step 0.31 ms against 0.21 ms.
     const long long tiles = (long long)((g.nx + 31) / 32) * ((g.ny + 7) / 8);
     c->collide_kind = (c->tma_ok && tiles >= 16LL * c->tma.blocks[g.force_model == LBM_FORCE_PSEUDO ? 1 : 0]) ? 1 : 0;
     refresh(c);
@@ -973,9 +1026,14 @@ lbm_status lbm_step(lbm_ctx* c, int64_t n) {
 
 lbm_status lbm_set_collide_kernel(lbm_ctx* c, int32_t kind) {
   if (!c || !c->built) return LBM_ESTATE;
-  if (kind != 0 && kind != 1) return fail(c, LBM_EINVAL, "collide kernel must be 0 (plain) or 1 (TMA-pipelined)");
-  if (kind == 1 && (c->fp64 || !c->tma_ok))
+  if (kind < 0 || kind > 2)
+    return fail(c, LBM_EINVAL, "collide kernel must be 0 (plain), 1 (TMA-pipelined) or 2 (column sweeps)");
+  if (kind >= 1 && (c->fp64 || !c->tma_ok))
     return fail(c, LBM_EINVAL, "the TMA-pipelined collide kernel needs FP32 and the CUDA driver's tensor-map encoder");
+  if (kind == 2 && (!sweep_shape(&c->cfg) || c->slab.on))
+    return fail(c, LBM_EINVAL,
+                "the column sweeps need the chemical-potential force with an equation of state, nx a multiple of 32 "
+                "and ny of 8, and a whole lattice");
   if (kind == c->collide_kind) return LBM_OK;
   c->collide_kind = kind;
   // captured launches carry the old kernel: capture again
@@ -1021,7 +1079,8 @@ lbm_status lbm_set_mu_kernel(lbm_ctx* c, int32_t kind) {
 
 lbm_status lbm_get_collide_kernel(lbm_ctx* c, int32_t* kind) {
   if (!c || !c->built || !kind) return LBM_ESTATE;
-  *kind = (!c->fp64 && c->tma_ok && c->collide_kind == 1) ? 1 : 0;
+  // the kernel the step runs: the sweeps give way to kind 1 under the fused chemical-potential pass
+  *kind = (c->fp64 || !c->tma_ok || c->collide_kind == 0) ? 0 : (step_sweeps(c->Lf, c->cur) ? 2 : 1);
   return LBM_OK;
 }
 

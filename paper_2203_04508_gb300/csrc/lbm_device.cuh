@@ -92,6 +92,8 @@ struct Lattice {
   const int* near_list;         // a boundary node (their mu waits for the boundary phase)
   const void* tma;              // host side: TMA descriptors of the pipelined collide kernel
                                 // (FP32), null for the plain kernel
+  int sweep;                    // host side: the step's collide kernel forms the next state's
+                                // density by column sweeps (FP32, chemical-potential force)
   // y-slab of a larger lattice: local row y is global row y + y_off (mod ny_glob when ny_glob >
   // 0); the audits sum rows [own_lo, own_hi) and the Eq. 18 sum boundary nodes [b_lo, b_hi)
   // only.  A whole lattice has y_off = ny_glob = 0, own = [0, ny), b = [0, n_bnodes).

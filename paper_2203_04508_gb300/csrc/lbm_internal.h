@@ -25,6 +25,11 @@ inline unsigned mass_blocks() { return 152 * 4; }
 template <typename real> cudaError_t launch_step(const Lattice<real>& L, int cur, cudaStream_t s);
 template <typename real> int launches_per_step(const Lattice<real>& L);
 template <typename real> cudaError_t launch_phase(const Lattice<real>& L, int cur, int phase, cudaStream_t s);
+// the phases of a step whose collide kernel forms the next density (column sweeps), and whether
+// the step from lattice cur runs that way
+template <typename real>
+cudaError_t launch_phase_sweep(const Lattice<real>& Lt, const Lattice<real>& Ln, int cur, int phase, cudaStream_t s);
+template <typename real> bool step_sweeps(const Lattice<real>& L, int cur);
 template <typename real> cudaError_t launch_macro(const Lattice<real>& L, int cur, cudaStream_t s);
 // step t with its boundary phase and the next state's solid layers overlapping the density
 // pass of step t+1 on stream s2 (Lt: rho = fluid and solid-layer densities of lattice cur,
@@ -55,11 +60,13 @@ struct CollideTma {
   const void* rho_ptr[2];       // descriptor pointing elsewhere runs the plain kernel
   const void* mu_ptr[2];
   int blocks[2];                // persistent grid of the chemical-potential / psi variant
+  int sweep_blocks;             // blocks of the column-sweep variant that fit on the device at once
+  float* edge;                  // its edge buffer (null: the sweep does not run)
 };
 // Encodes the descriptors for L (whose planes must not move afterwards) and sizes the grids;
 // false, with a message, when the CUDA driver cannot.
 bool collide_tma_setup(CollideTma* T, const Lattice<float>& L, const void* rho0, const void* rho1, const void* mu1,
-                       char* err);
+                       void* edge, char* err);
 
 // ---- halo messages of a y-slab (lbm_slab.cu)
 constexpr int SLAB_PLANES = 11;   // nine populations, density, psi'(rho) - mu_sat or psi

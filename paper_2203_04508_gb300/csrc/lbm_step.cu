@@ -585,9 +585,58 @@ __device__ __forceinline__ bool tma_halo(const Lattice<float>& L, int x0, int y0
   return x0 - h >= 0 && x0 + CT_X + h <= L.nx && (L.walls || (y0 - h >= 0 && y0 + CT_Y + h <= L.ny));
 }
 
-template <bool PSEUDO>
+// Column sweeps (SWEEP): the same force + collision + streaming, and the next state's density
+// with it (FP32, chemical-potential force, lattices of whole 32 x 8 tiles).  Block (strip,
+// band) walks the tiles of one 32-column strip upwards through a band of tile rows, and drops
+// each post-collision population, besides pushing it into the other lattice, into a
+// shared-memory ring at its destination: ring rows are destination rows (row - ya + 1) mod
+// SW_R of the band [ya, yb), ring columns x0 - 1 .. x0 + 32.  Once tile y0 has collided, rows
+// y0 - 1 .. y0 + 6 hold every population streaming into them, and the block sums them in the
+// density pass's order (density_sum) into the density and psi'(rho) - mu_sat of the strip's
+// inner 30 columns.  k_rho_sweep_fix finishes the rest: the strip's two edge columns, whose
+// incoming populations come partly from the neighbouring strips -- every block leaves the
+// values it holds for its own edge nodes and for its neighbours' in the edge buffer -- and the
+// band's first and last rows, whose neighbours across the band edge another block collides.
+// Boundary nodes' values are provisional, as in the density pass: the boundary phase changes
+// their populations and k_rho_scatter stores their final density.
+constexpr int SW_R = CT_Y + 2;                       // ring rows
+constexpr int SW_W = CT_X + 2;                       // ring columns
+constexpr int SW_RING_BYTES = 9 * SW_R * SW_W * 4;
+constexpr int SW_KIND_BYTES = SW_R * CT_X;
+static_assert(18 * CT_Y <= NODE_BLOCK, "one thread per edge-buffer entry of a tile");
+
+__host__ __device__ constexpr size_t collide_smem_bytes(bool pseudo, bool sweep) {
+  return (size_t)TMA_STAGES * tma_stage_bytes(pseudo) + (sweep ? (size_t)SW_RING_BYTES + SW_KIND_BYTES : 0);
+}
+
+// first tile row of band b of `bands` over `tile_rows` tile rows
+__host__ __device__ inline int sweep_band_start(int b, int bands, int tile_rows) {
+  return (int)((long long)b * tile_rows / bands);
+}
+
+struct SweepArgs {
+  float* rho_next;   // the next state's density plane
+  float* edge;       // edge buffer: direction i, edge column c, row y at (i * 2 strips + c) * ny + y;
+                     // edge column 2 s is strip s's first column, 2 s + 1 its last
+  int strips, bands, tile_rows;
+};
+
+// entry e (0..17) of one row of a strip's edge values: its direction, ring column and edge column.
+// 0-5: the strip's first column (directions arriving from inside the strip); 6-8: the column
+// left of the strip (directions leaving to the left); 9-14: the strip's last column; 15-17: the
+// column right of the strip.
+__device__ __forceinline__ void sweep_edge_entry(int e, int strip, int strips, int& dir, int& rcol, int& ecol) {
+  dir = (int)((e < 9 ? (0x763764320ULL >> (4 * e)) : (0x851854210ULL >> (4 * (e - 9)))) & 15ULL);
+  if (e < 6) { rcol = 1; ecol = 2 * strip; }
+  else if (e < 9) { rcol = 0; ecol = 2 * (strip == 0 ? strips - 1 : strip - 1) + 1; }
+  else if (e < 15) { rcol = CT_X; ecol = 2 * strip + 1; }
+  else { rcol = CT_X + 1; ecol = 2 * (strip + 1 == strips ? 0 : strip + 1); }
+}
+
+template <bool PSEUDO, bool SWEEP>
 __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, int cur, const __grid_constant__ CollideMaps M,
-                                                            int tiles_x, int n_tiles) {
+                                                            int tiles_x, int n_tiles, SweepArgs A) {
+  static_assert(!(PSEUDO && SWEEP), "the sweep forms the chemical-potential model's density");
   extern __shared__ __align__(128) unsigned char tma_smem[];
   __shared__ __align__(8) uint64_t bar[TMA_STAGES];
   constexpr int SB = tma_stage_bytes(PSEUDO);
@@ -597,9 +646,28 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, in
   // mu (or psi) right after the populations, the density (chemical potential) after it
   auto mu_of = [&](int s) { return reinterpret_cast<float*>(tma_smem + s * SB + TMA_F_BYTES); };
   auto rho_of = [&](int s) { return reinterpret_cast<float*>(tma_smem + s * SB + TMA_F_BYTES + TMA_M_BYTES); };
-  // thread 0: request tile t into stage s
-  auto issue = [&](int t, int s) {
-    const int x0 = (t % tiles_x) * CT_X, y0 = (t / tiles_x) * CT_Y;
+  float* ring = reinterpret_cast<float*>(tma_smem + TMA_STAGES * SB);
+  uint8_t* rkind = tma_smem + TMA_STAGES * SB + SW_RING_BYTES;
+  // this block's tiles: k = 0 .. nt - 1 at (x0 of k, y0 of k)
+  int nt, strip = 0, ya = 0;
+  if (SWEEP) {
+    strip = blockIdx.x % A.strips;
+    const int band = blockIdx.x / A.strips;
+    const int tr0 = sweep_band_start(band, A.bands, A.tile_rows);
+    nt = sweep_band_start(band + 1, A.bands, A.tile_rows) - tr0;
+    ya = tr0 * CT_Y;
+  } else {
+    nt = n_tiles > (int)blockIdx.x ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  }
+  auto tile_x0 = [&](int k) {
+    return SWEEP ? strip * CT_X : (((int)blockIdx.x + k * (int)gridDim.x) % tiles_x) * CT_X;
+  };
+  auto tile_y0 = [&](int k) {
+    return SWEEP ? ya + k * CT_Y : (((int)blockIdx.x + k * (int)gridDim.x) / tiles_x) * CT_Y;
+  };
+  // thread 0: request tile k into stage s
+  auto issue = [&](int k, int s) {
+    const int x0 = tile_x0(k), y0 = tile_y0(k);
     const bool h = stencils && tma_halo<PSEUDO>(L, x0, y0);
     mbar_expect_tx(&bar[s], TMA_F_BYTES + (h ? (PSEUDO ? 1 : 2) * TMA_M_BYTES : 0));
     tma_load_3d(f_of(s), &M.f, x0, y0, 0, &bar[s]);
@@ -614,15 +682,11 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, in
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int s = 0; s < TMA_STAGES; ++s) {
-      const int t = blockIdx.x + s * gridDim.x;
-      if (t < n_tiles) issue(t, s);
-    }
+    for (int s = 0; s < TMA_STAGES && s < nt; ++s) issue(s, s);
   }
-  int k = 0;
-  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++k) {
+  for (int k = 0; k < nt; ++k) {
     const int s = k % TMA_STAGES;
-    const int x0 = (t % tiles_x) * CT_X, y0 = (t / tiles_x) * CT_Y;
+    const int x0 = tile_x0(k), y0 = tile_y0(k);
     const int x = x0 + lx, y = y0 + ly;
     const bool fluid = x < L.nx && y < L.ny && L.kind[y * L.pitch + x] == KIND_FLUID;
     const bool ok = mbar_wait(&bar[s], (uint32_t)((k / TMA_STAGES) & 1), L.spin_limit);
@@ -630,10 +694,8 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, in
       // give up: flag it, let this block's copies still in flight land, and leave
       if (threadIdx.x == 0) {
         atomicOr(L.kerr, 1u);
-        for (int j = 0; j < TMA_STAGES; ++j) {
-          const int tj = t + j * gridDim.x;
-          if (tj < n_tiles) mbar_wait(&bar[(k + j) % TMA_STAGES], (uint32_t)(((k + j) / TMA_STAGES) & 1));
-        }
+        for (int j = 0; j < TMA_STAGES && k + j < nt; ++j)
+          mbar_wait(&bar[(k + j) % TMA_STAGES], (uint32_t)(((k + j) / TMA_STAGES) & 1));
       }
       __syncthreads();
       return;
@@ -667,17 +729,97 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, in
     }
     // every thread has read stage s: refill it with the tile TMA_STAGES ahead
     __syncthreads();
-    if (threadIdx.x == 0) {
-      const int tn = t + TMA_STAGES * gridDim.x;
-      if (tn < n_tiles) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue(tn, s);
+    if (threadIdx.x == 0 && k + TMA_STAGES < nt) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(k + TMA_STAGES, s);
+    }
+    if (!SWEEP) {
+      if (!fluid) continue;
+      collide_loaded(L, cur, x, y, fl,
+                     [&](float r, float& Fx, float& Fy) { tile_force<float, PSEUDO>(L, stencils, g, r, Fx, Fy); });
+      continue;
+    }
+    // ring rows of this node's row and of the rows below and above it
+    const int sc = (y - ya + 1) % SW_R;
+    const int sm1 = sc == 0 ? SW_R - 1 : sc - 1, sp1 = sc == SW_R - 1 ? 0 : sc + 1;
+    rkind[sc * CT_X + lx] = fluid ? 1 : 0;
+    if (fluid) {
+      collide_loaded(L, cur, x, y, fl,
+                     [&](float r, float& Fx, float& Fy) { tile_force<float, PSEUDO>(L, stencils, g, r, Fx, Fy); });
+      // fl holds the post-collision populations: direction i lands at (lx + ex(i), row + ey(i))
+      auto at = [&](int i, int slot, int col) -> float& { return ring[(i * SW_R + slot) * SW_W + col]; };
+      at(0, sc, lx + 1) = fl[0];
+      at(1, sc, lx + 2) = fl[1];
+      at(2, sp1, lx + 1) = fl[2];
+      at(3, sc, lx) = fl[3];
+      at(4, sm1, lx + 1) = fl[4];
+      at(5, sp1, lx + 2) = fl[5];
+      at(6, sp1, lx) = fl[6];
+      at(7, sm1, lx) = fl[7];
+      at(8, sm1, lx + 2) = fl[8];
+    }
+    __syncthreads();
+    // rows y0 - 1 .. y0 + 6 are complete; thread (lx, ly) forms row y0 - 1 + ly, whose ring row
+    // is sm1.  The band's first row, and the row below it, wait for k_rho_sweep_fix.
+    const int yd = y - 1;
+    if (yd > ya && lx > 0 && lx < CT_X - 1 && rkind[sm1 * CT_X + lx]) {
+      float fi[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) fi[i] = ring[(i * SW_R + sm1) * SW_W + lx + 1];
+      const float r = density_of(L, fi);
+      const int n = yd * L.pitch + x;
+      A.rho_next[n] = r;
+      L.psip[n] = psi_prime_shifted(L, r);
+    }
+    if (threadIdx.x < 18 * CT_Y) {
+      const int e = threadIdx.x / CT_Y, j = threadIdx.x % CT_Y;
+      const int ye = y0 - 1 + j;
+      if (ye > ya) {
+        int dir, rcol, ecol;
+        sweep_edge_entry(e, strip, A.strips, dir, rcol, ecol);
+        const int se = (ye - ya + 1) % SW_R;
+        A.edge[((long long)dir * 2 * A.strips + ecol) * L.ny + ye] = ring[(dir * SW_R + se) * SW_W + rcol];
       }
     }
-    if (!fluid) continue;
-    collide_loaded(L, cur, x, y, fl,
-                   [&](float r, float& Fx, float& Fy) { tile_force<float, PSEUDO>(L, stencils, g, r, Fx, Fy); });
   }
+}
+
+// What the sweep left: the densities (and psi'(rho) - mu_sat) of the strips' edge columns in
+// band-interior rows, from the edge buffer, then those of the bands' first and last rows, from
+// the new populations (lattice `cur`).  The same sum as the density pass.
+__global__ void __launch_bounds__(NODE_BLOCK) k_rho_sweep_fix(Lattice<float> L, int cur, SweepArgs A) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n_edge = 2LL * A.strips * L.ny;
+  float fi[9];
+  int n;
+  if (t < n_edge) {
+    const int col = (int)(t / L.ny), y = (int)(t - (long long)col * L.ny);
+    const int tr = y / CT_Y;
+    int b = (int)((long long)tr * A.bands / A.tile_rows);
+    while (b + 1 < A.bands && sweep_band_start(b + 1, A.bands, A.tile_rows) <= tr) ++b;
+    if (y == sweep_band_start(b, A.bands, A.tile_rows) * CT_Y || y == sweep_band_start(b + 1, A.bands, A.tile_rows) * CT_Y - 1)
+      return;
+    const int x = (col >> 1) * CT_X + ((col & 1) ? CT_X - 1 : 0);
+    n = y * L.pitch + x;
+    if (L.kind[n] != KIND_FLUID) return;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fi[i] = A.edge[((long long)i * 2 * A.strips + col) * L.ny + y];
+  } else {
+    const long long u = t - n_edge;
+    if (u >= 2LL * A.bands * L.nx) return;
+    const int row = (int)(u / L.nx), x = (int)(u - (long long)row * L.nx);
+    const int b = row >> 1;
+    const int y = (row & 1) ? sweep_band_start(b + 1, A.bands, A.tile_rows) * CT_Y - 1
+                            : sweep_band_start(b, A.bands, A.tile_rows) * CT_Y;
+    n = y * L.pitch + x;
+    if (L.kind[n] != KIND_FLUID) return;
+    const float* __restrict__ f = L.f[cur];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fi[i] = f[i * L.plane + n];
+  }
+  const float r = density_of(L, fi);
+  A.rho_next[n] = r;
+  L.psip[n] = psi_prime_shifted(L, r);
 }
 
 // Boundary links, then the deterministic domain sum of this step's Eq. 18 compensation into
@@ -982,26 +1124,72 @@ static inline void launch_mu(const Lattice<real>& L, cudaStream_t s) {
   } else if (L.psip && L.mu_kernel != 0) k_mu_vec<real><<<rho_grid(L), NODE_BLOCK, 0, s>>>(L);
   else k_mu<real><<<node_grid(L), node_block(), 0, s>>>(L);
 }
+static inline CollideMaps maps_for(const CollideTma* T, const Lattice<float>& L, int cur) {
+  CollideMaps M;
+  M.f = T->f[cur];
+  M.rho = T->rho[L.rho == T->rho_ptr[1] ? 1 : 0];
+  M.mu = T->mu[L.mu == T->mu_ptr[1] ? 1 : 0];
+  return M;
+}
+// does this step form the next density in the collide kernel (column sweeps)?
+template <typename real>
+static inline bool sweep_ready(const Lattice<real>& L, int cur) {
+  if constexpr (sizeof(real) == 4) {
+    const CollideTma* T = tma_for(L, cur);
+    return L.sweep && T && T->edge && !L.pseudo && L.eos != EOS_NONE && L.psip && L.mu_kernel != 3 &&
+           L.nx % CT_X == 0 && L.ny % CT_Y == 0;
+  }
+  return false;
+}
+// the sweep's work: strips of 32 columns by bands of tile rows, one block each, as many bands
+// as fill the device once
+static inline SweepArgs sweep_args(const Lattice<float>& L, const CollideTma* T, float* rho_next) {
+  SweepArgs A;
+  A.rho_next = rho_next;
+  A.edge = T->edge;
+  A.strips = L.nx / CT_X;
+  A.tile_rows = L.ny / CT_Y;
+  const int b = T->sweep_blocks / A.strips;
+  A.bands = b < 1 ? 1 : (b > A.tile_rows ? A.tile_rows : b);
+  return A;
+}
 template <typename real>
 static inline void launch_collide(const Lattice<real>& L, int cur, cudaStream_t s) {
   if constexpr (sizeof(real) == 4) {
     if (const CollideTma* T = tma_for(L, cur)) {
-      CollideMaps M;
-      M.f = T->f[cur];
-      M.rho = T->rho[L.rho == T->rho_ptr[1] ? 1 : 0];
-      M.mu = T->mu[L.mu == T->mu_ptr[1] ? 1 : 0];
+      const CollideMaps M = maps_for(T, L, cur);
       const int tiles_x = (L.nx + CT_X - 1) / CT_X;
       const int tiles = tiles_x * ((L.ny + CT_Y - 1) / CT_Y);
       const int P = L.pseudo ? 1 : 0;
       const int grid = tiles < T->blocks[P] ? tiles : T->blocks[P];
-      const size_t smem = (size_t)TMA_STAGES * tma_stage_bytes(L.pseudo);
-      if (L.pseudo) k_collide_tma<true><<<grid, NODE_BLOCK, smem, s>>>(L, cur, M, tiles_x, tiles);
-      else k_collide_tma<false><<<grid, NODE_BLOCK, smem, s>>>(L, cur, M, tiles_x, tiles);
+      const size_t smem = collide_smem_bytes(L.pseudo, false);
+      const SweepArgs none{};
+      if (L.pseudo) k_collide_tma<true, false><<<grid, NODE_BLOCK, smem, s>>>(L, cur, M, tiles_x, tiles, none);
+      else k_collide_tma<false, false><<<grid, NODE_BLOCK, smem, s>>>(L, cur, M, tiles_x, tiles, none);
       return;
     }
   }
   if (L.pseudo) k_collide<real, true><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
   else k_collide<real, false><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
+}
+// collide (column sweeps) of lattice cur into cur ^ 1, the next density into rho_next; then the
+// densities the sweep left
+template <typename real>
+static inline void launch_collide_sweep(const Lattice<real>& L, int cur, real* rho_next, cudaStream_t s) {
+  if constexpr (sizeof(real) == 4) {
+    const CollideTma* T = tma_for(L, cur);
+    const SweepArgs A = sweep_args(L, T, rho_next);
+    k_collide_tma<false, true><<<A.strips * A.bands, NODE_BLOCK, collide_smem_bytes(false, true), s>>>(
+        L, cur, maps_for(T, L, cur), 0, 0, A);
+  }
+}
+template <typename real>
+static inline void launch_sweep_fix(const Lattice<real>& Lt, const Lattice<real>& Ln, int cur, cudaStream_t s) {
+  if constexpr (sizeof(real) == 4) {
+    const SweepArgs A = sweep_args(Lt, tma_for(Lt, cur), Ln.rho);
+    const long long n = 2LL * A.strips * Ln.ny + 2LL * A.bands * Ln.nx;
+    k_rho_sweep_fix<<<grid_for(n, NODE_BLOCK), NODE_BLOCK, 0, s>>>(Ln, cur ^ 1, A);
+  }
 }
 template <typename real>
 static inline void launch_bc(const Lattice<real>& L, int cur, cudaStream_t s) {
@@ -1032,7 +1220,7 @@ static EncodeTiledFn encode_tiled() {
 }
 
 bool collide_tma_setup(CollideTma* T, const Lattice<float>& L, const void* rho0, const void* rho1, const void* mu1,
-                       char* err) {
+                       void* edge, char* err) {
   EncodeTiledFn enc = encode_tiled();
   if (!enc) {
     std::snprintf(err, 256, "the CUDA driver's tensor-map encoder is not available");
@@ -1072,18 +1260,22 @@ bool collide_tma_setup(CollideTma* T, const Lattice<float>& L, const void* rho0,
   T->mu_ptr[0] = L.mu;
   T->mu_ptr[1] = mu1;
   // persistent grids: every block that fits on the device at once
-  int dev = 0, sms = 0, b0 = 0, b1 = 0;
+  int dev = 0, sms = 0, b0 = 0, b1 = 0, b2 = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_collide_tma<false>, NODE_BLOCK,
-                                                    (size_t)TMA_STAGES * tma_stage_bytes(false)) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_collide_tma<true>, NODE_BLOCK,
-                                                    (size_t)TMA_STAGES * tma_stage_bytes(true)) != cudaSuccess) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_collide_tma<false, false>, NODE_BLOCK,
+                                                    collide_smem_bytes(false, false)) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_collide_tma<true, false>, NODE_BLOCK,
+                                                    collide_smem_bytes(true, false)) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_collide_tma<false, true>, NODE_BLOCK,
+                                                    collide_smem_bytes(false, true)) != cudaSuccess) {
     (void)cudaGetLastError();
     std::snprintf(err, 256, "occupancy query failed");
     return false;
   }
   T->blocks[0] = (b0 > 0 ? b0 : 1) * sms;
   T->blocks[1] = (b1 > 0 ? b1 : 1) * sms;
+  T->sweep_blocks = (b2 > 0 ? b2 : 1) * sms;
+  T->edge = static_cast<float*>(edge);
   return true;
 }
 
@@ -1114,8 +1306,10 @@ cudaError_t launch_step_overlap(const Lattice<real>& Lt, const Lattice<real>& Ln
   // the fused pass left this state's mu at the end of the previous step; psi (pseudopotential
   // force): the previous step's density pass, scatter and layers
   const bool fused = fused_mu(L);
+  const bool sweep = sweep_ready(L, cur);
   if (!L.pseudo && !fused) launch_mu(L, s);
-  launch_collide(L, cur, s);
+  if (sweep) launch_collide_sweep(L, cur, Ln.rho, s);
+  else launch_collide(L, cur, s);
   cudaError_t e = cudaEventRecord(fork, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, fork, 0);
   if (e != cudaSuccess) return e;
@@ -1123,7 +1317,9 @@ cudaError_t launch_step_overlap(const Lattice<real>& Lt, const Lattice<real>& Ln
   launch_bc(L, cur, s);
   if (Ln.n_s1 > 0) k_solid1_b<real><<<grid_for(Ln.n_s1, NODE_BLOCK), NODE_BLOCK, 0, s>>>(Ln);
   if (Ln.n_s2 > 0) k_solid<real><<<grid_for(Ln.n_s2, NODE_BLOCK), NODE_BLOCK, 0, s>>>(Ln, 2);
-  if (fused) {
+  if (sweep) {
+    launch_sweep_fix(L, Ln, cur, s2);
+  } else if (fused) {
     if constexpr (sizeof(real) == 4)
       k_rho_mu_tile<<<dim3((unsigned)((Ln.nx + RM_W - 1) / RM_W), (unsigned)((Ln.ny + RM_H - 1) / RM_H)), NODE_BLOCK, 0,
                       s2>>>(Ln, cur ^ 1);
@@ -1160,6 +1356,32 @@ cudaError_t launch_phase(const Lattice<real>& L, int cur, int phase, cudaStream_
     default: launch_bc(L, cur, s);
   }
   return cudaGetLastError();
+}
+
+// The phases of a step whose collide kernel sweeps (step_sweeps), one after another for the
+// per-phase timing, in their order: 2 chemical potential, 3 force + collide + stream + most of
+// the next density, 4 boundary links, 1 the next state's solid layers, 0 the densities the
+// sweep left and the boundary nodes'.  Lt, Ln as for launch_step_overlap.
+template <typename real>
+cudaError_t launch_phase_sweep(const Lattice<real>& Lt, const Lattice<real>& Ln, int cur, int phase, cudaStream_t s) {
+  switch (phase) {
+    case 0:
+      launch_sweep_fix(Lt, Ln, cur, s);
+      if (Lt.n_bnodes > 0) k_rho_scatter<real><<<grid_for(Lt.n_bnodes, NODE_BLOCK), NODE_BLOCK, 0, s>>>(Ln);
+      break;
+    case 1:
+      if (Ln.n_s1 > 0) k_solid1_b<real><<<grid_for(Ln.n_s1, NODE_BLOCK), NODE_BLOCK, 0, s>>>(Ln);
+      if (Ln.n_s2 > 0) k_solid<real><<<grid_for(Ln.n_s2, NODE_BLOCK), NODE_BLOCK, 0, s>>>(Ln, 2);
+      break;
+    case 2: launch_mu(Lt, s); break;
+    case 3: launch_collide_sweep(Lt, cur, Ln.rho, s); break;
+    default: launch_bc(Lt, cur, s);
+  }
+  return cudaGetLastError();
+}
+template <typename real>
+bool step_sweeps(const Lattice<real>& L, int cur) {
+  return sweep_ready(L, cur);
 }
 
 template <typename real>
@@ -1230,6 +1452,8 @@ cudaError_t launch_init(const Lattice<real>& L, const double* drops, int n_drop,
   template cudaError_t launch_step<real>(const Lattice<real>&, int, cudaStream_t);                      \
   template int launches_per_step<real>(const Lattice<real>&);                                           \
   template cudaError_t launch_phase<real>(const Lattice<real>&, int, int, cudaStream_t);                \
+  template cudaError_t launch_phase_sweep<real>(const Lattice<real>&, const Lattice<real>&, int, int, cudaStream_t); \
+  template bool step_sweeps<real>(const Lattice<real>&, int);                                           \
   template cudaError_t launch_macro<real>(const Lattice<real>&, int, cudaStream_t);                     \
   template cudaError_t launch_step_overlap<real>(const Lattice<real>&, const Lattice<real>&, int, cudaStream_t, \
                                                  cudaStream_t, cudaEvent_t, cudaEvent_t);                  \

@@ -210,7 +210,10 @@ class Lattice:
         return v.value
 
     def set_collide_kernel(self, kind: int):
-        """0: the plain collide kernel; 1: the TMA-pipelined one (FP32; the default where available)."""
+        """0: the plain collide kernel; 1: the TMA-pipelined one (FP32); 2: the TMA-pipelined column
+        sweeps that also form the next state's density (FP32, chemical-potential force, lattices of
+        whole 32 x 8 tiles; slower on GB300, so never the default).  lbm_build_links picks 1 on large
+        lattices, 0 otherwise."""
         self._c(self.lib.lbm_set_collide_kernel(self.ctx, int(kind)))
 
     def set_mu_kernel(self, kind: int):

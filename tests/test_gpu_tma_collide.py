@@ -74,8 +74,8 @@ def test_switching_back_and_forth_keeps_the_state():
 
 
 def test_the_default_follows_the_lattice_size():
-    """The pipeline pays off on large lattices only: the 2048 x 4096 impact lattice takes it,
-    the 1024 x 1024 one (about five tiles per persistent block) keeps the plain kernel."""
+    """The pipeline pays off on large lattices only: the 2048 x 4096 impact lattice takes it, the
+    1024 x 1024 one (about five tiles per persistent block) keeps the plain kernel."""
     assert make_lattice(S.c3_impact(), fp64=False).collide_kernel() == 1
     assert make_lattice(S.c2_fp32_single(), fp64=False).collide_kernel() == 0
 
