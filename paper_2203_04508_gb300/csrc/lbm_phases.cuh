@@ -57,9 +57,11 @@ __device__ __forceinline__ void phase_mu(const Lattice<real>& L, int x, int y) {
 // the node: from the density and chemical-potential planes (force_at), or from a tile of them
 // staged in shared memory -- the same values in the same order of operations.
 // The second half of the phase, for populations fl already loaded from lattice `cur`.
+// inner: the caller knows that no push of this node wraps around a lattice edge (a whole tile
+// one node away from every edge), which skips the per-node test; the destinations are the same.
 template <typename real, typename Force>
 __device__ __forceinline__ void collide_loaded(const Lattice<real>& L, int cur, int x, int y, real (&fl)[9],
-                                               Force&& force) {
+                                               Force&& force, bool inner = false) {
   const int n = y * L.pitch + x;
   real* __restrict__ fout = L.f[cur ^ 1];
   real drho, jx, jy;
@@ -69,7 +71,7 @@ __device__ __forceinline__ void collide_loaded(const Lattice<real>& L, int cur, 
   force(r, Fx, Fy);
   collide_node(L, fl, r, drho, jx, jy, Fx, Fy);
   int xm = x - 1, xp = x + 1, rowc = y * L.pitch, rowm = rowc - L.pitch, rowp = rowc + L.pitch;
-  if (!interior(L, x, y)) {
+  if (!inner && !interior(L, x, y)) {
     xm = wrap_x(L, x - 1);
     xp = wrap_x(L, x + 1);
     rowm = wrap_y(L, y - 1) * L.pitch;

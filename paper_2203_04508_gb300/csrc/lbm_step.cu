@@ -425,9 +425,11 @@ __device__ __forceinline__ void tile_force_terms(const real* sm, const real* sr,
 template <typename real, bool PSEUDO>
 __device__ __forceinline__ void tile_force(const Lattice<real>& L, bool stencils, const real (&g)[4], real r, real& Fx,
                                            real& Fy) {
-  Fx = r * L.gx;
-  Fy = r * L.gy;
-  if (!stencils) return;
+  if (!stencils) {
+    Fx = r * L.gx;
+    Fy = r * L.gy;
+    return;
+  }
   if (PSEUDO) {
     Fx = force_pp(r, L.gx, g[2], g[0]);
     Fy = force_pp(r, L.gy, g[2], g[1]);
@@ -648,26 +650,36 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, in
   auto rho_of = [&](int s) { return reinterpret_cast<float*>(tma_smem + s * SB + TMA_F_BYTES + TMA_M_BYTES); };
   float* ring = reinterpret_cast<float*>(tma_smem + TMA_STAGES * SB);
   uint8_t* rkind = tma_smem + TMA_STAGES * SB + SW_RING_BYTES;
-  // this block's tiles: k = 0 .. nt - 1 at (x0 of k, y0 of k)
-  int nt, strip = 0, ya = 0;
+  // this block's tiles k = 0 .. nt - 1, as tile coordinates (tx, ty) advanced without a division:
+  // tiles blockIdx.x + k gridDim.x of the row-major tile order, or its band of one strip
+  int nt, ya = 0, tx, ty, dx = 0, dy = 1;
   if (SWEEP) {
-    strip = blockIdx.x % A.strips;
+    tx = blockIdx.x % A.strips;
     const int band = blockIdx.x / A.strips;
     const int tr0 = sweep_band_start(band, A.bands, A.tile_rows);
     nt = sweep_band_start(band + 1, A.bands, A.tile_rows) - tr0;
+    ty = tr0;
     ya = tr0 * CT_Y;
   } else {
     nt = n_tiles > (int)blockIdx.x ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    tx = (int)blockIdx.x % tiles_x;
+    ty = (int)blockIdx.x / tiles_x;
+    dx = (int)gridDim.x % tiles_x;
+    dy = (int)gridDim.x / tiles_x;
   }
-  auto tile_x0 = [&](int k) {
-    return SWEEP ? strip * CT_X : (((int)blockIdx.x + k * (int)gridDim.x) % tiles_x) * CT_X;
+  auto advance = [&](int& ax, int& ay) {
+    ax += dx;
+    ay += dy;
+    if (ax >= tiles_x && !SWEEP) {
+      ax -= tiles_x;
+      ++ay;
+    }
   };
-  auto tile_y0 = [&](int k) {
-    return SWEEP ? ya + k * CT_Y : (((int)blockIdx.x + k * (int)gridDim.x) / tiles_x) * CT_Y;
-  };
-  // thread 0: request tile k into stage s
-  auto issue = [&](int k, int s) {
-    const int x0 = tile_x0(k), y0 = tile_y0(k);
+  int itx = tx, ity = ty;   // thread 0: the next tile to request
+  // thread 0: request the next tile into stage s
+  auto issue = [&](int s) {
+    const int x0 = itx * CT_X, y0 = ity * CT_Y;
+    advance(itx, ity);
     const bool h = stencils && tma_halo<PSEUDO>(L, x0, y0);
     mbar_expect_tx(&bar[s], TMA_F_BYTES + (h ? (PSEUDO ? 1 : 2) * TMA_M_BYTES : 0));
     tma_load_3d(f_of(s), &M.f, x0, y0, 0, &bar[s]);
@@ -682,12 +694,14 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, in
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int s = 0; s < TMA_STAGES && s < nt; ++s) issue(s, s);
+    for (int s = 0; s < TMA_STAGES && s < nt; ++s) issue(s);
   }
-  for (int k = 0; k < nt; ++k) {
+  for (int k = 0; k < nt; ++k, advance(tx, ty)) {
     const int s = k % TMA_STAGES;
-    const int x0 = tile_x0(k), y0 = tile_y0(k);
+    const int x0 = tx * CT_X, y0 = ty * CT_Y;
     const int x = x0 + lx, y = y0 + ly;
+    // no push of the tile wraps around an edge (with walls, rows never wrap)
+    const bool inner = x0 >= 1 && x0 + CT_X < L.nx && (L.walls || (y0 >= 1 && y0 + CT_Y < L.ny));
     const bool fluid = x < L.nx && y < L.ny && L.kind[y * L.pitch + x] == KIND_FLUID;
     const bool ok = mbar_wait(&bar[s], (uint32_t)((k / TMA_STAGES) & 1), L.spin_limit);
     if (__syncthreads_or(!ok)) {
@@ -731,12 +745,13 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, in
     __syncthreads();
     if (threadIdx.x == 0 && k + TMA_STAGES < nt) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(k + TMA_STAGES, s);
+      issue(s);
     }
     if (!SWEEP) {
       if (!fluid) continue;
-      collide_loaded(L, cur, x, y, fl,
-                     [&](float r, float& Fx, float& Fy) { tile_force<float, PSEUDO>(L, stencils, g, r, Fx, Fy); });
+      collide_loaded(
+          L, cur, x, y, fl, [&](float r, float& Fx, float& Fy) { tile_force<float, PSEUDO>(L, stencils, g, r, Fx, Fy); },
+          inner);
       continue;
     }
     // ring rows of this node's row and of the rows below and above it
@@ -744,8 +759,9 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, in
     const int sm1 = sc == 0 ? SW_R - 1 : sc - 1, sp1 = sc == SW_R - 1 ? 0 : sc + 1;
     rkind[sc * CT_X + lx] = fluid ? 1 : 0;
     if (fluid) {
-      collide_loaded(L, cur, x, y, fl,
-                     [&](float r, float& Fx, float& Fy) { tile_force<float, PSEUDO>(L, stencils, g, r, Fx, Fy); });
+      collide_loaded(
+          L, cur, x, y, fl, [&](float r, float& Fx, float& Fy) { tile_force<float, PSEUDO>(L, stencils, g, r, Fx, Fy); },
+          inner);
       // fl holds the post-collision populations: direction i lands at (lx + ex(i), row + ey(i))
       auto at = [&](int i, int slot, int col) -> float& { return ring[(i * SW_R + slot) * SW_W + col]; };
       at(0, sc, lx + 1) = fl[0];
@@ -776,7 +792,7 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, in
       const int ye = y0 - 1 + j;
       if (ye > ya) {
         int dir, rcol, ecol;
-        sweep_edge_entry(e, strip, A.strips, dir, rcol, ecol);
+        sweep_edge_entry(e, tx, A.strips, dir, rcol, ecol);
         const int se = (ye - ya + 1) % SW_R;
         A.edge[((long long)dir * 2 * A.strips + ecol) * L.ny + ye] = ring[(dir * SW_R + se) * SW_W + rcol];
       }
