@@ -298,6 +298,11 @@ void fill_lattice(lbm_ctx* c, Lattice<real>& L) {
   L.s_eps = (real)g.s_eps;
   L.s_q = (real)g.s_q;
   L.s_nu = (real)g.s_nu;
+  // in the storage precision, as a kernel would form them
+  L.keep_e = real(1) - L.s_e;
+  L.keep_eps = real(1) - L.s_eps;
+  L.keep_q = real(1) - L.s_q;
+  L.keep_nu = real(1) - L.s_nu;
   L.gx = (real)g.gx;
   L.gy = (real)g.gy;
   L.bc = g.bc;

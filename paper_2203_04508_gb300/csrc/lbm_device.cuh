@@ -51,6 +51,7 @@ struct Lattice {
   int coll;
   real omega;                   // 1 / tau (BGK)
   real s_e, s_eps, s_q, s_nu;
+  real keep_e, keep_eps, keep_q, keep_nu;   // 1 - s_k, formed once in the storage precision
   real gx, gy;
   int bc;
   // pseudopotential force model (instead of Eqs. 9 and 12): mu holds psi, the solid layers
@@ -423,12 +424,12 @@ __device__ __forceinline__ void collide_node(const Lattice<real>& L, real (&f)[9
     const real d13 = f[1] - f[3], d24 = f[2] - f[4];
     const real j2r = (jx * jx + jy * jy) * inv_r;
     // non-equilibrium moments, scaled by 1 - s_k
-    const real e = ((real(-4) * f[0] - s1234 + real(2) * s5678) + (real(2) * drho - real(3) * j2r)) * (real(1) - L.s_e);
-    const real eps = ((real(4) * f[0] - real(2) * s1234 + s5678) - (drho - real(3) * j2r)) * (real(1) - L.s_eps);
-    const real qx = ((jx - real(3) * d13) + jx) * (real(1) - L.s_q);
-    const real qy = ((jy - real(3) * d24) + jy) * (real(1) - L.s_q);
-    const real pxx = ((s13 - s24) - (jx * jx - jy * jy) * inv_r) * (real(1) - L.s_nu);
-    const real pxy = ((s57 - s68) - jx * jy * inv_r) * (real(1) - L.s_nu);
+    const real e = ((real(-4) * f[0] - s1234 + real(2) * s5678) + (real(2) * drho - real(3) * j2r)) * L.keep_e;
+    const real eps = ((real(4) * f[0] - real(2) * s1234 + s5678) - (drho - real(3) * j2r)) * L.keep_eps;
+    const real qx = ((jx - real(3) * d13) + jx) * L.keep_q;
+    const real qy = ((jy - real(3) * d24) + jy) * L.keep_q;
+    const real pxx = ((s13 - s24) - (jx * jx - jy * jy) * inv_r) * L.keep_nu;
+    const real pxy = ((s57 - s68) - jx * jy * inv_r) * L.keep_nu;
     const real e36 = e * real(1.0 / 36.0), e18 = e * real(1.0 / 18.0);
     const real s36 = eps * real(1.0 / 36.0), s18 = eps * real(1.0 / 18.0);
     const real qx6 = qx * real(1.0 / 6.0), qy6 = qy * real(1.0 / 6.0);

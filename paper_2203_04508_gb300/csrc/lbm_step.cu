@@ -641,6 +641,9 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, in
   static_assert(!(PSEUDO && SWEEP), "the sweep forms the chemical-potential model's density");
   extern __shared__ __align__(128) unsigned char tma_smem[];
   __shared__ __align__(8) uint64_t bar[TMA_STAGES];
+  // per stage, set by the thread that requests its tile: x0, y0, and flags (1: the halo came by
+  // TMA, 2: no push of the tile wraps around an edge)
+  __shared__ int4 info[TMA_STAGES];
   constexpr int SB = tma_stage_bytes(PSEUDO);
   const bool stencils = L.eos != EOS_NONE;
   const int lx = threadIdx.x % CT_X, ly = threadIdx.x / CT_X;
@@ -681,6 +684,9 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, in
     const int x0 = itx * CT_X, y0 = ity * CT_Y;
     advance(itx, ity);
     const bool h = stencils && tma_halo<PSEUDO>(L, x0, y0);
+    // with walls, rows never wrap
+    const bool inner = x0 >= 1 && x0 + CT_X < L.nx && (L.walls || (y0 >= 1 && y0 + CT_Y < L.ny));
+    info[s] = make_int4(x0, y0, (h ? 1 : 0) | (inner ? 2 : 0), 0);
     mbar_expect_tx(&bar[s], TMA_F_BYTES + (h ? (PSEUDO ? 1 : 2) * TMA_M_BYTES : 0));
     tma_load_3d(f_of(s), &M.f, x0, y0, 0, &bar[s]);
     if (h) {
@@ -696,12 +702,13 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, in
   if (threadIdx.x == 0) {
     for (int s = 0; s < TMA_STAGES && s < nt; ++s) issue(s);
   }
-  for (int k = 0; k < nt; ++k, advance(tx, ty)) {
+  __syncthreads();
+  for (int k = 0; k < nt; ++k) {
     const int s = k % TMA_STAGES;
-    const int x0 = tx * CT_X, y0 = ty * CT_Y;
+    const int4 tile = info[s];
+    const int x0 = tile.x, y0 = tile.y;
+    const bool inner = (tile.z & 2) != 0;
     const int x = x0 + lx, y = y0 + ly;
-    // no push of the tile wraps around an edge (with walls, rows never wrap)
-    const bool inner = x0 >= 1 && x0 + CT_X < L.nx && (L.walls || (y0 >= 1 && y0 + CT_Y < L.ny));
     const bool fluid = x < L.nx && y < L.ny && L.kind[y * L.pitch + x] == KIND_FLUID;
     const bool ok = mbar_wait(&bar[s], (uint32_t)((k / TMA_STAGES) & 1), L.spin_limit);
     if (__syncthreads_or(!ok)) {
@@ -716,7 +723,7 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, in
     }
     float* sm = mu_of(s);
     float* sr = rho_of(s);
-    if (stencils && !tma_halo<PSEUDO>(L, x0, y0)) {
+    if (stencils && !(tile.z & 1)) {
       // the halo wraps around a periodic edge: plain wrap-aware loads, as k_collide stages it
       const int h = PSEUDO ? 1 : CT_H;
       for (int e = threadIdx.x; e < TMA_HX * TMA_MY; e += NODE_BLOCK) {
