@@ -78,6 +78,22 @@ typedef enum {
                             the batch and reverse-mode calls return LBM_EINVAL for it. */
 } lbm_force_model;
 
+/* How the populations are held in memory (Eq. 5's streaming).
+ *  LBM_LAYOUT_AB: two lattices; the collide of each step reads one and pushes into the other.
+ *  LBM_LAYOUT_AA: one lattice, updated in place, half the population memory.  Steps alternate:
+ *    the first reads each node's own nine slots and writes its post-collision populations back
+ *    into the same node's slots, each into the slot of its opposite direction (the state then
+ *    holds f_i(x) in slot ibar of node x - e_i); the next reads the populations from those
+ *    slots and writes each f~_i(x) into slot i of node x + e_i (the state is in natural order
+ *    again).  Each node reads and writes the same nine locations, so no step races with another
+ *    node.  The boundary phase, the density pass and every read-out address the slots of the
+ *    state's current order; the pre-collision moments the boundary links need (Eq. 17's F_i
+ *    uses u at x1) are saved for the boundary nodes before the collide overwrites them.  The
+ *    values equal those of LBM_LAYOUT_AB bit for bit.  Single lattices only: the batch, slab and
+ *    reverse-mode calls return LBM_EINVAL for it, as do collide kernel 2 and the fused
+ *    chemical-potential pass (lbm_set_collide_kernel, lbm_set_mu_kernel). */
+typedef enum { LBM_LAYOUT_AB = 0, LBM_LAYOUT_AA = 1 } lbm_layout;
+
 /*
  * Configuration of one lattice.  Geometry: nodes sit at integer (x, y), 0 <= x < nx,
  * 0 <= y < ny.  A node is solid when it lies inside a cylinder, (x-cx)^2 + (y-cy)^2 <= r^2,
@@ -116,6 +132,7 @@ typedef struct {
   const double* dmu_w;
   double dmu_w_walls;          /* dmu_w of the two flat walls */
   int32_t force_model;         /* lbm_force_model */
+  int32_t layout;              /* lbm_layout; 0: two lattices */
 } lbm_config;
 
 /* Initial state, Eq. 19: around each droplet a tanh profile of width `width` between the
@@ -132,8 +149,9 @@ typedef struct {
 } lbm_init_spec;
 
 /* Bytes of device workspace one lattice of this configuration needs (populations in two
- * lattices, density and chemical-potential planes, node flags, boundary-link and solid-layer
- * lists sized for the geometry's upper bound, reduction scratch). */
+ * lattices, or in one plus three staging planes with LBM_LAYOUT_AA; density and
+ * chemical-potential planes, node flags, boundary-link and solid-layer lists sized for the
+ * geometry's upper bound, reduction scratch). */
 lbm_status lbm_workspace_size(const lbm_config* cfg, size_t* bytes);
 
 /* Validates cfg, solves the EOS set-up on the host (critical point and Maxwell coexistence

@@ -6,7 +6,8 @@ include/lbm.h; this package only marshals arguments and takes device memory and 
 PyTorch.  There is no CPU fallback: without the built library every call raises.
 """
 from . import _abi  # noqa: F401
-from ._abi import LBM_FP32, LBM_FP64, LBM_FORCE_CHEMPOT, LBM_FORCE_PSEUDO, LbmError, declared_symbols, load  # noqa: F401
+from ._abi import (LBM_FP32, LBM_FP64, LBM_FORCE_CHEMPOT, LBM_FORCE_PSEUDO, LBM_LAYOUT_AA, LBM_LAYOUT_AB,  # noqa: F401
+                   LbmError, declared_symbols, load)
 from .lattice import Batch, Lattice, make_config, workspace_size  # noqa: F401
 from .autograd import params_vector, rollout, with_params  # noqa: F401
 

@@ -11,6 +11,7 @@ LIB_PATH = os.path.join(HERE, "liblbm_gb300.so")
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ESTATE, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_EINTERNAL, LBM_ECORRUPT = range(9)
 LBM_FP32, LBM_FP64 = 0, 1
 LBM_FORCE_CHEMPOT, LBM_FORCE_PSEUDO = 0, 1
+LBM_LAYOUT_AB, LBM_LAYOUT_AA = 0, 1
 
 
 class lbm_config(C.Structure):
@@ -24,7 +25,7 @@ class lbm_config(C.Structure):
         ("bc", C.c_int32), ("precision", C.c_int32), ("rho_ref", C.c_double),
         ("n_cyl", C.c_int32), ("cx", C.POINTER(C.c_double)), ("cy", C.POINTER(C.c_double)),
         ("r", C.POINTER(C.c_double)), ("dmu_w", C.POINTER(C.c_double)), ("dmu_w_walls", C.c_double),
-        ("force_model", C.c_int32),
+        ("force_model", C.c_int32), ("layout", C.c_int32),
     ]
 
 

@@ -56,6 +56,10 @@ struct Layout {
   size_t sz;
   Caps cap;
   size_t fA, fB, rho, rho2, mu, mu2, psip, kind, body, near, edge, edge_bytes;
+  // one lattice (AA order): fB == fA, `stage` holds three planes for the read-outs and the
+  // set-up scratch (which use the idle second lattice otherwise), `bmom` the boundary nodes'
+  // saved moments
+  size_t stage, bmom;
   size_t lq64, lq, ldir, lx2f, bnode, bstart, carry, rhob;
   size_t s1node, s1mask, s1winv, s1nb, s2node, s2mask, s2winv;
   size_t cyl, drops, partials, counter, step_ctr, scalars, kerr, dm_ring, block_sums, totals;
@@ -66,7 +70,7 @@ struct Layout {
 // chemical-potential force with an equation of state, whole 32 x 8 tiles
 bool sweep_shape(const lbm_config* c) {
   return c->precision == LBM_FP32 && c->force_model == LBM_FORCE_CHEMPOT && c->eos != LBM_EOS_NONE && c->nx % 32 == 0 &&
-         c->ny % 8 == 0;
+         c->ny % 8 == 0 && c->layout != LBM_LAYOUT_AA;
 }
 
 Layout make_layout(const lbm_config* c) {
@@ -78,8 +82,10 @@ Layout make_layout(const lbm_config* c) {
   L.cap = list_caps(c);
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return at; };
+  const bool aa = c->layout == LBM_LAYOUT_AA;
   L.fA = take(9 * L.plane * L.sz);
-  L.fB = take(9 * L.plane * L.sz);
+  L.fB = aa ? L.fA : take(9 * L.plane * L.sz);
+  L.stage = aa ? take(3 * L.plane * L.sz) : 0;
   L.rho = take(L.plane * L.sz);
   L.rho2 = take(L.plane * L.sz);
   L.mu = take(L.plane * L.sz);
@@ -97,6 +103,7 @@ Layout make_layout(const lbm_config* c) {
   L.bstart = take((L.cap.bnodes + 1) * 4);
   L.carry = take(L.cap.bnodes * 8);
   L.rhob = take(L.cap.bnodes * L.sz);
+  L.bmom = take(aa ? 3 * L.cap.bnodes * L.sz : 0);
   L.s1node = take(L.cap.s1 * 4);
   L.s1mask = take(L.cap.s1);
   L.s1winv = take(L.cap.s1 * L.sz);
@@ -242,7 +249,8 @@ int default_mu_kernel(const lbm_ctx* c) {
     l2 = 0;
   }
   const bool chempot = c->cfg.force_model == LBM_FORCE_CHEMPOT && c->cfg.eos != LBM_EOS_NONE;
-  if (chempot && 72.0 * c->cfg.nx * c->cfg.ny <= (double)l2) return 3;
+  // (the fused pass reads the populations in 16-byte rows, which the AA order shifts)
+  if (chempot && c->cfg.layout != LBM_LAYOUT_AA && 72.0 * c->cfg.nx * c->cfg.ny <= (double)l2) return 3;
   const long long blocks = (long long)((c->cfg.nx + 511) / 512) * ((c->cfg.ny + 15) / 16);
   return blocks >= 4LL * sms ? 2 : 1;
 }
@@ -258,6 +266,8 @@ void fill_lattice(lbm_ctx* c, Lattice<real>& L) {
   L.plane = y.plane;
   L.f[0] = (real*)(w + y.fA);
   L.f[1] = (real*)(w + y.fB);
+  L.aa = c->cfg.layout == LBM_LAYOUT_AA ? 1 : 0;
+  L.bmom = L.aa ? (real*)(w + y.bmom) : nullptr;
   L.rho = (real*)(w + y.rho);
   L.rho_b = nullptr;
   L.mu = (real*)(w + y.mu);
@@ -393,6 +403,7 @@ lbm_status validate(const lbm_config* g, char* msg) {
     if (!std::isfinite(g->dmu_w[j])) return bad("wall chemical potential must be finite");
   }
   if (g->force_model != LBM_FORCE_CHEMPOT && g->force_model != LBM_FORCE_PSEUDO) return bad("unknown force_model");
+  if (g->layout != LBM_LAYOUT_AB && g->layout != LBM_LAYOUT_AA) return bad("layout must be LBM_LAYOUT_AB or LBM_LAYOUT_AA");
   if (g->force_model == LBM_FORCE_PSEUDO) {
     // the wall factor c_w multiplies psi by 1 + c_w, which must stay positive
     for (int j = 0; j < g->n_cyl; ++j)
@@ -564,6 +575,15 @@ lbm_status profile_steps(lbm_ctx* c, const Lattice<real>& L, long long n, double
 
 // Fluid nodes the mass audit counts: a slab's own rows only.
 long long fluid_count(const lbm_ctx* c) { return c->slab.on ? c->slab.n_fluid_own : c->n_fluid; }
+
+// Device staging memory of the read-outs: the lattice that the next step overwrites completely
+// (nine planes), or with one lattice (AA order) the three staging planes.
+char* stage_area(const lbm_ctx* c) {
+  if (c->cfg.layout == LBM_LAYOUT_AA) return c->ws + c->lay.stage;
+  return c->ws + (c->cur ? c->lay.fA : c->lay.fB);
+}
+// planes of populations the staging memory holds at once
+int stage_planes(const lbm_ctx* c) { return c->cfg.layout == LBM_LAYOUT_AA ? 3 : 9; }
 
 // A slab's local configuration: the global one with ny = the rows it holds and flat walls at
 // both ends of them -- the global walls where the slab reaches a global wall row, else two
@@ -782,6 +802,7 @@ lbm_status lbm_slab_workspace_size(const lbm_config* cfg, int32_t y0, int32_t y1
   char msg[256];
   lbm_status s = validate(cfg, msg);
   if (s != LBM_OK) return s;
+  if (cfg->layout != LBM_LAYOUT_AB) return LBM_EINVAL;
   lbm_config loc;
   lbm_ctx::Slab sl;
   s = slab_local_config(cfg, y0, y1, halo, &loc, &sl, msg);
@@ -799,6 +820,10 @@ lbm_status lbm_create_slab(const lbm_config* cfg, int32_t y0, int32_t y1, int32_
   lbm_status s = validate(cfg, msg);
   lbm_config loc{};
   lbm_ctx::Slab sl;
+  if (s == LBM_OK && cfg->layout != LBM_LAYOUT_AB) {
+    std::snprintf(msg, 256, "slabs exchange halos of two population lattices only");
+    s = LBM_EINVAL;
+  }
   if (s == LBM_OK) s = slab_local_config(cfg, y0, y1, halo, &loc, &sl, msg);
   if (s != LBM_OK) {
     lbm_ctx* c = new lbm_ctx();
@@ -864,10 +889,11 @@ lbm_status lbm_build_links(lbm_ctx* c) {
   gp.dmu_walls = g.dmu_w_walls;
   gp.y_off = c->slab.on ? c->slab.y_off : 0;
   gp.ny_glob = c->slab.on && c->slab.periodic ? c->slab.ny_glob : 0;
-  // the second lattice is free until lbm_init: it holds the per-node scratch of the set-up
+  // the second lattice (one lattice: the staging planes) is free until lbm_init: it holds the
+  // per-node scratch of the set-up
   GeomScratch sc{};
   sc.body = (int*)(w + y.body);
-  sc.cnt = (int*)(w + y.fB);
+  sc.cnt = (int*)(w + (c->cfg.layout == LBM_LAYOUT_AA ? y.stage : y.fB));
   sc.off = sc.cnt + y.plane;
   sc.block_sums = (int*)(w + y.block_sums);
   sc.totals = (int*)(w + y.totals);
@@ -1038,7 +1064,7 @@ lbm_status lbm_set_collide_kernel(lbm_ctx* c, int32_t kind) {
   if (kind == 2 && (!sweep_shape(&c->cfg) || c->slab.on))
     return fail(c, LBM_EINVAL,
                 "the column sweeps need the chemical-potential force with an equation of state, nx a multiple of 32 "
-                "and ny of 8, and a whole lattice");
+                "and ny of 8, and a whole lattice of two population lattices");
   if (kind == c->collide_kind) return LBM_OK;
   c->collide_kind = kind;
   // captured launches carry the old kernel: capture again
@@ -1068,6 +1094,8 @@ lbm_status lbm_set_mu_kernel(lbm_ctx* c, int32_t kind) {
   if (kind >= 2 && c->fp64) return fail(c, LBM_EINVAL, "the row-sweep and fused chemical-potential kernels are FP32 only");
   if (kind == 3 && (c->cfg.force_model != LBM_FORCE_CHEMPOT || c->cfg.eos == LBM_EOS_NONE))
     return fail(c, LBM_EINVAL, "the fused chemical-potential kernel needs the chemical-potential force");
+  if (kind == 3 && c->cfg.layout == LBM_LAYOUT_AA)
+    return fail(c, LBM_EINVAL, "the fused chemical-potential kernel needs two population lattices");
   c->mu_kind = kind;
   c->rho_ok = false;   // a change to or from the fused pass moves where mu is kept
   if (kind == 3 && !c->near_built) {
@@ -1102,8 +1130,7 @@ lbm_status lbm_fields(lbm_ctx* c, void* rho, void* vx, void* vy, int32_t on_devi
   if (!rho || !vx || !vy) return fail(c, LBM_EINVAL, "null output");
   const long long dn = (long long)c->cfg.nx * c->cfg.ny;
   const size_t sz = c->lay.sz;
-  // the lattice that the next step overwrites completely serves as staging memory
-  char* stage = c->ws + (c->cur ? c->lay.fA : c->lay.fB);
+  char* stage = stage_area(c);
   char* r = on_device ? (char*)rho : stage;
   char* u = on_device ? (char*)vx : stage + dn * sz;
   char* v = on_device ? (char*)vy : stage + 2 * dn * sz;
@@ -1151,6 +1178,7 @@ uint64_t config_hash(const lbm_ctx* c) {
   const double reals[] = {g.y_bottom, g.y_top, g.a, g.b, g.R, g.T_over_Tc, g.omega, g.k, g.kappa, g.tau,
                           g.s_e, g.s_eps, g.s_q, g.s_nu, g.gx, g.gy, c->rho_ref, g.dmu_w_walls};
   mix(ints, sizeof(ints));
+  if (g.layout != LBM_LAYOUT_AB) mix(&g.layout, sizeof(g.layout));
   mix(reals, sizeof(reals));
   for (const std::vector<double>* v : {&c->cx, &c->cy, &c->r, &c->dmu}) mix(v->data(), v->size() * sizeof(double));
   return h;
@@ -1266,8 +1294,7 @@ lbm_status lbm_column_density(lbm_ctx* c, int32_t x, int32_t y0, int32_t n, doub
   if (!out) return fail(c, LBM_EINVAL, "null output");
   if (x < 0 || x >= c->cfg.nx || y0 < 0 || n < 1 || (long long)y0 + n > c->cfg.ny)
     return fail(c, LBM_EINVAL, "column outside the lattice");
-  // the lattice that the next step overwrites completely serves as staging memory
-  double* d = on_device ? out : (double*)(c->ws + (c->cur ? c->lay.fA : c->lay.fB));
+  double* d = on_device ? out : (double*)stage_area(c);
   if (c->fp64) CUDA_OK(c, launch_column(c->Ld, c->cur, x, y0, n, d, c->stream));
   else CUDA_OK(c, launch_column(c->Lf, c->cur, x, y0, n, d, c->stream));
   if (!on_device) {
@@ -1282,8 +1309,7 @@ lbm_status lbm_max_speed(lbm_ctx* c, double* vmax) {
   if (!c || !c->inited) return LBM_ESTATE;
   if (c->sticky != LBM_OK) return c->sticky;
   if (!vmax) return fail(c, LBM_EINVAL, "null output");
-  // the lattice that the next step overwrites completely serves as the reduction slot
-  auto* d = (unsigned long long*)(c->ws + (c->cur ? c->lay.fA : c->lay.fB));
+  auto* d = (unsigned long long*)stage_area(c);
   CUDA_OK(c, cudaMemsetAsync(d, 0, 8, c->stream));
   if (c->fp64) CUDA_OK(c, launch_max_speed(c->Ld, c->cur, d, c->stream));
   else CUDA_OK(c, launch_max_speed(c->Lf, c->cur, d, c->stream));
@@ -1299,14 +1325,21 @@ lbm_status lbm_populations(lbm_ctx* c, void* f, int32_t on_device) {
   if (!f) return fail(c, LBM_EINVAL, "null output");
   const long long dn = (long long)c->cfg.nx * c->cfg.ny;
   const size_t sz = c->lay.sz;
-  char* stage = c->ws + (c->cur ? c->lay.fA : c->lay.fB);
-  char* out = on_device ? (char*)f : stage;
-  if (c->fp64) CUDA_OK(c, launch_populations(c->Ld, c->cur, (double*)out, c->stream));
-  else CUDA_OK(c, launch_populations(c->Lf, c->cur, (float*)out, c->stream));
-  if (!on_device) {
-    CUDA_OK(c, cudaMemcpyAsync(f, out, 9 * dn * sz, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  if (on_device) {
+    if (c->fp64) CUDA_OK(c, launch_populations(c->Ld, c->cur, (double*)f, 0, 9, c->stream));
+    else CUDA_OK(c, launch_populations(c->Lf, c->cur, (float*)f, 0, 9, c->stream));
+    return LBM_OK;
   }
+  // through the staging memory, as many planes at a time as it holds
+  char* stage = stage_area(c);
+  const int per = stage_planes(c);
+  for (int i0 = 0; i0 < 9; i0 += per) {
+    const int i1 = i0 + per < 9 ? i0 + per : 9;
+    if (c->fp64) CUDA_OK(c, launch_populations(c->Ld, c->cur, (double*)stage, i0, i1, c->stream));
+    else CUDA_OK(c, launch_populations(c->Lf, c->cur, (float*)stage, i0, i1, c->stream));
+    CUDA_OK(c, cudaMemcpyAsync((char*)f + i0 * dn * sz, stage, (i1 - i0) * dn * sz, cudaMemcpyDeviceToHost, c->stream));
+  }
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
   return LBM_OK;
 }
 
@@ -1318,13 +1351,21 @@ lbm_status lbm_set_populations(lbm_ctx* c, const void* f, int32_t on_device) {
   const Layout& y = c->lay;
   const long long dn = (long long)c->cfg.nx * c->cfg.ny;
   c->cur = 0;
-  const void* src = f;
-  if (!on_device) {
-    CUDA_OK(c, cudaMemcpyAsync(c->ws + y.fB, f, 9 * dn * y.sz, cudaMemcpyHostToDevice, c->stream));
-    src = c->ws + y.fB;
+  if (on_device) {
+    if (c->fp64) CUDA_OK(c, launch_set_populations(c->Ld, 0, (const double*)f, 0, 9, c->stream));
+    else CUDA_OK(c, launch_set_populations(c->Lf, 0, (const float*)f, 0, 9, c->stream));
+  } else {
+    // through the staging memory (the second lattice, or one lattice's three staging planes)
+    char* stage = c->ws + (c->cfg.layout == LBM_LAYOUT_AA ? y.stage : y.fB);
+    const int per = stage_planes(c);
+    for (int i0 = 0; i0 < 9; i0 += per) {
+      const int i1 = i0 + per < 9 ? i0 + per : 9;
+      CUDA_OK(c, cudaMemcpyAsync(stage, (const char*)f + i0 * dn * y.sz, (i1 - i0) * dn * y.sz,
+                                 cudaMemcpyHostToDevice, c->stream));
+      if (c->fp64) CUDA_OK(c, launch_set_populations(c->Ld, 0, (const double*)stage, i0, i1, c->stream));
+      else CUDA_OK(c, launch_set_populations(c->Lf, 0, (const float*)stage, i0, i1, c->stream));
+    }
   }
-  if (c->fp64) CUDA_OK(c, launch_set_populations(c->Ld, 0, (const double*)src, c->stream));
-  else CUDA_OK(c, launch_set_populations(c->Lf, 0, (const float*)src, c->stream));
   CUDA_OK(c, cudaMemsetAsync(c->ws + y.step_ctr, 0, 16, c->stream));
   CUDA_OK(c, cudaMemsetAsync(c->ws + y.dm_ring, 0, (size_t)(DM_RING + 1) * 8, c->stream));
   CUDA_OK(c, cudaMemsetAsync(c->ws + y.carry, 0, (size_t)y.cap.bnodes * 8, c->stream));
@@ -1475,6 +1516,7 @@ lbm_status plan_batch(int n, const lbm_config* cfgs, BatchPlan* P, char* msg) {
     if (s != LBM_OK) return s;
     if (cfgs[k].precision != cfgs[0].precision) { std::snprintf(msg, 256, "all instances of a batch share one precision"); return LBM_EINVAL; }
     if (cfgs[k].force_model != LBM_FORCE_CHEMPOT) { std::snprintf(msg, 256, "the batched kernel runs the chemical-potential force only"); return LBM_EINVAL; }
+    if (cfgs[k].layout != LBM_LAYOUT_AB) { std::snprintf(msg, 256, "the batched kernel runs two population lattices only"); return LBM_EINVAL; }
     Layout L = make_layout(&cfgs[k]);
     P->off[k] = o;
     P->bytes[k] = L.total;
@@ -2112,6 +2154,7 @@ extern "C" {
 lbm_status lbm_adjoint_workspace_size(lbm_ctx* c, int64_t n_steps, int64_t every, size_t* bytes) {
   if (!c || !c->built || !bytes) return LBM_ESTATE;
   if (c->cfg.force_model != LBM_FORCE_CHEMPOT) return fail(c, LBM_EINVAL, "the reverse mode covers the chemical-potential force only");
+  if (c->cfg.layout != LBM_LAYOUT_AB) return fail(c, LBM_EINVAL, "the reverse mode needs two population lattices");
   if (n_steps < 1 || every < 0) return fail(c, LBM_EINVAL, "n_steps must be positive and every non-negative");
   *bytes = make_adj_layout(c, n_steps, every).total;
   return LBM_OK;
@@ -2123,6 +2166,7 @@ lbm_status lbm_forward_checkpointed(lbm_ctx* c, int64_t n_steps, int64_t every, 
   if (c->sticky != LBM_OK) return c->sticky;
   if (n_steps < 1 || every < 0) return fail(c, LBM_EINVAL, "n_steps must be positive and every non-negative");
   if (c->cfg.force_model != LBM_FORCE_CHEMPOT) return fail(c, LBM_EINVAL, "the reverse mode covers the chemical-potential force only");
+  if (c->cfg.layout != LBM_LAYOUT_AB) return fail(c, LBM_EINVAL, "the reverse mode needs two population lattices");
   const AdjLayout A = make_adj_layout(c, n_steps, every);
   if (!workspace || ((uintptr_t)workspace) % ALIGN) return fail(c, LBM_EINVAL, "adjoint workspace must be 256-byte aligned");
   if (bytes < A.total) return fail(c, LBM_ENOMEM, "adjoint workspace of %zu bytes, %zu needed", bytes, A.total);
@@ -2145,6 +2189,7 @@ lbm_status lbm_objective(lbm_ctx* c, int32_t body, double* J, void* dJ_drho, int
   if (c->sticky != LBM_OK) return c->sticky;
   if (!J) return fail(c, LBM_EINVAL, "null output");
   if (body < 0 || body >= c->cfg.n_cyl) return fail(c, LBM_EINVAL, "body %d is not a cylinder", body);
+  if (c->cfg.layout != LBM_LAYOUT_AB) return fail(c, LBM_EINVAL, "the reverse mode needs two population lattices");
   return c->fp64 ? objective(c, c->Ld, body, J, dJ_drho, on_device) : objective(c, c->Lf, body, J, dJ_drho, on_device);
 }
 

@@ -29,7 +29,12 @@ template <typename real>
 struct Lattice {
   int nx, ny, pitch, walls;
   int plane;                    // pitch * ny (9 * plane < 2^31)
-  real* f[2];                   // the two population lattices (9 planes each)
+  real* f[2];                   // the two population lattices (9 planes each); with aa set both
+                                // point at the one lattice, updated in place
+  int aa;                       // one lattice (AA order): the state of lattice 0 is in natural
+                                // order, that of lattice 1 holds f_i(x) in slot opp(i) of x - e_i
+  real* bmom;                   // aa: per boundary node, the pre-collision (delta rho, jx, jy) the
+                                // boundary phase needs, saved before the collide overwrites them
   real* rho;                    // density plane (fluid and the two solid layers)
   real* rho_b;                  // if set: the boundary phase leaves the density of each
                                 // boundary node's final populations here (one per node)
@@ -123,6 +128,22 @@ __device__ __forceinline__ int wrap_y(const Lattice<real>& L, int y) {
 template <typename real>
 __device__ __forceinline__ int node_at(const Lattice<real>& L, int x, int y) {
   return wrap_y(L, y) * L.pitch + wrap_x(L, x);
+}
+
+// Index (into L.f[c]) of population i of node (x, y) of the state held as lattice c: slot i of
+// the node, or in AA order (aa, c = 1) slot opp(i) of node (x, y) - e_i.  x, y may lie one node
+// outside the lattice (wrapped like node_at).
+template <typename real>
+__device__ __forceinline__ int pop_index(const Lattice<real>& L, int c, int i, int x, int y) {
+  if (L.aa && c == 1) return opp(i) * L.plane + node_at(L, x - ex(i), y - ey(i));
+  return i * L.plane + node_at(L, x, y);
+}
+// the nine populations of node (x, y) of the state held as lattice c
+template <typename real>
+__device__ __forceinline__ void load_pops(const Lattice<real>& L, int c, int x, int y, real (&fl)[9]) {
+  const real* f = L.f[c];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) fl[i] = f[pop_index(L, c, i, x, y)];
 }
 
 // Sums of products with a fixed rounding order.  Where an expression adds two products

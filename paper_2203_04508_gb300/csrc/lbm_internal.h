@@ -39,12 +39,15 @@ cudaError_t launch_step_overlap(const Lattice<real>& Lt, const Lattice<real>& Ln
                                 cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join);
 template <typename real> int launches_per_step_overlap(const Lattice<real>& L);
 template <typename real> cudaError_t launch_fields(const Lattice<real>& L, int cur, real* r, real* vx, real* vy, cudaStream_t s);
-template <typename real> cudaError_t launch_populations(const Lattice<real>& L, int cur, real* out, cudaStream_t s);
+// populations i0 <= i < i1 of the current state, population i into dense plane i - i0 of out
+template <typename real>
+cudaError_t launch_populations(const Lattice<real>& L, int cur, real* out, int i0, int i1, cudaStream_t s);
 template <typename real>
 cudaError_t launch_column(const Lattice<real>& L, int cur, int x, int y0, int n, double* out, cudaStream_t s);
 template <typename real>
 cudaError_t launch_max_speed(const Lattice<real>& L, int cur, unsigned long long* out, cudaStream_t s);
-template <typename real> cudaError_t launch_set_populations(const Lattice<real>& L, int cur, const real* in, cudaStream_t s);
+template <typename real>
+cudaError_t launch_set_populations(const Lattice<real>& L, int cur, const real* in, int i0, int i1, cudaStream_t s);
 template <typename real> cudaError_t launch_mass(const Lattice<real>& L, int cur, cudaStream_t s);
 template <typename real> cudaError_t launch_init(const Lattice<real>& L, const double* drops, int n_drop, double W,
                                                  double rho_g, double rho_l, cudaStream_t s);

@@ -59,17 +59,26 @@ __device__ __forceinline__ void phase_mu(const Lattice<real>& L, int x, int y) {
 // The second half of the phase, for populations fl already loaded from lattice `cur`.
 // inner: the caller knows that no push of this node wraps around a lattice edge (a whole tile
 // one node away from every edge), which skips the per-node test; the destinations are the same.
-template <typename real, typename Force>
+// INPLACE (the first step of the AA order, one lattice): f~_i goes back into the node's own slot
+// opp(i) instead of being pushed to x + e_i -- the slot the AA order reads f_i(x + e_i) from.
+template <bool INPLACE = false, typename real, typename Force>
 __device__ __forceinline__ void collide_loaded(const Lattice<real>& L, int cur, int x, int y, real (&fl)[9],
                                                Force&& force, bool inner = false) {
   const int n = y * L.pitch + x;
-  real* __restrict__ fout = L.f[cur ^ 1];
   real drho, jx, jy;
   moments(fl, drho, jx, jy);
   const real r = L.rho_ref + drho;
   real Fx, Fy;
   force(r, Fx, Fy);
   collide_node(L, fl, r, drho, jx, jy, Fx, Fy);
+  if (INPLACE) {
+    // the one lattice is both source and destination; this node alone reads and writes its slots
+    real* f = L.f[0];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[opp(i) * L.plane + n] = fl[i];
+    return;
+  }
+  real* __restrict__ fout = L.f[cur ^ 1];
   int xm = x - 1, xp = x + 1, rowc = y * L.pitch, rowm = rowc - L.pitch, rowp = rowc + L.pitch;
   if (!inner && !interior(L, x, y)) {
     xm = wrap_x(L, x - 1);
@@ -134,8 +143,8 @@ template <typename real, int PREFETCH = 0, bool PSEUDO = false>
 __device__ __forceinline__ double phase_bc(const Lattice<real>& L, int cur, int b) {
   const int n = L.bnode[b];
   const int x = n % L.pitch, y = n / L.pitch;
-  const real* __restrict__ fin = L.f[cur];
   real* fout = L.f[cur ^ 1];
+  const int nc = cur ^ 1;   // the state after the collide, in its slot order (pop_index)
   const int l0 = L.bstart[b], l1 = L.bstart[b + 1];
   constexpr int P = PREFETCH > 0 ? PREFETCH : 1;
   int pd[P];
@@ -155,17 +164,26 @@ __device__ __forceinline__ double phase_bc(const Lattice<real>& L, int cur, int 
     for (int k = 0; k < P; ++k) {
       if (l0 + k < l1) {
         const int i = pd[k];
-        pa[k] = fout[i * L.plane + node_at(L, x + ex(i), y + ey(i))];
-        pb[k] = fout[i * L.plane + n];
-        pc[k] = fout[opp(i) * L.plane + node_at(L, x - ex(i), y - ey(i))];
+        pa[k] = fout[pop_index(L, nc, i, x + ex(i), y + ey(i))];
+        pb[k] = fout[pop_index(L, nc, i, x, y)];
+        pc[k] = fout[pop_index(L, nc, opp(i), x - ex(i), y - ey(i))];
       }
     }
   }
-  real fl[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) fl[i] = fin[i * L.plane + n];
   real drho, jx, jy;
-  moments(fl, drho, jx, jy);
+  if (L.aa) {
+    // one lattice: the collide has overwritten the node's pre-collision populations; their
+    // moments were saved before it (k_bmom, the same sums)
+    drho = L.bmom[3 * b];
+    jx = L.bmom[3 * b + 1];
+    jy = L.bmom[3 * b + 2];
+  } else {
+    const real* __restrict__ fin = L.f[cur];
+    real fl[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fl[i] = fin[i * L.plane + n];
+    moments(fl, drho, jx, jy);
+  }
   const real r = L.rho_ref + drho;
   real Fx, Fy;
   force_at<real, PSEUDO>(L, x, y, r, Fx, Fy);
@@ -187,15 +205,15 @@ __device__ __forceinline__ double phase_bc(const Lattice<real>& L, int cur, int 
       i = L.ldir[l];
       q = L.lq[l];
       x2f = L.lx2f[l];
-      a = fout[i * L.plane + node_at(L, x + ex(i), y + ey(i))];
-      b2 = fout[i * L.plane + n];
-      c = fout[opp(i) * L.plane + node_at(L, x - ex(i), y - ey(i))];
+      a = fout[pop_index(L, nc, i, x + ex(i), y + ey(i))];
+      b2 = fout[pop_index(L, nc, i, x, y)];
+      c = fout[pop_index(L, nc, opp(i), x - ex(i), y - ey(i))];
     }
     const int ib = opp(i);
     // F_i(x1, t) of direction i
     const real Fi = edm_dir<real>(i, r, ux, uy, dux, duy);
     const real v = link_rule<real>(L.bc, q, x2f, a, b2, c, Fi);
-    fout[ib * L.plane + n] = v;
+    fout[pop_index(L, nc, ib, x, y)] = v;
     sum += (double)a - (double)v;
   }
   if (L.bc == BC_PRESENT || L.bc == BC_MIBC) {
@@ -212,7 +230,7 @@ __device__ __forceinline__ double phase_bc(const Lattice<real>& L, int cur, int 
     // order of density_of, as the density pass would take it)
     real g[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) g[i] = fout[i * L.plane + n];
+    for (int i = 0; i < 9; ++i) g[i] = fout[pop_index(L, nc, i, x, y)];
     L.rho_b[b] = density_of(L, g);
   }
   return (L.bc == BC_PRESENT || L.bc == BC_MIBC) ? sum : 0.0;

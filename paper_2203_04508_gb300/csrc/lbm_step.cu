@@ -106,6 +106,39 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_rho_vec(Lattice<real> L, int cur
   }
 }
 
+// The density pass of a state in AA order (one lattice after its in-place step): f_i(x) lies in
+// slot opp(i) of x - e_i, so the rows are shifted per direction and the 16-byte loads of
+// k_rho_vec do not apply; one node a thread, the same sums and stores as k_rho_vec.
+template <typename real>
+__global__ void __launch_bounds__(NODE_BLOCK) k_rho_pull(Lattice<real> L, int cur) {
+  const int x = blockIdx.x * TILE_X + threadIdx.x, y = blockIdx.y * TILE_Y + threadIdx.y;
+  if (x >= L.nx || y >= L.ny) return;
+  const int n = y * L.pitch + x;
+  if (L.kind[n] != KIND_FLUID) return;
+  real fl[9];
+  load_pops(L, cur, x, y, fl);
+  const real r = density_of(L, fl);
+  L.rho[n] = r;
+  if (L.psip) L.psip[n] = psi_prime_shifted(L, r);
+  else if (L.pseudo && L.eos != EOS_NONE) L.mu[n] = psi_of(L, r);
+}
+
+// One lattice (AA order): the pre-collision moments of every boundary node, which the boundary
+// phase needs after the collide has overwritten the populations (the sums of `moments`).
+template <typename real>
+__global__ void __launch_bounds__(NODE_BLOCK) k_bmom(Lattice<real> L, int cur) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= L.n_bnodes) return;
+  const int n = L.bnode[b];
+  real fl[9];
+  load_pops(L, cur, n % L.pitch, n / L.pitch, fl);
+  real drho, jx, jy;
+  moments(fl, drho, jx, jy);
+  L.bmom[3 * b] = drho;
+  L.bmom[3 * b + 1] = jx;
+  L.bmom[3 * b + 2] = jy;
+}
+
 // psi(rho_s) (1 + c_w) of a solid-layer node whose density is rho_s (pseudopotential force)
 template <typename real>
 __device__ __forceinline__ real psi_wall(const Lattice<real>& L, int n, real rs) {
@@ -448,7 +481,10 @@ constexpr int CT_X = 32, CT_Y = NODE_BLOCK / CT_X, CT_H = 2;
 constexpr int CT_SX = CT_X + 2 * CT_H, CT_SY = CT_Y + 2 * CT_H;
 static_assert(CT_X == 32 && CT_SX - 32 <= 32, "one warp stages a row of the tile and its halo");
 
-template <typename real, bool PSEUDO>
+// LAY: 0 two lattices; one lattice in AA order, 1 its first step (natural order in, each node's
+// own slots rewritten in place), 2 its second (f_i(x) pulled from slot opp(i) of x - e_i, pushed
+// into slot i of x + e_i).
+template <typename real, bool PSEUDO, int LAY = 0>
 __global__ void __launch_bounds__(NODE_BLOCK) k_collide(Lattice<real> L, int cur) {
   __shared__ real s_rho[CT_SY][CT_SX];
   __shared__ real s_mu[CT_SY][CT_SX];
@@ -461,9 +497,20 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide(Lattice<real> L, int cur
   const bool fluid = x < L.nx && y < L.ny && L.kind[y * L.pitch + x] == KIND_FLUID;
   real fl[9];
   if (fluid) {
-    const real* __restrict__ fin = L.f[cur];
+    if (LAY == 2) {
+      const real* fin = L.f[0];
+      const int n = y * L.pitch + x;
+      if (interior(L, x, y)) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) fl[i] = fin[i * L.plane + y * L.pitch + x];
+        for (int i = 0; i < 9; ++i) fl[i] = fin[opp(i) * L.plane + n - ex(i) - ey(i) * L.pitch];
+      } else {
+        load_pops(L, 1, x, y, fl);
+      }
+    } else {
+      const real* __restrict__ fin = L.f[cur];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) fl[i] = fin[i * L.plane + y * L.pitch + x];
+    }
   }
   if (stencils) {
     if (x0 >= CT_H && x0 + CT_X + CT_H <= L.nx && y0 >= CT_H && y0 + CT_Y + CT_H <= L.ny) {
@@ -500,8 +547,8 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide(Lattice<real> L, int cur
   if (!fluid) return;
   real g[4] = {real(0), real(0), real(0), real(0)};
   if (stencils) tile_force_terms<real, PSEUDO>(&s_mu[0][0], &s_rho[0][0], CT_SX, (ly + CT_H) * CT_SX + lx + CT_H, g);
-  collide_loaded(L, cur, x, y, fl,
-                 [&](real r, real& Fx, real& Fy) { tile_force<real, PSEUDO>(L, stencils, g, r, Fx, Fy); });
+  collide_loaded<LAY == 1>(L, cur, x, y, fl,
+                           [&](real r, real& Fx, real& Fy) { tile_force<real, PSEUDO>(L, stencils, g, r, Fx, Fy); });
 }
 
 // ---------------------------------------------------------------------------------------
@@ -635,10 +682,13 @@ __device__ __forceinline__ void sweep_edge_entry(int e, int strip, int strips, i
   else { rcol = CT_X + 1; ecol = 2 * (strip + 1 == strips ? 0 : strip + 1); }
 }
 
-template <bool PSEUDO, bool SWEEP>
+// INPLACE: the first step of the AA order on one lattice -- tiles are loaded as in natural order
+// and every node's post-collision populations go back into its own slots (collide_loaded).
+template <bool PSEUDO, bool SWEEP, bool INPLACE = false>
 __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, int cur, const __grid_constant__ CollideMaps M,
                                                             int tiles_x, int n_tiles, SweepArgs A) {
   static_assert(!(PSEUDO && SWEEP), "the sweep forms the chemical-potential model's density");
+  static_assert(!(SWEEP && INPLACE), "the sweep pushes into a second lattice");
   extern __shared__ __align__(128) unsigned char tma_smem[];
   __shared__ __align__(8) uint64_t bar[TMA_STAGES];
   // per stage, set by the thread that requests its tile: x0, y0, and flags (1: the halo came by
@@ -756,7 +806,7 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, in
     }
     if (!SWEEP) {
       if (!fluid) continue;
-      collide_loaded(
+      collide_loaded<INPLACE>(
           L, cur, x, y, fl, [&](float r, float& Fx, float& Fy) { tile_force<float, PSEUDO>(L, stencils, g, r, Fx, Fy); },
           inner);
       continue;
@@ -905,10 +955,17 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_mass(Lattice<real> L, int cur) {
   for (long long n = n_lo + (long long)blockIdx.x * blockDim.x + threadIdx.x; n < n_hi;
        n += (long long)gridDim.x * blockDim.x) {
     if (L.kind[n] != KIND_FLUID) continue;
+    real fl[9];
+    if (L.aa) {
+      load_pops(L, cur, (int)(n % L.pitch), (int)(n / L.pitch), fl);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) fl[i] = f[i * L.plane + n];
+    }
     double t = 0.0;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      real v = f[i * L.plane + n];
+      const real v = fl[i];
       if (!isfinite(v)) bad += 1.0;
       t += (double)v;
     }
@@ -956,10 +1013,8 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_fields(Lattice<real> L, int cur,
     vy_out[d] = real(0);
     return;
   }
-  const real* __restrict__ f = L.f[cur];
   real fl[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) fl[i] = f[i * L.plane + n];
+  load_pops(L, cur, x, y, fl);
   real drho, jx, jy;
   moments(fl, drho, jx, jy);
   const real r = L.rho_ref + drho;
@@ -978,15 +1033,13 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_fields(Lattice<real> L, int cur,
 template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_max_speed(Lattice<real> L, int cur, unsigned long long* out) {
   unsigned long long b = 0ull;
-  const real* __restrict__ f = L.f[cur];
   const long long n_lo = (long long)L.own_lo * L.pitch, n_hi = (long long)L.own_hi * L.pitch;
   for (long long n = n_lo + (long long)blockIdx.x * blockDim.x + threadIdx.x; n < n_hi;
        n += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(n % L.pitch), y = (int)(n / L.pitch);
     if (x >= L.nx || L.kind[n] != KIND_FLUID) continue;
     real fl[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) fl[i] = f[i * L.plane + n];
+    load_pops(L, cur, x, y, fl);
     real drho, jx, jy;
     moments(fl, drho, jx, jy);
     const real r = L.rho_ref + drho;
@@ -1022,15 +1075,15 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_column(Lattice<real> L, int cur,
     out[j] = __longlong_as_double(0x7ff8000000000000LL);
     return;
   }
-  const real* __restrict__ f = L.f[cur];
   real fl[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) fl[i] = f[i * L.plane + node];
+  load_pops(L, cur, x, y0 + j, fl);
   out[j] = (double)density_of(L, fl);
 }
 
+// Populations i0 <= i < i1 of the current state as absolute values, population i into the
+// dense plane i - i0 of `out` (0 at non-fluid nodes).
 template <typename real>
-__global__ void k_populations(Lattice<real> L, int cur, real* out) {
+__global__ void k_populations(Lattice<real> L, int cur, real* out, int i0, int i1) {
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= L.plane) return;
   const int x = (int)(n % L.pitch), y = (int)(n / L.pitch);
@@ -1038,23 +1091,22 @@ __global__ void k_populations(Lattice<real> L, int cur, real* out) {
   const long long d = (long long)y * L.nx + x;
   const long long dn = (long long)L.nx * L.ny;
   const bool fluid = L.kind[n] == KIND_FLUID;
-#pragma unroll
-  for (int i = 0; i < 9; ++i)
-    out[i * dn + d] = fluid ? L.f[cur][i * L.plane + n] + real(wgt(i)) * L.rho_ref : real(0);
+  for (int i = i0; i < i1; ++i)
+    out[(i - i0) * dn + d] = fluid ? L.f[cur][pop_index(L, cur, i, x, y)] + real(wgt(i)) * L.rho_ref : real(0);
 }
 
 // inverse of k_populations: fluid nodes of lattice `cur` from 9 row-major arrays of absolute
 // populations (other nodes keep their values)
+// (populations i0 <= i < i1, population i from the dense plane i - i0 of `in`)
 template <typename real>
-__global__ void k_set_populations(Lattice<real> L, int cur, const real* in) {
+__global__ void k_set_populations(Lattice<real> L, int cur, const real* in, int i0, int i1) {
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= L.plane) return;
   const int x = (int)(n % L.pitch), y = (int)(n / L.pitch);
   if (x >= L.nx || L.kind[n] != KIND_FLUID) return;
   const long long d = (long long)y * L.nx + x;
   const long long dn = (long long)L.nx * L.ny;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) L.f[cur][i * L.plane + n] = in[i * dn + d] - real(wgt(i)) * L.rho_ref;
+  for (int i = i0; i < i1; ++i) L.f[cur][pop_index(L, cur, i, x, y)] = in[(i - i0) * dn + d] - real(wgt(i)) * L.rho_ref;
 }
 
 // Eq. 19 initial state: rho = (rho_g + rho_l)/2 + (rho_g - rho_l)/2 tanh(2(r - r0)/W) around
@@ -1069,7 +1121,10 @@ __global__ void k_init(Lattice<real> L, const double* __restrict__ drops, int n_
   real* f1 = L.f[1];
   if (x >= L.nx || L.kind[n] != KIND_FLUID) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) { f0[i * L.plane + n] = real(0); f1[i * L.plane + n] = real(0); }
+    for (int i = 0; i < 9; ++i) {
+      f0[i * L.plane + n] = real(0);
+      if (!L.aa) f1[i * L.plane + n] = real(0);
+    }
     return;
   }
   double phi = 0.0, u0 = 0.0, v0 = 0.0;
@@ -1089,7 +1144,7 @@ __global__ void k_init(Lattice<real> L, const double* __restrict__ drops, int n_
     double eu = ex(i) * ux + ey(i) * uy;
     double feq = wgt(i) * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - usq);
     f0[i * L.plane + n] = (real)(feq - wgt(i) * rref);
-    f1[i * L.plane + n] = real(0);
+    if (!L.aa) f1[i * L.plane + n] = real(0);
   }
   L.rho[n] = (real)r;
 }
@@ -1176,8 +1231,26 @@ static inline SweepArgs sweep_args(const Lattice<float>& L, const CollideTma* T,
   A.bands = b < 1 ? 1 : (b > A.tile_rows ? A.tile_rows : b);
   return A;
 }
+// the density pass of the state held as lattice cur (16-byte rows, or one node a thread where
+// the AA order shifts the slots)
+template <typename real>
+static inline void launch_density(const Lattice<real>& L, int cur, cudaStream_t s) {
+  if (L.aa && cur == 1) k_rho_pull<real><<<node_grid(L), node_block(), 0, s>>>(L, cur);
+  else k_rho_vec<real><<<rho_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
+}
+// AA order: the boundary nodes' pre-collision moments, before the collide overwrites them
+template <typename real>
+static inline void launch_bmom(const Lattice<real>& L, int cur, cudaStream_t s) {
+  if (L.aa && L.n_bnodes > 0) k_bmom<real><<<grid_for(L.n_bnodes, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, cur);
+}
 template <typename real>
 static inline void launch_collide(const Lattice<real>& L, int cur, cudaStream_t s) {
+  if (L.aa && cur == 1) {
+    // the second step of the AA order pulls along shifted rows: the plain kernel
+    if (L.pseudo) k_collide<real, true, 2><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
+    else k_collide<real, false, 2><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
+    return;
+  }
   if constexpr (sizeof(real) == 4) {
     if (const CollideTma* T = tma_for(L, cur)) {
       const CollideMaps M = maps_for(T, L, cur);
@@ -1187,13 +1260,25 @@ static inline void launch_collide(const Lattice<real>& L, int cur, cudaStream_t 
       const int grid = tiles < T->blocks[P] ? tiles : T->blocks[P];
       const size_t smem = collide_smem_bytes(L.pseudo, false);
       const SweepArgs none{};
-      if (L.pseudo) k_collide_tma<true, false><<<grid, NODE_BLOCK, smem, s>>>(L, cur, M, tiles_x, tiles, none);
-      else k_collide_tma<false, false><<<grid, NODE_BLOCK, smem, s>>>(L, cur, M, tiles_x, tiles, none);
+      if (L.aa) {
+        if (L.pseudo) k_collide_tma<true, false, true><<<grid, NODE_BLOCK, smem, s>>>(L, cur, M, tiles_x, tiles, none);
+        else k_collide_tma<false, false, true><<<grid, NODE_BLOCK, smem, s>>>(L, cur, M, tiles_x, tiles, none);
+      } else if (L.pseudo) {
+        k_collide_tma<true, false><<<grid, NODE_BLOCK, smem, s>>>(L, cur, M, tiles_x, tiles, none);
+      } else {
+        k_collide_tma<false, false><<<grid, NODE_BLOCK, smem, s>>>(L, cur, M, tiles_x, tiles, none);
+      }
       return;
     }
   }
-  if (L.pseudo) k_collide<real, true><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
-  else k_collide<real, false><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
+  if (L.aa) {
+    if (L.pseudo) k_collide<real, true, 1><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
+    else k_collide<real, false, 1><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
+  } else if (L.pseudo) {
+    k_collide<real, true><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
+  } else {
+    k_collide<real, false><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
+  }
 }
 // collide (column sweeps) of lattice cur into cur ^ 1, the next density into rho_next; then the
 // densities the sweep left
@@ -1304,11 +1389,11 @@ bool collide_tma_setup(CollideTma* T, const Lattice<float>& L, const void* rho0,
 
 template <typename real>
 cudaError_t launch_step(const Lattice<real>& L, int cur, cudaStream_t s) {
-  const unsigned gn = grid_for(L.plane, NODE_BLOCK);
-  k_rho_vec<real><<<rho_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
+  launch_density(L, cur, s);
   if (L.n_s1 > 0) k_solid<real><<<grid_for(L.n_s1, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 1);
   if (L.n_s2 > 0) k_solid<real><<<grid_for(L.n_s2, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 2);
   launch_mu(L, s);
+  launch_bmom(L, cur, s);
   launch_collide(L, cur, s);
   launch_bc(L, cur, s);
   return cudaGetLastError();
@@ -1330,10 +1415,22 @@ cudaError_t launch_step_overlap(const Lattice<real>& Lt, const Lattice<real>& Ln
   // force): the previous step's density pass, scatter and layers
   const bool fused = fused_mu(L);
   const bool sweep = sweep_ready(L, cur);
+  cudaError_t e;
+  const bool bmom = L.aa && L.n_bnodes > 0;
+  if (bmom) {
+    // one lattice: the boundary nodes' moments are saved on s2 while mu is formed on s
+    e = cudaEventRecord(fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, fork, 0);
+    if (e != cudaSuccess) return e;
+    launch_bmom(L, cur, s2);
+    e = cudaEventRecord(join, s2);
+    if (e != cudaSuccess) return e;
+  }
   if (!L.pseudo && !fused) launch_mu(L, s);
+  if (bmom && (e = cudaStreamWaitEvent(s, join, 0)) != cudaSuccess) return e;
   if (sweep) launch_collide_sweep(L, cur, Ln.rho, s);
   else launch_collide(L, cur, s);
-  cudaError_t e = cudaEventRecord(fork, s);
+  e = cudaEventRecord(fork, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, fork, 0);
   if (e != cudaSuccess) return e;
   const unsigned gb = grid_for(L.n_bnodes, NODE_BLOCK);
@@ -1347,7 +1444,7 @@ cudaError_t launch_step_overlap(const Lattice<real>& Lt, const Lattice<real>& Ln
       k_rho_mu_tile<<<dim3((unsigned)((Ln.nx + RM_W - 1) / RM_W), (unsigned)((Ln.ny + RM_H - 1) / RM_H)), NODE_BLOCK, 0,
                       s2>>>(Ln, cur ^ 1);
   } else {
-    k_rho_vec<real><<<rho_grid(Ln), NODE_BLOCK, 0, s2>>>(Ln, cur ^ 1);
+    launch_density(Ln, cur ^ 1, s2);
   }
   e = cudaEventRecord(join, s2);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join, 0);
@@ -1360,22 +1457,24 @@ cudaError_t launch_step_overlap(const Lattice<real>& Lt, const Lattice<real>& Ln
 template <typename real>
 int launches_per_step_overlap(const Lattice<real>& L) {
   return launches_per_step(L) + (L.n_bnodes > 0) - (L.pseudo && L.eos != EOS_NONE) - (fused_mu(L) ? 1 : 0) +
-         (fused_mu(L) && L.n_near > 0 ? 1 : 0);
+         (fused_mu(L) && L.n_near > 0 ? 1 : 0) + (L.aa && L.n_bnodes > 0 ? 1 : 0);
 }
 
 // one phase of a step: 0 density, 1 solid layers, 2 chemical potential, 3 force+collide+stream,
 // 4 boundary links
 template <typename real>
 cudaError_t launch_phase(const Lattice<real>& L, int cur, int phase, cudaStream_t s) {
-  const unsigned gn = grid_for(L.plane, NODE_BLOCK);
   switch (phase) {
-    case 0: k_rho_vec<real><<<rho_grid(L), NODE_BLOCK, 0, s>>>(L, cur); break;
+    case 0: launch_density(L, cur, s); break;
     case 1:
       if (L.n_s1 > 0) k_solid<real><<<grid_for(L.n_s1, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 1);
       if (L.n_s2 > 0) k_solid<real><<<grid_for(L.n_s2, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 2);
       break;
     case 2: launch_mu(L, s); break;
-    case 3: launch_collide(L, cur, s); break;
+    case 3:
+      launch_bmom(L, cur, s);
+      launch_collide(L, cur, s);
+      break;
     default: launch_bc(L, cur, s);
   }
   return cudaGetLastError();
@@ -1415,8 +1514,7 @@ int launches_per_step(const Lattice<real>& L) {
 // density / solid layers / chemical potential of the current state (for the read-outs)
 template <typename real>
 cudaError_t launch_macro(const Lattice<real>& L, int cur, cudaStream_t s) {
-  const unsigned gn = grid_for(L.plane, NODE_BLOCK);
-  k_rho_vec<real><<<rho_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
+  launch_density(L, cur, s);
   if (L.n_s1 > 0) k_solid<real><<<grid_for(L.n_s1, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 1);
   if (L.n_s2 > 0) k_solid<real><<<grid_for(L.n_s2, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, 2);
   launch_mu(L, s);
@@ -1447,14 +1545,14 @@ cudaError_t launch_column(const Lattice<real>& L, int cur, int x, int y0, int n,
 }
 
 template <typename real>
-cudaError_t launch_populations(const Lattice<real>& L, int cur, real* out, cudaStream_t s) {
-  k_populations<real><<<grid_for(L.plane, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, cur, out);
+cudaError_t launch_populations(const Lattice<real>& L, int cur, real* out, int i0, int i1, cudaStream_t s) {
+  k_populations<real><<<grid_for(L.plane, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, cur, out, i0, i1);
   return cudaGetLastError();
 }
 
 template <typename real>
-cudaError_t launch_set_populations(const Lattice<real>& L, int cur, const real* in, cudaStream_t s) {
-  k_set_populations<real><<<grid_for(L.plane, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, cur, in);
+cudaError_t launch_set_populations(const Lattice<real>& L, int cur, const real* in, int i0, int i1, cudaStream_t s) {
+  k_set_populations<real><<<grid_for(L.plane, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, cur, in, i0, i1);
   return cudaGetLastError();
 }
 
@@ -1482,10 +1580,10 @@ cudaError_t launch_init(const Lattice<real>& L, const double* drops, int n_drop,
                                                  cudaStream_t, cudaEvent_t, cudaEvent_t);                  \
   template int launches_per_step_overlap<real>(const Lattice<real>&);                                   \
   template cudaError_t launch_fields<real>(const Lattice<real>&, int, real*, real*, real*, cudaStream_t); \
-  template cudaError_t launch_populations<real>(const Lattice<real>&, int, real*, cudaStream_t);        \
+  template cudaError_t launch_populations<real>(const Lattice<real>&, int, real*, int, int, cudaStream_t); \
   template cudaError_t launch_column<real>(const Lattice<real>&, int, int, int, int, double*, cudaStream_t); \
   template cudaError_t launch_max_speed<real>(const Lattice<real>&, int, unsigned long long*, cudaStream_t); \
-  template cudaError_t launch_set_populations<real>(const Lattice<real>&, int, const real*, cudaStream_t); \
+  template cudaError_t launch_set_populations<real>(const Lattice<real>&, int, const real*, int, int, cudaStream_t); \
   template cudaError_t launch_mass<real>(const Lattice<real>&, int, cudaStream_t);                      \
   template cudaError_t launch_init<real>(const Lattice<real>&, const double*, int, double, double,      \
                                          double, cudaStream_t);

@@ -14,14 +14,16 @@ _PHYS_KEYS = ("nx", "ny", "walls", "y_bottom", "y_top", "eos", "a", "b", "R", "T
               "kappa", "coll", "tau", "s_e", "s_eps", "s_q", "s_nu", "gx", "gy", "bc", "dmu_w_walls")
 
 
-def make_config(phys: dict, precision: int, rho_ref: float = -1.0):
-    """lbm_config from a plain dict of physical parameters; returns (struct, keep-alive arrays)."""
+def make_config(phys: dict, precision: int, rho_ref: float = -1.0, layout: int = _abi.LBM_LAYOUT_AB):
+    """lbm_config from a plain dict of physical parameters; returns (struct, keep-alive arrays).
+    layout: LBM_LAYOUT_AB (two population lattices) or LBM_LAYOUT_AA (one, updated in place)."""
     keep = {k: np.ascontiguousarray(np.asarray(phys.get(k, []), dtype=np.float64).reshape(-1))
             for k in ("cx", "cy", "r", "dmu_w")}
     c = lbm_config()
     for k in _PHYS_KEYS:
         setattr(c, k, phys[k])
     c.force_model = int(phys.get("force_model", 0))
+    c.layout = int(layout)
     c.precision = precision
     c.rho_ref = rho_ref
     c.n_cyl = len(keep["r"])
@@ -30,8 +32,8 @@ def make_config(phys: dict, precision: int, rho_ref: float = -1.0):
     return c, keep
 
 
-def workspace_size(phys: dict, precision: int) -> int:
-    c, keep = make_config(phys, precision)
+def workspace_size(phys: dict, precision: int, layout: int = _abi.LBM_LAYOUT_AB) -> int:
+    c, keep = make_config(phys, precision, layout=layout)
     n = C.c_size_t()
     check(_abi.load().lbm_workspace_size(C.byref(c), C.byref(n)))
     return n.value
@@ -41,7 +43,7 @@ class Lattice:
     """One lattice on the current CUDA device."""
 
     def __init__(self, phys: dict, precision: int = _abi.LBM_FP32, rho_ref: float = -1.0,
-                 stream=None, build: bool = True):
+                 stream=None, build: bool = True, layout: int = _abi.LBM_LAYOUT_AB):
         import torch
         lib = _abi.load()
         if not torch.cuda.is_available():
@@ -51,7 +53,8 @@ class Lattice:
         self.precision = precision
         self.dtype = np.float64 if precision == _abi.LBM_FP64 else np.float32
         self.tdtype = torch.float64 if precision == _abi.LBM_FP64 else torch.float32
-        self._cfg, self._keep = make_config(phys, precision, rho_ref)
+        self.layout = int(layout)
+        self._cfg, self._keep = make_config(phys, precision, rho_ref, layout)
         n = C.c_size_t()
         check(lib.lbm_workspace_size(C.byref(self._cfg), C.byref(n)))
         self.workspace = torch.empty(n.value, dtype=torch.uint8, device="cuda")
