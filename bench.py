@@ -32,8 +32,10 @@ paper's Sec. 4.1-4.2 drops at full size with Peng-Robinson: mass change of the p
 and IBC at every q, 40 flat-wall lattices in one batch, and the curved substrate; and Sec. 4.5's
 drop impact at its three Bond numbers: the film on the cylinder's top against the h*(t*) laws), and
 `pseudopotential` (the impact lattice with the pseudopotential force in place of the
-chemical-potential one: step time, per-phase times, against the headline step).  `--mode kernels` / `--mode adjoint` run only the timed step loop / only the
-gradient workload (for profiler captures).
+chemical-potential one: step time, per-phase times, against the headline step), and `aa_layout`
+(the headline lattice with one population lattice in AA order: step time, workspace, against the
+two-lattice step).  `--mode kernels` / `--mode adjoint` run only the timed step loop / only the
+gradient workload (for profiler captures); `--layout 1` puts the headline lattice in AA order.
 """
 from __future__ import annotations
 
@@ -320,6 +322,37 @@ def run_pseudopotential(G, torch, steps, ms_chempot):
             "steps": steps, "ms_per_step": round(ms, 5), "mlups": round(sc.nodes / ms / 1e3, 1),
             "phase_ms": {k: round(float(v), 5) for k, v in zip(("rho", "solid", "psi", "collide", "bc"), phase_ms)},
             "step_time_vs_chemical_potential": round(ms / ms_chempot, 3), "mass_drift": M / M0 - 1}
+
+
+def run_aa(G, torch, sc, steps, ms_two):
+    """The headline lattice with ONE population lattice in AA order (LBM_LAYOUT_AA): the in-place
+    first step and the pull-push second alternate, so steps are timed in pairs.  Step time from
+    CUDA events over graph launches, the workspace against the two-lattice one, and the step time
+    against the two-lattice step of the headline (the values are the same bits: tests/test_gpu_aa.py)."""
+    lat = G.Lattice(sc.physics(), precision=G.LBM_FP32, layout=G.LBM_LAYOUT_AA)
+    lat.init_droplets(sc.droplets())
+    ws = lat.workspace.numel()
+    ws_two = G.workspace_size(sc.physics(), G.LBM_FP32)
+    lat.step(20)
+    lat.synchronize()
+    steps += steps % 2
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(lat.stream)
+    lat.step(steps)
+    e1.record(lat.stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    n_prof = max(10, min(100, steps // 5)) // 2 * 2
+    phase_ms = lat.profile_steps(n_prof) / n_prof
+    M, M0, _ = lat.mass()
+    del lat
+    torch.cuda.empty_cache()
+    return {"layout": "AA (one population lattice, in place)", "steps": steps, "ms_per_step": round(ms, 5),
+            "mlups": round(sc.nodes / ms / 1e3, 1), "workspace_GB": round(ws / 1e9, 4),
+            "two_lattice_workspace_GB": round(ws_two / 1e9, 4),
+            "phase_ms_pair_average": {k: round(float(v), 5) for k, v in
+                                      zip(("rho", "solid", "mu", "collide", "bc"), phase_ms)},
+            "step_time_vs_two_lattices": round(ms / ms_two, 3), "mass_drift": M / M0 - 1}
 
 
 def run_film(G, torch):
@@ -707,6 +740,10 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=4000,
                     help="steps of the gradient workload (0: skip it)")
     ap.add_argument("--adjoint-every", type=int, default=200)
+    ap.add_argument("--layout", type=int, default=0, choices=[0, 1],
+                    help="population layout of the headline lattice: 0 two lattices, 1 one lattice in AA order")
+    ap.add_argument("--aa-steps", type=int, default=2000,
+                    help="steps of the one-lattice (AA order) run of the headline lattice (0: skip it)")
     ap.add_argument("--accuracy", type=int, default=1,
                     help="1: FP32/FP64 against the oracle's stored full-size results (c2, c3, c5); 0: skip")
     ap.add_argument("--collide-kernel", type=int, default=-1, choices=[-1, 0, 1, 2],
@@ -755,7 +792,7 @@ def main():
         args.warmup = max(SLAB_EXCHANGE_EVERY, -(-args.warmup // SLAB_EXCHANGE_EVERY) * SLAB_EXCHANGE_EVERY)
         advance = dslab.step
     else:
-        lat = G.Lattice(sc.physics(), precision=G.LBM_FP32)
+        lat = G.Lattice(sc.physics(), precision=G.LBM_FP32, layout=args.layout)
         lat.init_droplets(sc.droplets())
         if args.collide_kernel >= 0:
             lat.set_collide_kernel(args.collide_kernel)
@@ -904,6 +941,10 @@ def main():
     if args.adjoint_steps > 0 and single:
         adjoint = run_adjoint(G, torch, args.adjoint_steps, args.adjoint_every)
 
+    aa = None
+    if args.aa_steps > 0 and single and args.workload in ("c3", "c2"):
+        aa = run_aa(G, torch, sc, args.aa_steps, ms_step)
+
     pseudo = None
     if args.pseudo_steps > 0 and single:
         pseudo = run_pseudopotential(G, torch, args.pseudo_steps, ms_step)
@@ -955,6 +996,7 @@ def main():
             "accuracy": accuracy,
             "batched": batched,
             "adjoint": adjoint,
+            "aa_layout": aa,
             "fp64": fp64,
             "pseudopotential": None if pseudo is None else {k: pseudo[k] for k in ("ms_per_step", "mlups",
                                                                                     "step_time_vs_chemical_potential")}

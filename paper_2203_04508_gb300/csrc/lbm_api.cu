@@ -128,7 +128,7 @@ Layout make_layout(const lbm_config* c) {
   L.scalars = take(4 * 8);
   L.kerr = take(16);
   L.dm_ring = take((size_t)(DM_RING + 1) * 8);   // the ring, then the last step's value
-  L.block_sums = take(((size_t)(L.plane + 1023) / 1024 + 1) * 4);
+  L.block_sums = take(((size_t)(L.plane + 1023) / 1024 + 1) * 4 * 5);
   L.totals = take(16 * 4);
   L.total = o;
   return L;
@@ -913,6 +913,9 @@ lbm_status lbm_build_links(lbm_ctx* c) {
   o.s2node = (int*)(w + y.s2node); o.s2mask = (uint8_t*)(w + y.s2mask); o.s2winv = w + y.s2winv;
   o.mu = w + y.mu;
   o.fp64 = c->fp64;
+  o.n_bnodes = (int)c->n_bnodes;
+  o.n_s1 = (int)c->n_s1;
+  o.n_s2 = (int)c->n_s2;
   CUDA_OK(c, geom_fill(gp, sc, o, 0.0, c->stream));
   int last = (int)c->n_links;
   CUDA_OK(c, cudaMemcpyAsync(o.bstart + c->n_bnodes, &last, 4, cudaMemcpyHostToDevice, c->stream));

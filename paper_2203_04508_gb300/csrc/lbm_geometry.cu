@@ -88,33 +88,36 @@ __global__ void k_layer(GeomParams g, uint8_t* kind, uint8_t from, uint8_t to) {
   }
 }
 
-// what = 0: cut links of a fluid node; 1: boundary-fluid node flag; 2: layer-1 flag;
-// 3: layer-2 flag; 4: fluid flag
-__global__ void k_count(GeomParams g, const uint8_t* kind, int* cnt, int what) {
-  long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// ---- the four lists (cut links, boundary nodes, first and second solid layer) and the fluid
+// count, compacted in node order: per block of SCAN_BLOCK consecutive nodes the counts of each
+// list are scanned in shared memory; one scan over the blocks' totals gives each block's offsets.
+enum { LANE_LINKS = 0, LANE_BNODE, LANE_S1, LANE_S2, LANE_FLUID, N_LANES };
+
+// counts of node n in the five lanes: its cut links (a fluid node with a non-fluid neighbour),
+// the boundary-node, layer flags and the fluid flag
+__device__ __forceinline__ void node_counts(const GeomParams& g, const uint8_t* kind, long long n, int (&c)[N_LANES]) {
+#pragma unroll
+  for (int l = 0; l < N_LANES; ++l) c[l] = 0;
   if (n >= g.plane) return;
-  int x = (int)(n % g.pitch), y = (int)(n / g.pitch);
-  uint8_t k = kind[n];
-  int c = 0;
-  if (what <= 1) {
-    if (k == KIND_FLUID) {
-      for (int i = 1; i < 9; ++i) {
-        int m;
-        if (gnb(g, x, y, i, &m) && kind[m] != KIND_FLUID) ++c;
-      }
-      if (what == 1) c = c > 0;
+  const int x = (int)(n % g.pitch), y = (int)(n / g.pitch);
+  const uint8_t k = kind[n];
+  if (k == KIND_FLUID) {
+    int links = 0;
+    for (int i = 1; i < 9; ++i) {
+      int m;
+      if (gnb(g, x, y, i, &m) && kind[m] != KIND_FLUID) ++links;
     }
-  } else if (what == 2) {
-    c = k == KIND_SOLID1;
-  } else if (what == 3) {
-    c = k == KIND_SOLID2;
-  } else {
-    c = k == KIND_FLUID;
+    c[LANE_LINKS] = links;
+    c[LANE_BNODE] = links > 0;
+    c[LANE_FLUID] = 1;
+  } else if (k == KIND_SOLID1) {
+    c[LANE_S1] = 1;
+  } else if (k == KIND_SOLID2) {
+    c[LANE_S2] = 1;
   }
-  cnt[n] = c;
 }
 
-// ---- deterministic exclusive scan of int32 counts (block scan, scan of block sums, add)
+// ---- block scans of int32 counts
 __device__ __forceinline__ int warp_incl_scan(int v) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -144,41 +147,32 @@ __device__ int block_excl_scan(int v, int* total) {
   return base + inc - v;
 }
 
-__global__ void k_scan_blocks(const int* in, int* out, int* block_sums, long long n) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  int v = i < n ? in[i] : 0;
-  int total;
-  int e = block_excl_scan(v, &total);
-  if (i < n) out[i] = e;
-  if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+// per block and lane the block's total, at sums[lane * nb + block]
+__global__ void __launch_bounds__(SCAN_BLOCK) k_count_blocks(GeomParams g, const uint8_t* kind, int* sums, int nb) {
+  int c[N_LANES];
+  node_counts(g, kind, (long long)blockIdx.x * blockDim.x + threadIdx.x, c);
+#pragma unroll
+  for (int l = 0; l < N_LANES; ++l) {
+    int t;
+    (void)block_excl_scan(c[l], &t);
+    if (threadIdx.x == 0) sums[l * nb + blockIdx.x] = t;
+  }
 }
 
-// single block: exclusive scan of nb block sums in place; grand total to *total
-__global__ void k_scan_sums(int* block_sums, int nb, int* total) {
+// one block per lane: exclusive scan of the lane's nb block totals in place, the lane's grand
+// total to totals[lane]
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_lanes(int* sums, int nb, int* totals) {
+  int* s = sums + (long long)blockIdx.x * nb;
   int carry = 0;
   for (int base = 0; base < nb; base += blockDim.x) {
-    int i = base + threadIdx.x;
-    int v = i < nb ? block_sums[i] : 0;
+    const int i = base + threadIdx.x;
+    const int v = i < nb ? s[i] : 0;
     int t;
-    int e = block_excl_scan(v, &t);
-    if (i < nb) block_sums[i] = e + carry;
+    const int e = block_excl_scan(v, &t);
+    if (i < nb) s[i] = e + carry;
     carry += t;
-    __syncthreads();
   }
-  if (threadIdx.x == 0) *total = carry;
-}
-
-__global__ void k_scan_add(int* out, const int* block_sums, long long n) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] += block_sums[blockIdx.x];
-}
-
-static cudaError_t excl_scan(const int* in, int* out, int* block_sums, int* total, long long n, cudaStream_t st) {
-  unsigned nb = (unsigned)((n + SCAN_BLOCK - 1) / SCAN_BLOCK);
-  k_scan_blocks<<<nb, SCAN_BLOCK, 0, st>>>(in, out, block_sums, n);
-  k_scan_sums<<<1, SCAN_BLOCK, 0, st>>>(block_sums, (int)nb, total);
-  k_scan_add<<<nb, SCAN_BLOCK, 0, st>>>(out, block_sums, n);
-  return cudaGetLastError();
+  if (threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
 cudaError_t geom_classify_and_count(const GeomParams& g, const GeomScratch& s, uint8_t* kind, cudaStream_t st) {
@@ -187,34 +181,54 @@ cudaError_t geom_classify_and_count(const GeomParams& g, const GeomScratch& s, u
   k_layer<<<gn, 256, 0, st>>>(g, kind, KIND_FLUID, KIND_SOLID1);
   k_layer<<<gn, 256, 0, st>>>(g, kind, KIND_SOLID1, KIND_SOLID2);
   // totals: 0 links, 1 bnodes, 2 s1, 3 s2, 4 fluid
-  for (int w = 0; w < 5; ++w) {
-    k_count<<<gn, 256, 0, st>>>(g, kind, s.cnt, w);
-    cudaError_t e = excl_scan(s.cnt, s.off, s.block_sums, s.totals + w, g.plane, st);
-    if (e != cudaSuccess) return e;
-  }
+  const int nb = (int)((g.plane + SCAN_BLOCK - 1) / SCAN_BLOCK);
+  k_count_blocks<<<nb, SCAN_BLOCK, 0, st>>>(g, kind, s.block_sums, nb);
+  k_scan_lanes<<<N_LANES, SCAN_BLOCK, 0, st>>>(s.block_sums, nb, s.totals);
   return cudaGetLastError();
 }
 
-// link CSR: per boundary node its first link; links sorted by (node, direction)
+// Each node's place in the lists: the boundary-node list (node, first link) and the two layer
+// lists (node), and the boundary index of every boundary node in the plane bidx (read back for
+// the first layer's neighbour table; other entries are never read).  The block offsets are the
+// scanned totals k_scan_lanes left.
+__global__ void __launch_bounds__(SCAN_BLOCK) k_fill_nodes(GeomParams g, const uint8_t* kind, const int* offs, int nb,
+                                                           GeomOut o, int* bidx) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int c[N_LANES], e[N_LANES];
+  node_counts(g, kind, n, c);
+#pragma unroll
+  for (int l = 0; l < LANE_FLUID; ++l) {
+    int t;
+    e[l] = block_excl_scan(c[l], &t) + offs[l * nb + blockIdx.x];
+  }
+  if (c[LANE_BNODE]) {
+    o.bnode[e[LANE_BNODE]] = (int)n;
+    o.bstart[e[LANE_BNODE]] = e[LANE_LINKS];
+    bidx[n] = e[LANE_BNODE];
+  }
+  if (c[LANE_S1]) o.s1node[e[LANE_S1]] = (int)n;
+  if (c[LANE_S2]) o.s2node[e[LANE_S2]] = (int)n;
+}
+
+// The links of boundary node b, from its first link on, sorted by direction: direction, q (the
+// nearest body's where a solid neighbour lies inside several), and whether x2 = x1 - e_i is fluid.
 template <typename real>
-__global__ void k_fill_links(GeomParams g, const uint8_t* kind, const int* link_off, const int* bnode_off,
-                             GeomOut o) {
-  long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= g.plane) return;
-  if (kind[n] != KIND_FLUID) return;
-  int x = (int)(n % g.pitch), y = (int)(n / g.pitch);
-  int base = link_off[n];
-  int l = base;
-  int nbodies = g.n_cyl + (g.walls ? 2 : 0);
+__global__ void k_fill_links(GeomParams g, const uint8_t* kind, int n_bnodes, GeomOut o) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_bnodes) return;
+  const int n = o.bnode[b];
+  const int x = n % g.pitch, y = n / g.pitch;
+  int l = o.bstart[b];
+  const int nbodies = g.n_cyl + (g.walls ? 2 : 0);
   for (int i = 1; i < 9; ++i) {
     int m;
     if (!gnb(g, x, y, i, &m) || kind[m] == KIND_FLUID) continue;
     int xs = m % g.pitch, ys = m / g.pitch;
     bool have = false;
     double qb = 0.0;
-    for (int b = 0; b < nbodies; ++b) {
-      if (!inside_body(g, b, xs, ys)) continue;
-      double q = q_body(g, b, x, y, i);
+    for (int bd = 0; bd < nbodies; ++bd) {
+      if (!inside_body(g, bd, xs, ys)) continue;
+      double q = q_body(g, bd, x, y, i);
       if (!have || q < qb) { qb = q; have = true; }
     }
     int m2 = 0;
@@ -225,31 +239,25 @@ __global__ void k_fill_links(GeomParams g, const uint8_t* kind, const int* link_
     o.lx2f[l] = (ok2 && kind[m2] == KIND_FLUID) ? 1 : 0;
     ++l;
   }
-  if (l > base) {
-    int b = bnode_off[n];
-    o.bnode[b] = (int)n;
-    o.bstart[b] = base;
-  }
 }
 
-// bidx, nb (first layer only): for each contributing neighbour (all of them are boundary-fluid
-// nodes) its index in the boundary-node list, nb[8 j + i - 1], -1 where bit i-1 of the mask is
-// clear
+// Entry j of a solid-layer list (node[j] of class cls): the mask of its neighbours of class
+// `from`, 1 / sum of their weights, and (first layer) for each contributing neighbour -- all of
+// them boundary-fluid nodes -- its index in the boundary-node list, nb[8 j + i - 1], -1 where
+// bit i-1 of the mask is clear
 template <typename real>
-__global__ void k_fill_layer(GeomParams g, const uint8_t* kind, const int* off, uint8_t cls, uint8_t from,
-                             int* node, uint8_t* mask, real* winv, const int* bidx, int* nb) {
-  long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= g.plane) return;
-  if (kind[n] != cls) return;
-  int x = (int)(n % g.pitch), y = (int)(n / g.pitch);
+__global__ void k_fill_layer(GeomParams g, const uint8_t* kind, int count, uint8_t from, const int* node,
+                             uint8_t* mask, real* winv, const int* bidx, int* nb) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= count) return;
+  const int n = node[j];
+  const int x = n % g.pitch, y = n / g.pitch;
   unsigned msk = 0;
   double wsum = 0.0;
   for (int i = 1; i < 9; ++i) {
     int m;
     if (gnb(g, x, y, i, &m) && kind[m] == from) { msk |= 1u << (i - 1); wsum += wgt(i); }
   }
-  int j = off[n];
-  node[j] = (int)n;
   mask[j] = (uint8_t)msk;
   winv[j] = (real)(1.0 / wsum);
   if (nb) {
@@ -278,33 +286,18 @@ __global__ void k_wall_mu(GeomParams g, const uint8_t* kind, const int* body, re
 template <typename real>
 static cudaError_t fill_typed(const GeomParams& g, const GeomScratch& s, const GeomOut& o, cudaStream_t st) {
   const unsigned gn = (unsigned)((g.plane + 255) / 256);
-  // per-node link offsets (scratch `off`) and boundary-node offsets (scratch `cnt`, scanned
-  // in place: each thread reads its element before any thread writes it)
-  int* link_off = s.off;
-  k_count<<<gn, 256, 0, st>>>(g, o.kind, s.cnt, 0);
-  cudaError_t e = excl_scan(s.cnt, link_off, s.block_sums, s.totals + 5, g.plane, st);
-  if (e != cudaSuccess) return e;
-  k_count<<<gn, 256, 0, st>>>(g, o.kind, s.cnt, 1);
-  e = excl_scan(s.cnt, s.cnt, s.block_sums, s.totals + 6, g.plane, st);
-  if (e != cudaSuccess) return e;
-  k_fill_links<real><<<gn, 256, 0, st>>>(g, o.kind, link_off, s.cnt, o);
-  // the boundary-node index of every boundary node (the scan just used) outlives the link
-  // offsets: keep it for the first layer's neighbour table
+  const int nb = (int)((g.plane + SCAN_BLOCK - 1) / SCAN_BLOCK);
+  // the block offsets geom_classify_and_count left in block_sums; the boundary index of each
+  // boundary node into the scratch plane `off`
   int* bidx = s.off;
-  e = cudaMemcpyAsync(bidx, s.cnt, (size_t)g.plane * sizeof(int), cudaMemcpyDeviceToDevice, st);
-  if (e != cudaSuccess) return e;
-  // layer 1 list
-  k_count<<<gn, 256, 0, st>>>(g, o.kind, s.cnt, 2);
-  e = excl_scan(s.cnt, s.cnt, s.block_sums, s.totals + 7, g.plane, st);
-  if (e != cudaSuccess) return e;
-  k_fill_layer<real><<<gn, 256, 0, st>>>(g, o.kind, s.cnt, KIND_SOLID1, KIND_FLUID, o.s1node, o.s1mask,
-                                         (real*)o.s1winv, bidx, o.s1nb);
-  // layer 2 list
-  k_count<<<gn, 256, 0, st>>>(g, o.kind, s.cnt, 3);
-  e = excl_scan(s.cnt, s.cnt, s.block_sums, s.totals + 7, g.plane, st);
-  if (e != cudaSuccess) return e;
-  k_fill_layer<real><<<gn, 256, 0, st>>>(g, o.kind, s.cnt, KIND_SOLID2, KIND_SOLID1, o.s2node, o.s2mask,
-                                         (real*)o.s2winv, nullptr, nullptr);
+  k_fill_nodes<<<nb, SCAN_BLOCK, 0, st>>>(g, o.kind, s.block_sums, nb, o, bidx);
+  if (o.n_bnodes > 0) k_fill_links<real><<<(o.n_bnodes + 255) / 256, 256, 0, st>>>(g, o.kind, o.n_bnodes, o);
+  if (o.n_s1 > 0)
+    k_fill_layer<real><<<(o.n_s1 + 255) / 256, 256, 0, st>>>(g, o.kind, o.n_s1, KIND_FLUID, o.s1node, o.s1mask,
+                                                             (real*)o.s1winv, bidx, o.s1nb);
+  if (o.n_s2 > 0)
+    k_fill_layer<real><<<(o.n_s2 + 255) / 256, 256, 0, st>>>(g, o.kind, o.n_s2, KIND_SOLID1, o.s2node, o.s2mask,
+                                                             (real*)o.s2winv, nullptr, nullptr);
   k_wall_mu<real><<<gn, 256, 0, st>>>(g, o.kind, s.body, (real*)o.mu);
   return cudaGetLastError();
 }

@@ -104,7 +104,7 @@ struct GeomScratch {
   int* body;                  // plane (kept: the body of every solid node)
   int* cnt;                   // plane
   int* off;                   // plane
-  int* block_sums;            // ceil(plane / 1024) + 1
+  int* block_sums;            // 5 x (ceil(plane / 1024) + 1): per list and 1024-node block
   int* totals;                // 8 ints on the device
 };
 
@@ -116,10 +116,12 @@ struct GeomOut {
   void* lq;   void* s1winv; void* s2winv;   // precision-typed
   void* mu;                                 // precision-typed plane
   int fp64;
+  int n_bnodes, n_s1, n_s2;                 // list lengths (from the counts)
 };
 
 // Classification, layers and counts.  Leaves totals = {n_links, n_bnodes, n_s1, n_s2, n_fluid}
-// on the device (and the per-node link offsets in scratch) for the host to check capacities.
+// on the device (and each node block's list offsets in block_sums) for the host to check
+// capacities.
 cudaError_t geom_classify_and_count(const GeomParams& g, const GeomScratch& s, uint8_t* kind, cudaStream_t st);
 // Fills the link CSR, the layer lists and the constant wall chemical potential.
 cudaError_t geom_fill(const GeomParams& g, const GeomScratch& s, const GeomOut& o, double k2_mu_sat_unused,

@@ -1111,9 +1111,30 @@ __global__ void k_set_populations(Lattice<real> L, int cur, const real* in, int 
 
 // Eq. 19 initial state: rho = (rho_g + rho_l)/2 + (rho_g - rho_l)/2 tanh(2(r - r0)/W) around
 // the droplet with the largest liquid fraction phi at the node, u = phi u0, f = f^eq.
+// Population i of the equilibrium with density r and velocity (ux, uy), in offset form (FP64, then
+// rounded to the storage type).
+template <typename real>
+__device__ __forceinline__ real init_pop(int i, double r, double ux, double uy, double rref) {
+  const double usq = 1.5 * (ux * ux + uy * uy);
+  const double eu = ex(i) * ux + ey(i) * uy;
+  const double feq = wgt(i) * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - usq);
+  return (real)(feq - wgt(i) * rref);
+}
+__device__ __forceinline__ double init_rho(double phi, double rho_g, double rho_l) {
+  return 0.5 * (rho_g + rho_l) + 0.5 * (rho_g - rho_l) * (1.0 - 2.0 * phi);
+}
+// A droplet contributes phi = 0 where 2(r - r0)/W >= 40, i.e. r >= r0 + 20 W: there tanh is 1 to
+// far below the last bit of a double, so the node skips the square root and tanh.  Nodes that no
+// droplet reaches (phi = 0, u = 0: the gas) all get the same populations, formed once per block.
 template <typename real>
 __global__ void k_init(Lattice<real> L, const double* __restrict__ drops, int n_drop, double W,
                        double rho_g, double rho_l) {
+  __shared__ real gas[9];
+  __shared__ real gas_rho;
+  const double rref = (double)L.rho_ref;
+  if (threadIdx.x < 9) gas[threadIdx.x] = init_pop<real>(threadIdx.x, init_rho(0.0, rho_g, rho_l), 0.0, 0.0, rref);
+  if (threadIdx.x == 0) gas_rho = (real)init_rho(0.0, rho_g, rho_l);
+  __syncthreads();
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= L.plane) return;
   const int x = (int)(n % L.pitch), y = (int)(n / L.pitch);
@@ -1131,19 +1152,27 @@ __global__ void k_init(Lattice<real> L, const double* __restrict__ drops, int n_
   for (int d = 0; d < n_drop; ++d) {
     const double* p = drops + 5 * d;
     double dx = x - p[0], dy = global_row(L, y) - p[1];
-    double rr = sqrt(dx * dx + dy * dy);
+    const double d2 = dx * dx + dy * dy;
+    const double far = p[2] + 20.0 * W;
+    if (far > 0.0 && d2 >= far * far * (1.0 + 1e-9)) continue;
+    double rr = sqrt(d2);
     double ph = 0.5 - 0.5 * tanh(2.0 * (rr - p[2]) / W);
     if (ph > phi) { phi = ph; u0 = p[3]; v0 = p[4]; }
   }
-  const double r = 0.5 * (rho_g + rho_l) + 0.5 * (rho_g - rho_l) * (1.0 - 2.0 * phi);
+  if (phi == 0.0) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      f0[i * L.plane + n] = gas[i];
+      if (!L.aa) f1[i * L.plane + n] = real(0);
+    }
+    L.rho[n] = gas_rho;
+    return;
+  }
+  const double r = init_rho(phi, rho_g, rho_l);
   const double ux = u0 * phi, uy = v0 * phi;
-  const double usq = 1.5 * (ux * ux + uy * uy);
-  const double rref = (double)L.rho_ref;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    double eu = ex(i) * ux + ey(i) * uy;
-    double feq = wgt(i) * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - usq);
-    f0[i * L.plane + n] = (real)(feq - wgt(i) * rref);
+    f0[i * L.plane + n] = init_pop<real>(i, r, ux, uy, rref);
     if (!L.aa) f1[i * L.plane + n] = real(0);
   }
   L.rho[n] = (real)r;
