@@ -86,6 +86,21 @@ __device__ __forceinline__ bool tile_node(const Lattice<real>& L, int log2w, int
   return x < L.nx && y < L.ny;
 }
 
+// Row vectors of node tile t for the density and chemical-potential phases: the tile's 256 nodes
+// as 256 / V vectors of V = 16/sizeof(real) consecutive nodes of a row (tile widths are at least
+// 16, a multiple of V); vector u starts at (x0, y).  False outside the lattice.
+template <typename real>
+__device__ __forceinline__ bool tile_vec(const Lattice<real>& L, int log2w, int t, int u, int& x0, int& y) {
+  constexpr int V = Vec16<real>::V;
+  const int w = 1 << log2w, h = BATCH_BLOCK >> log2w, wv = w / V;
+  const int tiles_x = (L.nx + w - 1) >> log2w;
+  const int ty = t / tiles_x, tx = t - ty * tiles_x;
+  const int row = u / wv, col = u - row * wv;
+  x0 = (tx << log2w) + col * V;
+  y = ty * h + row;
+  return x0 < L.nx && y < L.ny;
+}
+
 // The six phases of a step, in order; the compensation sums of a step follow its boundary
 // phase after a barrier.
 enum { PH_RHO = 0, PH_S1, PH_S2, PH_MU, PH_COLLIDE, PH_BC, N_PHASES };
@@ -112,12 +127,23 @@ __device__ __forceinline__ void run_phase(const BatchDev& B, const Lattice<real>
   int x, y;
   switch (p) {
     case PH_RHO:
-      for (int w = w0; w < w1; ++w) {
+    case PH_MU: {
+      // row vectors (the single-lattice passes' bodies, with psi' handed from the density to the
+      // chemical potential): a block takes V tiles at a time, each thread one vector of one of
+      // them, whose instance's descriptor it reads from the instance table
+      constexpr int V = Vec16<real>::V, U = BATCH_BLOCK / V;
+      const int sub = (int)threadIdx.x / U, u = (int)threadIdx.x - sub * U;
+      for (int wb = w0; wb < w1; wb += V) {
+        const int w = wb + sub;
+        if (w >= w1) continue;
         const int2 t = items[w];
-        load_lattice(L, lat, t.x, loaded);
-        if (tile_node(L, B.tile_log2w, t.y, x, y)) phase_rho(L, cur, x, y);
+        const Lattice<real>& Lk = lat[t.x];
+        if (!tile_vec(Lk, B.tile_log2w, t.y, u, x, y)) continue;
+        if (p == PH_RHO) phase_rho_vec(Lk, cur, x, y);
+        else if (Lk.eos != EOS_NONE) phase_mu_vec(Lk, x, y);
       }
       break;
+    }
     case PH_S1:
     case PH_S2: {
       const int layer = p == PH_S1 ? 1 : 2;
@@ -129,13 +155,6 @@ __device__ __forceinline__ void run_phase(const BatchDev& B, const Lattice<real>
       }
       break;
     }
-    case PH_MU:
-      for (int w = w0; w < w1; ++w) {
-        const int2 t = items[w];
-        load_lattice(L, lat, t.x, loaded);
-        if (L.eos != EOS_NONE && tile_node(L, B.tile_log2w, t.y, x, y)) phase_mu(L, x, y);
-      }
-      break;
     case PH_COLLIDE:
       for (int w = w0; w < w1; ++w) {
         const int2 t = items[w];

@@ -52,6 +52,121 @@ __device__ __forceinline__ void phase_mu(const Lattice<real>& L, int x, int y) {
   L.mu[n] = mu_of(L, psi_prime_shifted(L, r), lap4(L.rho, n, s));
 }
 
+// ---- 16-byte row vectors: V = 16/sizeof(real) consecutive nodes of a row per thread.  Rows
+// start on 128-byte boundaries (the pitch), so every vector at a multiple of V is aligned.
+template <typename real> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int V = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int V = 2; };
+
+template <typename real>
+__device__ __forceinline__ real lane_of(const typename Vec16<real>::type& v, int k);
+template <> __device__ __forceinline__ float lane_of<float>(const float4& v, int k) {
+  return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+template <> __device__ __forceinline__ double lane_of<double>(const double2& v, int k) { return k == 0 ? v.x : v.y; }
+template <typename real>
+__device__ __forceinline__ typename Vec16<real>::type make_vec(const real (&a)[Vec16<real>::V]);
+template <> __device__ __forceinline__ float4 make_vec<float>(const float (&a)[4]) { return make_float4(a[0], a[1], a[2], a[3]); }
+template <> __device__ __forceinline__ double2 make_vec<double>(const double (&a)[2]) { return make_double2(a[0], a[1]); }
+
+// Density of the fluid nodes x0 .. x0+V-1 of row y (x0 < nx, a multiple of V) from 16-byte loads
+// of lattice `cur` in natural slot order -- the values phase_rho stores -- and, while the density
+// is at hand, the pointwise part of Eq. 12 into psip (chemical-potential force) or psi itself into
+// mu (pseudopotential force): this pass is bound by its bytes, the chemical-potential pass by its
+// instructions.
+template <typename real>
+__device__ __forceinline__ void phase_rho_vec(const Lattice<real>& L, int cur, int x0, int y) {
+  using VT = typename Vec16<real>::type;
+  constexpr int V = Vec16<real>::V;
+  const int n0 = y * L.pitch + x0;
+  const real* __restrict__ f = L.f[cur];
+  VT fv[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) fv[i] = __ldg(reinterpret_cast<const VT*>(f + i * L.plane + n0));
+  bool fluid[V];
+  bool all = true;
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    fluid[k] = x0 + k < L.nx && L.kind[n0 + k] == KIND_FLUID;
+    all &= fluid[k];
+  }
+  real* second = L.psip ? L.psip : ((L.pseudo && L.eos != EOS_NONE) ? L.mu : nullptr);
+  real r[V], p[V];
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    real fl[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fl[i] = lane_of<real>(fv[i], k);
+    r[k] = density_of(L, fl);
+    p[k] = (!second || !fluid[k]) ? real(0) : (L.psip ? psi_prime_shifted(L, r[k]) : psi_of(L, r[k]));
+  }
+  if (all) {
+    // every node fluid: 16-byte stores (a solid node's slot belongs to the solid-layer kernels,
+    // which may be writing it concurrently, so mixed vectors take the scalar path)
+    *reinterpret_cast<VT*>(L.rho + n0) = make_vec<real>(r);
+    if (second) *reinterpret_cast<VT*>(second + n0) = make_vec<real>(p);
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    if (!fluid[k]) continue;
+    L.rho[n0 + k] = r[k];
+    if (second) second[n0 + k] = p[k];
+  }
+}
+
+// Eq. 12 at the fluid nodes x0 .. x0+V-1 of row y (x0 < nx, a multiple of V) with psi' from the
+// density pass: the centre row from three 16-byte loads (x0 - V .. x0 + 2V - 1), the four rows
+// above and below and psi' from one each, so the 9-point Laplacians of V nodes take 8 vector loads
+// instead of 9 V scalar ones.  Where the stencils would wrap around a periodic edge, node by node.
+// Same values and the same sums as phase_mu (lap4_of, mu_of).
+template <typename real>
+__device__ __forceinline__ void phase_mu_vec(const Lattice<real>& L, int x0, int y) {
+  using VT = typename Vec16<real>::type;
+  constexpr int V = Vec16<real>::V;
+  const int n0 = y * L.pitch + x0;
+  bool fluid[V];
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    fluid[k] = x0 + k < L.nx && L.kind[n0 + k] == KIND_FLUID;
+    any |= fluid[k];
+  }
+  if (!any) return;
+  // no wrap within two nodes (with walls a fluid row keeps two solid rows below and above it)
+  const bool inner = x0 - V >= 0 && x0 + V + 2 <= L.nx && (L.walls || (y >= 2 && y < L.ny - 2));
+  if (!inner) {
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      if (!fluid[k]) continue;
+      Stencil st = stencil_at(L, x0 + k, y);
+      L.mu[n0 + k] = mu_of(L, L.psip[n0 + k], lap4(L.rho, n0 + k, st));
+    }
+    return;
+  }
+  const real* __restrict__ r = L.rho;
+  real c[3 * V];   // the centre row, x0 - V .. x0 + 2V - 1
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const VT v = __ldg(reinterpret_cast<const VT*>(r + n0 + (j - 1) * V));
+#pragma unroll
+    for (int k = 0; k < V; ++k) c[j * V + k] = lane_of<real>(v, k);
+  }
+  const VT up1 = __ldg(reinterpret_cast<const VT*>(r + n0 + L.pitch));
+  const VT dn1 = __ldg(reinterpret_cast<const VT*>(r + n0 - L.pitch));
+  const VT up2 = __ldg(reinterpret_cast<const VT*>(r + n0 + 2 * L.pitch));
+  const VT dn2 = __ldg(reinterpret_cast<const VT*>(r + n0 - 2 * L.pitch));
+  const VT pp = __ldg(reinterpret_cast<const VT*>(L.psip + n0));
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    if (!fluid[k]) continue;
+    const int i = V + k;
+    const real lap = lap4_of(c[i], c[i + 1], c[i - 1], c[i + 2], c[i - 2], lane_of<real>(up1, k), lane_of<real>(dn1, k),
+                             lane_of<real>(up2, k), lane_of<real>(dn2, k));
+    L.mu[n0 + k] = mu_of(L, lane_of<real>(pp, k), lap);
+  }
+}
+
 // force (Eq. 9) + collision (Eq. 4) with exact-difference forcing (Eq. 13) + push streaming
 // (Eq. 5) of fluid node (x, y) into the other lattice.  Force(r, Fx, Fy) evaluates Eq. 9 at
 // the node: from the density and chemical-potential planes (force_at), or from a tile of them

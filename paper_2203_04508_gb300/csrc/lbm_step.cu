@@ -43,67 +43,11 @@ __device__ __forceinline__ bool node_of_thread(const Lattice<real>& L, int& x, i
 }
 
 // Density pass with 16-byte loads: each thread takes V = 16/sizeof(real) consecutive nodes of
-// a row (rows start on 128-byte boundaries, so every vector is aligned) and stores density_of
-// of each fluid node -- the values phase_rho stores, with more bytes in flight per thread.
-template <typename real> struct Vec16;
-template <> struct Vec16<float> { using type = float4; static constexpr int V = 4; };
-template <> struct Vec16<double> { using type = double2; static constexpr int V = 2; };
-
-template <typename real>
-__device__ __forceinline__ real lane_of(const typename Vec16<real>::type& v, int k);
-template <> __device__ __forceinline__ float lane_of<float>(const float4& v, int k) {
-  return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
-}
-template <> __device__ __forceinline__ double lane_of<double>(const double2& v, int k) { return k == 0 ? v.x : v.y; }
-template <typename real>
-__device__ __forceinline__ typename Vec16<real>::type make_vec(const real (&a)[Vec16<real>::V]);
-template <> __device__ __forceinline__ float4 make_vec<float>(const float (&a)[4]) { return make_float4(a[0], a[1], a[2], a[3]); }
-template <> __device__ __forceinline__ double2 make_vec<double>(const double (&a)[2]) { return make_double2(a[0], a[1]); }
-
+// a row (phase_rho_vec).
 template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_rho_vec(Lattice<real> L, int cur) {
-  using VT = typename Vec16<real>::type;
-  constexpr int V = Vec16<real>::V;
-  const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * V, y = blockIdx.y;
-  if (x0 >= L.nx) return;
-  const int n0 = y * L.pitch + x0;
-  const real* __restrict__ f = L.f[cur];
-  VT fv[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) fv[i] = __ldg(reinterpret_cast<const VT*>(f + i * L.plane + n0));
-  bool fluid[V];
-  bool all = true;
-#pragma unroll
-  for (int k = 0; k < V; ++k) {
-    fluid[k] = x0 + k < L.nx && L.kind[n0 + k] == KIND_FLUID;
-    all &= fluid[k];
-  }
-  // the pointwise part of Eq. 12 while the node's density is at hand (this pass is bound by its
-  // bytes, the chemical-potential pass by its instructions); with the pseudopotential force,
-  // psi itself
-  real* second = L.psip ? L.psip : ((L.pseudo && L.eos != EOS_NONE) ? L.mu : nullptr);
-  real r[V], p[V];
-#pragma unroll
-  for (int k = 0; k < V; ++k) {
-    real fl[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) fl[i] = lane_of<real>(fv[i], k);
-    r[k] = density_of(L, fl);
-    p[k] = (!second || !fluid[k]) ? real(0) : (L.psip ? psi_prime_shifted(L, r[k]) : psi_of(L, r[k]));
-  }
-  if (all) {
-    // every node fluid: 16-byte stores (a solid node's slot belongs to the solid-layer kernels,
-    // which may be writing it concurrently, so mixed vectors take the scalar path)
-    *reinterpret_cast<VT*>(L.rho + n0) = make_vec<real>(r);
-    if (second) *reinterpret_cast<VT*>(second + n0) = make_vec<real>(p);
-    return;
-  }
-#pragma unroll
-  for (int k = 0; k < V; ++k) {
-    if (!fluid[k]) continue;
-    L.rho[n0 + k] = r[k];
-    if (second) second[n0 + k] = p[k];
-  }
+  const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * Vec16<real>::V, y = blockIdx.y;
+  if (x0 < L.nx) phase_rho_vec(L, cur, x0, y);
 }
 
 // The density pass of a state in AA order (one lattice after its in-place step): f_i(x) lies in
@@ -176,57 +120,11 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_mu(Lattice<real> L) {
 }
 
 // The chemical-potential pass with psi' from the density pass, V = 16/sizeof(real) consecutive
-// nodes of a row per thread: the centre row from three 16-byte loads (x0 - V .. x0 + 2V - 1), the
-// four rows above and below and psi' from one each, so the 9-point Laplacians of V nodes take 8
-// vector loads instead of 9 V scalar ones.  Threads whose stencils would wrap around a periodic
-// edge take k_mu's per-node path.  Same values and the same sums as k_mu (lap4_of, mu_of).
+// nodes of a row per thread (phase_mu_vec).
 template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_mu_vec(Lattice<real> L) {
-  using VT = typename Vec16<real>::type;
-  constexpr int V = Vec16<real>::V;
-  const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * V, y = blockIdx.y;
-  if (x0 >= L.nx) return;
-  const int n0 = y * L.pitch + x0;
-  bool fluid[V];
-  bool any = false;
-#pragma unroll
-  for (int k = 0; k < V; ++k) {
-    fluid[k] = x0 + k < L.nx && L.kind[n0 + k] == KIND_FLUID;
-    any |= fluid[k];
-  }
-  if (!any) return;
-  // no wrap within two nodes (with walls a fluid row keeps two solid rows below and above it)
-  const bool inner = x0 - V >= 0 && x0 + V + 2 <= L.nx && (L.walls || (y >= 2 && y < L.ny - 2));
-  if (!inner) {
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
-      if (!fluid[k]) continue;
-      Stencil st = stencil_at(L, x0 + k, y);
-      L.mu[n0 + k] = mu_of(L, L.psip[n0 + k], lap4(L.rho, n0 + k, st));
-    }
-    return;
-  }
-  const real* __restrict__ r = L.rho;
-  real c[3 * V];   // the centre row, x0 - V .. x0 + 2V - 1
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    const VT v = __ldg(reinterpret_cast<const VT*>(r + n0 + (j - 1) * V));
-#pragma unroll
-    for (int k = 0; k < V; ++k) c[j * V + k] = lane_of<real>(v, k);
-  }
-  const VT up1 = __ldg(reinterpret_cast<const VT*>(r + n0 + L.pitch));
-  const VT dn1 = __ldg(reinterpret_cast<const VT*>(r + n0 - L.pitch));
-  const VT up2 = __ldg(reinterpret_cast<const VT*>(r + n0 + 2 * L.pitch));
-  const VT dn2 = __ldg(reinterpret_cast<const VT*>(r + n0 - 2 * L.pitch));
-  const VT pp = __ldg(reinterpret_cast<const VT*>(L.psip + n0));
-#pragma unroll
-  for (int k = 0; k < V; ++k) {
-    if (!fluid[k]) continue;
-    const int i = V + k;
-    const real lap = lap4_of(c[i], c[i + 1], c[i - 1], c[i + 2], c[i - 2], lane_of<real>(up1, k), lane_of<real>(dn1, k),
-                             lane_of<real>(up2, k), lane_of<real>(dn2, k));
-    L.mu[n0 + k] = mu_of(L, lane_of<real>(pp, k), lap);
-  }
+  const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * Vec16<real>::V, y = blockIdx.y;
+  if (x0 < L.nx) phase_mu_vec(L, x0, y);
 }
 
 // Chemical potential (FP32) by row sweeps: a thread holds four consecutive nodes of a row and
