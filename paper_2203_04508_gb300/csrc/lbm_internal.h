@@ -62,7 +62,11 @@ struct CollideTma {
   const void* f_ptr[2];         // the planes the descriptors were made for: a lattice
   const void* rho_ptr[2];       // descriptor pointing elsewhere runs the plain kernel
   const void* mu_ptr[2];
+  CUtensorMap f_pull;           // one lattice in AA order: its populations, box 40 x 10 x 9 from
+                                // (x0 - 4, y0 - 1), for the second step's shifted rows
+  bool pull_ok;                 // f_pull was encoded
   int blocks[2];                // persistent grid of the chemical-potential / psi variant
+  int blocks_pull[2];           // ... of the AA order's second step
   int sweep_blocks;             // blocks of the column-sweep variant that fit on the device at once
   float* edge;                  // its edge buffer (null: the sweep does not run)
 };

@@ -476,8 +476,19 @@ static_assert(TMA_F_BYTES % 128 == 0 && TMA_M_BYTES % 128 == 0, "stage buffers s
 static_assert((TMA_HOX * 4) % 16 == 0 && (CT_X * 4) % 16 == 0 && (TMA_HX * 4) % 16 == 0,
               "TMA boxes start and extend on 16-byte boundaries");
 static_assert(TMA_HOX >= CT_H && TMA_HX - TMA_HOX >= CT_X + CT_H, "the boxes cover the halo the stencils read");
+// The second step of the AA order pulls f_i(x) from slot opp(i) of x - e_i: a 40 x 10 x 9 box from
+// (x0 - 4, y0 - 1) covers every shifted row of a tile (its x start stays on a 16-byte boundary).
+constexpr int TMA_PX = 40, TMA_POX = 4, TMA_PY = CT_Y + 2;
+constexpr int TMA_FP_BOX = 9 * TMA_PY * TMA_PX * 4;                 // bytes the box delivers
+constexpr int TMA_FP_BYTES = (TMA_FP_BOX + 127) / 128 * 128;        // its stage area
+static_assert((TMA_POX * 4) % 16 == 0 && (TMA_PX * 4) % 16 == 0 && TMA_PX - TMA_POX >= CT_X + 1 && TMA_POX >= 1,
+              "the pull box covers a tile shifted by one node and starts on a 16-byte boundary");
 
-__host__ __device__ constexpr int tma_stage_bytes(bool pseudo) { return pseudo ? TMA_STAGE_PP : TMA_STAGE_CP; }
+// FMODE: 0 push into the other lattice, 1 in place (the AA order's first step), 2 pulled from
+// the shifted slots and pushed (its second step)
+__host__ __device__ constexpr int tma_stage_bytes(bool pseudo, int fmode = 0) {
+  return (fmode == 2 ? TMA_FP_BYTES : TMA_F_BYTES) + (pseudo ? 1 : 2) * TMA_M_BYTES;
+}
 
 struct CollideMaps {
   CUtensorMap f;      // populations of the input lattice, box 32 x 8 x 9
@@ -552,8 +563,8 @@ constexpr int SW_RING_BYTES = 9 * SW_R * SW_W * 4;
 constexpr int SW_KIND_BYTES = SW_R * CT_X;
 static_assert(18 * CT_Y <= NODE_BLOCK, "one thread per edge-buffer entry of a tile");
 
-__host__ __device__ constexpr size_t collide_smem_bytes(bool pseudo, bool sweep) {
-  return (size_t)TMA_STAGES * tma_stage_bytes(pseudo) + (sweep ? (size_t)SW_RING_BYTES + SW_KIND_BYTES : 0);
+__host__ __device__ constexpr size_t collide_smem_bytes(bool pseudo, bool sweep, int fmode = 0) {
+  return (size_t)TMA_STAGES * tma_stage_bytes(pseudo, fmode) + (sweep ? (size_t)SW_RING_BYTES + SW_KIND_BYTES : 0);
 }
 
 // first tile row of band b of `bands` over `tile_rows` tile rows
@@ -580,25 +591,29 @@ __device__ __forceinline__ void sweep_edge_entry(int e, int strip, int strips, i
   else { rcol = CT_X + 1; ecol = 2 * (strip + 1 == strips ? 0 : strip + 1); }
 }
 
-// INPLACE: the first step of the AA order on one lattice -- tiles are loaded as in natural order
-// and every node's post-collision populations go back into its own slots (collide_loaded).
-template <bool PSEUDO, bool SWEEP, bool INPLACE = false>
+// One lattice in AA order: FMODE 1, its first step -- tiles are loaded as in natural order and
+// every node's post-collision populations go back into its own slots (collide_loaded); FMODE 2,
+// its second -- M.f is the 40 x 10 x 9 pull box, each node reads f_i from slot opp(i) of x - e_i
+// in it (tiles whose shifted rows wrap around an edge read them from global memory) and pushes
+// into the same lattice.
+template <bool PSEUDO, bool SWEEP, int FMODE = 0>
 __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, int cur, const __grid_constant__ CollideMaps M,
                                                             int tiles_x, int n_tiles, SweepArgs A) {
   static_assert(!(PSEUDO && SWEEP), "the sweep forms the chemical-potential model's density");
-  static_assert(!(SWEEP && INPLACE), "the sweep pushes into a second lattice");
+  static_assert(!(SWEEP && FMODE != 0), "the sweep pushes into a second lattice");
+  constexpr int FB = FMODE == 2 ? TMA_FP_BYTES : TMA_F_BYTES;
   extern __shared__ __align__(128) unsigned char tma_smem[];
   __shared__ __align__(8) uint64_t bar[TMA_STAGES];
   // per stage, set by the thread that requests its tile: x0, y0, and flags (1: the halo came by
   // TMA, 2: no push of the tile wraps around an edge)
   __shared__ int4 info[TMA_STAGES];
-  constexpr int SB = tma_stage_bytes(PSEUDO);
+  constexpr int SB = tma_stage_bytes(PSEUDO, FMODE);
   const bool stencils = L.eos != EOS_NONE;
   const int lx = threadIdx.x % CT_X, ly = threadIdx.x / CT_X;
   auto f_of = [&](int s) { return reinterpret_cast<float*>(tma_smem + s * SB); };
   // mu (or psi) right after the populations, the density (chemical potential) after it
-  auto mu_of = [&](int s) { return reinterpret_cast<float*>(tma_smem + s * SB + TMA_F_BYTES); };
-  auto rho_of = [&](int s) { return reinterpret_cast<float*>(tma_smem + s * SB + TMA_F_BYTES + TMA_M_BYTES); };
+  auto mu_of = [&](int s) { return reinterpret_cast<float*>(tma_smem + s * SB + FB); };
+  auto rho_of = [&](int s) { return reinterpret_cast<float*>(tma_smem + s * SB + FB + TMA_M_BYTES); };
   float* ring = reinterpret_cast<float*>(tma_smem + TMA_STAGES * SB);
   uint8_t* rkind = tma_smem + TMA_STAGES * SB + SW_RING_BYTES;
   // this block's tiles k = 0 .. nt - 1, as tile coordinates (tx, ty) advanced without a division:
@@ -635,8 +650,9 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, in
     // with walls, rows never wrap
     const bool inner = x0 >= 1 && x0 + CT_X < L.nx && (L.walls || (y0 >= 1 && y0 + CT_Y < L.ny));
     info[s] = make_int4(x0, y0, (h ? 1 : 0) | (inner ? 2 : 0), 0);
-    mbar_expect_tx(&bar[s], TMA_F_BYTES + (h ? (PSEUDO ? 1 : 2) * TMA_M_BYTES : 0));
-    tma_load_3d(f_of(s), &M.f, x0, y0, 0, &bar[s]);
+    mbar_expect_tx(&bar[s], (FMODE == 2 ? TMA_FP_BOX : TMA_F_BYTES) + (h ? (PSEUDO ? 1 : 2) * TMA_M_BYTES : 0));
+    if (FMODE == 2) tma_load_3d(f_of(s), &M.f, x0 - TMA_POX, y0 - 1, 0, &bar[s]);
+    else tma_load_3d(f_of(s), &M.f, x0, y0, 0, &bar[s]);
     if (h) {
       tma_load_2d(mu_of(s), &M.mu, x0 - TMA_HOX, y0 - CT_H, &bar[s]);
       if (!PSEUDO) tma_load_2d(rho_of(s), &M.rho, x0 - TMA_HOX, y0 - CT_H, &bar[s]);
@@ -692,8 +708,17 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, in
     float g[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     if (fluid) {
       const float* sf = f_of(s);
+      if (FMODE == 2) {
+        if (inner) {
 #pragma unroll
-      for (int i = 0; i < 9; ++i) fl[i] = sf[(i * CT_Y + ly) * CT_X + lx];
+          for (int i = 0; i < 9; ++i) fl[i] = sf[(opp(i) * TMA_PY + ly + 1 - ey(i)) * TMA_PX + lx + TMA_POX - ex(i)];
+        } else {
+          load_pops(L, 1, x, y, fl);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fl[i] = sf[(i * CT_Y + ly) * CT_X + lx];
+      }
       if (stencils) tile_force_terms<float, PSEUDO>(sm, sr, TMA_HX, (ly + CT_H) * TMA_HX + lx + TMA_HOX, g);
     }
     // every thread has read stage s: refill it with the tile TMA_STAGES ahead
@@ -704,7 +729,7 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, in
     }
     if (!SWEEP) {
       if (!fluid) continue;
-      collide_loaded<INPLACE>(
+      collide_loaded<FMODE == 1>(
           L, cur, x, y, fl, [&](float r, float& Fx, float& Fy) { tile_force<float, PSEUDO>(L, stencils, g, r, Fx, Fy); },
           inner);
       continue;
@@ -1129,9 +1154,9 @@ static inline void launch_mu(const Lattice<real>& L, cudaStream_t s) {
   } else if (L.psip && L.mu_kernel != 0) k_mu_vec<real><<<rho_grid(L), NODE_BLOCK, 0, s>>>(L);
   else k_mu<real><<<node_grid(L), node_block(), 0, s>>>(L);
 }
-static inline CollideMaps maps_for(const CollideTma* T, const Lattice<float>& L, int cur) {
+static inline CollideMaps maps_for(const CollideTma* T, const Lattice<float>& L, int cur, bool pull = false) {
   CollideMaps M;
-  M.f = T->f[cur];
+  M.f = pull ? T->f_pull : T->f[cur];
   M.rho = T->rho[L.rho == T->rho_ptr[1] ? 1 : 0];
   M.mu = T->mu[L.mu == T->mu_ptr[1] ? 1 : 0];
   return M;
@@ -1173,7 +1198,23 @@ static inline void launch_bmom(const Lattice<real>& L, int cur, cudaStream_t s) 
 template <typename real>
 static inline void launch_collide(const Lattice<real>& L, int cur, cudaStream_t s) {
   if (L.aa && cur == 1) {
-    // the second step of the AA order pulls along shifted rows: the plain kernel
+    // the second step of the AA order pulls along shifted rows: the TMA-pipelined kernel with
+    // the pull box, or the plain one
+    if constexpr (sizeof(real) == 4) {
+      const CollideTma* T = tma_for(L, cur);
+      if (T && T->pull_ok) {
+        const CollideMaps M = maps_for(T, L, cur, true);
+        const int tiles_x = (L.nx + CT_X - 1) / CT_X;
+        const int tiles = tiles_x * ((L.ny + CT_Y - 1) / CT_Y);
+        const int P = L.pseudo ? 1 : 0;
+        const int grid = tiles < T->blocks_pull[P] ? tiles : T->blocks_pull[P];
+        const size_t smem = collide_smem_bytes(L.pseudo, false, 2);
+        const SweepArgs none{};
+        if (L.pseudo) k_collide_tma<true, false, 2><<<grid, NODE_BLOCK, smem, s>>>(L, cur, M, tiles_x, tiles, none);
+        else k_collide_tma<false, false, 2><<<grid, NODE_BLOCK, smem, s>>>(L, cur, M, tiles_x, tiles, none);
+        return;
+      }
+    }
     if (L.pseudo) k_collide<real, true, 2><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
     else k_collide<real, false, 2><<<collide_grid(L), NODE_BLOCK, 0, s>>>(L, cur);
     return;
@@ -1188,8 +1229,8 @@ static inline void launch_collide(const Lattice<real>& L, int cur, cudaStream_t 
       const size_t smem = collide_smem_bytes(L.pseudo, false);
       const SweepArgs none{};
       if (L.aa) {
-        if (L.pseudo) k_collide_tma<true, false, true><<<grid, NODE_BLOCK, smem, s>>>(L, cur, M, tiles_x, tiles, none);
-        else k_collide_tma<false, false, true><<<grid, NODE_BLOCK, smem, s>>>(L, cur, M, tiles_x, tiles, none);
+        if (L.pseudo) k_collide_tma<true, false, 1><<<grid, NODE_BLOCK, smem, s>>>(L, cur, M, tiles_x, tiles, none);
+        else k_collide_tma<false, false, 1><<<grid, NODE_BLOCK, smem, s>>>(L, cur, M, tiles_x, tiles, none);
       } else if (L.pseudo) {
         k_collide_tma<true, false><<<grid, NODE_BLOCK, smem, s>>>(L, cur, M, tiles_x, tiles, none);
       } else {
@@ -1277,6 +1318,15 @@ bool collide_tma_setup(CollideTma* T, const Lattice<float>& L, const void* rho0,
     if (r != CUDA_SUCCESS) return fail_enc("the populations", r);
     T->f_ptr[c] = L.f[c];
   }
+  {
+    // one lattice in AA order: the pull box of its second step
+    const cuuint64_t dim[3] = {(cuuint64_t)L.pitch, (cuuint64_t)L.ny, 9};
+    const cuuint64_t stride[2] = {(cuuint64_t)L.pitch * 4, (cuuint64_t)L.plane * 4};
+    const cuuint32_t box[3] = {TMA_PX, TMA_PY, 9};
+    T->pull_ok = L.aa && enc(&T->f_pull, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)L.f[0], dim, stride, box, unit,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  }
   auto plane = [&](CUtensorMap* m, const void* base, CUtensorMapDataType type, int esize, cuuint32_t bx, cuuint32_t by) {
     const cuuint64_t dim[2] = {(cuuint64_t)L.pitch, (cuuint64_t)L.ny};
     const cuuint64_t stride[1] = {(cuuint64_t)L.pitch * esize};
@@ -1295,14 +1345,18 @@ bool collide_tma_setup(CollideTma* T, const Lattice<float>& L, const void* rho0,
   T->mu_ptr[0] = L.mu;
   T->mu_ptr[1] = mu1;
   // persistent grids: every block that fits on the device at once
-  int dev = 0, sms = 0, b0 = 0, b1 = 0, b2 = 0;
+  int dev = 0, sms = 0, b0 = 0, b1 = 0, b2 = 0, p0 = 0, p1 = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_collide_tma<false, false>, NODE_BLOCK,
                                                     collide_smem_bytes(false, false)) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_collide_tma<true, false>, NODE_BLOCK,
                                                     collide_smem_bytes(true, false)) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_collide_tma<false, true>, NODE_BLOCK,
-                                                    collide_smem_bytes(false, true)) != cudaSuccess) {
+                                                    collide_smem_bytes(false, true)) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p0, k_collide_tma<false, false, 2>, NODE_BLOCK,
+                                                    collide_smem_bytes(false, false, 2)) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, k_collide_tma<true, false, 2>, NODE_BLOCK,
+                                                    collide_smem_bytes(true, false, 2)) != cudaSuccess) {
     (void)cudaGetLastError();
     std::snprintf(err, 256, "occupancy query failed");
     return false;
@@ -1310,6 +1364,8 @@ bool collide_tma_setup(CollideTma* T, const Lattice<float>& L, const void* rho0,
   T->blocks[0] = (b0 > 0 ? b0 : 1) * sms;
   T->blocks[1] = (b1 > 0 ? b1 : 1) * sms;
   T->sweep_blocks = (b2 > 0 ? b2 : 1) * sms;
+  T->blocks_pull[0] = (p0 > 0 ? p0 : 1) * sms;
+  T->blocks_pull[1] = (p1 > 0 ? p1 : 1) * sms;
   T->edge = static_cast<float*>(edge);
   return true;
 }

@@ -2,8 +2,8 @@
 populations, densities, velocities, mass and Eq. 18 compensation history, bit for bit, after odd
 and even step counts (the state alternates between natural and shifted slot order), on lattices
 that take every path -- walls and periodic boxes, ragged edges, several cylinders, both force
-models, FP32 and FP64, BGK and MRT, every boundary scheme, the TMA-pipelined in-place collide
-and the plain one -- and through the graph-launched and the phase-by-phase step.  The AA order
+models, FP32 and FP64, BGK and MRT, every boundary scheme, the TMA-pipelined collide in both of
+the order's steps and the plain one -- and through the graph-launched and the phase-by-phase step.  The AA order
 is an implementation choice of streaming (Eq. 5), so the values must not change at all."""
 from __future__ import annotations
 
@@ -86,17 +86,21 @@ def test_aa_order_equals_two_lattices(name):
 
 
 @pytest.mark.parametrize("kind", [0, 1])
-def test_aa_order_with_each_collide_kernel(kind):
-    """The in-place first step by the TMA-pipelined kernel (1) and by the plain kernel (0)."""
+@pytest.mark.parametrize("name", ["impact_512", "periodic_200x150", "pseudo_ragged"])
+def test_aa_order_with_each_collide_kernel(kind, name):
+    """Both steps of the AA order by the TMA-pipelined kernel (1: in place, then from the pull
+    box, with tiles whose shifted rows wrap around a periodic edge read from global memory) and
+    by the plain kernel (0)."""
     import paper_2203_04508_gb300 as G
-    sc = S.c3_impact(512, 512)
+    sc, fp64 = (lambda: S.c3_impact(512, 512), False) if name == "impact_512" else CASES[name]
+    sc = sc()
     a = lattice(sc, False, G.LBM_LAYOUT_AB)
     b = lattice(sc, False, G.LBM_LAYOUT_AA)
     b.set_collide_kernel(kind)
     for n in (1, 4, 25):
         a.step(n)
         b.step(n)
-    same_state(a, b, f"collide kernel {kind}")
+        same_state(a, b, f"collide kernel {kind}")
 
 
 def test_aa_order_halves_the_population_memory():
