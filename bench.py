@@ -749,9 +749,12 @@ def main():
     ap.add_argument("--collide-kernel", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="collide kernel of the single lattice (-1: the library's choice; 2: the column "
                          "sweeps that also form the next density, for comparison)")
-    ap.add_argument("--mode", default="full", choices=["full", "kernels", "adjoint"],
+    ap.add_argument("--mode", default="full", choices=["full", "kernels", "adjoint", "batch"],
                     help="kernels: only warm-up and timed steps; adjoint: only the gradient "
-                         "workload (both for profiler captures)")
+                         "workload; batch: only the batched kernel on the first --batch-instances "
+                         "lattices of the 256-lattice mix, one launch of --warmup steps and one of "
+                         "--steps (all for profiler captures)")
+    ap.add_argument("--batch-instances", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -775,6 +778,22 @@ def main():
     G.load()
     if args.mode == "adjoint":
         print(json.dumps({"mode": "adjoint", **run_adjoint(G, torch, args.adjoint_steps, args.adjoint_every)}))
+        return
+    if args.mode == "batch":
+        import scenarios as S
+        scs = S.c4_batch()[:args.batch_instances]
+        b = G.Batch([x.physics() for x in scs], precision=G.LBM_FP32)
+        b.init([x.droplets() for x in scs])
+        b.set_tile(5)
+        b.set_schedule(2)
+        b.step(args.warmup)
+        b.synchronize()
+        b.check()
+        b.step(args.steps)
+        b.synchronize()
+        b.check()
+        print(json.dumps({"mode": "batch", "instances": len(scs), "nodes": sum(x.nodes for x in scs),
+                          "tile": "32x8", "schedule": "two groups", "steps": args.steps, "warmup": args.warmup}))
         return
 
     sc, wname = workload(args.workload)

@@ -156,6 +156,10 @@ __device__ __forceinline__ void run_phase(const BatchDev& B, const Lattice<real>
       break;
     }
     case PH_COLLIDE:
+      // per node, the stencils through L1: staging each tile's halo in shared memory (the
+      // single-lattice collide kernel's way) took 27.7 against 21.6 ms per 10 steps on the
+      // 256-lattice mix -- two block barriers a tile in a persistent loop without other work to
+      // hide them
       for (int w = w0; w < w1; ++w) {
         const int2 t = items[w];
         load_lattice(L, lat, t.x, loaded);

@@ -167,6 +167,87 @@ __device__ __forceinline__ void phase_mu_vec(const Lattice<real>& L, int x0, int
   }
 }
 
+// ---- collide tiles of 32 x 8 nodes with a two-node halo of the stencil fields in shared memory
+constexpr int CT_X = 32, CT_Y = 8, CT_H = 2;
+constexpr int CT_SX = CT_X + 2 * CT_H, CT_SY = CT_Y + 2 * CT_H;
+static_assert(CT_X == 32 && CT_SX - 32 <= 32, "one warp stages a row of the tile and its halo");
+
+// Terms of the force at a node from a staged tile (row stride W, the node at index c): the
+// undivided fourth-order differences of mu and rho of Eq. 9 (diff4_of), or the two sums and the
+// centre value of the pseudopotential force.  Both collide kernels take them before the
+// collision and finish the force with tile_force, so that they evaluate it with the same
+// operations as force_at.
+template <typename real, bool PSEUDO>
+__device__ __forceinline__ void tile_force_terms(const real* sm, const real* sr, int W, int c, real (&g)[4]) {
+  if (PSEUDO) {
+    pp_sums(sm[c + 1], sm[c + W], sm[c - 1], sm[c - W], sm[c + W + 1], sm[c + W - 1], sm[c - W - 1], sm[c - W + 1],
+            g[0], g[1]);
+    g[2] = sm[c];
+    g[3] = real(0);
+  } else {
+    g[0] = diff4_of(sm[c + 1], sm[c - 1], sm[c + 2], sm[c - 2]);
+    g[1] = diff4_of(sm[c + W], sm[c - W], sm[c + 2 * W], sm[c - 2 * W]);
+    g[2] = diff4_of(sr[c + 1], sr[c - 1], sr[c + 2], sr[c - 2]);
+    g[3] = diff4_of(sr[c + W], sr[c - W], sr[c + 2 * W], sr[c - 2 * W]);
+  }
+}
+// F = rho g plus the nonideal force from those terms (force_at's operations)
+template <typename real, bool PSEUDO>
+__device__ __forceinline__ void tile_force(const Lattice<real>& L, bool stencils, const real (&g)[4], real r, real& Fx,
+                                           real& Fy) {
+  if (!stencils) {
+    Fx = r * L.gx;
+    Fy = r * L.gy;
+    return;
+  }
+  if (PSEUDO) {
+    Fx = force_pp(r, L.gx, g[2], g[0]);
+    Fy = force_pp(r, L.gy, g[2], g[1]);
+  } else {
+    Fx = force_cp(r, L.gx, g[0], g[2]);
+    Fy = force_cp(r, L.gy, g[1], g[3]);
+  }
+}
+
+// The density and chemical potential (or psi) of the 32 x 8 collide tile at (x0, y0) and of a
+// two-node halo into shared memory, by all CT_X * CT_Y threads of the block (the caller
+// synchronises before reading them): one warp per row where tile and halo lie inside the
+// lattice, else element by element with the periodic wrap.
+template <typename real, bool PSEUDO>
+__device__ __forceinline__ void stage_tile(const Lattice<real>& L, int x0, int y0, real (*s_rho)[CT_SX],
+                                           real (*s_mu)[CT_SX]) {
+  constexpr int NT = CT_X * CT_Y;
+  if (x0 >= CT_H && x0 + CT_X + CT_H <= L.nx && y0 >= CT_H && y0 + CT_Y + CT_H <= L.ny) {
+    // tile and halo inside the lattice (block-uniform): one warp per staged row, plain offsets
+    const int lane = threadIdx.x & 31, wr = threadIdx.x >> 5;
+    const int base = (y0 - CT_H) * L.pitch + (x0 - CT_H);
+    for (int r = wr; r < CT_SY; r += NT / 32) {
+      const int row = base + r * L.pitch;
+      if (!PSEUDO) s_rho[r][lane] = L.rho[row + lane];
+      s_mu[r][lane] = L.mu[row + lane];
+      if (lane < CT_SX - 32) {
+        if (!PSEUDO) s_rho[r][32 + lane] = L.rho[row + 32 + lane];
+        s_mu[r][32 + lane] = L.mu[row + 32 + lane];
+      }
+    }
+  } else {
+    for (int e = threadIdx.x; e < CT_SX * CT_SY; e += NT) {
+      const int ly = e / CT_SX, lx = e - ly * CT_SX;
+      const int x = x0 + lx - CT_H, y = y0 + ly - CT_H;
+      real r = real(0), m = real(0);
+      // a fluid node's stencil reaches x in [-2, nx+1] (wrapped) and, with walls, stays
+      // inside the rows; other slots are never read
+      if (x <= L.nx + 1 && (L.walls ? (y >= 0 && y < L.ny) : (y <= L.ny + 1))) {
+        const int n = node_at(L, x, y);
+        if (!PSEUDO) r = L.rho[n];
+        m = L.mu[n];
+      }
+      if (!PSEUDO) s_rho[ly][lx] = r;
+      s_mu[ly][lx] = m;
+    }
+  }
+}
+
 // force (Eq. 9) + collision (Eq. 4) with exact-difference forcing (Eq. 13) + push streaming
 // (Eq. 5) of fluid node (x, y) into the other lattice.  Force(r, Fx, Fy) evaluates Eq. 9 at
 // the node: from the density and chemical-potential planes (force_at), or from a tile of them

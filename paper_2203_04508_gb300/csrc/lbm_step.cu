@@ -333,51 +333,14 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_psi(Lattice<real> L) {
   }
 }
 
-// Terms of the force at a node from a staged tile (row stride W, the node at index c): the
-// undivided fourth-order differences of mu and rho of Eq. 9 (diff4_of), or the two sums and the
-// centre value of the pseudopotential force.  Both collide kernels take them before the
-// collision and finish the force with tile_force, so that they evaluate it with the same
-// operations as force_at.
-template <typename real, bool PSEUDO>
-__device__ __forceinline__ void tile_force_terms(const real* sm, const real* sr, int W, int c, real (&g)[4]) {
-  if (PSEUDO) {
-    pp_sums(sm[c + 1], sm[c + W], sm[c - 1], sm[c - W], sm[c + W + 1], sm[c + W - 1], sm[c - W - 1], sm[c - W + 1],
-            g[0], g[1]);
-    g[2] = sm[c];
-    g[3] = real(0);
-  } else {
-    g[0] = diff4_of(sm[c + 1], sm[c - 1], sm[c + 2], sm[c - 2]);
-    g[1] = diff4_of(sm[c + W], sm[c - W], sm[c + 2 * W], sm[c - 2 * W]);
-    g[2] = diff4_of(sr[c + 1], sr[c - 1], sr[c + 2], sr[c - 2]);
-    g[3] = diff4_of(sr[c + W], sr[c - W], sr[c + 2 * W], sr[c - 2 * W]);
-  }
-}
-// F = rho g plus the nonideal force from those terms (force_at's operations)
-template <typename real, bool PSEUDO>
-__device__ __forceinline__ void tile_force(const Lattice<real>& L, bool stencils, const real (&g)[4], real r, real& Fx,
-                                           real& Fy) {
-  if (!stencils) {
-    Fx = r * L.gx;
-    Fy = r * L.gy;
-    return;
-  }
-  if (PSEUDO) {
-    Fx = force_pp(r, L.gx, g[2], g[0]);
-    Fy = force_pp(r, L.gy, g[2], g[1]);
-  } else {
-    Fx = force_cp(r, L.gx, g[0], g[2]);
-    Fy = force_cp(r, L.gy, g[1], g[3]);
-  }
-}
+static_assert(CT_X * CT_Y == NODE_BLOCK, "a collide tile is one node a thread");
 
 // Force + collision + streaming.  A block of 32 x 8 nodes (one warp per 128-byte row) first
 // stages the density and chemical potential of its tile and of a two-node halo in shared
-// memory, so that the fourth-order gradients of Eq. 9 read 16 neighbours there instead of
-// through the L1/L2 path; the arithmetic is force_at's, operation for operation.  PSEUDO: the
-// pseudopotential force from the staged psi tile (its one-node halo); no density staging.
-constexpr int CT_X = 32, CT_Y = NODE_BLOCK / CT_X, CT_H = 2;
-constexpr int CT_SX = CT_X + 2 * CT_H, CT_SY = CT_Y + 2 * CT_H;
-static_assert(CT_X == 32 && CT_SX - 32 <= 32, "one warp stages a row of the tile and its halo");
+// memory (stage_tile), so that the fourth-order gradients of Eq. 9 read 16 neighbours there
+// instead of through the L1/L2 path; the arithmetic is force_at's, operation for operation.
+// PSEUDO: the pseudopotential force from the staged psi tile (its one-node halo); no density
+// staging.
 
 // LAY: 0 two lattices; one lattice in AA order, 1 its first step (natural order in, each node's
 // own slots rewritten in place), 2 its second (f_i(x) pulled from slot opp(i) of x - e_i, pushed
@@ -411,35 +374,7 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide(Lattice<real> L, int cur
     }
   }
   if (stencils) {
-    if (x0 >= CT_H && x0 + CT_X + CT_H <= L.nx && y0 >= CT_H && y0 + CT_Y + CT_H <= L.ny) {
-      // tile and halo inside the lattice (block-uniform): one warp per staged row, plain offsets
-      const int lane = threadIdx.x & 31, wr = threadIdx.x >> 5;
-      const int base = (y0 - CT_H) * L.pitch + (x0 - CT_H);
-      for (int r = wr; r < CT_SY; r += NODE_BLOCK / 32) {
-        const int row = base + r * L.pitch;
-        if (!PSEUDO) s_rho[r][lane] = L.rho[row + lane];
-        s_mu[r][lane] = L.mu[row + lane];
-        if (lane < CT_SX - 32) {
-          if (!PSEUDO) s_rho[r][32 + lane] = L.rho[row + 32 + lane];
-          s_mu[r][32 + lane] = L.mu[row + 32 + lane];
-        }
-      }
-    } else {
-      for (int e = threadIdx.x; e < CT_SX * CT_SY; e += NODE_BLOCK) {
-        const int ly = e / CT_SX, lx = e - ly * CT_SX;
-        const int x = x0 + lx - CT_H, y = y0 + ly - CT_H;
-        real r = real(0), m = real(0);
-        // a fluid node's stencil reaches x in [-2, nx+1] (wrapped) and, with walls, stays
-        // inside the rows; other slots are never read
-        if (x <= L.nx + 1 && (L.walls ? (y >= 0 && y < L.ny) : (y <= L.ny + 1))) {
-          const int n = node_at(L, x, y);
-          if (!PSEUDO) r = L.rho[n];
-          m = L.mu[n];
-        }
-        if (!PSEUDO) s_rho[ly][lx] = r;
-        s_mu[ly][lx] = m;
-      }
-    }
+    stage_tile<real, PSEUDO>(L, x0, y0, s_rho, s_mu);
     __syncthreads();
   }
   if (!fluid) return;

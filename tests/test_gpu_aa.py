@@ -3,8 +3,9 @@ populations, densities, velocities, mass and Eq. 18 compensation history, bit fo
 and even step counts (the state alternates between natural and shifted slot order), on lattices
 that take every path -- walls and periodic boxes, ragged edges, several cylinders, both force
 models, FP32 and FP64, BGK and MRT, every boundary scheme, the TMA-pipelined collide in both of
-the order's steps and the plain one -- and through the graph-launched and the phase-by-phase step.  The AA order
-is an implementation choice of streaming (Eq. 5), so the values must not change at all."""
+the order's steps and the plain one -- and through the graph-launched and the phase-by-phase
+step.  The AA order is an implementation choice of streaming (Eq. 5), so the values must not
+change at all."""
 from __future__ import annotations
 
 import os
