@@ -13,18 +13,20 @@ instead, flushing L2 before every timed step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
-Under torchrun each rank advances its own replica of the workload (weak scaling, no
-collective on the data path); rank 0 prints one JSON line.  `--impl reference` times the FP64
-reference oracle on the host cores instead (rank 0 only).
+Under torchrun the headline lattice is split into y-slabs, one per rank, whose halos are
+exchanged over NCCL every few steps (strong scaling); rank 0 prints one JSON line.
+`--impl reference` times the FP64 reference oracle on the host cores instead (rank 0 only).
+Before the clock starts the graphs that the timed steps launch are captured (lbm_prepare_steps),
+so that no capture happens inside the timed region; nothing is stepped by it.
 
 Besides the contract keys the line carries: `roofline` (the collide kernel's algorithmic bytes
 over its CUDA-event time, against the measured HBM copy bandwidth, with the per-phase times),
 `cpu_baseline` (the oracle on the host cores), `e2e` (through the C-ABI with host buffers),
 `clocks`, `fp64` (the same workload with FP64 populations: MLUPS and the FP32/FP64 speed
 ratio; the drop's interface on the centre line in FP32 and FP64 over 10000 steps; the 128 x 128
-FP64 case's mass change with the present scheme and IBC), `batched` (256 instances of 128^2..768^2 in one persistent launch against the same
-instances stepped one by one; the autotuned tile shape; the same comparison on 1024 instances
-of 64^2..128^2), and `adjoint` (512 x 512, 4000 steps, checkpoint every 200: forward,
+FP64 case's mass change with the present scheme and IBC), `batched` (256 instances of
+128^2..768^2 in one persistent launch against the same instances stepped one by one; the
+autotuned tile shape; the same comparison on 1024 instances of 64^2..128^2), and `adjoint` (512 x 512, 4000 steps, checkpoint every 200: forward,
 checkpointed forward and reverse-sweep times, one reverse step against one forward step, and
 the gradient), and `bc_comparison` (the boundary schemes of the paper's Sec. 4.3-4.4 on
 reduced-size drops: late per-step compensation and spurious currents), and `paper_runs` (the
@@ -34,8 +36,9 @@ drop impact at its three Bond numbers: the film on the cylinder's top against th
 `pseudopotential` (the impact lattice with the pseudopotential force in place of the
 chemical-potential one: step time, per-phase times, against the headline step), and `aa_layout`
 (the headline lattice with one population lattice in AA order: step time, workspace, against the
-two-lattice step).  `--mode kernels` / `--mode adjoint` run only the timed step loop / only the
-gradient workload (for profiler captures); `--layout 1` puts the headline lattice in AA order.
+two-lattice step).  `--mode kernels` / `--mode adjoint` / `--mode batch` run only the timed
+step loop / only the gradient workload / only the batched kernel (for profiler captures);
+`--layout 1` puts the headline lattice in AA order.
 """
 from __future__ import annotations
 
@@ -833,6 +836,10 @@ def main():
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     advance(args.warmup)
+    if world == 1:
+        # the graphs the timed lbm_step(K) launches, captured now, so that the clock does not run
+        # while the host captures one (nothing is stepped)
+        lat.prepare_steps(args.steps if flush is None else 1)
     lat.synchronize()
     if world > 1:
         dist.barrier()

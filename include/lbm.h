@@ -196,6 +196,12 @@ lbm_status lbm_init(lbm_ctx* ctx, const lbm_init_spec* init);
  * device memory is allocated); to the caller the work is on the context's stream. */
 lbm_status lbm_step(lbm_ctx* ctx, int64_t n);
 
+/* Captures and instantiates the step graphs that lbm_step(n) will launch from the current state,
+ * without running them, so that the first such call spends no host time on capture (n >= 0;
+ * nothing to do on the legacy default stream, which lbm_step does not capture).  LBM_ESTATE
+ * before lbm_init. */
+lbm_status lbm_prepare_steps(lbm_ctx* ctx, int64_t n);
+
 /* Density and velocity v = u + F/(2 rho) of the current state (the macroscopic velocity
  * defined under Eq. 14) into caller-owned arrays of nx*ny values of the context's precision
  * (float or double); zero at solid nodes.  on_device != 0: device pointers, written

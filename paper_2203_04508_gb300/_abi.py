@@ -58,6 +58,7 @@ _SIGS = {
     "lbm_get_kind": (I32, [P, P]),
     "lbm_init": (I32, [P, C.POINTER(lbm_init_spec)]),
     "lbm_step": (I32, [P, I64]),
+    "lbm_prepare_steps": (I32, [P, I64]),
     "lbm_fields": (I32, [P, P, P, P, I32]),
     "lbm_populations": (I32, [P, P, I32]),
     "lbm_set_populations": (I32, [P, P, I32]),

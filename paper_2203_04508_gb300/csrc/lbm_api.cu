@@ -437,14 +437,61 @@ void step_lattices(const lbm_ctx* c, const Lattice<real>& L, int cur, Lattice<re
 // graph launches, and so fewer gaps between them, for long runs.
 constexpr int STEPS_LONG = 8;
 
-template <typename real>
-lbm_status do_step(lbm_ctx* c, const Lattice<real>& L, long long n) {
-  if (n <= 0) return LBM_OK;
+// the second stream and events of the overlapped step (created on first use)
+lbm_status step_streams(lbm_ctx* c) {
   if (!c->side) {
     CUDA_OK(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
     CUDA_OK(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     CUDA_OK(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   }
+  return LBM_OK;
+}
+
+// The graph of `steps` (1, 2 or STEPS_LONG) steps from lattice parity p, captured and
+// instantiated on first use: slot p (two steps), 2 + p (one) or 4 + p (STEPS_LONG).
+template <typename real>
+lbm_status step_graph(lbm_ctx* c, const Lattice<real>& L, int p, int steps, cudaGraphExec_t* out) {
+  cudaGraphExec_t& slot = c->graph[(steps == 2 ? 0 : steps == 1 ? 2 : 4) + p];
+  if (!slot) {
+    Lattice<real> Lt, Ln;
+    cudaGraph_t g;
+    CUDA_OK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e1 = cudaSuccess;
+    for (int k = 0; k < steps && e1 == cudaSuccess; ++k) {
+      step_lattices(c, L, p ^ (k & 1), Lt, Ln);
+      e1 = launch_step_overlap(Lt, Ln, p ^ (k & 1), c->stream, c->side, c->ev_fork, c->ev_join);
+    }
+    cudaError_t e3 = cudaStreamEndCapture(c->stream, &g);
+    if (e1 != cudaSuccess || e3 != cudaSuccess)
+      return fail(c, LBM_ECUDA, "graph capture failed: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e3));
+    cudaError_t e4 = cudaGraphInstantiate(&slot, g, 0);
+    cudaGraphDestroy(g);
+    if (e4 != cudaSuccess) return fail(c, LBM_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e4));
+  }
+  *out = slot;
+  return LBM_OK;
+}
+
+// The graphs lbm_step(n) launches from the current parity, captured without running them.
+template <typename real>
+lbm_status prepare_steps(lbm_ctx* c, const Lattice<real>& L, long long n) {
+  if (n <= 0 || c->stream == nullptr) return LBM_OK;
+  lbm_status st = step_streams(c);
+  if (st != LBM_OK) return st;
+  cudaGraphExec_t g;
+  if (n >= STEPS_LONG && (st = step_graph(c, L, c->cur, STEPS_LONG, &g)) != LBM_OK) return st;
+  n -= STEPS_LONG * (n / STEPS_LONG);
+  if (n >= 2 && (st = step_graph(c, L, c->cur, 2, &g)) != LBM_OK) return st;
+  n -= 2 * (n / 2);
+  if (n == 1 && (st = step_graph(c, L, c->cur, 1, &g)) != LBM_OK) return st;
+  return LBM_OK;
+}
+
+template <typename real>
+lbm_status do_step(lbm_ctx* c, const Lattice<real>& L, long long n) {
+  if (n <= 0) return LBM_OK;
+  lbm_status sst = step_streams(c);
+  if (sst != LBM_OK) return sst;
   Lattice<real> Lt, Ln;
   if (!c->rho_ok) {
     // density of the current lattice and its solid layers, which the overlapped step expects
@@ -455,28 +502,7 @@ lbm_status do_step(lbm_ctx* c, const Lattice<real>& L, long long n) {
     if (L.mu_kernel == 3) CUDA_OK(c, launch_phase(Lt, c->cur, 2, c->stream));
     c->rho_ok = true;
   }
-  // graphs of two steps (slot p), one step (slot 2 + p) and STEPS_LONG steps (slot 4 + p) from
-  // lattice parity p
-  auto graph_of = [&](int p, int steps, cudaGraphExec_t* out) -> lbm_status {
-    cudaGraphExec_t& slot = c->graph[(steps == 2 ? 0 : steps == 1 ? 2 : 4) + p];
-    if (!slot) {
-      cudaGraph_t g;
-      CUDA_OK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e1 = cudaSuccess;
-      for (int k = 0; k < steps && e1 == cudaSuccess; ++k) {
-        step_lattices(c, L, p ^ (k & 1), Lt, Ln);
-        e1 = launch_step_overlap(Lt, Ln, p ^ (k & 1), c->stream, c->side, c->ev_fork, c->ev_join);
-      }
-      cudaError_t e3 = cudaStreamEndCapture(c->stream, &g);
-      if (e1 != cudaSuccess || e3 != cudaSuccess)
-        return fail(c, LBM_ECUDA, "graph capture failed: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e3));
-      cudaError_t e4 = cudaGraphInstantiate(&slot, g, 0);
-      cudaGraphDestroy(g);
-      if (e4 != cudaSuccess) return fail(c, LBM_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e4));
-    }
-    *out = slot;
-    return LBM_OK;
-  };
+  auto graph_of = [&](int p, int steps, cudaGraphExec_t* out) { return step_graph(c, L, p, steps, out); };
   if (n >= STEPS_LONG && c->stream != nullptr) {
     cudaGraphExec_t gl;
     lbm_status st = graph_of(c->cur, STEPS_LONG, &gl);
@@ -1056,6 +1082,14 @@ lbm_status lbm_step(lbm_ctx* c, int64_t n) {
   if (s == LBM_OK) c->steps += n;
   if (n > 0) c->tape.valid = false;
   return s;
+}
+
+lbm_status lbm_prepare_steps(lbm_ctx* c, int64_t n) {
+  LBM_RANGE("lbm_prepare_steps");
+  if (!c || !c->inited) return LBM_ESTATE;
+  if (c->sticky != LBM_OK) return c->sticky;
+  if (n < 0) return fail(c, LBM_EINVAL, "negative step count");
+  return c->fp64 ? prepare_steps(c, c->Ld, n) : prepare_steps(c, c->Lf, n);
 }
 
 lbm_status lbm_set_collide_kernel(lbm_ctx* c, int32_t kind) {

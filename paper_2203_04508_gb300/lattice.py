@@ -117,6 +117,10 @@ class Lattice:
     def step(self, n: int = 1):
         self._c(self.lib.lbm_step(self.ctx, int(n)))
 
+    def prepare_steps(self, n: int):
+        """Captures the step graphs step(n) will launch, without running them (lbm_prepare_steps)."""
+        self._c(self.lib.lbm_prepare_steps(self.ctx, int(n)))
+
     def synchronize(self):
         self.stream.synchronize()
 
