@@ -67,6 +67,7 @@ struct CollideTma {
   bool pull_ok;                 // f_pull was encoded
   int blocks[2];                // persistent grid of the chemical-potential / psi variant
   int blocks_pull[2];           // ... of the AA order's second step
+  int blocks_inplace[2];        // ... of its first step
   int sweep_blocks;             // blocks of the column-sweep variant that fit on the device at once
   float* edge;                  // its edge buffer (null: the sweep does not run)
 };
