@@ -1581,7 +1581,7 @@ lbm_status plan_batch(int n, const lbm_config* cfgs, BatchPlan* P, char* msg) {
   P->t_first = take((size_t)n * sizeof(int2));
   P->t_group = take((size_t)n);
   P->t_part = take((size_t)(P->cap_bc + 1) * sizeof(double));
-  P->t_bar = take(16);
+  P->t_bar = take(16 + BATCH_WORK_COUNTERS * 8);   // barrier words, then the work counters
   P->t_err = take(16);
   P->total = P->tab_off + t;
   return LBM_OK;
@@ -1672,6 +1672,7 @@ lbm_status batch_tables(lbm_batch* b) {
   d.inst_bc = (const int2*)(t + b->t_first);
   d.bc_partials = (double*)(t + b->t_part);
   d.bar = (unsigned int*)(t + b->t_bar);
+  d.work = (unsigned long long*)(t + b->t_bar + 16);
   d.err = (int*)(t + b->t_err);
   d.spin_limit = b->spin_limit;
   b->grid = batch_grid_size(b->fp64);

@@ -49,9 +49,9 @@ __device__ __forceinline__ bool grid_sync(const BatchDev& B, unsigned int target
   return ok != 0;
 }
 
-// Copy of an instance's lattice descriptor into shared memory.  Each block takes a contiguous
-// range of every work list, so consecutive items mostly belong to one instance and the copy
-// is redone only when the instance changes.
+// Copy of an instance's lattice descriptor into shared memory.  A block takes the items of a work
+// list in chunks of consecutive items, which mostly belong to one instance; the copy is redone
+// only when the instance changes.
 template <typename real>
 __device__ __forceinline__ void load_lattice(Lattice<real>& dst, const Lattice<real>* lat, int k, int& loaded) {
   if (k == loaded) return;   // block-uniform
@@ -65,11 +65,12 @@ __device__ __forceinline__ void load_lattice(Lattice<real>& dst, const Lattice<r
   loaded = k;
 }
 
-// this block's share [w0, w1) of a list of n items
-__device__ __forceinline__ void block_range(int n, int& w0, int& w1) {
-  w0 = (int)(((long long)n * blockIdx.x) / gridDim.x);
-  w1 = (int)(((long long)n * (blockIdx.x + 1)) / gridDim.x);
-}
+// Items are handed out in chunks from a counter per tick and group, so that blocks whose items
+// are cheap (tiles inside a cylinder, say) take more of them instead of waiting at the next
+// barrier.  Three counters per group rotate over the ticks: tick tau takes counter tau % 3 and
+// zeroes counter (tau + 1) % 3, which no block touches in tick tau and which the grid barrier
+// publishes before tick tau + 1.
+constexpr int WORK_CHUNK = 4;
 
 // Node tiles are 2D blocks of 2^tile_log2w x (256 / 2^tile_log2w) nodes of an instance's
 // lattice, row-major over the tiles of each instance: tile t of an instance with tiles_x tiles
@@ -160,6 +161,9 @@ __device__ __forceinline__ void run_phase(const BatchDev& B, const Lattice<real>
       // single-lattice collide kernel's way) took 27.7 against 21.6 ms per 10 steps on the
       // 256-lattice mix -- two block barriers a tile in a persistent loop without other work to
       // hide them
+      // (reading each instance's descriptor from the table instead of a shared-memory copy:
+      // 410 against 402 ms for 200 steps of the mix, although a block's chunks rarely share an
+      // instance)
       for (int w = w0; w < w1; ++w) {
         const int2 t = items[w];
         load_lattice(L, lat, t.x, loaded);
@@ -189,6 +193,7 @@ __global__ void __launch_bounds__(BATCH_BLOCK, 6) k_batch(BatchDev B, int n_step
   __shared__ __align__(16) Lattice<real> Ls[2];
   __shared__ double red[32];
   __shared__ int loaded[2];     // instance whose descriptor Ls[g] holds (block-uniform)
+  __shared__ unsigned long long grab;   // the chunk thread 0 took
   const Lattice<real>* lat = static_cast<const Lattice<real>*>(B.lat);
   const int G = B.groups;
   const int last_q = N_PHASES * n_steps;               // q of the final compensation sums
@@ -228,11 +233,20 @@ __global__ void __launch_bounds__(BATCH_BLOCK, 6) k_batch(BatchDev B, int n_step
       const int p = q % N_PHASES;
       const int cur = cur0 ^ ((q / N_PHASES) & 1);
       const int2* items;
-      int first, last, w0, w1;
+      int first, last;
       phase_list(B, p, g, items, first, last);
-      block_range(last - first, w0, w1);
-      run_phase(B, lat, Ls[g], loaded[g], p, cur, items, first + w0, first + w1, red);
+      unsigned long long* ctr = B.work + 2 * (tau % 3) + g;
+      for (;;) {
+        if (threadIdx.x == 0) grab = atomicAdd(ctr, (unsigned long long)WORK_CHUNK);
+        __syncthreads();
+        const long long w = (long long)grab;
+        __syncthreads();   // every thread has read `grab` before thread 0 takes the next chunk
+        if (w >= last - first) break;   // block-uniform
+        const int w1 = (int)(w + WORK_CHUNK < last - first ? w + WORK_CHUNK : last - first);
+        run_phase(B, lat, Ls[g], loaded[g], p, cur, items, first + (int)w, first + w1, red);
+      }
     }
+    if (blockIdx.x == 0 && threadIdx.x < 2) B.work[2 * ((tau + 1) % 3) + threadIdx.x] = 0ull;
   }
 }
 
@@ -257,6 +271,7 @@ int batch_grid_size(int fp64) {
 
 cudaError_t launch_batch(const BatchDev& B, int fp64, int grid, int n_steps, int cur0, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(B.bar, 0, 2 * sizeof(unsigned int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(B.work, 0, BATCH_WORK_COUNTERS * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   BatchDev b = B;
   void* args[] = {&b, &n_steps, &cur0};

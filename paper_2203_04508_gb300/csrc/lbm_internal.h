@@ -148,10 +148,13 @@ struct BatchDev {
   const int2* inst_bc;          // bc items of instance k: [inst_bc[k].x, inst_bc[k].y)
   double* bc_partials;          // one compensation sum per bc item
   unsigned int* bar;            // grid barrier: arrivals, completed barriers
+  unsigned long long* work;     // BATCH_WORK_COUNTERS work counters: items handed out in tick tau
+                                // to group g at work[2 (tau % 3) + g] (zeroed before the launch)
   int* err;                     // set when a barrier wait gave up
   long long spin_limit;         // polls before a barrier wait gives up
 };
 int batch_block_size();
+constexpr int BATCH_WORK_COUNTERS = 6;
 // node tiles of width 2^log2w (and height 256 / 2^log2w) of one instance; the shapes a batch
 // may use are log2w = BATCH_TILE_LOG2W_MIN .. BATCH_TILE_LOG2W_MAX (16x16 .. 256x1)
 constexpr int BATCH_TILE_LOG2W_MIN = 4, BATCH_TILE_LOG2W_MAX = 8, BATCH_TILE_LOG2W_DEFAULT = 5;
