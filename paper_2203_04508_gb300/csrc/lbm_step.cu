@@ -43,10 +43,12 @@ __device__ __forceinline__ bool node_of_thread(const Lattice<real>& L, int& x, i
 }
 
 // Density pass with 16-byte loads: each thread takes V = 16/sizeof(real) consecutive nodes of
-// a row (phase_rho_vec).
+// a row (phase_rho_vec).  Rows are taken from the top down: the collide kernel writes the new
+// populations roughly from the bottom up, so the rows it wrote last are still in L2 when this pass
+// starts, and the rows this pass reads last are the ones the next collide reads first.
 template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_rho_vec(Lattice<real> L, int cur) {
-  const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * Vec16<real>::V, y = blockIdx.y;
+  const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * Vec16<real>::V, y = L.ny - 1 - (int)blockIdx.y;
   if (x0 < L.nx) phase_rho_vec(L, cur, x0, y);
 }
 
@@ -58,8 +60,9 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_rho_vec(Lattice<real> L, int cur
 // dependent loads.)
 template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_rho_pull(Lattice<real> L, int cur) {
-  const int x = blockIdx.x * TILE_X + threadIdx.x, y = blockIdx.y * TILE_Y + threadIdx.y;
-  if (x >= L.nx || y >= L.ny) return;
+  // rows from the top down, as k_rho_vec takes them
+  const int x = blockIdx.x * TILE_X + threadIdx.x, y = L.ny - 1 - (int)(blockIdx.y * TILE_Y + threadIdx.y);
+  if (x >= L.nx || y < 0) return;
   const int n = y * L.pitch + x;
   if (L.kind[n] != KIND_FLUID) return;
   real fl[9];
