@@ -183,7 +183,9 @@ lbm_status lbm_get_links(lbm_ctx* ctx, int64_t capacity, int32_t* x1, int32_t* d
  * 2 second solid layer, 3 deeper solid. */
 lbm_status lbm_get_kind(lbm_ctx* ctx, uint8_t* kind);
 
-/* Eq. 19 initial state on the device, then the initial mass M0 (FP64).  Synchronises. */
+/* Eq. 19 initial state on the device, then the audit of its mass M0 (FP64), both queued on the
+ * context's stream; the host reads M0 at the first call that needs it (lbm_mass, lbm_save).
+ * Does not wait for the device; the init arrays may be reused on return. */
 lbm_status lbm_init(lbm_ctx* ctx, const lbm_init_spec* init);
 
 /* Advances n time steps, asynchronously on the context's stream (captured into a CUDA
@@ -314,7 +316,8 @@ lbm_status lbm_set_spin_limit(lbm_ctx* ctx, int64_t polls);
  * absolute populations in the context's precision, population i at offset i*nx*ny (the layout
  * lbm_populations writes); values at non-fluid nodes are ignored.  Clears the step counter,
  * the compensation history and the Eq. 18 carries, and takes the state's mass as the new M0.
- * on_device: 1 if f is a device pointer, 0 for host memory.  Synchronises the stream.  With
+ * on_device: 1 if f is a device pointer, 0 for host memory (which may be reused on return; the
+ * call does not wait for the device, M0 is read when first needed, as after lbm_init).  With
  * FP32 offset storage the values are stored as f_i - w_i rho_ref, so a state read out by
  * lbm_populations comes back to within an ulp of each offset population. */
 lbm_status lbm_set_populations(lbm_ctx* ctx, const void* f, int32_t on_device);

@@ -159,6 +159,9 @@ struct lbm_ctx {
   Lattice<float> Lf{};
   Lattice<double> Ld{};
   double mass0 = 0;
+  // M0 of lbm_init / lbm_set_populations is left on the device (scalars[2]) without waiting for
+  // it; the first call that needs it reads it
+  bool mass0_pending = false;
   // step graphs (x lattice parity): 2 steps, 1 step, STEPS_LONG steps
   cudaGraphExec_t graph[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   // FP32: TMA descriptors of the pipelined collide kernel (set up by lbm_build_links) and the
@@ -601,6 +604,26 @@ lbm_status profile_steps(lbm_ctx* c, const Lattice<real>& L, long long n, double
 
 // Fluid nodes the mass audit counts: a slab's own rows only.
 long long fluid_count(const lbm_ctx* c) { return c->slab.on ? c->slab.n_fluid_own : c->n_fluid; }
+
+// The mass audit of the state just set (lbm_init, lbm_set_populations), kept on the device in
+// scalars[2..3] (later audits overwrite scalars[0..1]); nothing waits for it.
+cudaError_t mass0_async(lbm_ctx* c) {
+  cudaError_t e = c->fp64 ? launch_mass(c->Ld, 0, c->stream) : launch_mass(c->Lf, 0, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->ws + c->lay.scalars + 16, c->ws + c->lay.scalars, 16, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) c->mass0_pending = true;
+  return e;
+}
+// M0 on the host, read from the device the first time it is needed (synchronises the stream).
+lbm_status resolve_mass0(lbm_ctx* c) {
+  if (!c->mass0_pending) return LBM_OK;
+  double sc[2];
+  CUDA_OK(c, cudaMemcpyAsync(sc, c->ws + c->lay.scalars + 16, 16, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  c->mass0 = sc[0] + (double)fluid_count(c) * c->rho_ref;
+  c->mass0_pending = false;
+  return LBM_OK;
+}
 
 // Device staging memory of the read-outs: the lattice that the next step overwrites completely
 // (nine planes), or with one lattice (AA order) the three staging planes.
@@ -1062,11 +1085,7 @@ lbm_status lbm_init(lbm_ctx* c, const lbm_init_spec* s) {
   CUDA_OK(c, cudaMemsetAsync(c->ws + y.carry, 0, (size_t)y.cap.bnodes * 8, c->stream));
   c->cur = 0;
   c->steps = 0;
-  if (c->fp64) CUDA_OK(c, launch_mass(c->Ld, 0, c->stream)); else CUDA_OK(c, launch_mass(c->Lf, 0, c->stream));
-  double sc[2];
-  CUDA_OK(c, cudaMemcpyAsync(sc, c->ws + y.scalars, 16, cudaMemcpyDeviceToHost, c->stream));
-  CUDA_OK(c, cudaStreamSynchronize(c->stream));
-  c->mass0 = sc[0] + (double)fluid_count(c) * c->rho_ref;
+  CUDA_OK(c, mass0_async(c));
   c->inited = true;
   c->rho_ok = false;
   c->tape.valid = false;
@@ -1250,6 +1269,8 @@ lbm_status lbm_save(lbm_ctx* c, const char* path) {
   h.config_hash = config_hash(c);
   h.steps = c->steps;
   h.n_bnodes = (uint64_t)c->n_bnodes;
+  lbm_status ms = resolve_mass0(c);
+  if (ms != LBM_OK) return ms;
   h.mass0 = c->mass0;
   h.pop_bytes = 9ull * (uint64_t)y.plane * y.sz;
   const size_t ring_bytes = (size_t)(DM_RING + 1) * 8;
@@ -1318,6 +1339,7 @@ lbm_status lbm_load(lbm_ctx* c, const char* path) {
   c->cur = h.cur;
   c->steps = h.steps;
   c->mass0 = h.mass0;
+  c->mass0_pending = false;
   c->inited = true;
   c->rho_ok = false;     // the next step forms the density and solid layers from the populations
   c->tape.valid = false;
@@ -1407,11 +1429,7 @@ lbm_status lbm_set_populations(lbm_ctx* c, const void* f, int32_t on_device) {
   CUDA_OK(c, cudaMemsetAsync(c->ws + y.dm_ring, 0, (size_t)(DM_RING + 1) * 8, c->stream));
   CUDA_OK(c, cudaMemsetAsync(c->ws + y.carry, 0, (size_t)y.cap.bnodes * 8, c->stream));
   c->steps = 0;
-  if (c->fp64) CUDA_OK(c, launch_mass(c->Ld, 0, c->stream)); else CUDA_OK(c, launch_mass(c->Lf, 0, c->stream));
-  double sc[2];
-  CUDA_OK(c, cudaMemcpyAsync(sc, c->ws + y.scalars, 16, cudaMemcpyDeviceToHost, c->stream));
-  CUDA_OK(c, cudaStreamSynchronize(c->stream));
-  c->mass0 = sc[0] + (double)fluid_count(c) * c->rho_ref;
+  CUDA_OK(c, mass0_async(c));
   c->inited = true;
   c->rho_ok = false;
   c->tape.valid = false;
@@ -1438,6 +1456,8 @@ lbm_status lbm_mass(lbm_ctx* c, double* M, double* M0, double* dM_last) {
   double last = 0.0;
   if (ctr > 0)
     CUDA_OK(c, cudaMemcpy(&last, c->ws + y.dm_ring + ((ctr - 1) % DM_RING) * 8, 8, cudaMemcpyDeviceToHost));
+  lbm_status ms = resolve_mass0(c);
+  if (ms != LBM_OK) return ms;
   if (M) *M = sc[0] + (double)fluid_count(c) * c->rho_ref;
   if (M0) *M0 = c->mass0;
   if (dM_last) *dM_last = last;
