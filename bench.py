@@ -789,7 +789,7 @@ def main():
         b = G.Batch([x.physics() for x in scs], precision=G.LBM_FP32)
         b.init([x.droplets() for x in scs])
         b.set_tile(5)
-        b.set_schedule(2)
+        b.set_schedule(1)   # 32 x 8 tiles in lockstep: the autotuner's choice on the 256-lattice mix
         b.step(args.warmup)
         b.synchronize()
         b.check()
@@ -797,7 +797,7 @@ def main():
         b.synchronize()
         b.check()
         print(json.dumps({"mode": "batch", "instances": len(scs), "nodes": sum(x.nodes for x in scs),
-                          "tile": "32x8", "schedule": "two groups", "steps": args.steps, "warmup": args.warmup}))
+                          "tile": "32x8", "schedule": "lockstep", "steps": args.steps, "warmup": args.warmup}))
         return
 
     sc, wname = workload(args.workload)
