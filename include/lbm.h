@@ -207,7 +207,8 @@ lbm_status lbm_prepare_steps(lbm_ctx* ctx, int64_t n);
 /* Density and velocity v = u + F/(2 rho) of the current state (the macroscopic velocity
  * defined under Eq. 14) into caller-owned arrays of nx*ny values of the context's precision
  * (float or double); zero at solid nodes.  on_device != 0: device pointers, written
- * asynchronously; 0: host pointers, the call synchronises. */
+ * asynchronously; 0: host pointers, the call synchronises (page-locked host arrays are written
+ * by the read-out kernel directly, others through device staging memory and copies). */
 lbm_status lbm_fields(lbm_ctx* ctx, void* rho, void* vx, void* vy, int32_t on_device);
 
 /* Checkpoint / resume.  lbm_save writes the state of an initialised context to `path`: a

@@ -1179,6 +1179,16 @@ lbm_status lbm_launches_per_step(lbm_ctx* c, int64_t* n) {
   return LBM_OK;
 }
 
+// The device address of page-locked host memory (which kernels can write directly), else null.
+void* mapped_host(void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 lbm_status lbm_fields(lbm_ctx* c, void* rho, void* vx, void* vy, int32_t on_device) {
   LBM_RANGE("lbm_fields");
   if (!c || !c->inited) return LBM_ESTATE;
@@ -1186,6 +1196,18 @@ lbm_status lbm_fields(lbm_ctx* c, void* rho, void* vx, void* vy, int32_t on_devi
   if (!rho || !vx || !vy) return fail(c, LBM_EINVAL, "null output");
   const long long dn = (long long)c->cfg.nx * c->cfg.ny;
   const size_t sz = c->lay.sz;
+  if (!on_device) {
+    // page-locked host arrays: the read-out kernel writes them directly, no staging copies
+    void* hr = mapped_host(rho);
+    void* hu = mapped_host(vx);
+    void* hv = mapped_host(vy);
+    if (hr && hu && hv) {
+      if (c->fp64) CUDA_OK(c, launch_fields(c->Ld, c->cur, (double*)hr, (double*)hu, (double*)hv, c->stream));
+      else CUDA_OK(c, launch_fields(c->Lf, c->cur, (float*)hr, (float*)hu, (float*)hv, c->stream));
+      CUDA_OK(c, cudaStreamSynchronize(c->stream));
+      return LBM_OK;
+    }
+  }
   char* stage = stage_area(c);
   char* r = on_device ? (char*)rho : stage;
   char* u = on_device ? (char*)vx : stage + dn * sz;

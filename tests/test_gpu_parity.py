@@ -237,20 +237,25 @@ def test_single_steps_and_the_asynchronous_read_back():
     assert a.last_dM() == hist[-1]
 
 
-def test_fields_into_caller_buffers():
-    """fields(out=...) fills caller-owned page-locked host tensors with the values fields()
-    returns, and refuses buffers of the wrong shape or precision."""
+@pytest.mark.parametrize("fp64,layout", [(False, 0), (True, 0), (False, 1)])
+def test_fields_into_caller_buffers(fp64, layout):
+    """fields(out=...) fills caller-owned page-locked host tensors (which the read-out kernel
+    writes directly) with the values fields() returns through its staging copies, in both
+    precisions and both population layouts, and refuses buffers of the wrong shape or precision."""
     import torch
+    import paper_2203_04508_gb300 as G
     sc = S.small_parity()
-    lat = make_lattice(sc, fp64=False)
+    lat = G.Lattice(sc.physics(), precision=G.LBM_FP64 if fp64 else G.LBM_FP32, layout=layout)
+    lat.init_droplets(sc.droplets())
     lat.step(7)
     ref = lat.fields()
-    out = [torch.empty((sc.ny, sc.nx), dtype=torch.float32, pin_memory=True) for _ in range(3)]
+    dt = torch.float64 if fp64 else torch.float32
+    out = [torch.empty((sc.ny, sc.nx), dtype=dt, pin_memory=True) for _ in range(3)]
     got = lat.fields(out=out)
     for a, b in zip(ref, got):
         assert np.array_equal(a, b.numpy())
     with pytest.raises(ValueError):
-        lat.fields(out=[torch.empty((sc.ny, sc.nx), dtype=torch.float64) for _ in range(3)])
+        lat.fields(out=[torch.empty((sc.ny, sc.nx), dtype=torch.float32 if fp64 else torch.float64) for _ in range(3)])
 
 
 def test_fp64_degenerate_geometry():
