@@ -124,7 +124,24 @@ def run_batched(G, torch, rank, world, steps, small=False):
     b.check()
     ms_b = e0.elapsed_time(e1)
     info = b.info()
+    ws_b = b.workspace.numel()
     del b
+    torch.cuda.empty_cache()
+    # the same batch with one population lattice per instance in AA order (same tile shape)
+    ba = G.Batch([sc.physics() for sc in scs], precision=G.LBM_FP32, layout=G.LBM_LAYOUT_AA)
+    ba.init([sc.droplets() for sc in scs])
+    ba.set_tile(int(tuned["log2w"]))
+    ba.set_schedule(int(tuned["groups"]))
+    ba.step(2)
+    ba.check()
+    e0.record(ba.stream)
+    ba.step(steps)
+    e1.record(ba.stream)
+    e1.synchronize()
+    ba.check()
+    ms_aa = e0.elapsed_time(e1)
+    ws_aa = ba.workspace.numel()
+    del ba
     torch.cuda.empty_cache()
     # looping single-instance launches, same instances, same steps
     lats = []
@@ -148,6 +165,9 @@ def run_batched(G, torch, rank, world, steps, small=False):
             "persistent_grid": info["grid"], "graph_captured": info["graph"],
             "tile": tuned["tile"], "schedule": "two groups" if tuned["groups"] == 2 else "lockstep",
             "autotune_ms_per_10_steps": tuned["ms"],
+            "workspace_GB": round(ws_b / 1e9, 3),
+            "aa_layout": {"ms_batched": round(ms_aa, 3), "mlups_batched": round(nodes * steps / ms_aa / 1e3, 1),
+                          "workspace_GB": round(ws_aa / 1e9, 3)},
             "looped_timing": "host wall clock around all instances' lbm_step calls, synchronised"}
 
 

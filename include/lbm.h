@@ -89,9 +89,10 @@ typedef enum {
  *    node.  The boundary phase, the density pass and every read-out address the slots of the
  *    state's current order; the pre-collision moments the boundary links need (Eq. 17's F_i
  *    uses u at x1) are saved for the boundary nodes before the collide overwrites them.  The
- *    values equal those of LBM_LAYOUT_AB bit for bit.  Single lattices only: the batch, slab and
- *    reverse-mode calls return LBM_EINVAL for it, as do collide kernel 2 and the fused
- *    chemical-potential pass (lbm_set_collide_kernel, lbm_set_mu_kernel). */
+ *    values equal those of LBM_LAYOUT_AB bit for bit, also in a batch (lbm_batch_*, whose
+ *    instances may mix both layouts).  The slab and reverse-mode calls return LBM_EINVAL for it,
+ *    as do collide kernel 2 and the fused chemical-potential pass (lbm_set_collide_kernel,
+ *    lbm_set_mu_kernel). */
 typedef enum { LBM_LAYOUT_AB = 0, LBM_LAYOUT_AA = 1 } lbm_layout;
 
 /*

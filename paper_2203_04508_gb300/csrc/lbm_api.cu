@@ -1595,7 +1595,6 @@ lbm_status plan_batch(int n, const lbm_config* cfgs, BatchPlan* P, char* msg) {
     if (s != LBM_OK) return s;
     if (cfgs[k].precision != cfgs[0].precision) { std::snprintf(msg, 256, "all instances of a batch share one precision"); return LBM_EINVAL; }
     if (cfgs[k].force_model != LBM_FORCE_CHEMPOT) { std::snprintf(msg, 256, "the batched kernel runs the chemical-potential force only"); return LBM_EINVAL; }
-    if (cfgs[k].layout != LBM_LAYOUT_AB) { std::snprintf(msg, 256, "the batched kernel runs two population lattices only"); return LBM_EINVAL; }
     Layout L = make_layout(&cfgs[k]);
     P->off[k] = o;
     P->bytes[k] = L.total;
@@ -1608,7 +1607,9 @@ lbm_status plan_batch(int n, const lbm_config* cfgs, BatchPlan* P, char* msg) {
     }
     P->cap_tiles += most;
     P->cap_s1 += (L.cap.s1 + bb - 1) / bb;
-    P->cap_s2 += (L.cap.s2 + bb - 1) / bb;
+    // one lattice in AA order: the boundary nodes' moments are saved in the second solid layer's
+    // phase, in chunks that follow the layer's own
+    P->cap_s2 += (L.cap.s2 + bb - 1) / bb + (cfgs[k].layout == LBM_LAYOUT_AA ? (L.cap.bnodes + bb - 1) / bb : 0);
     P->cap_bc += (L.cap.bnodes + bb - 1) / bb;
   }
   P->tab_off = o;
@@ -1680,6 +1681,8 @@ lbm_status batch_tables(lbm_batch* b) {
       for (long long t = 0; t < nt; ++t) tiles.push_back(make_int2(k, (int)t));
       for (int j = 0; j < L.n_s1; j += bb) s1.push_back(make_int2(k, j));
       for (int j = 0; j < L.n_s2; j += bb) s2.push_back(make_int2(k, j));
+      if (L.aa)
+        for (int j = 0; j < L.n_bnodes; j += bb) s2.push_back(make_int2(k, j | BATCH_BMOM_ITEM));
       inst_bc[k].x = (int)bc.size();
       for (int j = 0; j < L.n_bnodes; j += bb) bc.push_back(make_int2(k, j));
       inst_bc[k].y = (int)bc.size();

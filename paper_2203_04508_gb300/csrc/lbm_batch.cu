@@ -140,8 +140,16 @@ __device__ __forceinline__ void run_phase(const BatchDev& B, const Lattice<real>
         const int2 t = items[w];
         const Lattice<real>& Lk = lat[t.x];
         if (!tile_vec(Lk, B.tile_log2w, t.y, u, x, y)) continue;
-        if (p == PH_RHO) phase_rho_vec(Lk, cur, x, y);
-        else if (Lk.eos != EOS_NONE) phase_mu_vec(Lk, x, y);
+        if (p == PH_RHO) {
+          if (Lk.aa && cur == 1) {
+            // one lattice in the shifted AA order: node by node through pop_index
+            for (int k = 0; k < V && x + k < Lk.nx; ++k) phase_rho_pull(Lk, cur, x + k, y);
+          } else {
+            phase_rho_vec(Lk, cur, x, y);
+          }
+        } else if (Lk.eos != EOS_NONE) {
+          phase_mu_vec(Lk, x, y);
+        }
       }
       break;
     }
@@ -151,6 +159,12 @@ __device__ __forceinline__ void run_phase(const BatchDev& B, const Lattice<real>
       for (int w = w0; w < w1; ++w) {
         const int2 t = items[w];
         load_lattice(L, lat, t.x, loaded);
+        if (layer == 2 && (t.y & BATCH_BMOM_ITEM)) {
+          // one lattice in AA order: the pre-collision moments of 256 boundary nodes
+          const int b = (t.y & ~BATCH_BMOM_ITEM) + (int)threadIdx.x;
+          if (b < L.n_bnodes) phase_bmom(L, cur, b);
+          continue;
+        }
         const int j = t.y + threadIdx.x;
         if (j < (layer == 1 ? L.n_s1 : L.n_s2)) phase_solid(L, layer, j);
       }
@@ -167,7 +181,10 @@ __device__ __forceinline__ void run_phase(const BatchDev& B, const Lattice<real>
       for (int w = w0; w < w1; ++w) {
         const int2 t = items[w];
         load_lattice(L, lat, t.x, loaded);
-        if (tile_node(L, B.tile_log2w, t.y, x, y)) phase_collide(L, cur, x, y);
+        if (tile_node(L, B.tile_log2w, t.y, x, y)) {
+          if (L.aa) phase_collide_aa(L, cur, x, y);
+          else phase_collide(L, cur, x, y);
+        }
       }
       break;
     default:

@@ -155,6 +155,9 @@ struct BatchDev {
 };
 int batch_block_size();
 constexpr int BATCH_WORK_COUNTERS = 6;
+// a second-solid-layer item (instance, first entry | BATCH_BMOM_ITEM) that saves the moments of
+// 256 boundary nodes of a lattice in AA order instead
+constexpr int BATCH_BMOM_ITEM = 1 << 30;
 // node tiles of width 2^log2w (and height 256 / 2^log2w) of one instance; the shapes a batch
 // may use are log2w = BATCH_TILE_LOG2W_MIN .. BATCH_TILE_LOG2W_MAX (16x16 .. 256x1)
 constexpr int BATCH_TILE_LOG2W_MIN = 4, BATCH_TILE_LOG2W_MAX = 8, BATCH_TILE_LOG2W_DEFAULT = 5;

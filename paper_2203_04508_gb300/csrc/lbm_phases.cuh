@@ -52,6 +52,37 @@ __device__ __forceinline__ void phase_mu(const Lattice<real>& L, int x, int y) {
   L.mu[n] = mu_of(L, psi_prime_shifted(L, r), lap4(L.rho, n, s));
 }
 
+// ---- one population lattice in AA order (aa set; the state of lattice 1 holds f_i(x) in slot
+// opp(i) of x - e_i, pop_index)
+
+// density of fluid node (x, y) of the state in lattice `cur`, read through pop_index, and the
+// pointwise part of Eq. 12 (or psi) with it -- the values phase_rho_vec stores
+template <typename real>
+__device__ __forceinline__ void phase_rho_pull(const Lattice<real>& L, int cur, int x, int y) {
+  const int n = y * L.pitch + x;
+  if (L.kind[n] != KIND_FLUID) return;
+  real fl[9];
+  load_pops(L, cur, x, y, fl);
+  const real r = density_of(L, fl);
+  L.rho[n] = r;
+  if (L.psip) L.psip[n] = psi_prime_shifted(L, r);
+  else if (L.pseudo && L.eos != EOS_NONE) L.mu[n] = psi_of(L, r);
+}
+
+// the pre-collision moments of boundary node b, which the boundary phase needs after the collide
+// has overwritten the populations (the sums of `moments`)
+template <typename real>
+__device__ __forceinline__ void phase_bmom(const Lattice<real>& L, int cur, int b) {
+  const int n = L.bnode[b];
+  real fl[9];
+  load_pops(L, cur, n % L.pitch, n / L.pitch, fl);
+  real drho, jx, jy;
+  moments(fl, drho, jx, jy);
+  L.bmom[3 * b] = drho;
+  L.bmom[3 * b + 1] = jx;
+  L.bmom[3 * b + 2] = jy;
+}
+
 // ---- 16-byte row vectors: V = 16/sizeof(real) consecutive nodes of a row per thread.  Rows
 // start on 128-byte boundaries (the pitch), so every vector at a multiple of V is aligned.
 template <typename real> struct Vec16;
@@ -307,6 +338,20 @@ __device__ __forceinline__ void phase_collide_with(const Lattice<real>& L, int c
 template <typename real>
 __device__ __forceinline__ void phase_collide(const Lattice<real>& L, int cur, int x, int y) {
   phase_collide_with(L, cur, x, y, [&](real r, real& Fx, real& Fy) { force_at(L, x, y, r, Fx, Fy); });
+}
+
+// The collide of one lattice in AA order: from the natural order (cur 0) each node's own slots
+// are read and rewritten in place; from the shifted order (cur 1) f_i(x) is pulled from slot
+// opp(i) of x - e_i and f~_i(x) pushed into slot i of x + e_i.  The arithmetic of phase_collide.
+template <typename real>
+__device__ __forceinline__ void phase_collide_aa(const Lattice<real>& L, int cur, int x, int y) {
+  const int n = y * L.pitch + x;
+  if (L.kind[n] != KIND_FLUID) return;
+  real fl[9];
+  load_pops(L, cur, x, y, fl);
+  auto force = [&](real r, real& Fx, real& Fy) { force_at(L, x, y, r, Fx, Fy); };
+  if (cur == 0) collide_loaded<true>(L, cur, x, y, fl, force);
+  else collide_loaded<false>(L, cur, x, y, fl, force);
 }
 
 // Boundary node b (one per thread): rebuild (rho, u, F) of step t at x1 from the

@@ -62,15 +62,7 @@ template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_rho_pull(Lattice<real> L, int cur) {
   // rows from the top down, as k_rho_vec takes them
   const int x = blockIdx.x * TILE_X + threadIdx.x, y = L.ny - 1 - (int)(blockIdx.y * TILE_Y + threadIdx.y);
-  if (x >= L.nx || y < 0) return;
-  const int n = y * L.pitch + x;
-  if (L.kind[n] != KIND_FLUID) return;
-  real fl[9];
-  load_pops(L, cur, x, y, fl);
-  const real r = density_of(L, fl);
-  L.rho[n] = r;
-  if (L.psip) L.psip[n] = psi_prime_shifted(L, r);
-  else if (L.pseudo && L.eos != EOS_NONE) L.mu[n] = psi_of(L, r);
+  if (x < L.nx && y >= 0) phase_rho_pull(L, cur, x, y);
 }
 
 // One lattice (AA order): the pre-collision moments of every boundary node, which the boundary
@@ -78,15 +70,7 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_rho_pull(Lattice<real> L, int cu
 template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_bmom(Lattice<real> L, int cur) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= L.n_bnodes) return;
-  const int n = L.bnode[b];
-  real fl[9];
-  load_pops(L, cur, n % L.pitch, n / L.pitch, fl);
-  real drho, jx, jy;
-  moments(fl, drho, jx, jy);
-  L.bmom[3 * b] = drho;
-  L.bmom[3 * b + 1] = jx;
-  L.bmom[3 * b + 2] = jy;
+  if (b < L.n_bnodes) phase_bmom(L, cur, b);
 }
 
 // psi(rho_s) (1 + c_w) of a solid-layer node whose density is rho_s (pseudopotential force)

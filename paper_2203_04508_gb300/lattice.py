@@ -325,13 +325,14 @@ class _InstanceView(Lattice):
 class Batch:
     """Many independent lattices advanced together by the persistent batched kernel."""
 
-    def __init__(self, physics: list, precision: int = _abi.LBM_FP32, stream=None):
+    def __init__(self, physics: list, precision: int = _abi.LBM_FP32, stream=None,
+                 layout: int = _abi.LBM_LAYOUT_AB):
         import torch
         lib = _abi.load()
         self.lib = lib
         self.n = len(physics)
         self.precision = precision
-        made = [make_config(p, precision) for p in physics]
+        made = [make_config(p, precision, layout=layout) for p in physics]
         self._keep = made
         arr = (lbm_config * self.n)(*[m[0] for m in made])
         self._cfgs = arr

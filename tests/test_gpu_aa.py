@@ -178,5 +178,4 @@ def test_aa_order_refuses_what_needs_two_lattices():
     cfg, keep = G.make_config(phys[0], G.LBM_FP32, layout=G.LBM_LAYOUT_AA)
     import ctypes as C
     n = C.c_size_t()
-    assert G.load().lbm_batch_workspace_size(1, C.byref(cfg), C.byref(n)) == G._abi.LBM_EINVAL
     assert G.load().lbm_slab_workspace_size(C.byref(cfg), 0, 60, 8, C.byref(n)) == G._abi.LBM_EINVAL

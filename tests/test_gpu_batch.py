@@ -59,6 +59,32 @@ def test_batch_equals_each_lattice_stepped_alone(fp64):
         assert abs(Mb / M0b - 1) < (1e-12 if fp64 else 1e-6)
 
 
+@pytest.mark.parametrize("fp64", [False, True])
+def test_batch_in_aa_order_equals_the_two_lattice_batch(fp64):
+    """Instances that each keep one population lattice in AA order, advanced by the batched
+    kernel (in-place and pulled collides, shifted-order density, the boundary moments saved in
+    the second solid layer's phase): the two-lattice batch's values bit for bit, after odd and
+    even step counts, in less workspace."""
+    import paper_2203_04508_gb300 as G
+    scs = _mixed(fp64)
+    prec = G.LBM_FP64 if fp64 else G.LBM_FP32
+    a = G.Batch([sc.physics() for sc in scs], precision=prec)
+    c = G.Batch([sc.physics() for sc in scs], precision=prec, layout=G.LBM_LAYOUT_AA)
+    assert c.workspace.numel() < a.workspace.numel()
+    for b in (a, c):
+        b.init([sc.droplets() for sc in scs])
+    for n in (1, 4, 9):
+        a.step(n)
+        c.step(n)
+        a.check()
+        c.check()
+        for k, sc in enumerate(scs):
+            fa, fc = a.instances[k].populations(), c.instances[k].populations()
+            assert np.array_equal(fa, fc), (sc.name, n)
+            assert a.instances[k].mass() == c.instances[k].mass(), (sc.name, n)
+            assert np.array_equal(a.instances[k].dM_history(), c.instances[k].dM_history()), (sc.name, n)
+
+
 def test_fp64_batch_matches_the_oracle():
     scs = _mixed(True)
     b = _batch(scs, True)
