@@ -372,7 +372,8 @@ lbm_status lbm_adjoint(lbm_ctx* ctx, const void* dJ_drho, const void* dJ_df, int
                        void* dJ_df0);
 
 /* ---- Batches: many independent lattices advanced together -------------------------------
- * All instances share one precision; sizes, physics, geometry and initial states may differ.
+ * All instances share one precision and the chemical-potential force; sizes, physics, geometry,
+ * initial states and population layouts (lbm_config.layout) may differ.
  * Each instance is an ordinary lbm_ctx inside the batch (lbm_batch_instance), so lbm_fields,
  * lbm_mass, lbm_dM_history ... work on it; lbm_step on a single instance is not allowed while it
  * belongs to a batch (lbm_batch_step then returns LBM_ESTATE). */
