@@ -791,6 +791,24 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_rho_scatter(Lattice<real> L) {
   }
 }
 
+// A binary32 value as binary64, exactly: normal numbers and zeros by rebuilding the bit fields
+// (sign; exponent rebiased from 127 to 1023; the 23 fraction bits on top of the 52), on the
+// integer units -- GB300's FP64 units are few, and the audit's nine conversions a node would
+// compete with its nine additions for them; subnormal, infinite and NaN inputs by the conversion.
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(float v) {
+  const unsigned int u = __float_as_uint(v);
+  const unsigned int e = (u >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  if (e == 0u || e == 0xffu) {
+    if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)sign);
+    return (double)v;
+  }
+  const unsigned long long bits =
+      sign | ((unsigned long long)(e + (1023u - 127u)) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
 // FP64 mass audit: sum over fluid nodes of sum_i (f_i - w_i rho_ref), plus a count of
 // non-finite populations.  The host adds n_fluid * rho_ref.
 template <typename real>
@@ -798,6 +816,7 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_mass(Lattice<real> L, int cur) {
   __shared__ double red[32];
   __shared__ double red2[32];
   double s = 0.0, bad = 0.0;
+  int nbad = 0;
   const real* __restrict__ f = L.f[cur];
   const long long n_lo = (long long)L.own_lo * L.pitch, n_hi = (long long)L.own_hi * L.pitch;
   for (long long n = n_lo + (long long)blockIdx.x * blockDim.x + threadIdx.x; n < n_hi;
@@ -814,11 +833,12 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_mass(Lattice<real> L, int cur) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const real v = fl[i];
-      if (!isfinite(v)) bad += 1.0;
-      t += (double)v;
+      nbad += isfinite(v) ? 0 : 1;
+      t += to_f64(v);
     }
     s += t;
   }
+  bad = (double)nbad;
   double bs = block_sum(s, red);
   double bb = block_sum(bad, red2);
   __shared__ bool last;

@@ -269,3 +269,22 @@ def test_fp64_degenerate_geometry():
     orc.step(50)
     er, ev, ef = compare(lat, orc)
     assert ef < 1e-10 and er < 1e-10, (er, ev, ef)
+
+
+@pytest.mark.parametrize("fp64,layout", [(False, 0), (True, 0), (False, 1)])
+def test_mass_audit_equals_the_sum_of_the_populations(fp64, layout):
+    """lbm_mass's M (the FP64 audit, which converts FP32 populations to FP64 by their bit fields)
+    against the sum of the read-out populations over the fluid nodes, formed in FP64 on the host,
+    for the initial state and after some steps."""
+    import paper_2203_04508_gb300 as G
+    sc = S.small_parity()
+    lat = G.Lattice(sc.physics(), precision=G.LBM_FP64 if fp64 else G.LBM_FP32, layout=layout)
+    lat.init_droplets(sc.droplets())
+    fluid = lat.kind() == 0
+    for n in (0, 9):
+        lat.step(n)
+        M, M0, _ = lat.mass()
+        f = lat.populations().astype(np.float64)
+        ref = float(f[:, fluid].sum())
+        # the read-out adds w_i rho_ref to the stored offset values in the storage precision
+        assert abs(M - ref) <= (1e-12 if fp64 else 2e-7) * ref, (n, M, ref)
