@@ -8,6 +8,8 @@
 //   q = (-B - sqrt(B^2 - 4 A C)) / (2 A)      (smaller root of |x1 + q e_i - c|^2 = r^2)
 // and q = y1 - y_bottom or y_top - y1 for the flat walls.  A node is solid when
 // dx^2 + dy^2 <= r^2 (nodes on the circle are solid) or y <= y_bottom or y >= y_top.
+#include <climits>
+
 #include "lbm_internal.h"
 
 namespace lbmgb {
@@ -63,25 +65,76 @@ __device__ __forceinline__ double q_body(const GeomParams& g, int b, int x, int 
   return g.y_top - (double)y;
 }
 
-__global__ void k_classify(GeomParams g, uint8_t* kind, int* body) {
-  long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= g.plane) return;
-  int x = (int)(n % g.pitch), y = (int)(n / g.pitch);
+// An FP32 screen of the disc test of inside_body, exact where it decides.  For node
+// coordinates, centres and radii below 2^13 the FP32 d^2 lies within 134 of the exact one (the
+// centre and the difference rounded once each, 2^-10 in all; the two squares and their sum),
+// and the FP64 d^2 and r^2 within 1e-6 of theirs; so d2f > r^2 + 256 and d2f < r^2 - 256, with
+// both bounds rounded to FP32 (within 4), give the FP64 test's answer.  Nodes in the ring
+// between the bounds, and centres or radii out of range (bounds -inf, +inf), take the FP64
+// test.  GB300's FP64 rate makes the plain test the cost of the classification.
+constexpr int SCREEN_MAX = 32;
+constexpr int SCREEN_COORD = 8192;
+
+__device__ __forceinline__ float4 disc_screen(const double* c) {
+  const bool ok = fabs(c[0]) < (double)SCREEN_COORD && fabs(c[1]) < (double)SCREEN_COORD && c[2] >= 0.0 &&
+                  c[2] < (double)SCREEN_COORD;
+  if (!ok) return make_float4(0.f, 0.f, __int_as_float((int)0xff800000), __int_as_float(0x7f800000));
+  const double r2 = c[2] * c[2];
+  return make_float4((float)c[0], (float)c[1], (float)(r2 - 256.0), (float)(r2 + 256.0));
+}
+
+// 1 inside, 0 outside, -1 undecided
+__device__ __forceinline__ int screen_disc(float4 s, int x, int gy) {
+  const float dx = (float)x - s.x, dy = (float)gy - s.y;
+  const float d2 = dx * dx + dy * dy;
+  return d2 > s.w ? 0 : (d2 < s.z ? 1 : -1);
+}
+
+// The flat walls' tests (double)y <= y_bottom and (double)y >= y_top for integer rows y in
+// [0, 2^30): y <= floor(y_bottom) and y >= ceil(y_top), with NaN bounds never met.
+__device__ __forceinline__ int wall_lo_row(double yb) {
+  if (!(yb >= -1073741824.0)) return INT_MIN / 2;
+  return yb >= 1073741824.0 ? 1073741824 : (int)floor(yb);
+}
+__device__ __forceinline__ int wall_hi_row(double yt) {
+  if (!(yt <= 1073741824.0)) return INT_MAX / 2;
+  return yt <= -1073741824.0 ? -1073741824 : (int)ceil(yt);
+}
+
+// grid (ceil(pitch / 256), rows), 256 threads: one node each
+__global__ void __launch_bounds__(256) k_classify(GeomParams g, uint8_t* kind, int* body) {
+  __shared__ float4 scr[SCREEN_MAX];
+  __shared__ int wl, wh;
+  const int ns = g.n_cyl < SCREEN_MAX ? g.n_cyl : SCREEN_MAX;
+  if ((int)threadIdx.x < ns) scr[threadIdx.x] = disc_screen(g.cyl + 4 * threadIdx.x);
+  if (threadIdx.x == 0) { wl = wall_lo_row(g.y_bottom); wh = wall_hi_row(g.y_top); }
+  __syncthreads();
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= g.pitch) return;
+  const long long n = (long long)y * g.pitch + x;
   if (x >= g.nx) { kind[n] = KIND_PAD; body[n] = -1; return; }
-  int nb = g.n_cyl + (g.walls ? 2 : 0);
+  const int gy = grow(g, y);
+  const bool fast = x < SCREEN_COORD && gy >= 0 && gy < SCREEN_COORD;
   int bd = -1;
-  for (int b = 0; b < nb; ++b)
-    if (inside_body(g, b, x, y)) { bd = b; break; }
+  for (int b = 0; b < g.n_cyl; ++b) {
+    int in = fast && b < SCREEN_MAX ? screen_disc(scr[b], x, gy) : -1;
+    if (in < 0) in = inside_body(g, b, x, y) ? 1 : 0;
+    if (in) { bd = b; break; }
+  }
+  if (bd < 0 && g.walls) {
+    if (y <= wl) bd = g.n_cyl;
+    else if (y >= wh) bd = g.n_cyl + 1;
+  }
   body[n] = bd;
   kind[n] = bd >= 0 ? KIND_DEEP : KIND_FLUID;
 }
 
 // solid nodes with a neighbour of class `from` (and currently DEEP) become class `to`
-__global__ void k_layer(GeomParams g, uint8_t* kind, uint8_t from, uint8_t to) {
-  long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= g.plane) return;
+__global__ void __launch_bounds__(256) k_layer(GeomParams g, uint8_t* kind, uint8_t from, uint8_t to) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= g.pitch) return;
+  const long long n = (long long)y * g.pitch + x;
   if (kind[n] != KIND_DEEP) return;
-  int x = (int)(n % g.pitch), y = (int)(n / g.pitch);
   for (int i = 1; i < 9; ++i) {
     int m;
     if (gnb(g, x, y, i, &m) && kind[m] == from) { kind[n] = to; return; }
@@ -93,13 +146,21 @@ __global__ void k_layer(GeomParams g, uint8_t* kind, uint8_t from, uint8_t to) {
 // list are scanned in shared memory; one scan over the blocks' totals gives each block's offsets.
 enum { LANE_LINKS = 0, LANE_BNODE, LANE_S1, LANE_S2, LANE_FLUID, N_LANES };
 
-// counts of node n in the five lanes: its cut links (a fluid node with a non-fluid neighbour),
-// the boundary-node, layer flags and the fluid flag
-__device__ __forceinline__ void node_counts(const GeomParams& g, const uint8_t* kind, long long n, int (&c)[N_LANES]) {
-#pragma unroll
-  for (int l = 0; l < N_LANES; ++l) c[l] = 0;
-  if (n >= g.plane) return;
-  const int x = (int)(n % g.pitch), y = (int)(n / g.pitch);
+// Bit offsets of the five lanes in one packed 64-bit count: a block of SCAN_BLOCK nodes holds
+// at most 8 x 1024 cut links (14 bits) and 1024 of each other lane (in fields of 12 bits), so a block scan of
+// the packed counts never carries from one field into the next.
+// (bits 0, 14, 26, 38, 50; 14 bits for the links, 12 for the others)
+__host__ __device__ constexpr int lane_shift(int l) { return l == 0 ? 0 : 2 + 12 * l; }
+
+__device__ __forceinline__ int lane_of_packed(unsigned long long v, int l) {
+  return (int)((v >> lane_shift(l)) & (l == 0 ? 0x3fffull : 0xfffull));
+}
+
+// packed counts of node (x, y), n = y * pitch + x < plane: its cut links (a fluid node with a
+// non-fluid neighbour), the boundary-node, layer flags and the fluid flag
+__device__ __forceinline__ unsigned long long node_counts(const GeomParams& g, const uint8_t* kind, long long n, int x,
+                                                          int y) {
+  if (n >= g.plane) return 0ull;
   const uint8_t k = kind[n];
   if (k == KIND_FLUID) {
     int links = 0;
@@ -107,17 +168,32 @@ __device__ __forceinline__ void node_counts(const GeomParams& g, const uint8_t* 
       int m;
       if (gnb(g, x, y, i, &m) && kind[m] != KIND_FLUID) ++links;
     }
-    c[LANE_LINKS] = links;
-    c[LANE_BNODE] = links > 0;
-    c[LANE_FLUID] = 1;
-  } else if (k == KIND_SOLID1) {
-    c[LANE_S1] = 1;
-  } else if (k == KIND_SOLID2) {
-    c[LANE_S2] = 1;
+    return ((unsigned long long)links << lane_shift(LANE_LINKS)) |
+           ((unsigned long long)(links > 0) << lane_shift(LANE_BNODE)) | (1ull << lane_shift(LANE_FLUID));
   }
+  if (k == KIND_SOLID1) return 1ull << lane_shift(LANE_S1);
+  if (k == KIND_SOLID2) return 1ull << lane_shift(LANE_S2);
+  return 0ull;
 }
 
-// ---- block scans of int32 counts
+// node index and coordinates of thread threadIdx.x of a block of SCAN_BLOCK consecutive nodes:
+// the block's first node divided by the pitch once, by thread 0
+__device__ __forceinline__ long long block_node(const GeomParams& g, int* x, int* y) {
+  __shared__ int b0[2];
+  const long long base = (long long)blockIdx.x * SCAN_BLOCK;
+  if (threadIdx.x == 0) {
+    const long long r = base / g.pitch;
+    b0[0] = (int)r;
+    b0[1] = (int)(base - r * g.pitch);
+  }
+  __syncthreads();
+  const unsigned t = (unsigned)b0[1] + threadIdx.x;
+  *y = b0[0] + (int)(t / (unsigned)g.pitch);
+  *x = (int)(t % (unsigned)g.pitch);
+  return base + threadIdx.x;
+}
+
+// ---- block scans of int32 and packed 64-bit counts
 __device__ __forceinline__ int warp_incl_scan(int v) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -128,20 +204,31 @@ __device__ __forceinline__ int warp_incl_scan(int v) {
   return v;
 }
 
-__device__ int block_excl_scan(int v, int* total) {
-  __shared__ int ws[32];
+__device__ __forceinline__ unsigned long long warp_incl_scan(unsigned long long v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+template <typename T>
+__device__ T block_excl_scan(T v, T* total) {
+  __shared__ T ws[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int inc = warp_incl_scan(v);
+  T inc = warp_incl_scan(v);
   if (lane == 31) ws[warp] = inc;
   __syncthreads();
   if (warp == 0) {
     int nw = blockDim.x >> 5;
-    int s = lane < nw ? ws[lane] : 0;
+    T s = lane < nw ? ws[lane] : T(0);
     s = warp_incl_scan(s);
     ws[lane] = s;
   }
   __syncthreads();
-  int base = warp > 0 ? ws[warp - 1] : 0;
+  T base = warp > 0 ? ws[warp - 1] : T(0);
   *total = ws[(blockDim.x >> 5) - 1];
   __syncthreads();
   return base + inc - v;
@@ -149,14 +236,11 @@ __device__ int block_excl_scan(int v, int* total) {
 
 // per block and lane the block's total, at sums[lane * nb + block]
 __global__ void __launch_bounds__(SCAN_BLOCK) k_count_blocks(GeomParams g, const uint8_t* kind, int* sums, int nb) {
-  int c[N_LANES];
-  node_counts(g, kind, (long long)blockIdx.x * blockDim.x + threadIdx.x, c);
-#pragma unroll
-  for (int l = 0; l < N_LANES; ++l) {
-    int t;
-    (void)block_excl_scan(c[l], &t);
-    if (threadIdx.x == 0) sums[l * nb + blockIdx.x] = t;
-  }
+  int x, y;
+  const long long n = block_node(g, &x, &y);
+  unsigned long long t;
+  (void)block_excl_scan(node_counts(g, kind, n, x, y), &t);
+  if (threadIdx.x < N_LANES) sums[threadIdx.x * nb + blockIdx.x] = lane_of_packed(t, threadIdx.x);
 }
 
 // one block per lane: exclusive scan of the lane's nb block totals in place, the lane's grand
@@ -176,10 +260,10 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_scan_lanes(int* sums, int nb, in
 }
 
 cudaError_t geom_classify_and_count(const GeomParams& g, const GeomScratch& s, uint8_t* kind, cudaStream_t st) {
-  const unsigned gn = (unsigned)((g.plane + 255) / 256);
-  k_classify<<<gn, 256, 0, st>>>(g, kind, s.body);
-  k_layer<<<gn, 256, 0, st>>>(g, kind, KIND_FLUID, KIND_SOLID1);
-  k_layer<<<gn, 256, 0, st>>>(g, kind, KIND_SOLID1, KIND_SOLID2);
+  const dim3 grid((unsigned)((g.pitch + 255) / 256), (unsigned)(g.plane / g.pitch));
+  k_classify<<<grid, 256, 0, st>>>(g, kind, s.body);
+  k_layer<<<grid, 256, 0, st>>>(g, kind, KIND_FLUID, KIND_SOLID1);
+  k_layer<<<grid, 256, 0, st>>>(g, kind, KIND_SOLID1, KIND_SOLID2);
   // totals: 0 links, 1 bnodes, 2 s1, 3 s2, 4 fluid
   const int nb = (int)((g.plane + SCAN_BLOCK - 1) / SCAN_BLOCK);
   k_count_blocks<<<nb, SCAN_BLOCK, 0, st>>>(g, kind, s.block_sums, nb);
@@ -193,21 +277,21 @@ cudaError_t geom_classify_and_count(const GeomParams& g, const GeomScratch& s, u
 // scanned totals k_scan_lanes left.
 __global__ void __launch_bounds__(SCAN_BLOCK) k_fill_nodes(GeomParams g, const uint8_t* kind, const int* offs, int nb,
                                                            GeomOut o, int* bidx) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  int c[N_LANES], e[N_LANES];
-  node_counts(g, kind, n, c);
+  int x, y;
+  const long long n = block_node(g, &x, &y);
+  const unsigned long long c = node_counts(g, kind, n, x, y);
+  unsigned long long t;
+  const unsigned long long ex = block_excl_scan(c, &t);
+  int e[LANE_FLUID];
 #pragma unroll
-  for (int l = 0; l < LANE_FLUID; ++l) {
-    int t;
-    e[l] = block_excl_scan(c[l], &t) + offs[l * nb + blockIdx.x];
-  }
-  if (c[LANE_BNODE]) {
+  for (int l = 0; l < LANE_FLUID; ++l) e[l] = lane_of_packed(ex, l) + offs[l * nb + blockIdx.x];
+  if (lane_of_packed(c, LANE_BNODE)) {
     o.bnode[e[LANE_BNODE]] = (int)n;
     o.bstart[e[LANE_BNODE]] = e[LANE_LINKS];
     bidx[n] = e[LANE_BNODE];
   }
-  if (c[LANE_S1]) o.s1node[e[LANE_S1]] = (int)n;
-  if (c[LANE_S2]) o.s2node[e[LANE_S2]] = (int)n;
+  if (lane_of_packed(c, LANE_S1)) o.s1node[e[LANE_S1]] = (int)n;
+  if (lane_of_packed(c, LANE_S2)) o.s2node[e[LANE_S2]] = (int)n;
 }
 
 // The links of boundary node b, from its first link on, sorted by direction: direction, q (the
@@ -275,12 +359,12 @@ __global__ void k_wall_mu(GeomParams g, const uint8_t* kind, const int* body, re
   long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.plane) return;
   uint8_t k = kind[n];
-  double v = 0.0;
+  real v = real(0);
   if (k == KIND_SOLID1 || k == KIND_SOLID2) {
     int b = body[n];
-    v = b < g.n_cyl ? g.cyl[4 * b + 3] : g.dmu_walls;
+    v = (real)(b < g.n_cyl ? g.cyl[4 * b + 3] : g.dmu_walls);
   }
-  mu[n] = (real)v;
+  mu[n] = v;
 }
 
 template <typename real>

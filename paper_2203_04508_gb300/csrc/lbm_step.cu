@@ -809,6 +809,30 @@ __device__ __forceinline__ double to_f64(float v) {
   return __longlong_as_double((long long)bits);
 }
 
+// The sum of a node's nine populations.  FP64: in FP64.  FP32: Knuth's TwoSum carries the
+// rounding error of each FP32 addition exactly, and the errors are summed in FP32; the node's sum
+// is the FP32 sum plus that error term, both widened to FP64 (the compensated summation of
+// Ogita, Rump and Oishi, 2005: within gamma_8^2 sum_i |f_i| ~ (8 u)^2 sum_i |f_i| of the exact
+// sum, u = 2^-24, i.e. 2.3e-13 of sum_i |f_i|, against the FP32 state's own 6e-8).  It takes two FP64 additions a node where the
+// plain FP64 sum takes nine; GB300's FP64 rate made those the audit's cost.
+__device__ __forceinline__ double node_sum(const double (&fl)[9]) {
+  double t = 0.0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) t += fl[i];
+  return t;
+}
+__device__ __forceinline__ double node_sum(const float (&fl)[9]) {
+  float p = fl[0], e = 0.f;
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    const float a = p, b = fl[i];
+    p = __fadd_rn(a, b);
+    const float bb = __fsub_rn(p, a);
+    e = __fadd_rn(e, __fadd_rn(__fsub_rn(a, __fsub_rn(p, bb)), __fsub_rn(b, bb)));
+  }
+  return to_f64(p) + to_f64(e);
+}
+
 // FP64 mass audit: sum over fluid nodes of sum_i (f_i - w_i rho_ref), plus a count of
 // non-finite populations.  The host adds n_fluid * rho_ref.
 template <typename real>
@@ -829,14 +853,9 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_mass(Lattice<real> L, int cur) {
 #pragma unroll
       for (int i = 0; i < 9; ++i) fl[i] = f[i * L.plane + n];
     }
-    double t = 0.0;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const real v = fl[i];
-      nbad += isfinite(v) ? 0 : 1;
-      t += to_f64(v);
-    }
-    s += t;
+    for (int i = 0; i < 9; ++i) nbad += isfinite(fl[i]) ? 0 : 1;
+    s += node_sum(fl);
   }
   bad = (double)nbad;
   double bs = block_sum(s, red);
@@ -994,18 +1013,36 @@ __device__ __forceinline__ double init_rho(double phi, double rho_g, double rho_
 // A droplet contributes phi = 0 where 2(r - r0)/W >= 40, i.e. r >= r0 + 20 W: there tanh is 1 to
 // far below the last bit of a double, so the node skips the square root and tanh.  Nodes that no
 // droplet reaches (phi = 0, u = 0: the gas) all get the same populations, formed once per block.
+// An FP32 screen of the far test below, exact where it decides: for node coordinates, drop
+// centres and far radii below 2^13 the FP32 d^2 lies within 134 of the exact one (the centre and
+// the difference rounded once each, 2^-10 in all; the two squares and their sum), so a node with
+// d2f > far^2 (1 + 1e-9) + 256 (that bound rounded to FP32, within 4) is far in the FP64 test
+// too.  The rest, and drops out of range (bound +inf), take the FP64 test.
+constexpr int INIT_SCREEN_MAX = 32;
+constexpr int INIT_SCREEN_COORD = 8192;
+
+// grid (ceil(pitch / NODE_BLOCK), rows): one node a thread
 template <typename real>
-__global__ void k_init(Lattice<real> L, const double* __restrict__ drops, int n_drop, double W,
-                       double rho_g, double rho_l) {
+__global__ void __launch_bounds__(NODE_BLOCK) k_init(Lattice<real> L, const double* __restrict__ drops, int n_drop,
+                                                     double W, double rho_g, double rho_l) {
   __shared__ real gas[9];
   __shared__ real gas_rho;
+  __shared__ float3 scr[INIT_SCREEN_MAX];
   const double rref = (double)L.rho_ref;
   if (threadIdx.x < 9) gas[threadIdx.x] = init_pop<real>(threadIdx.x, init_rho(0.0, rho_g, rho_l), 0.0, 0.0, rref);
   if (threadIdx.x == 0) gas_rho = (real)init_rho(0.0, rho_g, rho_l);
+  if ((int)threadIdx.x < n_drop && threadIdx.x < INIT_SCREEN_MAX) {
+    const double* p = drops + 5 * threadIdx.x;
+    const double far = p[2] + 20.0 * W;
+    const double lim = (double)INIT_SCREEN_COORD;
+    const bool ok = fabs(p[0]) < lim && fabs(p[1]) < lim && far > 0.0 && far < lim;
+    scr[threadIdx.x] = ok ? make_float3((float)p[0], (float)p[1], (float)(far * far * (1.0 + 1e-9) + 256.0))
+                          : make_float3(0.f, 0.f, __int_as_float(0x7f800000));
+  }
   __syncthreads();
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= L.plane) return;
-  const int x = (int)(n % L.pitch), y = (int)(n / L.pitch);
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= L.pitch) return;
+  const long long n = (long long)y * L.pitch + x;
   real* f0 = L.f[0];
   real* f1 = L.f[1];
   if (x >= L.nx || L.kind[n] != KIND_FLUID) {
@@ -1016,10 +1053,17 @@ __global__ void k_init(Lattice<real> L, const double* __restrict__ drops, int n_
     }
     return;
   }
+  const int gy = global_row(L, y);
+  const bool fast = x < INIT_SCREEN_COORD && gy >= 0 && gy < INIT_SCREEN_COORD;
   double phi = 0.0, u0 = 0.0, v0 = 0.0;
   for (int d = 0; d < n_drop; ++d) {
+    if (fast && d < INIT_SCREEN_MAX) {
+      const float3 sc = scr[d];
+      const float dxf = __fsub_rn((float)x, sc.x), dyf = __fsub_rn((float)gy, sc.y);
+      if (__fadd_rn(__fmul_rn(dxf, dxf), __fmul_rn(dyf, dyf)) > sc.z) continue;
+    }
     const double* p = drops + 5 * d;
-    double dx = x - p[0], dy = global_row(L, y) - p[1];
+    double dx = x - p[0], dy = gy - p[1];
     const double d2 = dx * dx + dy * dy;
     const double far = p[2] + 20.0 * W;
     if (far > 0.0 && d2 >= far * far * (1.0 + 1e-9)) continue;
@@ -1500,7 +1544,8 @@ cudaError_t launch_mass(const Lattice<real>& L, int cur, cudaStream_t s) {
 template <typename real>
 cudaError_t launch_init(const Lattice<real>& L, const double* drops, int n_drop, double W, double rho_g,
                         double rho_l, cudaStream_t s) {
-  k_init<real><<<grid_for(L.plane, NODE_BLOCK), NODE_BLOCK, 0, s>>>(L, drops, n_drop, W, rho_g, rho_l);
+  const dim3 grid((unsigned)((L.pitch + NODE_BLOCK - 1) / NODE_BLOCK), (unsigned)(L.plane / L.pitch));
+  k_init<real><<<grid, NODE_BLOCK, 0, s>>>(L, drops, n_drop, W, rho_g, rho_l);
   return cudaGetLastError();
 }
 
