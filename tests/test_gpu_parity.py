@@ -18,7 +18,7 @@ import pytest
 
 import oracle as O
 import scenarios as S
-from harness import compare, make_lattice, make_oracle, rho_err, vel_err
+from harness import compare, make_lattice, make_oracle, pop_err, rho_err, vel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -50,6 +50,11 @@ GEOMETRIES = {
     # (solid) and links are cut at exactly q = 1; flat walls at q = 1 (y_b = 1) and q = 1/2
     "node_centred": lambda: S.Scenario(name="n", nx=64, ny=64, walls=1, y_bottom=1.0, cx=[32.0], cy=[32.0],
                                        r=[10.0], dmu_w=[0.0], x0=[32.0], y0=[47.0], r0=[6.0]),
+    # nodes and centres on both sides of x = 8192, where the FP32 pre-screens of the disc and
+    # droplet tests give way to the FP64 tests; one cylinder straddles the line, one lies beyond it
+    "beyond_screen": lambda: S.Scenario(name="w", nx=8250, ny=32, walls=1, cx=[8190.37, 8232.81],
+                                        cy=[12.2, 15.6], r=[6.3, 5.1], dmu_w=[0.02, -0.02],
+                                        x0=[8170.4, 8208.9], y0=[20.3, 24.1], r0=[5.0, 3.5]),
 }
 
 
@@ -69,6 +74,19 @@ def test_links_and_classes_bit_exact(name):
     c = lat.counts()
     assert c["fluid"] == int((ko == 0).sum())
     assert c["solid1"] == int((ko == 1).sum()) and c["solid2"] == int((ko == 2).sum())
+
+
+@pytest.mark.parametrize("name", [k for k in GEOMETRIES if GEOMETRIES[k]().r0])
+def test_initial_state_matches_the_oracle(name):
+    """The initial populations (Sec. 4: tanh profiles, the gas state where no droplet reaches,
+    FP64) against the oracle's, and the FP32 ones within their rounding."""
+    sc = GEOMETRIES[name]()
+    orc = make_oracle(sc)
+    fo = orc.populations()
+    m = orc.kind()[0] == 0
+    for fp64, bar in ((True, 1e-14), (False, 2e-7)):
+        lat = make_lattice(sc, fp64=fp64)
+        assert pop_err(lat.populations(), fo, m) <= bar, (fp64, pop_err(lat.populations(), fo, m))
 
 
 @pytest.mark.parametrize("coll", [S.COLL_MRT, S.COLL_BGK])
