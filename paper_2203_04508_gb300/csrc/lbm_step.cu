@@ -146,14 +146,21 @@ __global__ void __launch_bounds__(MU_BLOCK) k_mu_sweep(Lattice<float> L) {
   // lanes whose centre-row neighbours the next lanes hold
   const bool left_ok = lane > 0 && full;
   const bool right_ok = lane < 31 && x0 + 6 <= L.nx;
+  // the node classes and psi' of the current row, requested a row ahead like the densities
+  uchar4 kind_c = make_uchar4(KIND_PAD, KIND_PAD, KIND_PAD, KIND_PAD);
+  float4 pp_c = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (live && ya < yb) {
+    kind_c = __ldg(reinterpret_cast<const uchar4*>(L.kind + ya * L.pitch + x0));
+    pp_c = __ldg(reinterpret_cast<const float4*>(L.psip + ya * L.pitch + x0));
+  }
   for (int y = ya; y < yb; ++y) {
     const float4 ahead = y + 1 < yb ? row(y + 3) : w4;
     const int n0 = y * L.pitch + x0;
-    uchar4 kind = make_uchar4(KIND_PAD, KIND_PAD, KIND_PAD, KIND_PAD);
-    float4 pp = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (live) {
-      kind = __ldg(reinterpret_cast<const uchar4*>(L.kind + n0));
-      pp = __ldg(reinterpret_cast<const float4*>(L.psip + n0));
+    const uchar4 kind = kind_c;
+    const float4 pp = pp_c;
+    if (live && y + 1 < yb) {
+      kind_c = __ldg(reinterpret_cast<const uchar4*>(L.kind + n0 + L.pitch));
+      pp_c = __ldg(reinterpret_cast<const float4*>(L.psip + n0 + L.pitch));
     }
     const float lz = __shfl_up_sync(0xffffffffu, w2.z, 1), lw = __shfl_up_sync(0xffffffffu, w2.w, 1);
     const float rx = __shfl_down_sync(0xffffffffu, w2.x, 1), ry = __shfl_down_sync(0xffffffffu, w2.y, 1);
@@ -175,12 +182,18 @@ __global__ void __launch_bounds__(MU_BLOCK) k_mu_sweep(Lattice<float> L) {
       const float up1[4] = {w3.x, w3.y, w3.z, w3.w}, dn1[4] = {w1.x, w1.y, w1.z, w1.w};
       const float up2[4] = {w4.x, w4.y, w4.z, w4.w}, dn2[4] = {w0.x, w0.y, w0.z, w0.w};
       const float ps[4] = {pp.x, pp.y, pp.z, pp.w};
+      float m[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        if (!fl[k]) continue;
         const int i = k + 2;
-        const float lap = lap4_of(c[i], c[i + 1], c[i - 1], c[i + 2], c[i - 2], up1[k], dn1[k], up2[k], dn2[k]);
-        L.mu[n0 + k] = mu_of(L, ps[k], lap);
+        m[k] = mu_of(L, ps[k], lap4_of(c[i], c[i + 1], c[i - 1], c[i + 2], c[i - 2], up1[k], dn1[k], up2[k], dn2[k]));
+      }
+      if (fl[0] && fl[1] && fl[2] && fl[3]) {
+        *reinterpret_cast<float4*>(L.mu + n0) = make_float4(m[0], m[1], m[2], m[3]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (fl[k]) L.mu[n0 + k] = m[k];
       }
     }
     w0 = w1; w1 = w2; w2 = w3; w3 = w4; w4 = ahead;
