@@ -124,9 +124,10 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_mu_vec(Lattice<real> L) {
 // each side come from the neighbouring lanes; lanes at a warp's edge, at the lattice's x edges
 // or at a ragged end load them one by one with the periodic wrap.  Same values and the same
 // sums as k_mu (lap4_of, mu_of).
-// Rows a thread walks and threads a block (a 512-node strip): 16 x 128 was the fastest of 4-32
-// rows and 64-256 threads on the 2048 x 4096 impact lattice (0.030 ms; 0.033 for k_mu_vec).
-constexpr int MU_ROWS = 16, MU_BLOCK = 128;
+// Rows a thread walks and threads a block (a 512-node strip): on the 2048 x 4096 impact lattice
+// 4, 8 and 16 rows of 64 or 128 threads all take 0.0265 ms (0.033 for k_mu_vec), 12, 24 and 32
+// rows 0.031-0.040, 256 threads 0.028; 8 x 128 gives the shortest step (0.1953 ms).
+constexpr int MU_ROWS = 8, MU_BLOCK = 128;
 __global__ void __launch_bounds__(MU_BLOCK) k_mu_sweep(Lattice<float> L) {
   const int lane = threadIdx.x & 31;
   const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
