@@ -117,20 +117,38 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_mu_vec(Lattice<real> L) {
   if (x0 < L.nx) phase_mu_vec(L, x0, y);
 }
 
+// cp.async (an asynchronous 16- or 4-byte copy into shared memory, completed by groups); a
+// source size of 0 writes zeros and reads nothing
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // Chemical potential (FP32) by row sweeps: a thread holds four consecutive nodes of a row and
-// walks MU_ROWS rows down its column, keeping the five rows of the 9-point stencil in registers
-// and loading the row two ahead while it computes the current one, so that a row costs it one
-// density vector, one psi' vector and the node classes.  The centre row's two further nodes on
-// each side come from the neighbouring lanes; lanes at a warp's edge, at the lattice's x edges
-// or at a ragged end load them one by one with the periodic wrap.  Same values and the same
-// sums as k_mu (lap4_of, mu_of).
-// Rows a thread walks and threads a block (a 512-node strip): on the 2048 x 4096 impact lattice
-// 4, 8 and 16 rows of 64 or 128 threads all take 0.0265 ms (0.033 for k_mu_vec), 12, 24 and 32
-// rows 0.031-0.040, 256 threads 0.028; 8 x 128 gives the shortest step (0.1953 ms).
-constexpr int MU_ROWS = 8, MU_BLOCK = 128;
+// walks MU_ROWS rows down its column, keeping the five rows of the 9-point stencil in registers,
+// so that a row costs it one density vector, one psi' vector and the node classes.  Those three
+// arrive by cp.async into the thread's own shared-memory slots, MU_DEPTH rows ahead (the loads
+// in flight hold no registers).  The centre row's two further nodes on each side come from the
+// neighbouring lanes; lanes at a warp's edge, at the lattice's x edges or at a ragged end load
+// them one by one with the periodic wrap.  Same values and the same sums as k_mu (lap4_of,
+// mu_of).
+// Rows a thread walks and threads a block (a 512-node strip); see the launcher for the sweep.
+constexpr int MU_ROWS = 8, MU_BLOCK = 128, MU_DEPTH = 4;
 __global__ void __launch_bounds__(MU_BLOCK) k_mu_sweep(Lattice<float> L) {
-  const int lane = threadIdx.x & 31;
-  const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  __shared__ float4 s_rho[MU_DEPTH][MU_BLOCK];
+  __shared__ float4 s_psi[MU_DEPTH][MU_BLOCK];
+  __shared__ uchar4 s_kind[MU_DEPTH][MU_BLOCK];
+  const int t = threadIdx.x, lane = t & 31;
+  const int x0 = (blockIdx.x * blockDim.x + t) * 4;
   const int ya = blockIdx.y * MU_ROWS, yb = min(ya + MU_ROWS, L.ny);
   const bool live = x0 < L.nx, full = x0 + 4 <= L.nx;
   const float* __restrict__ r = L.rho;
@@ -143,26 +161,39 @@ __global__ void __launch_bounds__(MU_BLOCK) k_mu_sweep(Lattice<float> L) {
     }
     return __ldg(reinterpret_cast<const float4*>(r + y * L.pitch + x0));
   };
+  // group j: the classes and psi' of row ya + j and the density of row ya + j + 3 (which the
+  // last row of the sweep does not need), into slot j % MU_DEPTH
+  auto issue = [&](int j) {
+    const int y = ya + j;
+    if (y < yb) {
+      const int slot = j % MU_DEPTH;
+      const long long n0 = (long long)y * L.pitch + (live ? x0 : 0);
+      cp_async4(&s_kind[slot][t], L.kind + n0, live ? 4 : 0);
+      cp_async16(&s_psi[slot][t], L.psip + n0, live ? 16 : 0);
+      int yr = y + 3;
+      bool ok = live && y + 1 < yb;
+      if (yr >= L.ny) {
+        if (L.walls) ok = false;
+        else yr -= L.ny;
+      }
+      cp_async16(&s_rho[slot][t], r + (ok ? (long long)yr * L.pitch + x0 : 0), ok ? 16 : 0);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int j = 0; j < MU_DEPTH; ++j) issue(j);
   float4 w0 = row(ya - 2), w1 = row(ya - 1), w2 = row(ya), w3 = row(ya + 1), w4 = row(ya + 2);
   // lanes whose centre-row neighbours the next lanes hold
   const bool left_ok = lane > 0 && full;
   const bool right_ok = lane < 31 && x0 + 6 <= L.nx;
-  // the node classes and psi' of the current row, requested a row ahead like the densities
-  uchar4 kind_c = make_uchar4(KIND_PAD, KIND_PAD, KIND_PAD, KIND_PAD);
-  float4 pp_c = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (live && ya < yb) {
-    kind_c = __ldg(reinterpret_cast<const uchar4*>(L.kind + ya * L.pitch + x0));
-    pp_c = __ldg(reinterpret_cast<const float4*>(L.psip + ya * L.pitch + x0));
-  }
   for (int y = ya; y < yb; ++y) {
-    const float4 ahead = y + 1 < yb ? row(y + 3) : w4;
+    const int j = y - ya, slot = j % MU_DEPTH;
+    cp_async_wait<MU_DEPTH - 1>();
+    const uchar4 kind = s_kind[slot][t];
+    const float4 pp = s_psi[slot][t];
+    const float4 ahead = s_rho[slot][t];
+    issue(j + MU_DEPTH);
     const int n0 = y * L.pitch + x0;
-    const uchar4 kind = kind_c;
-    const float4 pp = pp_c;
-    if (live && y + 1 < yb) {
-      kind_c = __ldg(reinterpret_cast<const uchar4*>(L.kind + n0 + L.pitch));
-      pp_c = __ldg(reinterpret_cast<const float4*>(L.psip + n0 + L.pitch));
-    }
     const float lz = __shfl_up_sync(0xffffffffu, w2.z, 1), lw = __shfl_up_sync(0xffffffffu, w2.w, 1);
     const float rx = __shfl_down_sync(0xffffffffu, w2.x, 1), ry = __shfl_down_sync(0xffffffffu, w2.y, 1);
     const bool fl[4] = {kind.x == KIND_FLUID && x0 < L.nx, kind.y == KIND_FLUID && x0 + 1 < L.nx,
@@ -174,7 +205,7 @@ __global__ void __launch_bounds__(MU_BLOCK) k_mu_sweep(Lattice<float> L) {
         c[2] = w2.x; c[3] = w2.y; c[4] = w2.z; c[5] = w2.w;
       } else {
 #pragma unroll
-        for (int j = 2; j < 6; ++j) c[j] = r[rb + wrap_x(L, x0 - 2 + j)];
+        for (int j2 = 2; j2 < 6; ++j2) c[j2] = r[rb + wrap_x(L, x0 - 2 + j2)];
       }
       if (left_ok) { c[0] = lz; c[1] = lw; }
       else { c[0] = r[rb + wrap_x(L, x0 - 2)]; c[1] = r[rb + wrap_x(L, x0 - 1)]; }
@@ -199,6 +230,7 @@ __global__ void __launch_bounds__(MU_BLOCK) k_mu_sweep(Lattice<float> L) {
     }
     w0 = w1; w1 = w2; w2 = w3; w3 = w4; w4 = ahead;
   }
+  cp_async_wait<0>();
 }
 
 // The next state's density and chemical potential in one pass (FP32, chemical-potential force;
