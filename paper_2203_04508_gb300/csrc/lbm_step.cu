@@ -141,8 +141,11 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // neighbouring lanes; lanes at a warp's edge, at the lattice's x edges or at a ragged end load
 // them one by one with the periodic wrap.  Same values and the same sums as k_mu (lap4_of,
 // mu_of).
-// Rows a thread walks and threads a block (a 512-node strip); see the launcher for the sweep.
-constexpr int MU_ROWS = 8, MU_BLOCK = 128, MU_DEPTH = 4;
+// Rows a thread walks, threads a block (a 512-node strip) and rows in flight.  On the
+// 2048 x 4096 impact lattice: 4 x 128 x 4 0.0243 ms, 8 x 128 x 4 (or 6) 0.0246, 16 x 128 x 4
+// 0.0250, 8 and 16 rows with 8 in flight 0.027 and 0.031; with the loads in registers one row
+// ahead the best was 0.0265 and with the classes and psi' not ahead 0.030.
+constexpr int MU_ROWS = 4, MU_BLOCK = 128, MU_DEPTH = 4;
 __global__ void __launch_bounds__(MU_BLOCK) k_mu_sweep(Lattice<float> L) {
   __shared__ float4 s_rho[MU_DEPTH][MU_BLOCK];
   __shared__ float4 s_psi[MU_DEPTH][MU_BLOCK];
