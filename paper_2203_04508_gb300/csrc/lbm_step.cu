@@ -648,17 +648,9 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, in
     const bool inner = (tile.z & 2) != 0;
     const int x = x0 + lx, y = y0 + ly;
     const bool fluid = x < L.nx && y < L.ny && L.kind[y * L.pitch + x] == KIND_FLUID;
+    // a wait that gives up is acted on at the block barrier below, once every thread has read
+    // the stage (what a thread whose wait gave up read is never used)
     const bool ok = mbar_wait(&bar[s], (uint32_t)((k / TMA_STAGES) & 1), L.spin_limit);
-    if (__syncthreads_or(!ok)) {
-      // give up: flag it, let this block's copies still in flight land, and leave
-      if (threadIdx.x == 0) {
-        atomicOr(L.kerr, 1u);
-        for (int j = 0; j < TMA_STAGES && k + j < nt; ++j)
-          mbar_wait(&bar[(k + j) % TMA_STAGES], (uint32_t)(((k + j) / TMA_STAGES) & 1));
-      }
-      __syncthreads();
-      return;
-    }
     float* sm = mu_of(s);
     float* sr = rho_of(s);
     if (stencils && !(tile.z & 1)) {
@@ -695,8 +687,17 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_collide_tma(Lattice<float> L, in
       }
       if (stencils) tile_force_terms<float, PSEUDO>(sm, sr, TMA_HX, (ly + CT_H) * TMA_HX + lx + TMA_HOX, g);
     }
-    // every thread has read stage s: refill it with the tile TMA_STAGES ahead
-    __syncthreads();
+    // every thread has read stage s: refill it with the tile TMA_STAGES ahead -- or give up:
+    // flag it, let this block's copies still in flight land, and leave
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicOr(L.kerr, 1u);
+        for (int j = 0; j < TMA_STAGES && k + j < nt; ++j)
+          mbar_wait(&bar[(k + j) % TMA_STAGES], (uint32_t)(((k + j) / TMA_STAGES) & 1));
+      }
+      __syncthreads();
+      return;
+    }
     if (threadIdx.x == 0 && k + TMA_STAGES < nt) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(s);
