@@ -493,7 +493,8 @@ lbm_status lbm_slab_unpack(lbm_ctx* ctx, int32_t edge, const void* device_buffer
  *          type float (precision LBM_FP32) or double (LBM_FP64), e.g. from lbm_populations;
  * kind:    device pointer to n_nodes bytes; nodes with kind 0 (fluid) are summed;
  * n_nodes: 1 .. LBM_NOALLOC_MAX_NODES, otherwise LBM_EINVAL and nothing is launched;
- * stream:  cudaStream_t the work is issued on (may be NULL);
+ * stream:  cudaStream_t the work is issued on (may be NULL); a stream that is capturing gives
+ *          LBM_ESTATE, with nothing issued (the call ends in a synchronising host copy);
  * out2:    HOST pointer to 2 doubles: sum over fluid nodes of sum_i f_i (FP64, deterministic
  *          order), and the number of non-finite values.  The call synchronises the stream.
  *

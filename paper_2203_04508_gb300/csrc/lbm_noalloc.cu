@@ -117,9 +117,13 @@ extern "C" lbm_status lbm_mass_noalloc(const void* f, const uint8_t* kind, int64
     return LBM_EINVAL;
   }
   if (precision != LBM_FP32 && precision != LBM_FP64) return LBM_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the call ends in a pageable copy and a synchronisation, which a capture cannot hold
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return LBM_ECUDA;
+  if (cap != cudaStreamCaptureStatusNone) return LBM_ESTATE;
   double* scratch = nullptr;
   if (scratch_on_current_device(&scratch) != cudaSuccess) return LBM_ECUDA;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (cudaMemsetAsync(scratch, 0, sizeof(double), s) != cudaSuccess) return LBM_ECUDA;   // the counter
   long long blocks = (n_nodes + NA_BLOCK - 1) / NA_BLOCK;
   if (blocks > NA_MAX_BLOCKS) blocks = NA_MAX_BLOCKS;

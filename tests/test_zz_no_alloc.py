@@ -73,3 +73,29 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
     too_many = (1 << 30) + 1
     assert lib.lbm_mass_noalloc(C.c_void_p(256), C.c_void_p(256), too_many, 0, None, out.ctypes.data) == 1
     assert lib.lbm_mass_noalloc(C.c_void_p(256), C.c_void_p(256), 0, 0, None, out.ctypes.data) == 1
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    """The call ends in a synchronising copy to host memory, which no capture can hold: on a
+    stream that is capturing it returns LBM_ESTATE and issues nothing."""
+    import torch
+    from paper_2203_04508_gb300 import _abi
+    lib = _abi.load()
+    f = torch.zeros(9 * 64, dtype=torch.float32, device="cuda")
+    kind = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    x = torch.zeros(4, device="cuda")
+    out = np.zeros(2)
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        x.add_(1.0)
+        st = lib.lbm_mass_noalloc(C.c_void_p(f.data_ptr()), C.c_void_p(kind.data_ptr()), 64, _abi.LBM_FP32,
+                                  C.c_void_p(torch.cuda.current_stream().cuda_stream), out.ctypes.data)
+    assert st == _abi.LBM_ESTATE
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(x[0]) == 1.0
+    # outside the capture the same call runs
+    st = lib.lbm_mass_noalloc(C.c_void_p(f.data_ptr()), C.c_void_p(kind.data_ptr()), 64, _abi.LBM_FP32, None,
+                              out.ctypes.data)
+    assert st == 0 and out[0] == 0.0 and out[1] == 0.0
