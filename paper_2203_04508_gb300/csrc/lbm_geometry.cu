@@ -142,26 +142,26 @@ __global__ void __launch_bounds__(256) k_layer(GeomParams g, uint8_t* kind, uint
 }
 
 // ---- the four lists (cut links, boundary nodes, first and second solid layer) and the fluid
-// count, compacted in node order: per block of SCAN_BLOCK consecutive nodes the counts of each
-// list are scanned in shared memory; one scan over the blocks' totals gives each block's offsets.
+// count, compacted in node order: per block of LIST_NODES consecutive nodes (LIST_NPT
+// consecutive nodes of one row a thread) the counts of each list are scanned in shared memory;
+// one scan over the blocks' totals gives each block's offsets.
 enum { LANE_LINKS = 0, LANE_BNODE, LANE_S1, LANE_S2, LANE_FLUID, N_LANES };
+constexpr int LIST_BLOCK = 256, LIST_NPT = 8, LIST_NODES = LIST_BLOCK * LIST_NPT;
 
-// Bit offsets of the five lanes in one packed 64-bit count: a block of SCAN_BLOCK nodes holds
-// at most 8 x 1024 cut links (14 bits) and 1024 of each other lane (in fields of 12 bits), so a block scan of
-// the packed counts never carries from one field into the next.
-// (bits 0, 14, 26, 38, 50; 14 bits for the links, 12 for the others)
-__host__ __device__ constexpr int lane_shift(int l) { return l == 0 ? 0 : 2 + 12 * l; }
+// Bit offsets of the five lanes in one packed 64-bit count: a block of LIST_NODES = 2048 nodes
+// holds at most 8 x 2048 cut links (15 bits) and 2048 of each other lane (in fields of 12 bits),
+// so a block scan of the packed counts never carries from one field into the next
+// (bits 0, 15, 27, 39, 51).
+__host__ __device__ constexpr int lane_shift(int l) { return l == 0 ? 0 : 3 + 12 * l; }
 
 __device__ __forceinline__ int lane_of_packed(unsigned long long v, int l) {
-  return (int)((v >> lane_shift(l)) & (l == 0 ? 0x3fffull : 0xfffull));
+  return (int)((v >> lane_shift(l)) & (l == 0 ? 0x7fffull : 0xfffull));
 }
 
-// packed counts of node (x, y), n = y * pitch + x < plane: its cut links (a fluid node with a
-// non-fluid neighbour), the boundary-node, layer flags and the fluid flag
-__device__ __forceinline__ unsigned long long node_counts(const GeomParams& g, const uint8_t* kind, long long n, int x,
+// packed counts of node (x, y) of class k: its cut links (a fluid node with a non-fluid
+// neighbour), the boundary-node, layer flags and the fluid flag
+__device__ __forceinline__ unsigned long long node_counts(const GeomParams& g, const uint8_t* kind, uint8_t k, int x,
                                                           int y) {
-  if (n >= g.plane) return 0ull;
-  const uint8_t k = kind[n];
   if (k == KIND_FLUID) {
     int links = 0;
     for (int i = 1; i < 9; ++i) {
@@ -176,21 +176,36 @@ __device__ __forceinline__ unsigned long long node_counts(const GeomParams& g, c
   return 0ull;
 }
 
-// node index and coordinates of thread threadIdx.x of a block of SCAN_BLOCK consecutive nodes:
-// the block's first node divided by the pitch once, by thread 0
-__device__ __forceinline__ long long block_node(const GeomParams& g, int* x, int* y) {
+// The LIST_NPT nodes of thread threadIdx.x: its first node n0 (returned; >= plane for threads
+// past the end), their row y and first column x0 (all in one row: the pitch is a multiple of 32
+// and blocks start at multiples of LIST_NODES), their classes and packed counts.  The block's
+// first node is divided by the pitch once, by thread 0.
+__device__ __forceinline__ long long thread_counts(const GeomParams& g, const uint8_t* kind, int* x0, int* y,
+                                                   uint8_t (&k)[LIST_NPT], unsigned long long (&c)[LIST_NPT]) {
   __shared__ int b0[2];
-  const long long base = (long long)blockIdx.x * SCAN_BLOCK;
+  const long long base = (long long)blockIdx.x * LIST_NODES;
   if (threadIdx.x == 0) {
     const long long r = base / g.pitch;
     b0[0] = (int)r;
     b0[1] = (int)(base - r * g.pitch);
   }
   __syncthreads();
-  const unsigned t = (unsigned)b0[1] + threadIdx.x;
+  const unsigned t = (unsigned)b0[1] + LIST_NPT * threadIdx.x;
   *y = b0[0] + (int)(t / (unsigned)g.pitch);
-  *x = (int)(t % (unsigned)g.pitch);
-  return base + threadIdx.x;
+  *x0 = (int)(t % (unsigned)g.pitch);
+  const long long n0 = base + LIST_NPT * threadIdx.x;
+  if (n0 >= g.plane) {
+#pragma unroll
+    for (int j = 0; j < LIST_NPT; ++j) { k[j] = KIND_PAD; c[j] = 0ull; }
+    return n0;
+  }
+  const uint2 kk = *reinterpret_cast<const uint2*>(kind + n0);
+#pragma unroll
+  for (int j = 0; j < LIST_NPT; ++j) {
+    k[j] = (uint8_t)(((j < 4 ? kk.x : kk.y) >> (8 * (j & 3))) & 0xffu);
+    c[j] = node_counts(g, kind, k[j], *x0 + j, *y);
+  }
+  return n0;
 }
 
 // ---- block scans of int32 and packed 64-bit counts
@@ -235,11 +250,15 @@ __device__ T block_excl_scan(T v, T* total) {
 }
 
 // per block and lane the block's total, at sums[lane * nb + block]
-__global__ void __launch_bounds__(SCAN_BLOCK) k_count_blocks(GeomParams g, const uint8_t* kind, int* sums, int nb) {
-  int x, y;
-  const long long n = block_node(g, &x, &y);
-  unsigned long long t;
-  (void)block_excl_scan(node_counts(g, kind, n, x, y), &t);
+__global__ void __launch_bounds__(LIST_BLOCK) k_count_blocks(GeomParams g, const uint8_t* kind, int* sums, int nb) {
+  int x0, y;
+  uint8_t k[LIST_NPT];
+  unsigned long long c[LIST_NPT];
+  (void)thread_counts(g, kind, &x0, &y, k, c);
+  unsigned long long sum = 0ull, t;
+#pragma unroll
+  for (int j = 0; j < LIST_NPT; ++j) sum += c[j];
+  (void)block_excl_scan(sum, &t);
   if (threadIdx.x < N_LANES) sums[threadIdx.x * nb + blockIdx.x] = lane_of_packed(t, threadIdx.x);
 }
 
@@ -265,8 +284,8 @@ cudaError_t geom_classify_and_count(const GeomParams& g, const GeomScratch& s, u
   k_layer<<<grid, 256, 0, st>>>(g, kind, KIND_FLUID, KIND_SOLID1);
   k_layer<<<grid, 256, 0, st>>>(g, kind, KIND_SOLID1, KIND_SOLID2);
   // totals: 0 links, 1 bnodes, 2 s1, 3 s2, 4 fluid
-  const int nb = (int)((g.plane + SCAN_BLOCK - 1) / SCAN_BLOCK);
-  k_count_blocks<<<nb, SCAN_BLOCK, 0, st>>>(g, kind, s.block_sums, nb);
+  const int nb = (int)((g.plane + LIST_NODES - 1) / LIST_NODES);
+  k_count_blocks<<<nb, LIST_BLOCK, 0, st>>>(g, kind, s.block_sums, nb);
   k_scan_lanes<<<N_LANES, SCAN_BLOCK, 0, st>>>(s.block_sums, nb, s.totals);
   return cudaGetLastError();
 }
@@ -275,23 +294,32 @@ cudaError_t geom_classify_and_count(const GeomParams& g, const GeomScratch& s, u
 // lists (node), and the boundary index of every boundary node in the plane bidx (read back for
 // the first layer's neighbour table; other entries are never read).  The block offsets are the
 // scanned totals k_scan_lanes left.
-__global__ void __launch_bounds__(SCAN_BLOCK) k_fill_nodes(GeomParams g, const uint8_t* kind, const int* offs, int nb,
+__global__ void __launch_bounds__(LIST_BLOCK) k_fill_nodes(GeomParams g, const uint8_t* kind, const int* offs, int nb,
                                                            GeomOut o, int* bidx) {
-  int x, y;
-  const long long n = block_node(g, &x, &y);
-  const unsigned long long c = node_counts(g, kind, n, x, y);
-  unsigned long long t;
-  const unsigned long long ex = block_excl_scan(c, &t);
-  int e[LANE_FLUID];
+  int x0, y;
+  uint8_t k[LIST_NPT];
+  unsigned long long c[LIST_NPT];
+  const long long n0 = thread_counts(g, kind, &x0, &y, k, c);
+  unsigned long long sum = 0ull, t;
 #pragma unroll
-  for (int l = 0; l < LANE_FLUID; ++l) e[l] = lane_of_packed(ex, l) + offs[l * nb + blockIdx.x];
-  if (lane_of_packed(c, LANE_BNODE)) {
-    o.bnode[e[LANE_BNODE]] = (int)n;
-    o.bstart[e[LANE_BNODE]] = e[LANE_LINKS];
-    bidx[n] = e[LANE_BNODE];
+  for (int j = 0; j < LIST_NPT; ++j) sum += c[j];
+  unsigned long long ex = block_excl_scan(sum, &t);
+  int off[LANE_FLUID];
+#pragma unroll
+  for (int l = 0; l < LANE_FLUID; ++l) off[l] = offs[l * nb + blockIdx.x];
+#pragma unroll
+  for (int j = 0; j < LIST_NPT; ++j) {
+    const long long n = n0 + j;
+    if (lane_of_packed(c[j], LANE_BNODE)) {
+      const int e = lane_of_packed(ex, LANE_BNODE) + off[LANE_BNODE];
+      o.bnode[e] = (int)n;
+      o.bstart[e] = lane_of_packed(ex, LANE_LINKS) + off[LANE_LINKS];
+      bidx[n] = e;
+    }
+    if (lane_of_packed(c[j], LANE_S1)) o.s1node[lane_of_packed(ex, LANE_S1) + off[LANE_S1]] = (int)n;
+    if (lane_of_packed(c[j], LANE_S2)) o.s2node[lane_of_packed(ex, LANE_S2) + off[LANE_S2]] = (int)n;
+    ex += c[j];
   }
-  if (lane_of_packed(c, LANE_S1)) o.s1node[e[LANE_S1]] = (int)n;
-  if (lane_of_packed(c, LANE_S2)) o.s2node[e[LANE_S2]] = (int)n;
 }
 
 // The links of boundary node b, from its first link on, sorted by direction: direction, q (the
@@ -370,11 +398,11 @@ __global__ void k_wall_mu(GeomParams g, const uint8_t* kind, const int* body, re
 template <typename real>
 static cudaError_t fill_typed(const GeomParams& g, const GeomScratch& s, const GeomOut& o, cudaStream_t st) {
   const unsigned gn = (unsigned)((g.plane + 255) / 256);
-  const int nb = (int)((g.plane + SCAN_BLOCK - 1) / SCAN_BLOCK);
+  const int nb = (int)((g.plane + LIST_NODES - 1) / LIST_NODES);
   // the block offsets geom_classify_and_count left in block_sums; the boundary index of each
   // boundary node into the scratch plane `off`
   int* bidx = s.off;
-  k_fill_nodes<<<nb, SCAN_BLOCK, 0, st>>>(g, o.kind, s.block_sums, nb, o, bidx);
+  k_fill_nodes<<<nb, LIST_BLOCK, 0, st>>>(g, o.kind, s.block_sums, nb, o, bidx);
   if (o.n_bnodes > 0) k_fill_links<real><<<(o.n_bnodes + 255) / 256, 256, 0, st>>>(g, o.kind, o.n_bnodes, o);
   if (o.n_s1 > 0)
     k_fill_layer<real><<<(o.n_s1 + 255) / 256, 256, 0, st>>>(g, o.kind, o.n_s1, KIND_FLUID, o.s1node, o.s1mask,

@@ -109,7 +109,7 @@ struct GeomScratch {
   int* body;                  // plane (kept: the body of every solid node)
   int* cnt;                   // plane
   int* off;                   // plane
-  int* block_sums;            // 5 x (ceil(plane / 1024) + 1): per list and 1024-node block
+  int* block_sums;            // 5 x (ceil(plane / 1024) + 1): per list and node block (2048 nodes)
   int* totals;                // 8 ints on the device
 };
 
