@@ -101,7 +101,9 @@ __device__ __forceinline__ int wall_hi_row(double yt) {
   return yt <= -1073741824.0 ? -1073741824 : (int)ceil(yt);
 }
 
-// grid (ceil(pitch / 256), rows), 256 threads: one node each
+// grid (ceil(pitch / 256), up to GEOM_ROW_BLOCKS), 256 threads: one node of a row each, rows
+// blockIdx.y, blockIdx.y + gridDim.y, ... (the per-block set-up is paid once for all of them)
+constexpr int GEOM_ROW_BLOCKS = 512;
 __global__ void __launch_bounds__(256) k_classify(GeomParams g, uint8_t* kind, int* body) {
   __shared__ float4 scr[SCREEN_MAX];
   __shared__ int wl, wh;
@@ -109,35 +111,42 @@ __global__ void __launch_bounds__(256) k_classify(GeomParams g, uint8_t* kind, i
   if ((int)threadIdx.x < ns) scr[threadIdx.x] = disc_screen(g.cyl + 4 * threadIdx.x);
   if (threadIdx.x == 0) { wl = wall_lo_row(g.y_bottom); wh = wall_hi_row(g.y_top); }
   __syncthreads();
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= g.pitch) return;
-  const long long n = (long long)y * g.pitch + x;
-  if (x >= g.nx) { kind[n] = KIND_PAD; body[n] = -1; return; }
-  const int gy = grow(g, y);
-  const bool fast = x < SCREEN_COORD && gy >= 0 && gy < SCREEN_COORD;
-  int bd = -1;
-  for (int b = 0; b < g.n_cyl; ++b) {
-    int in = fast && b < SCREEN_MAX ? screen_disc(scr[b], x, gy) : -1;
-    if (in < 0) in = inside_body(g, b, x, y) ? 1 : 0;
-    if (in) { bd = b; break; }
+  const int rows = (int)(g.plane / g.pitch);
+  for (int y = blockIdx.y; y < rows; y += gridDim.y) {
+    const long long n = (long long)y * g.pitch + x;
+    if (x >= g.nx) { kind[n] = KIND_PAD; body[n] = -1; continue; }
+    const int gy = grow(g, y);
+    const bool fast = x < SCREEN_COORD && gy >= 0 && gy < SCREEN_COORD;
+    int bd = -1;
+    for (int b = 0; b < g.n_cyl; ++b) {
+      int in = fast && b < SCREEN_MAX ? screen_disc(scr[b], x, gy) : -1;
+      if (in < 0) in = inside_body(g, b, x, y) ? 1 : 0;
+      if (in) { bd = b; break; }
+    }
+    if (bd < 0 && g.walls) {
+      if (y <= wl) bd = g.n_cyl;
+      else if (y >= wh) bd = g.n_cyl + 1;
+    }
+    body[n] = bd;
+    kind[n] = bd >= 0 ? KIND_DEEP : KIND_FLUID;
   }
-  if (bd < 0 && g.walls) {
-    if (y <= wl) bd = g.n_cyl;
-    else if (y >= wh) bd = g.n_cyl + 1;
-  }
-  body[n] = bd;
-  kind[n] = bd >= 0 ? KIND_DEEP : KIND_FLUID;
 }
 
 // solid nodes with a neighbour of class `from` (and currently DEEP) become class `to`
+// the same grid as k_classify
 __global__ void __launch_bounds__(256) k_layer(GeomParams g, uint8_t* kind, uint8_t from, uint8_t to) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= g.pitch) return;
-  const long long n = (long long)y * g.pitch + x;
-  if (kind[n] != KIND_DEEP) return;
-  for (int i = 1; i < 9; ++i) {
-    int m;
-    if (gnb(g, x, y, i, &m) && kind[m] == from) { kind[n] = to; return; }
+  const int rows = (int)(g.plane / g.pitch);
+  for (int y = blockIdx.y; y < rows; y += gridDim.y) {
+    const long long n = (long long)y * g.pitch + x;
+    if (kind[n] != KIND_DEEP) continue;
+    for (int i = 1; i < 9; ++i) {
+      int m;
+      if (gnb(g, x, y, i, &m) && kind[m] == from) { kind[n] = to; break; }
+    }
   }
 }
 
@@ -279,7 +288,8 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_scan_lanes(int* sums, int nb, in
 }
 
 cudaError_t geom_classify_and_count(const GeomParams& g, const GeomScratch& s, uint8_t* kind, cudaStream_t st) {
-  const dim3 grid((unsigned)((g.pitch + 255) / 256), (unsigned)(g.plane / g.pitch));
+  const long long rows = g.plane / g.pitch;
+  const dim3 grid((unsigned)((g.pitch + 255) / 256), (unsigned)(rows < GEOM_ROW_BLOCKS ? rows : GEOM_ROW_BLOCKS));
   k_classify<<<grid, 256, 0, st>>>(g, kind, s.body);
   k_layer<<<grid, 256, 0, st>>>(g, kind, KIND_FLUID, KIND_SOLID1);
   k_layer<<<grid, 256, 0, st>>>(g, kind, KIND_SOLID1, KIND_SOLID2);

@@ -1071,7 +1071,9 @@ __device__ __forceinline__ double init_rho(double phi, double rho_g, double rho_
 constexpr int INIT_SCREEN_MAX = 32;
 constexpr int INIT_SCREEN_COORD = 8192;
 
-// grid (ceil(pitch / NODE_BLOCK), rows): one node a thread
+// grid (ceil(pitch / NODE_BLOCK), up to INIT_ROW_BLOCKS): one node of a row a thread, rows
+// blockIdx.y, blockIdx.y + gridDim.y, ... (the per-block set-up is paid once for all of them)
+constexpr int INIT_ROW_BLOCKS = 512;
 template <typename real>
 __global__ void __launch_bounds__(NODE_BLOCK) k_init(Lattice<real> L, const double* __restrict__ drops, int n_drop,
                                                      double W, double rho_g, double rho_l) {
@@ -1090,54 +1092,57 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_init(Lattice<real> L, const doub
                           : make_float3(0.f, 0.f, __int_as_float(0x7f800000));
   }
   __syncthreads();
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= L.pitch) return;
-  const long long n = (long long)y * L.pitch + x;
   real* f0 = L.f[0];
   real* f1 = L.f[1];
-  if (x >= L.nx || L.kind[n] != KIND_FLUID) {
+  const int rows = (int)(L.plane / L.pitch);
+  for (int y = blockIdx.y; y < rows; y += gridDim.y) {
+    const long long n = (long long)y * L.pitch + x;
+    if (x >= L.nx || L.kind[n] != KIND_FLUID) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        f0[i * L.plane + n] = real(0);
+        if (!L.aa) f1[i * L.plane + n] = real(0);
+      }
+      continue;
+    }
+    const int gy = global_row(L, y);
+    const bool fast = x < INIT_SCREEN_COORD && gy >= 0 && gy < INIT_SCREEN_COORD;
+    double phi = 0.0, u0 = 0.0, v0 = 0.0;
+    for (int d = 0; d < n_drop; ++d) {
+      if (fast && d < INIT_SCREEN_MAX) {
+        const float3 sc = scr[d];
+        const float dxf = __fsub_rn((float)x, sc.x), dyf = __fsub_rn((float)gy, sc.y);
+        if (__fadd_rn(__fmul_rn(dxf, dxf), __fmul_rn(dyf, dyf)) > sc.z) continue;
+      }
+      const double* p = drops + 5 * d;
+      double dx = x - p[0], dy = gy - p[1];
+      const double d2 = dx * dx + dy * dy;
+      const double far = p[2] + 20.0 * W;
+      if (far > 0.0 && d2 >= far * far * (1.0 + 1e-9)) continue;
+      double rr = sqrt(d2);
+      double ph = 0.5 - 0.5 * tanh(2.0 * (rr - p[2]) / W);
+      if (ph > phi) { phi = ph; u0 = p[3]; v0 = p[4]; }
+    }
+    if (phi == 0.0) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        f0[i * L.plane + n] = gas[i];
+        if (!L.aa) f1[i * L.plane + n] = real(0);
+      }
+      L.rho[n] = gas_rho;
+      continue;
+    }
+    const double r = init_rho(phi, rho_g, rho_l);
+    const double ux = u0 * phi, uy = v0 * phi;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      f0[i * L.plane + n] = real(0);
+      f0[i * L.plane + n] = init_pop<real>(i, r, ux, uy, rref);
       if (!L.aa) f1[i * L.plane + n] = real(0);
     }
-    return;
+    L.rho[n] = (real)r;
   }
-  const int gy = global_row(L, y);
-  const bool fast = x < INIT_SCREEN_COORD && gy >= 0 && gy < INIT_SCREEN_COORD;
-  double phi = 0.0, u0 = 0.0, v0 = 0.0;
-  for (int d = 0; d < n_drop; ++d) {
-    if (fast && d < INIT_SCREEN_MAX) {
-      const float3 sc = scr[d];
-      const float dxf = __fsub_rn((float)x, sc.x), dyf = __fsub_rn((float)gy, sc.y);
-      if (__fadd_rn(__fmul_rn(dxf, dxf), __fmul_rn(dyf, dyf)) > sc.z) continue;
-    }
-    const double* p = drops + 5 * d;
-    double dx = x - p[0], dy = gy - p[1];
-    const double d2 = dx * dx + dy * dy;
-    const double far = p[2] + 20.0 * W;
-    if (far > 0.0 && d2 >= far * far * (1.0 + 1e-9)) continue;
-    double rr = sqrt(d2);
-    double ph = 0.5 - 0.5 * tanh(2.0 * (rr - p[2]) / W);
-    if (ph > phi) { phi = ph; u0 = p[3]; v0 = p[4]; }
-  }
-  if (phi == 0.0) {
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      f0[i * L.plane + n] = gas[i];
-      if (!L.aa) f1[i * L.plane + n] = real(0);
-    }
-    L.rho[n] = gas_rho;
-    return;
-  }
-  const double r = init_rho(phi, rho_g, rho_l);
-  const double ux = u0 * phi, uy = v0 * phi;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    f0[i * L.plane + n] = init_pop<real>(i, r, ux, uy, rref);
-    if (!L.aa) f1[i * L.plane + n] = real(0);
-  }
-  L.rho[n] = (real)r;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1594,7 +1599,9 @@ cudaError_t launch_mass(const Lattice<real>& L, int cur, cudaStream_t s) {
 template <typename real>
 cudaError_t launch_init(const Lattice<real>& L, const double* drops, int n_drop, double W, double rho_g,
                         double rho_l, cudaStream_t s) {
-  const dim3 grid((unsigned)((L.pitch + NODE_BLOCK - 1) / NODE_BLOCK), (unsigned)(L.plane / L.pitch));
+  const long long rows = L.plane / L.pitch;
+  const dim3 grid((unsigned)((L.pitch + NODE_BLOCK - 1) / NODE_BLOCK),
+                  (unsigned)(rows < INIT_ROW_BLOCKS ? rows : INIT_ROW_BLOCKS));
   k_init<real><<<grid, NODE_BLOCK, 0, s>>>(L, drops, n_drop, W, rho_g, rho_l);
   return cudaGetLastError();
 }
