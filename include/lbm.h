@@ -259,11 +259,12 @@ lbm_status lbm_dM_history(lbm_ctx* ctx, double* out, int64_t n, int64_t* n_out);
 /* Domain sum of the Eq. 18 compensation of the last step (8 bytes read back; synchronises). */
 lbm_status lbm_last_dM(lbm_ctx* ctx, double* dM);
 
-/* The same 8 bytes, copied on the context's stream into host memory `dM` without waiting: the
+/* The same 8 bytes, written on the context's stream into host memory `dM` without waiting: the
  * value is there once the stream has reached this point (any synchronising call, or the
- * stream's own synchronisation).  With page-locked `dM` the copy overlaps the following steps,
- * so a caller can read every step's result without stalling the GPU; with pageable memory the
- * copy itself waits for the stream. */
+ * stream's own synchronisation).  Page-locked `dM` is stored into by a one-thread kernel, which
+ * costs the following steps less than a copy-engine copy would, so a caller can read every
+ * step's result without stalling the GPU; pageable memory is copied, and that copy itself
+ * waits for the stream. */
 lbm_status lbm_last_dM_async(lbm_ctx* ctx, double* dM);
 
 /* Advances n steps like lbm_step, launching the five phases one by one with CUDA events on

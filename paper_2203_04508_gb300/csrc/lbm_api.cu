@@ -1514,7 +1514,14 @@ lbm_status lbm_last_dM(lbm_ctx* c, double* dM) {
 lbm_status lbm_last_dM_async(lbm_ctx* c, double* dM) {
   if (!c || !c->inited || !dM) return LBM_ESTATE;
   if (c->sticky != LBM_OK) return c->sticky;
-  CUDA_OK(c, cudaMemcpyAsync(dM, c->ws + c->lay.dm_ring + (size_t)DM_RING * 8, 8, cudaMemcpyDeviceToHost, c->stream));
+  const double* src = reinterpret_cast<const double*>(c->ws + c->lay.dm_ring + (size_t)DM_RING * 8);
+  // page-locked host memory: one thread stores the value into it (a copy-engine copy between
+  // two steps would hold the next step back for its own latency); other memory: a copy
+  if (void* dst = mapped_host(dM)) {
+    CUDA_OK(c, launch_copy8(src, static_cast<double*>(dst), c->stream));
+    return LBM_OK;
+  }
+  CUDA_OK(c, cudaMemcpyAsync(dM, src, 8, cudaMemcpyDeviceToHost, c->stream));
   return LBM_OK;
 }
 

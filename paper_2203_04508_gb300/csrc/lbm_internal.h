@@ -38,6 +38,8 @@ template <typename real>
 cudaError_t launch_step_overlap(const Lattice<real>& Lt, const Lattice<real>& Ln, int cur, cudaStream_t s,
                                 cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join);
 template <typename real> int launches_per_step_overlap(const Lattice<real>& L);
+// one double into page-locked host memory (its device address dst), in stream order
+cudaError_t launch_copy8(const double* src, double* dst, cudaStream_t s);
 template <typename real> cudaError_t launch_fields(const Lattice<real>& L, int cur, real* r, real* vx, real* vy, cudaStream_t s);
 // populations i0 <= i < i1 of the current state, population i into dense plane i - i0 of out
 template <typename real>

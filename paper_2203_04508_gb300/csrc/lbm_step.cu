@@ -963,6 +963,13 @@ __global__ void __launch_bounds__(NODE_BLOCK) k_fields(Lattice<real> L, int cur,
   vy_out[d] = (jy + real(0.5) * Fy) / r;
 }
 
+// One double into page-locked host memory (its device address), in stream order.
+__global__ void k_copy8(const double* __restrict__ src, double* dst) { *dst = *src; }
+cudaError_t launch_copy8(const double* src, double* dst, cudaStream_t s) {
+  k_copy8<<<1, 1, 0, s>>>(src, dst);
+  return cudaGetLastError();
+}
+
 // Largest speed |v| = |u + F/(2 rho)| over the fluid nodes of the current state, combined into
 // *out as FP64 bits (the caller zeroes it): non-negative doubles order like their bit patterns,
 // and a NaN, stored as the positive quiet NaN, lies above every number.  The speed is formed in
