@@ -46,8 +46,10 @@ __device__ __forceinline__ bool node_of_thread(const Lattice<real>& L, int& x, i
 // a row (phase_rho_vec).  Rows are taken from the top down: the collide kernel writes the new
 // populations roughly from the bottom up, so the rows it wrote last are still in L2 when this pass
 // starts, and the rows this pass reads last are the ones the next collide reads first.
+// FP32: five blocks an SM (48 registers, 8 bytes spilled) instead of four (56): 0.0590 -> 0.0583 ms
+// on the 2048 x 4096 impact lattice.
 template <typename real>
-__global__ void __launch_bounds__(NODE_BLOCK) k_rho_vec(Lattice<real> L, int cur) {
+__global__ void __launch_bounds__(NODE_BLOCK, sizeof(real) == 4 ? 5 : 1) k_rho_vec(Lattice<real> L, int cur) {
   const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * Vec16<real>::V, y = L.ny - 1 - (int)blockIdx.y;
   if (x0 < L.nx) phase_rho_vec(L, cur, x0, y);
 }
