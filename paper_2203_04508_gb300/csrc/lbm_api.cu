@@ -676,6 +676,7 @@ lbm_status slab_local_config(const lbm_config* g, int y0, int y1, int H, lbm_con
 // fluid nodes of the own rows.
 lbm_status slab_ranges(lbm_ctx* c) {
   const Layout& y = c->lay;
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
   std::vector<int> bnode(c->n_bnodes > 0 ? c->n_bnodes : 1);
   std::vector<uint8_t> kind(y.plane);
   if (c->n_bnodes > 0)
@@ -705,6 +706,7 @@ lbm_status slab_ranges(lbm_ctx* c) {
 // axes) reaches a solid node or a boundary node: the fused density + mu pass cannot finish them,
 // since those densities come from the solid-layer kernels and the boundary phase.
 lbm_status near_list(lbm_ctx* c) {
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
   const Layout& y = c->lay;
   const int nx = c->cfg.nx, ny = c->cfg.ny, P = y.pitch;
   std::vector<uint8_t> kind(y.plane);
@@ -973,7 +975,8 @@ lbm_status lbm_build_links(lbm_ctx* c) {
   CUDA_OK(c, cudaMemsetAsync(w + y.kerr, 0, 16, c->stream));
   CUDA_OK(c, cudaMemsetAsync(w + y.dm_ring, 0, (size_t)(DM_RING + 1) * 8, c->stream));
   CUDA_OK(c, cudaMemsetAsync(w + y.rho, 0, y.plane * y.sz, c->stream));
-  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  // the lists are filled on the stream while the host goes on; the calls that read them back
+  // (lbm_get_links, lbm_get_kind, the slab ranges, the near-node list) wait for the stream
   if (c->slab.on) {
     lbm_status st = slab_ranges(c);
     if (st != LBM_OK) return st;
@@ -1031,6 +1034,7 @@ lbm_status lbm_get_links(lbm_ctx* c, int64_t capacity, int32_t* x1, int32_t* dir
   std::vector<int> bnode(B), bstart(B + 1);
   std::vector<uint8_t> d(L), f2(L);
   std::vector<double> qq(L);
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
   CUDA_OK(c, cudaMemcpy(bnode.data(), c->ws + y.bnode, B * 4, cudaMemcpyDeviceToHost));
   CUDA_OK(c, cudaMemcpy(bstart.data(), c->ws + y.bstart, (B + 1) * 4, cudaMemcpyDeviceToHost));
   CUDA_OK(c, cudaMemcpy(d.data(), c->ws + y.ldir, L, cudaMemcpyDeviceToHost));
@@ -1059,6 +1063,7 @@ lbm_status lbm_get_kind(lbm_ctx* c, uint8_t* kind) {
   if (!c || !c->built) return LBM_ESTATE;
   if (c->sticky != LBM_OK) return c->sticky;
   const Layout& y = c->lay;
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
   CUDA_OK(c, cudaMemcpy2D(kind, c->cfg.nx, c->ws + y.kind, y.pitch, c->cfg.nx, c->cfg.ny, cudaMemcpyDeviceToHost));
   return LBM_OK;
 }
@@ -1293,6 +1298,9 @@ lbm_status lbm_save(lbm_ctx* c, const char* path) {
   h.n_bnodes = (uint64_t)c->n_bnodes;
   lbm_status ms = resolve_mass0(c);
   if (ms != LBM_OK) return ms;
+  // the steps queued on the context's stream finish before the state is copied out (the copies
+  // below do not order themselves after a non-blocking stream)
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
   h.mass0 = c->mass0;
   h.pop_bytes = 9ull * (uint64_t)y.plane * y.sz;
   const size_t ring_bytes = (size_t)(DM_RING + 1) * 8;
