@@ -736,7 +736,8 @@ lbm_status near_list(lbm_ctx* c) {
   if ((long long)list.size() > cap)
     return fail(c, LBM_ENOMEM, "near-boundary list of %zu nodes exceeds its capacity %lld", list.size(), cap);
   if (!list.empty())
-    CUDA_OK(c, cudaMemcpy(c->ws + y.near, list.data(), list.size() * 4, cudaMemcpyHostToDevice));
+    CUDA_OK(c, cudaMemcpyAsync(c->ws + y.near, list.data(), list.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    CUDA_OK(c, cudaStreamSynchronize(c->stream));
   c->n_near = (long long)list.size();
   c->near_built = true;
   return LBM_OK;
@@ -1357,15 +1358,18 @@ lbm_status lbm_load(lbm_ctx* c, const char* path) {
       h.pop_bytes != 9ull * (uint64_t)y.plane * y.sz || (h.cur != 0 && h.cur != 1))
     return fail(c, LBM_EINVAL, "%s is a checkpoint of another configuration", path);
   const unsigned char* p = buf.data() + sizeof(h);
-  CUDA_OK(c, cudaStreamSynchronize(c->stream));
-  CUDA_OK(c, cudaMemcpy(c->ws + (h.cur ? y.fB : y.fA), p, h.pop_bytes, cudaMemcpyHostToDevice));
+  // on the context's stream, so that the steps queued after the load see the loaded state (a
+  // copy on the default stream returns before its data has landed and is not ordered before a
+  // non-blocking stream's work); finished before the host buffer goes
+  CUDA_OK(c, cudaMemcpyAsync(c->ws + (h.cur ? y.fB : y.fA), p, h.pop_bytes, cudaMemcpyHostToDevice, c->stream));
   p += h.pop_bytes;
-  if (h.n_bnodes) CUDA_OK(c, cudaMemcpy(c->ws + y.carry, p, h.n_bnodes * 8, cudaMemcpyHostToDevice));
+  if (h.n_bnodes) CUDA_OK(c, cudaMemcpyAsync(c->ws + y.carry, p, h.n_bnodes * 8, cudaMemcpyHostToDevice, c->stream));
   p += h.n_bnodes * 8;
-  CUDA_OK(c, cudaMemcpy(c->ws + y.dm_ring, p, ring_bytes, cudaMemcpyHostToDevice));
+  CUDA_OK(c, cudaMemcpyAsync(c->ws + y.dm_ring, p, ring_bytes, cudaMemcpyHostToDevice, c->stream));
   p += ring_bytes;
-  CUDA_OK(c, cudaMemcpy(c->ws + y.step_ctr, p, 8, cudaMemcpyHostToDevice));
-  CUDA_OK(c, cudaMemset(c->ws + y.kerr, 0, 16));
+  CUDA_OK(c, cudaMemcpyAsync(c->ws + y.step_ctr, p, 8, cudaMemcpyHostToDevice, c->stream));
+  CUDA_OK(c, cudaMemsetAsync(c->ws + y.kerr, 0, 16, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
   c->cur = h.cur;
   c->steps = h.steps;
   c->mass0 = h.mass0;
