@@ -304,8 +304,8 @@ lbm_status lbm_get_collide_kernel(lbm_ctx* ctx, int32_t* kind);
 /* The chemical-potential pass (Eq. 12) of the chemical-potential force model: 0 one node a
  * thread, 1 four (FP64: two) consecutive nodes of a row a thread from 16-byte loads, 2 (FP32
  * only) row sweeps, a thread walking down a column of four-node groups with the stencil's rows
- * in registers.  The default is 2 for FP32 lattices whose sweeps (512-node strips x 16 rows)
- * number at least four per SM, else 1.  All three give the same bits.  Call
+ * in registers.  The default is 2 for FP32 lattices of at least four 512 x 16-node blocks per
+ * SM, else 1.  All three give the same bits.  Call
  * after lbm_build_links; the step graphs are captured again.  LBM_EINVAL for another value or
  * for 2 on an FP64 lattice. */
 lbm_status lbm_set_mu_kernel(lbm_ctx* ctx, int32_t kind);
