@@ -253,6 +253,14 @@ def test_single_steps_and_the_asynchronous_read_back():
     hist = b.dM_history(n)
     assert np.array_equal(buf.numpy(), hist)
     assert a.last_dM() == hist[-1]
+    # pageable memory takes the copy path (page-locked memory is stored into by a kernel)
+    c = make_lattice(sc, fp64=False)
+    pageable = torch.empty(n, dtype=torch.float64)
+    for k in range(n):
+        c.step(1)
+        c.last_dM_async(pageable, k)
+    c.synchronize()
+    assert np.array_equal(pageable.numpy(), hist)
 
 
 @pytest.mark.parametrize("fp64,layout", [(False, 0), (True, 0), (False, 1)])
